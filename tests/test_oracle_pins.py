@@ -1,0 +1,507 @@
+"""Pins of the FP64 CPU oracle against facts fixed by the paper and by
+mathematics (not by re-typing its formulas): lattice moment identities,
+conservation laws, exact special cases, closed forms and transport
+coefficients.  Each test names the equation or section it pins.
+
+All tests here are CPU-only.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1412_6238_gb300 import workloads as wl
+
+CS2 = 1.0 / 3.0
+
+
+# --------------------------------------------------------------- lattice
+
+def test_d2q9_moment_identities(orc):
+    """D2Q9 weights (Eq. 5, Eq. 6 use w_i and c_s without listing them):
+    sum w = 1, odd moments vanish, sum w xi xi = cs2 I, and the fourth moment
+    is isotropic cs2^2 (d d + d d + d d)."""
+    ex, ey, w, opp, cs2 = orc.lattice()
+    assert cs2 == pytest.approx(1.0 / 3.0, abs=0)
+    xi = np.stack([ex, ey], 1).astype(float)
+    assert w.sum() == pytest.approx(1.0, abs=1e-15)
+    assert np.abs((w[:, None] * xi).sum(0)).max() < 1e-16
+    M2 = np.einsum("i,ia,ib->ab", w, xi, xi)
+    assert np.abs(M2 - cs2 * np.eye(2)).max() < 1e-15
+    M3 = np.einsum("i,ia,ib,ic->abc", w, xi, xi, xi)
+    assert np.abs(M3).max() < 1e-16
+    M4 = np.einsum("i,ia,ib,ic,id->abcd", w, xi, xi, xi, xi)
+    d = np.eye(2)
+    iso = cs2 ** 2 * (np.einsum("ab,cd->abcd", d, d) + np.einsum("ac,bd->abcd", d, d)
+                      + np.einsum("ad,bc->abcd", d, d))
+    assert np.abs(M4 - iso).max() < 1e-15
+    for i in range(9):
+        assert xi[opp[i]].tolist() == (-xi[i]).tolist()
+
+
+def _terms(orc, **kw):
+    p = wl.base_params(1, 2, mobility=0.07, tau_g=0.9, rho=1.3, cv=0.8)
+    args = dict(c=0.37, p=0.011, T=1.7, mu=-0.02, ux=0.031, uy=-0.047,
+                Fx=2e-3, Fy=-3e-3, gpx=4e-4, gpy=1e-4)
+    args.update(kw)
+    return p, args, orc.cell_terms(p, **args)
+
+
+def test_equilibrium_moments(orc):
+    """Eq. 5: sum f_eq = p, sum xi f_eq = rho cs2 u.
+    Eq. 21-22: sum g_eq = c, sum xi g_eq = c u, sum xi xi g_eq = Gm mu I + c u u.
+    Eq. aEq9: sum h_eq = rho c_v T, sum xi h_eq = rho c_v T u."""
+    ex, ey, w, _, _ = orc.lattice()
+    xi = np.stack([ex, ey], 1).astype(float)
+    p, a, t = _terms(orc)
+    u = np.array([a["ux"], a["uy"]])
+    Gm = p["mobility"] / (p["tau_g"] - 0.5)
+    assert t["feq"].sum() == pytest.approx(a["p"], rel=1e-14)
+    assert np.allclose(xi.T @ t["feq"], p["rho"] * CS2 * u, rtol=1e-14, atol=0)
+    assert t["geq"].sum() == pytest.approx(a["c"], rel=1e-14)
+    assert np.allclose(xi.T @ t["geq"], a["c"] * u, rtol=1e-13, atol=0)
+    M2 = np.einsum("i,ia,ib->ab", t["geq"], xi, xi)
+    assert np.allclose(M2, Gm * a["mu"] * np.eye(2) + a["c"] * np.outer(u, u),
+                       rtol=1e-13, atol=1e-17)
+    rcT = p["rho"] * p["cv"] * a["T"]
+    assert t["heq"].sum() == pytest.approx(rcT, rel=1e-14)
+    assert np.allclose(xi.T @ t["heq"], rcT * u, rtol=1e-13, atol=0)
+    # Eq. 6: second moment of Gamma_i(u) is cs2 I + u u
+    M2h = np.einsum("i,ia,ib->ab", t["heq"], xi, xi) / rcT
+    assert np.allclose(M2h, CS2 * np.eye(2) + np.outer(u, u), rtol=1e-13, atol=1e-17)
+
+
+def test_source_moments(orc):
+    """The forcing terms add no mass (zeroth moments vanish) and the right
+    momentum: first moment of the Eq. 12 source is cs2 F (this is what fixes
+    the c_s^2 of the half-step force in u), of the Eq. 27 source c (F - grad p)/rho,
+    of the Eq. aEq12 source c_v T Fbar (Appendix A)."""
+    ex, ey, _, _, _ = orc.lattice()
+    xi = np.stack([ex, ey], 1).astype(float)
+    p, a, t = _terms(orc)
+    F = np.array([a["Fx"], a["Fy"]])
+    gp = np.array([a["gpx"], a["gpy"]])
+    for k in ("fsrc", "gsrc", "hsrc"):
+        assert abs(t[k].sum()) < 1e-17
+    assert np.allclose(xi.T @ t["fsrc"], CS2 * F, rtol=1e-13, atol=0)
+    assert np.allclose(xi.T @ t["gsrc"], a["c"] * (F - gp) / p["rho"], rtol=1e-13, atol=0)
+    assert np.allclose(xi.T @ t["hsrc"], p["cv"] * a["T"] * (F - gp), rtol=1e-13, atol=0)
+
+
+# --------------------------------------------------------------- stencils
+
+def _quadratic_fields(nx, ny):
+    x = np.arange(nx, dtype=float)[None, :]
+    y = np.arange(ny, dtype=float)[:, None]
+    c = 0.3 + 0.01 * x - 0.02 * y + 1e-3 * x * x + 2e-3 * x * y - 3e-3 * y * y
+    T = 1.0 - 0.05 * x + 0.07 * y + 4e-3 * x * x - 1e-3 * x * y + 2e-3 * y * y
+    p = 0.01 * x + 0.02 * y - 1e-3 * x * x
+    return c + 0 * y, T + 0 * y, p + 0 * y
+
+
+def test_stencils_exact_on_quadratics(orc):
+    """The isotropic gradient and Laplacian reproduce the derivatives of any
+    quadratic exactly (away from the periodic seam and the wall ghosts)."""
+    nx, ny = 16, 12
+    c, T, p = _quadratic_fields(nx, ny)
+    par = wl.base_params(nx, ny)
+    o = orc.scalar_ops(par, c, p, T, np.zeros(nx), np.zeros(nx))
+    x = np.arange(nx, dtype=float)[None, :]
+    y = np.arange(ny, dtype=float)[:, None]
+    sl = (slice(2, ny - 2), slice(2, nx - 2))
+    ex = {"gcx": 0.01 + 2e-3 * x + 2e-3 * y, "gcy": -0.02 + 2e-3 * x - 6e-3 * y,
+          "lapc": 2e-3 - 6e-3 + 0 * x * y,
+          "gTx": -0.05 + 8e-3 * x - 1e-3 * y, "gTy": 0.07 - 1e-3 * x + 4e-3 * y,
+          "gpx": 0.01 - 2e-3 * x + 0 * y, "gpy": 0.02 + 0 * x * y}
+    for k, v in ex.items():
+        v = np.broadcast_to(v, (ny, nx))
+        assert np.abs(o[k][sl] - v[sl]).max() < 1e-14, k
+
+
+def test_wall_ghosts(orc):
+    """Ghost rows: c and p mirror about the wall (zero normal gradient, a
+    neutral wall), T is antisymmetric about the wall temperature, so a linear
+    T between T_bot at y=-1/2 and T_top at y=ny-1/2 has an exact gradient in
+    every row including the first and last."""
+    nx, ny = 8, 10
+    y = np.arange(ny, dtype=float)[:, None] * np.ones((1, nx))
+    Tb, Tt = 2.0, -1.0
+    T = Tb + (Tt - Tb) * (y + 0.5) / ny
+    c = 0.2 + 0.0 * y
+    par = wl.base_params(nx, ny)
+    o = orc.scalar_ops(par, c, c, T, np.full(nx, Tb), np.full(nx, Tt))
+    assert np.abs(o["gTy"] - (Tt - Tb) / ny).max() < 1e-14
+    assert np.abs(o["gTx"]).max() < 1e-14
+    # mirrored scalar: first row gradient of a field symmetric about the wall
+    c2 = (y - 3.0) ** 2
+    o2 = orc.scalar_ops(par, c2, c2, T, np.full(nx, Tb), np.full(nx, Tt))
+    # ghost c(-1) = c(0) = 9 -> gy(0) = (c(1) - c(-1))/2 = (4 - 9)/2
+    assert o2["gcy"][0, 3] == pytest.approx((4.0 - 9.0) / 2.0, abs=1e-14)
+    # top: ghost p(ny) = p(ny-1) = 36 -> gy(ny-1) = (36 - 25)/2
+    assert o2["gpy"][ny - 1, 3] == pytest.approx((36.0 - 25.0) / 2.0, abs=1e-14)
+
+
+def test_delta_normalisation_alpha(orc):
+    """Sec. II: eps*alpha*int |c'(z)|^2 dz = 1 fixes alpha = 6 sqrt(2) for the
+    profile c = (1 + tanh(z/(2 sqrt 2 eps)))/2.  (i) quadrature of the
+    continuous profile with that alpha gives 1 (independent of the oracle);
+    (ii) the oracle's discrete sum of eps*alpha*|grad c|^2 across a planar
+    interface tends to 1 at second order in 1/W."""
+    for eps in (0.5, 1.0, 3.0):
+        z = np.linspace(-60 * eps, 60 * eps, 400001)
+        dc = np.gradient(0.5 * (1 + np.tanh(z / (2 * math.sqrt(2) * eps))), z)
+        assert eps * 6 * math.sqrt(2) * np.trapezoid(dc * dc, z) == pytest.approx(1.0, rel=1e-6)
+    errs = []
+    for W in (4.0, 8.0, 16.0):
+        nx, ny = 4, 240
+        par = wl.base_params(nx, ny, eps=wl.eps_from_width(W))
+        d = (np.arange(ny) - 119.5)[:, None] * np.ones((1, nx))
+        c = wl.tanh_profile(d, W)
+        # the force with sigma = 1, no curvature: only |grad c|^2 matters here,
+        # read it from the stencil outputs
+        o = orc.scalar_ops(par, c, 0 * c, 0 * c, np.zeros(nx), np.zeros(nx))
+        s = par["eps"] * 6 * math.sqrt(2) * (o["gcx"] ** 2 + o["gcy"] ** 2)[:, 0].sum()
+        errs.append(1.0 - s)
+    assert abs(errs[-1]) < 5e-3
+    assert 3.0 < errs[0] / errs[1] < 5.0 and 3.0 < errs[1] / errs[2] < 5.0
+
+
+def test_curvature_of_circle(orc):
+    """kappa = div n (Eq. 3) of a diffuse circle of radius R is -1/R on the
+    interface (n points into the drop, phase 1, so kappa is negative)."""
+    for R in (12.0, 20.0, 30.0):
+        nx = ny = 96
+        par = wl.base_params(nx, ny, eps=wl.eps_from_width(4.0))
+        c = wl.tanh_profile(wl._drop_distance(nx, ny, R, 48.0, 48.0), 4.0)
+        o = orc.scalar_ops(par, c, 0 * c, 0 * c, np.zeros(nx), np.zeros(nx))
+        g2 = o["gcx"] ** 2 + o["gcy"] ** 2
+        k = (o["kappa"] * g2).sum() / g2.sum()
+        assert k == pytest.approx(-1.0 / R, rel=5e-3)
+
+
+def test_force_direction_and_marangoni(orc):
+    """Eq. 3 with Eq. aEq3.  (i) At uniform sigma the force on a drop points
+    inward (towards phase 1) everywhere on the interface.  (ii) With
+    sigma = sigma0 - sigmaT (T - Tref) the normal component of F is the
+    capillary term with the local sigma(T), F.grad c = -sigma(T) kappa
+    eps alpha |grad c|^3, so the Marangoni term is purely tangential.
+    (iii) The net force on a closed interface vanishes (the integral of
+    d(sigma t)/ds around a closed curve), with or without a sigma gradient,
+    while the tangential part alone pulls towards the cold side (higher
+    sigma)."""
+    nx = ny = 96
+    R = 16.0
+    c = wl.tanh_profile(wl._drop_distance(nx, ny, R, 48.0, 48.0), 4.0)
+    y = np.arange(ny, dtype=float)[:, None] * np.ones((1, nx))
+    T = 0.01 * y
+    Tb, Tt = np.full(nx, -0.005), np.full(nx, 0.01 * ny - 0.005)
+    par = wl.base_params(nx, ny, eps=wl.eps_from_width(4.0), sigma0=0.02, sigmaT=0.0)
+    o = orc.scalar_ops(par, c, 0 * c, T, Tb, Tt)
+    r = np.stack([np.arange(nx)[None, :] - 48.0 + 0 * y, y - 48.0])
+    Fr = (o["Fx"] * r[0] + o["Fy"] * r[1])
+    assert Fr[np.abs(c - 0.5) < 0.3].max() < 0
+    Fabs = np.abs(o["Fx"]).sum()
+    assert abs(o["Fy"].sum()) < 1e-3 * Fabs and abs(o["Fx"].sum()) < 1e-3 * Fabs
+    par2 = dict(par, sigma0=0.02, sigmaT=0.02, Tref=0.48)
+    o2 = orc.scalar_ops(par2, c, 0 * c, T, Tb, Tt)
+    sig = 0.02 - 0.02 * (T - 0.48)
+    g2 = o2["gcx"] ** 2 + o2["gcy"] ** 2
+    ea = par["eps"] * 6 * math.sqrt(2)
+    Fn = o2["Fx"] * o2["gcx"] + o2["Fy"] * o2["gcy"]
+    expect = -sig * o2["kappa"] * ea * g2 ** 1.5
+    assert np.abs(Fn - expect).max() < 1e-12 * np.abs(expect).max()
+    assert abs(o2["Fy"].sum()) < 2e-3 * np.abs(o2["Fy"]).sum()
+    tang_y = o2["Fy"] - np.where(g2 > 0, Fn * o2["gcy"] / np.where(g2 > 0, g2, 1), 0)
+    assert tang_y.sum() < -0.1 * np.abs(tang_y).sum()
+    par3 = dict(par, sigma0=0.0, sigmaT=0.0)
+    o3 = orc.scalar_ops(par3, c, 0 * c, T, Tb, Tt)
+    assert np.abs(o3["Fx"]).max() == 0 and np.abs(o3["Fy"]).max() == 0
+
+
+# --------------------------------------------------------------- exact cases
+
+def _equilibrium_f_state(orc, par, ux, uy, p=None):
+    """Populations with f = f_eq(p, u), g = 0 (c = 0), hbar = w T (T = 1)."""
+    ny, nx = ux.shape
+    pop = orc.init(par, np.zeros((ny, nx)), np.ones((ny, nx)), np.ones(nx), np.ones(nx))
+    for y in range(ny):
+        for x in range(nx):
+            t = orc.cell_terms(par, 0.0, 0.0 if p is None else p[y, x], 1.0, 0.0,
+                               ux[y, x], uy[y, x], 0, 0, 0, 0)
+            pop[0:9, y, x] = t["feq"]
+    return pop
+
+
+def test_single_phase_poiseuille_magic_tau(orc):
+    """Halfway bounce-back with BGK and the Eq. 12 forcing: for
+    (tau_f - 1/2)^2 = 3/16 the steady force-driven channel flow is the exact
+    parabola u = a (y+1/2)(ny-1/2-y) / (2 nu) (up to O(u^2) terms of the
+    forcing, negligible at u ~ 1e-6); any other tau leaves an O(1e-3) slip
+    error.  Pins eta = rho cs2 (tau_f - 1/2) and the no-slip rule."""
+    ny, nx = 16, 2
+    y = np.arange(ny, dtype=float)
+    res = {}
+    for tau in (0.5 + math.sqrt(3.0) / 4.0, 1.0):
+        eta = CS2 * (tau - 0.5)
+        a = 1e-6 * 8 * eta / ny ** 2
+        par = wl.base_params(nx, ny, eta1=eta, eta2=eta, ax=a, sigma0=0.0)
+        pop = orc.init(par, np.zeros((ny, nx)), np.ones((ny, nx)), np.ones(nx), np.ones(nx))
+        pop = orc.run(par, pop, np.ones(nx), np.ones(nx), 12000)
+        u = orc.fields(par, pop, np.ones(nx), np.ones(nx))["ux"][:, 0]
+        exact = a / (2 * eta) * (y + 0.5) * (ny - 0.5 - y)
+        res[tau] = np.abs(u - exact).max() / exact.max()
+    taus = sorted(res)
+    assert res[taus[0]] < 1e-8, res
+    assert res[taus[1]] > 1e-4, res
+
+
+def test_conduction_linear_profile_exact(orc):
+    """Uniform conductivity, no flow: the anti-bounce-back walls and the
+    thermal LBE (Eq. aEq12) hold the linear conduction profile between
+    T_bot at y=-1/2 and T_top at y=ny-1/2 exactly, for any tau_h."""
+    nx, ny = 3, 20
+    for lam in (0.02, 0.3):
+        par = wl.base_params(nx, ny, lam1=lam, lam2=lam)
+        Tb, Tt = np.full(nx, 1.5), np.full(nx, -0.5)
+        T0 = np.full((ny, nx), 0.3)
+        pop = orc.init(par, np.zeros((ny, nx)), T0, Tb, Tt)
+        pop = orc.run(par, pop, Tb, Tt, int(40 * ny * ny / max(lam * 3, 0.3)))
+        T = orc.fields(par, pop, Tb, Tt)["T"][:, 0]
+        exact = 1.5 + (-2.0) * (np.arange(ny) + 0.5) / ny
+        assert np.abs(T - exact).max() < 1e-11, lam
+
+
+def test_shear_wave_viscosity(orc):
+    """A decaying shear wave u_y = A sin(k x) (periodic in x and y) decays at
+    nu k^2 with nu = cs2 (tau_f - 1/2) (Sec. II, eta = rho cs2 (tau_f - 1/2))."""
+    nx, ny = 48, 2
+    k = 2 * math.pi / nx
+    for eta in (0.05, 0.2):
+        par = wl.base_params(nx, ny, eta1=eta, eta2=eta, periodic_y=1)
+        x = np.arange(nx, dtype=float)
+        uy = 1e-4 * np.sin(k * x)[None, :] * np.ones((ny, 1))
+        pop = _equilibrium_f_state(orc, par, 0 * uy, uy)
+        n = 400
+        out = orc.run(par, pop, np.ones(nx), np.ones(nx), n)
+        u1 = orc.fields(par, out, np.ones(nx), np.ones(nx))["uy"][0]
+        A1 = 2 * (u1 * np.sin(k * x)).mean()
+        out2 = orc.run(par, out, np.ones(nx), np.ones(nx), n)
+        u2 = orc.fields(par, out2, np.ones(nx), np.ones(nx))["uy"][0]
+        A2 = 2 * (u2 * np.sin(k * x)).mean()
+        nu = -math.log(A2 / A1) / (n * k * k)
+        assert nu == pytest.approx(eta, rel=2e-3), (eta, nu)
+
+
+def test_thermal_wave_conductivity(orc):
+    """A temperature wave T = T0 + A sin(k x) at rest decays at lambda k^2 /
+    (rho c_v) with lambda = rho c_v cs2 tau_h and omega_T = 2/(2 tau_h + 1)
+    (Eq. aEq12, Eq. aEq14, Appendix A)."""
+    nx, ny = 48, 2
+    k = 2 * math.pi / nx
+    x = np.arange(nx, dtype=float)
+    for lam in (0.02, 0.2):
+        par = wl.base_params(nx, ny, lam1=lam, lam2=lam, periodic_y=1)
+        T0 = 1.0 + 1e-3 * np.sin(k * x)[None, :] * np.ones((ny, 1))
+        pop = orc.init(par, np.zeros((ny, nx)), T0, np.ones(nx), np.ones(nx))
+        n = 300
+        out = orc.run(par, pop, np.ones(nx), np.ones(nx), n)
+        T1 = orc.fields(par, out, np.ones(nx), np.ones(nx))["T"][0] - 1.0
+        out2 = orc.run(par, out, np.ones(nx), np.ones(nx), n)
+        T2 = orc.fields(par, out2, np.ones(nx), np.ones(nx))["T"][0] - 1.0
+        A1 = 2 * (T1 * np.sin(k * x)).mean()
+        A2 = 2 * (T2 * np.sin(k * x)).mean()
+        kap = -math.log(A2 / A1) / (n * k * k)
+        assert kap == pytest.approx(lam, rel=3e-3), (lam, kap)
+
+
+def test_cahn_hilliard_mobility(orc):
+    """With beta = 0 and no flow, the CH LBE (Eq. 27, Eq. 21-22) gives
+    d_t c = M lap mu = -M eps^2 lap^2 c (Eq. 16), so a small wave
+    c = 1/2 + A sin(k x) decays at M eps^2 k^4 with M = Gm (tau_g - 1/2)."""
+    nx, ny = 24, 2
+    k = 2 * math.pi / nx
+    x = np.arange(nx, dtype=float)
+    for M, tau_g in ((0.1, 1.0), (0.05, 0.8)):
+        par = wl.base_params(nx, ny, beta=0.0, eps=1.0, mobility=M, tau_g=tau_g,
+                             periodic_y=1)
+        c0 = 0.5 + 1e-3 * np.sin(k * x)[None, :] * np.ones((ny, 1))
+        pop = orc.init(par, c0, np.ones((ny, nx)), np.ones(nx), np.ones(nx))
+        n = 1500
+        out = orc.run(par, pop, np.ones(nx), np.ones(nx), n)
+        c1 = orc.fields(par, out, np.ones(nx), np.ones(nx))["c"][0] - 0.5
+        out2 = orc.run(par, out, np.ones(nx), np.ones(nx), n)
+        c2 = orc.fields(par, out2, np.ones(nx), np.ones(nx))["c"][0] - 0.5
+        A1 = 2 * (c1 * np.sin(k * x)).mean()
+        A2 = 2 * (c2 * np.sin(k * x)).mean()
+        rate = -math.log(A2 / A1) / n
+        assert rate == pytest.approx(M * k ** 4, rel=2e-2), (M, rate, M * k ** 4)
+
+
+# --------------------------------------------------------------- invariants
+
+def test_mass_conservation_drop(orc):
+    """sum c is conserved exactly by the CH LBE with bounce-back walls
+    (Eq. 28: sum g_eq = c and the source has no zeroth moment)."""
+    w = wl.droplet(48, 96, 8.0, 24.0, 30.0, Re=1.0, Ma=10.0, Ca=0.05, eta_m=0.2,
+                   eta_r=0.5, lam_r=0.5)
+    pop = orc.init(w.params, w.c0, w.T0, w.Tbot, w.Ttop)
+    s0 = pop[9:18].sum()
+    out = orc.run(w.params, pop, w.Tbot, w.Ttop, 400)
+    s1 = out[9:18].sum()
+    assert abs(s1 - s0) / s0 < 1e-13
+    # p is conserved as well (sum f_eq = p, sum of the f source = 0)
+    assert abs(out[0:9].sum() - pop[0:9].sum()) < 1e-13
+
+
+def test_momentum_budget_periodic(orc):
+    """With periodic boundaries in both directions the total momentum
+    sum xi f changes per step by exactly cs2 sum F (the first moment of the
+    Eq. 12 source, with u of Eq. 13); c, p and sum hbar are conserved."""
+    nx, ny = 40, 40
+    par = wl.base_params(nx, ny, sigma0=0.02, sigmaT=0.01, periodic_y=1, ax=1e-6,
+                         ay=-2e-6, eta2=0.05, lam2=0.03)
+    c = wl.tanh_profile(wl._drop_distance(nx, ny, 9.0, 17.0, 21.0), 4.0)
+    y = np.arange(ny, dtype=float)[:, None] * np.ones((1, nx))
+    T = 1.0 + 0.3 * np.sin(2 * math.pi * y / ny + 0.4)
+    pop = orc.init(par, c, T, np.ones(nx), np.ones(nx))
+    pop = orc.run(par, pop, np.ones(nx), np.ones(nx), 30)  # develop u, p
+    ex, ey, _, _, _ = orc.lattice()
+    F = orc.fields(par, pop, np.ones(nx), np.ones(nx))
+    s = orc.scalar_ops(par, F["c"], F["p"], F["T"], np.ones(nx), np.ones(nx))
+    out = orc.run(par, pop, np.ones(nx), np.ones(nx), 1)
+    for comp, e, Fk in ((0, ex, "Fx"), (1, ey, "Fy")):
+        P0 = np.tensordot(e.astype(float), pop[0:9], 1).sum()
+        P1 = np.tensordot(e.astype(float), out[0:9], 1).sum()
+        dP = P1 - P0
+        expect = CS2 * s[Fk].sum()
+        scale = CS2 * np.abs(s[Fk]).sum()
+        assert abs(dP - expect) < 1e-12 * scale, (comp, dP, expect)
+    for a, b in ((0, 9), (9, 18), (18, 27)):
+        assert abs(out[a:b].sum() - pop[a:b].sum()) < 1e-12 * abs(pop[a:b]).sum()
+
+
+def test_mirror_symmetry(orc):
+    """A drop centred on the x-mirror line x = nx/2 stays mirror-symmetric:
+    c, T, u_y even and u_x odd under x -> nx - x (mod nx)."""
+    nx, ny = 32, 64
+    w = wl.droplet(nx, ny, 8.0, nx / 2.0, 20.0, Re=1.0, Ma=10.0, Ca=0.05, eta_m=0.2,
+                   eta_r=0.5, lam_r=2.0)
+    pop = orc.init(w.params, w.c0, w.T0, w.Tbot, w.Ttop)
+    out = orc.run(w.params, pop, w.Tbot, w.Ttop, 300)
+    F = orc.fields(w.params, out, w.Tbot, w.Ttop)
+    m = (-np.arange(nx)) % nx
+    for k, sgn in (("c", 1), ("T", 1), ("p", 1), ("uy", 1), ("ux", -1)):
+        a = F[k]
+        assert np.abs(a - sgn * a[:, m]).max() <= 1e-12 * (np.abs(a).max() + 1e-300), k
+    assert np.abs(F["uy"]).max() > 1e-6
+
+
+def test_planar_interface_at_rest(orc):
+    """A planar tanh interface (the equilibrium profile of Sec. II) at uniform
+    T stays at rest (|u| < 1e-9) and settles on the scheme's discrete
+    equilibrium, which departs from the tanh by O(1/W^2): about 4x less when
+    W doubles (mobility scaled by (4/W)^2 to keep M eps^2 fixed)."""
+    devs = []
+    for W in (4.0, 8.0):
+        nx, ny = 4, 96
+        par = wl.base_params(nx, ny, sigma0=0.01, eps=wl.eps_from_width(W),
+                             mobility=0.1 * (4.0 / W) ** 2)
+        d = (np.arange(ny) - 47.5)[:, None] * np.ones((1, nx))
+        c0 = wl.tanh_profile(d, W)
+        pop = orc.init(par, c0, np.ones((ny, nx)), np.ones(nx), np.ones(nx))
+        out = orc.run(par, pop, np.ones(nx), np.ones(nx), 6000)
+        F = orc.fields(par, out, np.ones(nx), np.ones(nx))
+        assert np.abs(F["ux"]).max() < 1e-9 and np.abs(F["uy"]).max() < 1e-9
+        assert abs(F["c"].sum() - c0.sum()) < 1e-11 * c0.sum()
+        devs.append(np.abs(F["c"] - c0).max())
+    assert devs[0] < 1e-2
+    assert 3.0 < devs[0] / devs[1] < 5.0
+
+
+def test_laplace_pressure_static_drop(orc):
+    """A drop at uniform T relaxes to a pressure jump p_in - p_out = sigma/R
+    (2D Laplace law; Eq. 2 normal force), within the diffuse-interface error."""
+    nx = ny = 64
+    R = 14.0
+    for sigma in (0.01, 0.02):
+        par = wl.base_params(nx, ny, sigma0=sigma, eta1=0.1667, eta2=0.1667)
+        c0 = wl.tanh_profile(wl._drop_distance(nx, ny, R, 32.0, 32.0), 4.0)
+        pop = orc.init(par, c0, np.ones((ny, nx)), np.ones(nx), np.ones(nx))
+        out = orc.run(par, pop, np.ones(nx), np.ones(nx), 3000)
+        F = orc.fields(par, out, np.ones(nx), np.ones(nx))
+        c = F["c"]
+        Reff = math.sqrt(c.sum() / math.pi)
+        dp = F["p"][c > 0.99].mean() - F["p"][c < 0.01].mean()
+        assert dp == pytest.approx(sigma / Reff, rel=4e-2), (dp, sigma / Reff)
+
+
+# --------------------------------------------------------------- closed forms
+
+def test_closed_forms_satisfy_their_conditions():
+    """Eq. 32/33 and the Pendse solution satisfy no-slip, the wall
+    temperatures, continuity and the stress/flux jump conditions at y = 0
+    (checked numerically, independent of the printed constants)."""
+    from oracle import analytic as an
+    h, H, e1, e2, a = 30.0, 50.0, 0.1, 0.3, 1e-5
+    u = lambda y: an.poiseuille_u(y, h, H, e1, e2, 1.0, a)
+    assert abs(u(-h)) < 1e-15 and abs(u(H)) < 1e-15
+    d = 1e-6
+    assert abs(u(-1e-12) - u(1e-12)) < 1e-14
+    s_lo = e1 * (u(0.0) - u(-d)) / d
+    s_up = e2 * (u(d) - u(0.0)) / d
+    assert s_lo == pytest.approx(s_up, rel=1e-5)
+    # momentum balance in each layer: eta u'' = -rho a
+    for yy, e in ((-10.0, e1), (20.0, e2)):
+        upp = (u(yy + 1e-3) - 2 * u(yy) + u(yy - 1e-3)) / 1e-6
+        assert e * upp == pytest.approx(-a, rel=1e-4)
+    l1, l2 = 0.1, 0.35
+    T = lambda y: an.poiseuille_T(y, h, H, l1, l2, 1.0, 0.0)
+    assert T(-h) == pytest.approx(1.0, abs=1e-14) and abs(T(H)) < 1e-14
+    assert l1 * (T(0.0) - T(-d)) / d == pytest.approx(l2 * (T(d) - T(0.0)) / d, rel=1e-6)
+
+    L, h, H = 512.0, 128.0, 96.0
+    eu, el, lu, ll = 0.2, 0.35, 0.2, 0.5
+    sT = -5e-4
+    args = (L, h, H, eu, el, lu, ll, 10.0, 20.0, 4.0, sT)
+    xs = np.linspace(-L / 2, L / 2, 37)
+    ux, uy, T = an.pendse(xs, H, *args)
+    assert np.abs(ux).max() < 1e-16 and np.abs(uy).max() < 1e-16
+    assert np.abs(T - 10.0).max() < 1e-12
+    ux, uy, T = an.pendse(xs, -h, *args)
+    assert np.abs(ux).max() < 1e-16 and np.abs(uy).max() < 1e-16
+    assert np.abs(T - (20.0 + 4.0 * np.cos(2 * np.pi * xs / L))).max() < 1e-12
+    eps = 1e-7
+    up = an.pendse(xs, eps, *args)
+    lo = an.pendse(xs, -eps, *args)
+    z = an.pendse(xs, 0.0, *args)
+    assert np.abs(up[0] - lo[0]).max() < 1e-9 and np.abs(z[1]).max() < 1e-18
+    assert np.abs(up[2] - lo[2]).max() < 1e-5
+    # tangential stress jump = -d sigma/dx, sigma = sigma0 + sT (T - T0)
+    dux_up = (up[0] - z[0]) / eps
+    dux_lo = (z[0] - lo[0]) / eps
+    dTdx = (an.pendse(xs + 1e-4, 0.0, *args)[2] - an.pendse(xs - 1e-4, 0.0, *args)[2]) / 2e-4
+    lhs = eu * dux_up - el * dux_lo
+    assert np.allclose(lhs, -sT * dTdx, rtol=1e-4, atol=1e-9)
+    # heat-flux continuity
+    fl_up = lu * (up[2] - z[2]) / eps
+    fl_lo = ll * (z[2] - lo[2]) / eps
+    assert np.allclose(fl_up, fl_lo, rtol=1e-4, atol=1e-6)
+    # incompressibility inside each layer
+    for yy in (40.0, -60.0):
+        a1 = an.pendse(xs + 1e-4, yy, *args)[0]
+        a0 = an.pendse(xs - 1e-4, yy, *args)[0]
+        b1 = an.pendse(xs, yy + 1e-4, *args)[1]
+        b0 = an.pendse(xs, yy - 1e-4, *args)[1]
+        assert np.abs((a1 - a0) / 2e-4 + (b1 - b0) / 2e-4).max() < 1e-10
+
+
+def test_ygb_printed_value():
+    """Sec. IV.C prints U_YGB = 1.333e-4 for R = 20, |grad T| = 0.1,
+    eta = 0.1 and unit ratios (Eq. 42, Eq. 43); the paper does not print
+    sigma_T for that run; sigma_T = -5e-5 is the value that reproduces it."""
+    from oracle import analytic as an
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "ygb_printed.json")))
+    v = an.ygb_velocity(g["sigma_T"], g["gradT"], g["R"], g["eta"], 1.0, 1.0)
+    assert v == pytest.approx(g["U_YGB"], rel=1e-3)
