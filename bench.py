@@ -1,0 +1,317 @@
+#!/usr/bin/env python
+"""Throughput of the fused coupled-LBE step on GB300, in coupled MLUPS
+(cell updates of all three lattices per second) and as a fraction of the
+HBM roofline.
+
+Workload: the thermocapillary drop problem (Re = 1, Ma = 10, Ca = 0.05,
+viscosity and conductivity ratios 0.5, |grad T| = 1e-3, W = 4) on a
+4096 x 4096 grid (R = 256 at (2048, 1024)), FP32 population storage.  One
+step = one launch of the fused step kernel over all cells.  The state
+(2 x 1.81 GB) is far larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) each rank runs an independent replica (the method
+needs no exchange between independent problems), timing is max over ranks
+and the value is the whole-job aggregate.  ``--impl reference`` times the
+FP64 CPU oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "coupled-LBE MLUPS & % HBM roofline; mixed/batched vs plain FP32 at stated error"
+UNIT = "MLUPS"
+NX = NY = 4096
+BYTES_PER_CELL = {"f64": 432, "f32": 216, "f16dev": 112, "bf16dev": 112}
+PROFILE = os.path.join(ROOT, "profiles", "lbe_step_f32_droplet_4096x4096.md")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nx", type=int, default=NX)
+    ap.add_argument("--ny", type=int, default=NY)
+    ap.add_argument("--storage", default="f32", choices=list(BYTES_PER_CELL))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------ distributed
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(ws, v: float) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64,
+                     device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------ measurement aids
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, r[4:8]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def hbm_peak():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1412_6238_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source."""
+    try:
+        kv = {}
+        for line in open(PROFILE):
+            if ":" in line and line.lstrip().startswith("- "):
+                k, v = line.lstrip()[2:].split(":", 1)
+                kv[k.strip()] = v.strip().strip("`")
+        if kv.get("source_sha") != kernel_source_sha():
+            return None
+        return float(kv["traffic_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+# ------------------------------------------------------------ CPU oracle leg
+def band_workload():
+    """Bounded CPU sample of the benchmark problem: the same drop problem on
+    a 4096 x 256 band (R = 96)."""
+    from paper_1412_6238_gb300 import workloads as wl
+    return wl.droplet(4096, 256, 96.0, 2048.0, 128.0, Re=1.0, Ma=10.0, Ca=0.05, eta_m=0.2,
+                      eta_r=0.5, lam_r=0.5)
+
+
+def oracle_sample(target_s: float = 12.0, steps: int | None = None, warmup: int = 1):
+    """The FP64 oracle as it stands, on the host cores, on the band sample;
+    ``steps`` timed steps (or as many as fill ``target_s``)."""
+    import oracle
+    w = band_workload()
+    pop = oracle.init(w.params, w.c0, w.T0, w.Tbot, w.Ttop)
+    t = time.perf_counter()
+    pop = oracle.run(w.params, pop, w.Tbot, w.Ttop, max(1, warmup))
+    one = (time.perf_counter() - t) / max(1, warmup)
+    n = steps if steps else max(1, min(200, int(target_s / max(one, 1e-3))))
+    t = time.perf_counter()
+    oracle.run(w.params, pop, w.Tbot, w.Ttop, n)
+    dt = time.perf_counter() - t
+    return {"value": w.cells * n / dt / 1e6, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": "FP64 oracle, %d steps of the drop problem on a 4096 x 256 band "
+                      "(%.1f s)" % (n, dt)}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    # each timed step is one oracle step of the band sample; K bounds the run
+    cb = oracle_sample(steps=max(1, min(args.steps, 400)), warmup=max(1, min(args.warmup, 5)))
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "droplet_4096x4096 (sampled: 4096 x 256 band)",
+                       "storage": "f64 CPU oracle"},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------ GPU leg
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_1412_6238_gb300 import workloads as wl
+    from paper_1412_6238_gb300.lbe import LBE
+
+    torch.cuda.set_device(local)
+    w = wl.droplet_scaled(args.nx, args.ny)
+    cells = w.cells
+    sim = LBE(w, storage=args.storage)
+    stream = sim.stream
+    sim.step(args.warmup)
+    sim.synchronize()
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    clk = Clocks(torch.cuda.current_device())
+    time.sleep(0.3)
+    t0.record(stream)
+    sim.step(args.steps)
+    t1.record(stream)
+    t1.synchronize()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    barrier(ws)
+    ms = t0.elapsed_time(t1)
+    ms_max = allmax(ws, ms)
+    value = cells * args.steps * ws / (ms_max / 1e3) / 1e6
+    launch_ms = ms / args.steps
+    algo_bytes = cells * BYTES_PER_CELL[args.storage]
+    achieved = algo_bytes / (launch_ms / 1e3) / 1e9
+    peak, peak_kind = hbm_peak()
+    traffic = profiled_traffic() if (args.storage == "f32" and args.nx == NX and args.ny == NY) else None
+    fin = sim.sums()
+    del sim
+    torch.cuda.empty_cache()
+
+    # end to end through the public API, host buffers in and out
+    e2e = None
+    if not args.no_e2e:
+        c0 = torch.from_numpy(w.c0).pin_memory()
+        T0 = torch.from_numpy(w.T0).pin_memory()
+        outs = {k: torch.empty((w.ny, w.nx), dtype=torch.float64).pin_memory()
+                for k in ("c", "p", "ux", "uy", "T")}
+        w2 = wl.Workload(w.name, w.params, c0.numpy(), T0.numpy(), w.Tbot, w.Ttop, w.steps)
+        barrier(ws)
+        torch.cuda.synchronize()
+        ts = time.perf_counter()
+        s2 = LBE(w2, storage=args.storage)
+        s2.step(args.steps)
+        F = s2.fields(device="cpu")
+        for k in outs:
+            outs[k].copy_(F[k])
+        te = time.perf_counter() - ts
+        te = allmax(ws, te)
+        del s2
+        h2d = (2 * cells + 2 * w.nx) * 8
+        d2h = 5 * cells * 8
+        e2e = {"value": cells * args.steps * ws / te / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "note": "lbe_init from host c0/T0/walls + %d steps + lbe_fields to host, "
+                       "wall clock" % args.steps}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample()
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if args.storage != "f64" else "f64", "data": "synthetic",
+                "config": {"workload": "droplet_%dx%d" % (args.nx, args.ny),
+                           "problem": "thermocapillary drop, R=%g at (%g, %g), Re=1, Ma=10, "
+                                      "Ca=0.05, ratios 0.5, |grad T|=1e-3, W=4"
+                                      % (w.info["R"], w.info["xc"], w.info["yc"]),
+                           "storage": args.storage, "cells": cells,
+                           "l2": "state 2 x %.2f GB >> L2 (no flush needed)"
+                                 % (algo_bytes / 2 / 1e9),
+                           "parallelism": "replicas x%d" % ws},
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
+                             "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                             "peak_kind": peak_kind,
+                             "algorithmic_bytes_per_launch": algo_bytes},
+                "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": args.steps,
+                "check": {"sum_c": fin["sum_c"], "nonfinite": fin["nonfinite"]}}
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    ws, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

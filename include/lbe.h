@@ -1,0 +1,190 @@
+/*
+ * lbe.h -- C ABI of the GB300 (sm_103a) CSF lattice Boltzmann library for
+ * thermocapillary flow (Zheng, Zheng & Zhai, arXiv:1412.6238).
+ *
+ * One call of lbe_step advances, for every cell, the three coupled D2Q9
+ * lattices of the paper by one time step:
+ *   - the Cahn-Hilliard LBE for the order parameter c (Sec. II, Eq. 27 with
+ *     the equilibrium of Eq. 21-22, c = sum g_i by Eq. 28),
+ *   - the flow LBE forced by the continuous surface force (Sec. II, Eq. 12
+ *     with Eq. 5, Eq. 6 and the moments of Eq. 13), the force being
+ *     F = eps*alpha*|grad c|^2 (-sigma kappa n + grad_s sigma) + rho a
+ *     (Eq. 3) with sigma(T) linear in T (Eq. aEq3),
+ *   - the thermal LBE for T (Sec. III, Eq. aEq12 with h_eq of Eq. aEq9,
+ *     T from Eq. aEq13, conductivity lambda = rho c_v c_s^2 tau_h, Eq. aEq14).
+ * Problem statement (Sec. IV): periodic in x, no-slip walls with imposed
+ * temperatures at the bottom and top; lattice units dx = dt = 1.
+ *
+ * Conventions
+ *   - Cells x = 0..nx-1, y = 0..ny-1; arrays are [ny][nx], x fastest, y = 0 is
+ *     the bottom row.  The walls lie half a cell outside the first and last
+ *     rows (halfway bounce-back for f and g, anti-bounce-back for hbar; the
+ *     paper names the boundary conditions but gives no scheme).
+ *   - Phase c = 0 has viscosity eta1 and conductivity lam1, phase c = 1 has
+ *     eta2 and lam2; both vary linearly in c in between.
+ *   - sigma(T) = sigma0 - sigmaT (T - Tref); sigmaT here is MINUS the paper's
+ *     d sigma / d T, so it is positive for the usual fluids.
+ *   - Population state arrays are [27][ny][nx] doubles, planes f_0..f_8,
+ *     g_0..g_8, hbar_0..hbar_8, velocity order 0 (0,0), 1 (1,0), 2 (0,1),
+ *     3 (-1,0), 4 (0,-1), 5 (1,1), 6 (-1,1), 7 (-1,-1), 8 (1,-1); they hold
+ *     the pre-collision (post-streaming) populations of the current step.
+ *
+ * Ownership and errors
+ *   - The library owns every device buffer it allocates.  Inputs are copied
+ *     during the call; output buffers belong to the caller.
+ *   - Every call returns an lbe_status; on failure lbe_last_error() gives a
+ *     message.  A handle that returned LBE_ECUDA or LBE_ENAN stays usable
+ *     only through lbe_set_state / lbe_load / lbe_destroy.
+ *   - All work is ordered on one CUDA stream per handle (the caller's, or a
+ *     private non-blocking stream when NULL is passed).  Waits on the host are
+ *     bounded (LBE_TIMEOUT_MS environment variable, default 600000 ms) and
+ *     return LBE_ETIMEOUT rather than blocking forever.
+ */
+#ifndef LBE_H
+#define LBE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBE_ABI_VERSION 1
+
+typedef struct lbe_handle lbe_handle;
+
+typedef enum {
+  LBE_OK = 0,
+  LBE_EINVAL = -1,   /* bad argument or parameter set (message says which) */
+  LBE_ENOMEM = -2,   /* device or host allocation failed */
+  LBE_ECUDA = -3,    /* a CUDA runtime call or kernel launch failed */
+  LBE_ENAN = -4,     /* the periodic check found a NaN/Inf in the fields */
+  LBE_ETIMEOUT = -5, /* a bounded host wait ran out */
+  LBE_ESTATE = -6    /* call not valid in the handle's current state */
+} lbe_status;
+
+/* Population storage.  Arithmetic is FP64 for LBE_F64 and FP32 otherwise.
+ * The deviation forms store f_i, g_i (i > 0) and hbar_i - w_i rho c_v T_r(y)
+ * (T_r the linear conduction profile between the wall means) scaled by a
+ * power of two in 16 bits; g_0 (which carries c) stays FP32. */
+typedef enum {
+  LBE_F64 = 0,     /* 216 B per cell per buffer (parity mode)      */
+  LBE_F32 = 1,     /* 108 B per cell per buffer                    */
+  LBE_F16DEV = 2,  /* 56 B per cell per buffer (26 fp16 + 1 fp32)  */
+  LBE_BF16DEV = 3  /* 56 B per cell per buffer (26 bf16 + 1 fp32)  */
+} lbe_storage;
+
+/* Parameters of one instance, lattice units.  Validity (LBE_EINVAL
+ * otherwise): nx >= 1, ny >= 2, rho > 0, cv > 0, eta1, eta2 > 0,
+ * lam1, lam2 >= 0, eps > 0, tau_g > 1/2, mobility >= 0, eta_n > 0, and
+ * 0 < omega < 2 for every relaxation rate at c = 0 and c = 1. */
+typedef struct {
+  int32_t nx, ny;       /* cells; periodic in x, walls in y           */
+  int32_t storage;      /* lbe_storage; must be equal for all instances */
+  int32_t check_every;  /* FP64 sums + NaN scan every k steps of lbe_step
+                           (then lbe_step waits for the stream); 0 = off */
+  double rho, cv;       /* density (uniform), specific heat            */
+  double eta1, eta2;    /* dynamic viscosity of phase c=0, c=1         */
+  double lam1, lam2;    /* conductivity of phase c=0, c=1              */
+  double sigma0, sigmaT, Tref; /* sigma = sigma0 - sigmaT (T - Tref)   */
+  double eps, beta;     /* interface parameter and free-energy coefficient,
+                           E_0 = beta c^2 (c-1)^2 (Sec. II)            */
+  double tau_g;         /* CH relaxation time; omega_g = 1/tau_g        */
+  double mobility;      /* M = Gamma (tau_g - 1/2) (Eq. 16)            */
+  double ax, ay;        /* body acceleration (force rho a)             */
+  double eta_n;         /* n = grad c / sqrt(|grad c|^2 + eta_n^2)      */
+} lbe_params;
+
+/* Initial and boundary data of one instance (host pointers, copied). */
+typedef struct {
+  const double* c0;   /* [ny][nx] initial order parameter            */
+  const double* T0;   /* [ny][nx] initial temperature                */
+  const double* Tbot; /* [nx] wall temperature at y = -1/2            */
+  const double* Ttop; /* [nx] wall temperature at y = ny - 1/2        */
+} lbe_init_fields;
+
+/* Field mask bits for lbe_fields. */
+#define LBE_FIELD_C 1u
+#define LBE_FIELD_P 2u
+#define LBE_FIELD_UX 4u
+#define LBE_FIELD_UY 8u
+#define LBE_FIELD_T 16u
+
+int32_t lbe_abi_version(void);
+
+/* Create a handle holding one instance and set its state to the
+ * equilibrium of Sec. II/III at rest: u = 0, p = 0, c = c0, T = T0
+ * (f_i = 0, g_i = g_eq(c0, mu(c0), 0) with mu from the discrete Laplacian,
+ * hbar_i = w_i rho c_v T0).  stream: a cudaStream_t or NULL. */
+lbe_status lbe_init(const lbe_params* params, const lbe_init_fields* init,
+                    void* stream, lbe_handle** out);
+
+/* Same for n independent instances (params[n], init[n]) of possibly
+ * different sizes and parameters, advanced together by one persistent
+ * kernel launch per step. */
+lbe_status lbe_init_batch(int32_t n, const lbe_params* params,
+                          const lbe_init_fields* init, void* stream,
+                          lbe_handle** out);
+
+/* Enqueue nsteps time steps of every instance on the handle's stream
+ * (replayed from a captured CUDA graph).  Returns after enqueueing when
+ * check_every == 0; otherwise runs the FP64 NaN/Inf scan every check_every
+ * steps, waits for the stream and returns LBE_ENAN if any was found. */
+lbe_status lbe_step(lbe_handle* h, int64_t nsteps);
+
+/* Bounded wait until all work on the handle's stream is done. */
+lbe_status lbe_synchronize(lbe_handle* h);
+
+/* Macroscopic fields of one instance at the current step: c = sum g_i
+ * (Eq. 28), p = sum f_i (Eq. 13), u = sum xi_i f_i/(rho c_s^2) + F/(2 rho)
+ * (Eq. 13 with the c_s^2 of the Eq. 12 source), T = sum hbar_i / (rho c_v)
+ * (Eq. aEq13).  dst[0..4] receive c, p, ux, uy, T for the bits set in mask
+ * (entries for unset bits are ignored), each [ny][nx] contiguous, on the
+ * device (on_device = 1) or in host memory (0), as double (dtype 0) or
+ * float (dtype 1).  Waits for completion. */
+lbe_status lbe_fields(lbe_handle* h, int32_t instance, uint32_t mask,
+                      void* const dst[5], int32_t on_device, int32_t dtype);
+
+/* FP64 diagnostics of one instance: out[0] = sum c, out[1] = sum p,
+ * out[2] = sum_i,x hbar_i, out[3] = ||u^n - u^(n-1)||_2 / ||u^n||_2 (the
+ * per-step velocity residual, 0 before the first step), out[4] = number of
+ * non-finite values among c, p, ux, uy, T.  Deterministic.  Waits. */
+lbe_status lbe_sums(lbe_handle* h, int32_t instance, double out[5]);
+
+/* Copy the pre-collision population state of one instance to / from a
+ * [27][ny][nx] double array (device memory if on_device, else host).
+ * Setting a state converts it to the handle's storage and clears a
+ * LBE_ENAN / LBE_ECUDA condition.  Both wait for completion. */
+lbe_status lbe_get_state(lbe_handle* h, int32_t instance, double* pops,
+                         int32_t on_device);
+lbe_status lbe_set_state(lbe_handle* h, int32_t instance, const double* pops,
+                         int32_t on_device);
+
+/* Checkpoint: write every instance's parameters, walls, step count and
+ * state to a file / restore them into a handle of the same layout. */
+lbe_status lbe_save(lbe_handle* h, const char* path);
+lbe_status lbe_load(lbe_handle* h, const char* path);
+
+/* Tile shape of the step kernel (autotuner hook).  lbe_num_tiles() shapes
+ * exist; lbe_tile_shape() gives the cells of one CTA tile.  Setting a shape
+ * the handle's storage does not provide returns LBE_EINVAL.  grid_ctas sets
+ * the persistent grid size (0 = 2 x the SM count x resident CTAs/SM). */
+int32_t lbe_num_tiles(void);
+lbe_status lbe_tile_shape(int32_t tile_id, int32_t* tx, int32_t* ty);
+lbe_status lbe_set_tile(lbe_handle* h, int32_t tile_id, int32_t grid_ctas);
+
+/* Introspection. */
+int64_t lbe_steps_done(const lbe_handle* h);
+void* lbe_stream(const lbe_handle* h);         /* the cudaStream_t used   */
+int32_t lbe_num_instances(const lbe_handle* h);
+int64_t lbe_state_bytes(const lbe_handle* h); /* both population buffers */
+
+void lbe_destroy(lbe_handle* h);
+
+/* Last error message of the handle (or of this thread if h is NULL). */
+const char* lbe_last_error(const lbe_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBE_H */

@@ -1,0 +1,706 @@
+// Host side of the C ABI declared in include/lbe.h: parameter validation,
+// device memory, stream and graph management, bounded waits, checkpoints.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/lbe.h"
+#include "lbe_launch.h"
+
+using namespace lbe;
+
+namespace {
+
+thread_local std::string g_thread_err;
+
+struct InstHost {
+  lbe_params p{};
+  int nx = 0, ny = 0, pitch = 0;
+  uint64_t plane_bytes = 0, g0_off = 0, buf_bytes = 0;
+  char* arena = nullptr;  // two buffers of buf_bytes
+  double* walls = nullptr;  // device: Tbot[nx], Ttop[nx]
+  std::vector<double> Tbot, Ttop;
+};
+
+}  // namespace
+
+struct lbe_handle {
+  int n = 0;
+  int storage = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  int num_sms = 0;
+  std::vector<InstHost> inst;
+  std::vector<InstDev> idev;     // step descriptors (tile_begin for the step shape)
+  InstDev* d_inst = nullptr;     // [n] for the step kernel
+  InstDev* d_finst = nullptr;    // [n] for the field kernel (shape 0, tile_begin 0)
+  int tile = 0;
+  int grid_req = 0;              // 0 = auto, -1 = one CTA per tile, >0 = CTAs
+  int grid = 0;
+  int64_t total_tiles = 0;
+  int parity = 0;
+  int64_t steps = 0;
+  bool prev_valid = false;       // buf[parity^1] holds the previous step
+  bool bad = false;              // after LBE_ENAN / LBE_ECUDA
+  cudaGraphExec_t gexec = nullptr;
+  bool graph_failed = false;
+  cudaEvent_t ev = nullptr;
+  double* scratch = nullptr;     // fields of two states: 10 * max_cells doubles
+  int64_t max_cells = 0;
+  double* d_partial = nullptr;   // sums partials
+  double* d_sums = nullptr;      // 6 doubles
+  std::string err;
+};
+
+namespace {
+
+lbe_status fail(lbe_handle* h, lbe_status st, const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (h) {
+    h->err = buf;
+    if (st == LBE_ECUDA || st == LBE_ENAN) h->bad = true;
+  } else {
+    g_thread_err = buf;
+  }
+  return st;
+}
+
+#define CU(h, call)                                                                         \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return fail((h), e_ == cudaErrorMemoryAllocation ? LBE_ENOMEM : LBE_ECUDA, "%s: %s", \
+                  #call, cudaGetErrorString(e_));                                           \
+  } while (0)
+
+long timeout_ms() {
+  const char* s = getenv("LBE_TIMEOUT_MS");
+  long v = s ? atol(s) : 600000;
+  return v > 0 ? v : 600000;
+}
+
+bool fault_alloc() {
+  const char* s = getenv("LBE_FAULT");
+  return s && strcmp(s, "alloc") == 0;
+}
+
+// Bounded wait for all work enqueued on the handle's stream so far.
+lbe_status wait(lbe_handle* h) {
+  CU(h, cudaEventRecord(h->ev, h->stream));
+  const auto t0 = std::chrono::steady_clock::now();
+  const long lim = timeout_ms();
+  int spins = 0;
+  for (;;) {
+    cudaError_t e = cudaEventQuery(h->ev);
+    if (e == cudaSuccess) return LBE_OK;
+    if (e != cudaErrorNotReady)
+      return fail(h, LBE_ECUDA, "while waiting for the stream: %s", cudaGetErrorString(e));
+    const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(
+                        std::chrono::steady_clock::now() - t0).count();
+    if (ms > lim) return fail(h, LBE_ETIMEOUT, "stream not done after %ld ms", lim);
+    if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+lbe_status check_params(const lbe_params& p, int index) {
+  auto bad = [&](const char* what) {
+    return fail(nullptr, LBE_EINVAL, "instance %d: %s", index, what);
+  };
+  if (p.nx < 1) return bad("nx must be >= 1");
+  if (p.ny < 2) return bad("ny must be >= 2");
+  if ((int64_t)p.nx * p.ny > (int64_t)1 << 31) return bad("nx*ny must be < 2^31");
+  if (p.storage < LBE_F64 || p.storage > LBE_BF16DEV) return bad("unknown storage");
+  if (p.check_every < 0) return bad("check_every must be >= 0");
+  if (!(p.rho > 0) || !(p.cv > 0)) return bad("rho and cv must be > 0");
+  if (!(p.eta1 > 0) || !(p.eta2 > 0)) return bad("eta1, eta2 must be > 0 (0 < omega_f < 2)");
+  if (!(p.lam1 >= 0) || !(p.lam2 >= 0)) return bad("lam1, lam2 must be >= 0");
+  if (!(p.eps > 0)) return bad("eps must be > 0");
+  if (!(p.tau_g > 0.5)) return bad("tau_g must be > 1/2 (0 < omega_g < 2)");
+  if (!(p.mobility >= 0)) return bad("mobility must be >= 0");
+  if (!(p.eta_n > 0)) return bad("eta_n must be > 0");
+  const double vals[] = {p.beta, p.sigma0, p.sigmaT, p.Tref, p.ax, p.ay};
+  for (double v : vals)
+    if (!std::isfinite(v)) return bad("non-finite parameter");
+  return LBE_OK;
+}
+
+void fill_desc(lbe_handle* h, int j, InstDev& D) {
+  const InstHost& H = h->inst[j];
+  const lbe_params& p = H.p;
+  memset(&D, 0, sizeof D);
+  D.nx = H.nx;
+  D.ny = H.ny;
+  D.pitch = H.pitch;
+  D.storage = h->storage;
+  D.plane_bytes = H.plane_bytes;
+  D.g0_off = H.g0_off;
+  D.buf[0] = H.arena;
+  D.buf[1] = H.arena + H.buf_bytes;
+  D.Tbot = H.walls;
+  D.Ttop = H.walls + H.nx;
+  D.rho = p.rho;
+  D.inv_rho = 1.0 / p.rho;
+  D.rho_cv = p.rho * p.cv;
+  D.inv_rho_cv = 1.0 / (p.rho * p.cv);
+  D.eta1 = p.eta1;
+  D.deta = p.eta2 - p.eta1;
+  D.lam1 = p.lam1;
+  D.dlam = p.lam2 - p.lam1;
+  D.sigma0 = p.sigma0;
+  D.sigmaT = p.sigmaT;
+  D.Tref = p.Tref;
+  D.eps2 = p.eps * p.eps;
+  D.ea = p.eps * 6.0 * std::sqrt(2.0);  // alpha = 6 sqrt 2 (Sec. II)
+  D.beta2 = 2.0 * p.beta;
+  D.omega_g = 1.0 / p.tau_g;
+  D.Gm3 = 3.0 * p.mobility / (p.tau_g - 0.5);
+  D.Fbx = p.rho * p.ax;
+  D.Fby = p.rho * p.ay;
+  D.eta_n2 = p.eta_n * p.eta_n;
+  // hbar reference: linear profile between the mean wall temperatures
+  double tb = 0, tt = 0;
+  for (int x = 0; x < H.nx; x++) {
+    tb += H.Tbot[x];
+    tt += H.Ttop[x];
+  }
+  tb /= H.nx;
+  tt /= H.nx;
+  D.hr1 = (tt - tb) / H.ny;
+  D.hr0 = tb + 0.5 * D.hr1;
+  // power-of-two scales keep the 16-bit deviations in the normal range with
+  // a wide margin below the FP16 maximum (65504)
+  double dev = 1e-6 * (std::fabs(tb) + std::fabs(tt) + 1.0);
+  for (int x = 0; x < H.nx; x++) {
+    dev = std::fmax(dev, std::fabs(H.Tbot[x] - tb));
+    dev = std::fmax(dev, std::fabs(H.Ttop[x] - tt));
+  }
+  dev = std::fmax(dev, 0.05 * std::fabs(tt - tb));
+  const double hmax = (4.0 / 9.0) * p.rho * p.cv * dev;
+  int eh = (int)std::floor(std::log2(65504.0 / 64.0 / hmax));
+  eh = eh < -30 ? -30 : (eh > 30 ? 30 : eh);
+  const int e[3] = {12, 12, eh};
+  for (int k = 0; k < 3; k++) {
+    D.s[k] = std::ldexp(1.0f, e[k]);
+    D.inv_s[k] = std::ldexp(1.0f, -e[k]);
+  }
+}
+
+void free_handle(lbe_handle* h) {
+  if (!h) return;
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  for (auto& H : h->inst) {
+    if (H.arena) cudaFree(H.arena);
+    if (H.walls) cudaFree(H.walls);
+  }
+  if (h->d_inst) cudaFree(h->d_inst);
+  if (h->d_finst) cudaFree(h->d_finst);
+  if (h->scratch) cudaFree(h->scratch);
+  if (h->d_partial) cudaFree(h->d_partial);
+  if (h->d_sums) cudaFree(h->d_sums);
+  if (h->ev) cudaEventDestroy(h->ev);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+// (Re)build the step descriptors for the current tile shape and upload them.
+lbe_status setup_tiles(lbe_handle* h) {
+  const TileShape ts = TILE_SHAPES[h->tile];
+  int64_t begin = 0;
+  for (int j = 0; j < h->n; j++) {
+    InstDev& D = h->idev[j];
+    D.tiles_x = (D.nx + ts.tx - 1) / ts.tx;
+    D.tiles_y = (D.ny + ts.ty - 1) / ts.ty;
+    D.tile_begin = begin;
+    begin += (int64_t)D.tiles_x * D.tiles_y;
+  }
+  h->total_tiles = begin;
+  CU(h, cudaMemcpyAsync(h->d_inst, h->idev.data(), sizeof(InstDev) * h->n,
+                        cudaMemcpyHostToDevice, h->stream));
+  const int occ = step_occupancy(h->storage, h->tile);
+  if (occ <= 0) return fail(h, LBE_ECUDA, "step kernel for tile %d cannot be resident", h->tile);
+  if (h->grid_req == -1)
+    h->grid = (int)(h->total_tiles < 2147483647 ? h->total_tiles : 2147483647);
+  else if (h->grid_req > 0)
+    h->grid = h->grid_req;
+  else
+    h->grid = occ * h->num_sms;
+  if (h->gexec) {
+    cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+  }
+  h->graph_failed = false;
+  return wait(h);
+}
+
+lbe_status launch_steps_direct(lbe_handle* h, int64_t k) {
+  for (int64_t s = 0; s < k; s++) {
+    cudaError_t e = launch_step(h->storage, h->tile, h->d_inst, h->n, h->total_tiles,
+                                h->parity, h->grid, h->stream);
+    if (e != cudaSuccess) return fail(h, LBE_ECUDA, "step launch: %s", cudaGetErrorString(e));
+    h->parity ^= 1;
+    h->steps++;
+    h->prev_valid = true;
+  }
+  return LBE_OK;
+}
+
+// Graph of two steps (parity 0 -> 1 -> 0), captured once per tile setup.
+void ensure_graph(lbe_handle* h) {
+  if (h->gexec || h->graph_failed) return;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    h->graph_failed = true;
+    return;
+  }
+  cudaError_t e1 = launch_step(h->storage, h->tile, h->d_inst, h->n, h->total_tiles, 0, h->grid,
+                               h->stream);
+  cudaError_t e2 = launch_step(h->storage, h->tile, h->d_inst, h->n, h->total_tiles, 1, h->grid,
+                               h->stream);
+  cudaError_t e3 = cudaStreamEndCapture(h->stream, &g);
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || !g ||
+      cudaGraphInstantiate(&h->gexec, g, 0) != cudaSuccess) {
+    cudaGetLastError();
+    h->gexec = nullptr;
+    h->graph_failed = true;
+  }
+  if (g) cudaGraphDestroy(g);
+}
+
+lbe_status run_steps(lbe_handle* h, int64_t k) {
+  if (k <= 0) return LBE_OK;
+  if (h->parity == 1) {
+    lbe_status st = launch_steps_direct(h, 1);
+    if (st) return st;
+    k--;
+  }
+  ensure_graph(h);
+  if (h->gexec) {
+    for (; k >= 2; k -= 2) {
+      cudaError_t e = cudaGraphLaunch(h->gexec, h->stream);
+      if (e != cudaSuccess) return fail(h, LBE_ECUDA, "graph launch: %s", cudaGetErrorString(e));
+      h->steps += 2;
+      h->prev_valid = true;
+    }
+  }
+  return launch_steps_direct(h, k);
+}
+
+lbe_status ensure_scratch(lbe_handle* h) {
+  if (h->scratch) return LBE_OK;
+  CU(h, cudaMalloc(&h->scratch, sizeof(double) * 10 * (size_t)h->max_cells));
+  CU(h, cudaMalloc(&h->d_partial, sizeof(double) * 6 * sums_blocks()));
+  CU(h, cudaMalloc(&h->d_sums, sizeof(double) * 6));
+  return LBE_OK;
+}
+
+lbe_status compute_fields(lbe_handle* h, int j, int which_parity, double* out) {
+  const InstHost& H = h->inst[j];
+  const TileShape ts = TILE_SHAPES[0];
+  const int64_t tiles = (int64_t)((H.nx + ts.tx - 1) / ts.tx) * ((H.ny + ts.ty - 1) / ts.ty);
+  cudaError_t e = launch_fields(h->storage, h->d_finst + j, tiles, which_parity, out, h->stream);
+  if (e != cudaSuccess) return fail(h, LBE_ECUDA, "field kernel: %s", cudaGetErrorString(e));
+  return LBE_OK;
+}
+
+// sums of instance j into host out6 (c, p, T, |du|^2, |u|^2, nonfinite)
+lbe_status sums6(lbe_handle* h, int j, double out6[6]) {
+  lbe_status st = ensure_scratch(h);
+  if (st) return st;
+  const InstHost& H = h->inst[j];
+  const int64_t N = (int64_t)H.nx * H.ny;
+  double* cur = h->scratch;
+  double* prev = h->scratch + 5 * (size_t)h->max_cells;
+  if ((st = compute_fields(h, j, h->parity, cur))) return st;
+  const bool hp = h->prev_valid;
+  if (hp && (st = compute_fields(h, j, h->parity ^ 1, prev))) return st;
+  cudaError_t e = launch_sums(cur, hp ? prev : nullptr, N, h->d_partial, h->d_sums, h->stream);
+  if (e != cudaSuccess) return fail(h, LBE_ECUDA, "sums kernel: %s", cudaGetErrorString(e));
+  CU(h, cudaMemcpyAsync(out6, h->d_sums, 6 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  return wait(h);
+}
+
+lbe_status create(int32_t n, const lbe_params* params, const lbe_init_fields* init, void* stream,
+                  lbe_handle** out) {
+  if (!out) return fail(nullptr, LBE_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || !params || !init) return fail(nullptr, LBE_EINVAL, "need n >= 1, params, init");
+  for (int j = 0; j < n; j++) {
+    lbe_status st = check_params(params[j], j);
+    if (st) return st;
+    if (params[j].storage != params[0].storage)
+      return fail(nullptr, LBE_EINVAL, "all instances must use the same storage");
+    if (!init[j].c0 || !init[j].T0 || !init[j].Tbot || !init[j].Ttop)
+      return fail(nullptr, LBE_EINVAL, "instance %d: NULL initial field", j);
+  }
+  if (fault_alloc()) return fail(nullptr, LBE_ENOMEM, "allocation failed (LBE_FAULT=alloc)");
+  lbe_handle* h = new lbe_handle();
+  h->n = n;
+  h->storage = params[0].storage;
+  h->inst.resize(n);
+  h->idev.resize(n);
+  auto bail = [&](lbe_status st) {
+    std::string m = h->err;
+    free_handle(h);
+    g_thread_err = m;
+    return st;
+  };
+#define CUB(call)                                                                           \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return bail(fail(h, e_ == cudaErrorMemoryAllocation ? LBE_ENOMEM : LBE_ECUDA, "%s: %s", \
+                       #call, cudaGetErrorString(e_)));                                     \
+  } while (0)
+  CUB(cudaGetDevice(&h->device));
+  CUB(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
+  if (stream) {
+    h->stream = (cudaStream_t)stream;
+  } else {
+    CUB(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    h->own_stream = true;
+  }
+  CUB(cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming));
+  const int st = h->storage;
+  const size_t esz = st == LBE_F64 ? 8 : (st == LBE_F32 ? 4 : 2);
+  for (int j = 0; j < n; j++) {
+    InstHost& H = h->inst[j];
+    H.p = params[j];
+    H.nx = params[j].nx;
+    H.ny = params[j].ny;
+    H.pitch = round_up(H.nx, 64);
+    H.plane_bytes = ((uint64_t)H.ny * H.pitch * esz + 255) / 256 * 256;
+    if (st >= LBE_F16DEV) {
+      H.g0_off = 26 * H.plane_bytes;
+      H.buf_bytes = H.g0_off + (((uint64_t)H.ny * H.pitch * 4 + 255) / 256 * 256);
+    } else {
+      H.g0_off = 0;
+      H.buf_bytes = 27 * H.plane_bytes;
+    }
+    CUB(cudaMalloc(&H.arena, 2 * H.buf_bytes));
+    CUB(cudaMemsetAsync(H.arena, 0, 2 * H.buf_bytes, h->stream));
+    CUB(cudaMalloc(&H.walls, sizeof(double) * 2 * H.nx));
+    H.Tbot.assign(init[j].Tbot, init[j].Tbot + H.nx);
+    H.Ttop.assign(init[j].Ttop, init[j].Ttop + H.nx);
+    CUB(cudaMemcpyAsync(H.walls, H.Tbot.data(), sizeof(double) * H.nx, cudaMemcpyHostToDevice,
+                        h->stream));
+    CUB(cudaMemcpyAsync(H.walls + H.nx, H.Ttop.data(), sizeof(double) * H.nx,
+                        cudaMemcpyHostToDevice, h->stream));
+    fill_desc(h, j, h->idev[j]);
+    h->max_cells = std::max<int64_t>(h->max_cells, (int64_t)H.nx * H.ny);
+  }
+  CUB(cudaMalloc(&h->d_inst, sizeof(InstDev) * n));
+  CUB(cudaMalloc(&h->d_finst, sizeof(InstDev) * n));
+  {
+    std::vector<InstDev> f = h->idev;
+    const TileShape ts = TILE_SHAPES[0];
+    for (auto& D : f) {
+      D.tiles_x = (D.nx + ts.tx - 1) / ts.tx;
+      D.tiles_y = (D.ny + ts.ty - 1) / ts.ty;
+      D.tile_begin = 0;
+    }
+    CUB(cudaMemcpyAsync(h->d_finst, f.data(), sizeof(InstDev) * n, cudaMemcpyHostToDevice,
+                        h->stream));
+    CUB(cudaStreamSynchronize(h->stream));
+  }
+  // initial state of each instance: compute the pre-collision state at rest
+  // and push it into buffer 0
+  for (int j = 0; j < n; j++) {
+    InstHost& H = h->inst[j];
+    const size_t N = (size_t)H.nx * H.ny;
+    double *c0 = nullptr, *pre = nullptr;
+    CUB(cudaMalloc(&c0, sizeof(double) * 2 * N));
+    cudaError_t e = cudaMalloc(&pre, sizeof(double) * 27 * N);
+    if (e != cudaSuccess) {
+      cudaFree(c0);
+      CUB(e);
+    }
+    cudaMemcpyAsync(c0, init[j].c0, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream);
+    cudaMemcpyAsync(c0 + N, init[j].T0, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream);
+    e = launch_init_state(h->d_finst + j, H.nx, H.ny, c0, c0 + N, pre, h->stream);
+    if (e == cudaSuccess) e = launch_push(h->storage, h->d_finst + j, H.nx, H.ny, pre, 0, h->stream);
+    cudaError_t es = cudaStreamSynchronize(h->stream);
+    cudaFree(c0);
+    cudaFree(pre);
+    CUB(e);
+    CUB(es);
+  }
+  h->tile = 0;
+  lbe_status s2 = setup_tiles(h);
+  if (s2) return bail(s2);
+  *out = h;
+  return LBE_OK;
+#undef CUB
+}
+
+lbe_status check_handle(lbe_handle* h, int32_t instance) {
+  if (!h) return fail(nullptr, LBE_EINVAL, "handle is NULL");
+  if (instance < 0 || instance >= h->n) return fail(h, LBE_EINVAL, "instance %d out of range", instance);
+  return LBE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t lbe_abi_version(void) { return LBE_ABI_VERSION; }
+
+lbe_status lbe_init(const lbe_params* params, const lbe_init_fields* init, void* stream,
+                    lbe_handle** out) {
+  return create(1, params, init, stream, out);
+}
+
+lbe_status lbe_init_batch(int32_t n, const lbe_params* params, const lbe_init_fields* init,
+                          void* stream, lbe_handle** out) {
+  return create(n, params, init, stream, out);
+}
+
+lbe_status lbe_step(lbe_handle* h, int64_t nsteps) {
+  if (!h) return fail(nullptr, LBE_EINVAL, "handle is NULL");
+  if (nsteps < 0) return fail(h, LBE_EINVAL, "nsteps must be >= 0");
+  if (h->bad) return fail(h, LBE_ESTATE, "handle is in an error state; set a state or load a checkpoint");
+  int ce = 0;
+  for (auto& H : h->inst)
+    if (H.p.check_every > 0 && (ce == 0 || H.p.check_every < ce)) ce = H.p.check_every;
+  if (ce == 0) return run_steps(h, nsteps);
+  int64_t left = nsteps;
+  while (left > 0) {
+    int64_t to_check = ce - (h->steps % ce);
+    int64_t k = left < to_check ? left : to_check;
+    lbe_status st = run_steps(h, k);
+    if (st) return st;
+    left -= k;
+    if (h->steps % ce == 0) {
+      for (int j = 0; j < h->n; j++) {
+        double s6[6];
+        if ((st = sums6(h, j, s6))) return st;
+        if (s6[5] != 0)
+          return fail(h, LBE_ENAN, "instance %d: %.0f non-finite field values at step %lld", j,
+                      s6[5], (long long)h->steps);
+      }
+    }
+  }
+  return wait(h);
+}
+
+lbe_status lbe_synchronize(lbe_handle* h) {
+  if (!h) return fail(nullptr, LBE_EINVAL, "handle is NULL");
+  return wait(h);
+}
+
+lbe_status lbe_fields(lbe_handle* h, int32_t instance, uint32_t mask, void* const dst[5],
+                      int32_t on_device, int32_t dtype) {
+  lbe_status st = check_handle(h, instance);
+  if (st) return st;
+  if (!dst) return fail(h, LBE_EINVAL, "dst is NULL");
+  if (dtype != 0 && dtype != 1) return fail(h, LBE_EINVAL, "dtype must be 0 (f64) or 1 (f32)");
+  for (int k = 0; k < 5; k++)
+    if ((mask >> k & 1u) && !dst[k]) return fail(h, LBE_EINVAL, "dst[%d] is NULL", k);
+  if ((st = ensure_scratch(h))) return st;
+  const InstHost& H = h->inst[instance];
+  const int64_t N = (int64_t)H.nx * H.ny;
+  double* cur = h->scratch;
+  if ((st = compute_fields(h, instance, h->parity, cur))) return st;
+  float* tmp32 = reinterpret_cast<float*>(h->scratch + 5 * (size_t)h->max_cells);
+  for (int k = 0; k < 5; k++) {
+    if (!(mask >> k & 1u)) continue;
+    const double* src = cur + k * N;
+    if (dtype == 0) {
+      CU(h, cudaMemcpyAsync(dst[k], src, sizeof(double) * N,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                            h->stream));
+    } else if (on_device) {
+      cudaError_t e = launch_f64_to_f32(src, reinterpret_cast<float*>(dst[k]), N, h->stream);
+      if (e != cudaSuccess) return fail(h, LBE_ECUDA, "cast kernel: %s", cudaGetErrorString(e));
+    } else {
+      cudaError_t e = launch_f64_to_f32(src, tmp32, N, h->stream);
+      if (e != cudaSuccess) return fail(h, LBE_ECUDA, "cast kernel: %s", cudaGetErrorString(e));
+      CU(h, cudaMemcpyAsync(dst[k], tmp32, sizeof(float) * N, cudaMemcpyDeviceToHost, h->stream));
+      if ((st = wait(h))) return st;  // tmp32 is reused by the next field
+    }
+  }
+  return wait(h);
+}
+
+lbe_status lbe_sums(lbe_handle* h, int32_t instance, double out[5]) {
+  lbe_status st = check_handle(h, instance);
+  if (st) return st;
+  if (!out) return fail(h, LBE_EINVAL, "out is NULL");
+  double s6[6];
+  if ((st = sums6(h, instance, s6))) return st;
+  const InstHost& H = h->inst[instance];
+  out[0] = s6[0];
+  out[1] = s6[1];
+  out[2] = s6[2] * H.p.rho * H.p.cv;
+  out[3] = (h->prev_valid && s6[4] > 0) ? std::sqrt(s6[3]) / std::sqrt(s6[4]) : 0.0;
+  out[4] = s6[5];
+  return LBE_OK;
+}
+
+lbe_status lbe_get_state(lbe_handle* h, int32_t instance, double* pops, int32_t on_device) {
+  lbe_status st = check_handle(h, instance);
+  if (st) return st;
+  if (!pops) return fail(h, LBE_EINVAL, "pops is NULL");
+  const InstHost& H = h->inst[instance];
+  const size_t N = (size_t)H.nx * H.ny;
+  double* d = pops;
+  if (!on_device) CU(h, cudaMalloc(&d, sizeof(double) * 27 * N));
+  cudaError_t e = launch_pull(h->storage, h->d_finst + instance, H.nx, H.ny, d, h->parity, h->stream);
+  if (e == cudaSuccess && !on_device)
+    e = cudaMemcpyAsync(pops, d, sizeof(double) * 27 * N, cudaMemcpyDeviceToHost, h->stream);
+  st = wait(h);
+  if (!on_device) cudaFree(d);
+  if (e != cudaSuccess) return fail(h, LBE_ECUDA, "get_state: %s", cudaGetErrorString(e));
+  return st;
+}
+
+lbe_status lbe_set_state(lbe_handle* h, int32_t instance, const double* pops, int32_t on_device) {
+  lbe_status st = check_handle(h, instance);
+  if (st) return st;
+  if (!pops) return fail(h, LBE_EINVAL, "pops is NULL");
+  const InstHost& H = h->inst[instance];
+  const size_t N = (size_t)H.nx * H.ny;
+  double* d = const_cast<double*>(pops);
+  if (!on_device) {
+    CU(h, cudaMalloc(&d, sizeof(double) * 27 * N));
+    cudaError_t e = cudaMemcpyAsync(d, pops, sizeof(double) * 27 * N, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) {
+      cudaFree(d);
+      return fail(h, LBE_ECUDA, "set_state copy: %s", cudaGetErrorString(e));
+    }
+  }
+  cudaError_t e = launch_push(h->storage, h->d_finst + instance, H.nx, H.ny, d, h->parity, h->stream);
+  st = wait(h);
+  if (!on_device) cudaFree(d);
+  if (e != cudaSuccess) return fail(h, LBE_ECUDA, "set_state: %s", cudaGetErrorString(e));
+  if (st) return st;
+  h->bad = false;
+  h->prev_valid = false;
+  return LBE_OK;
+}
+
+// checkpoint format: "LBECKPT1", int32 n, int32 storage, int64 steps, then per
+// instance: lbe_params, Tbot[nx], Ttop[nx], state[27][ny][nx] (double)
+lbe_status lbe_save(lbe_handle* h, const char* path) {
+  if (!h || !path) return fail(h, LBE_EINVAL, "handle or path is NULL");
+  FILE* fp = fopen(path, "wb");
+  if (!fp) return fail(h, LBE_EINVAL, "cannot open %s for writing", path);
+  const char magic[8] = {'L', 'B', 'E', 'C', 'K', 'P', 'T', '1'};
+  const int32_t hdr[2] = {h->n, h->storage};
+  const int64_t steps = h->steps;
+  bool ok = fwrite(magic, 1, 8, fp) == 8 && fwrite(hdr, sizeof hdr, 1, fp) == 1 &&
+            fwrite(&steps, sizeof steps, 1, fp) == 1;
+  for (int j = 0; ok && j < h->n; j++) {
+    const InstHost& H = h->inst[j];
+    std::vector<double> s((size_t)27 * H.nx * H.ny);
+    lbe_status st = lbe_get_state(h, j, s.data(), 0);
+    if (st) {
+      fclose(fp);
+      return st;
+    }
+    ok = fwrite(&H.p, sizeof H.p, 1, fp) == 1 &&
+         fwrite(H.Tbot.data(), sizeof(double), H.nx, fp) == (size_t)H.nx &&
+         fwrite(H.Ttop.data(), sizeof(double), H.nx, fp) == (size_t)H.nx &&
+         fwrite(s.data(), sizeof(double), s.size(), fp) == s.size();
+  }
+  if (fclose(fp) != 0) ok = false;
+  return ok ? LBE_OK : fail(h, LBE_EINVAL, "short write to %s", path);
+}
+
+lbe_status lbe_load(lbe_handle* h, const char* path) {
+  if (!h || !path) return fail(h, LBE_EINVAL, "handle or path is NULL");
+  FILE* fp = fopen(path, "rb");
+  if (!fp) return fail(h, LBE_EINVAL, "cannot open %s", path);
+  char magic[8];
+  int32_t hdr[2];
+  int64_t steps;
+  bool ok = fread(magic, 1, 8, fp) == 8 && memcmp(magic, "LBECKPT1", 8) == 0 &&
+            fread(hdr, sizeof hdr, 1, fp) == 1 && fread(&steps, sizeof steps, 1, fp) == 1;
+  if (!ok || hdr[0] != h->n || hdr[1] != h->storage) {
+    fclose(fp);
+    return fail(h, LBE_EINVAL, "%s: not a checkpoint of this handle's layout", path);
+  }
+  for (int j = 0; j < h->n; j++) {
+    InstHost& H = h->inst[j];
+    lbe_params p;
+    std::vector<double> tb(H.nx), tt(H.nx), s((size_t)27 * H.nx * H.ny);
+    ok = fread(&p, sizeof p, 1, fp) == 1 && p.nx == H.nx && p.ny == H.ny &&
+         fread(tb.data(), sizeof(double), H.nx, fp) == (size_t)H.nx &&
+         fread(tt.data(), sizeof(double), H.nx, fp) == (size_t)H.nx &&
+         fread(s.data(), sizeof(double), s.size(), fp) == s.size();
+    if (!ok) {
+      fclose(fp);
+      return fail(h, LBE_EINVAL, "%s: truncated or mismatched instance %d", path, j);
+    }
+    if (memcmp(&p, &H.p, sizeof p) != 0 || tb != H.Tbot || tt != H.Ttop) {
+      fclose(fp);
+      return fail(h, LBE_EINVAL, "%s: instance %d has other parameters or walls", path, j);
+    }
+    lbe_status st = lbe_set_state(h, j, s.data(), 0);
+    if (st) {
+      fclose(fp);
+      return st;
+    }
+  }
+  fclose(fp);
+  h->steps = steps;
+  return LBE_OK;
+}
+
+int32_t lbe_num_tiles(void) { return NUM_TILES; }
+
+lbe_status lbe_tile_shape(int32_t tile_id, int32_t* tx, int32_t* ty) {
+  if (tile_id < 0 || tile_id >= NUM_TILES || !tx || !ty)
+    return fail(nullptr, LBE_EINVAL, "tile id %d out of range", tile_id);
+  *tx = TILE_SHAPES[tile_id].tx;
+  *ty = TILE_SHAPES[tile_id].ty;
+  return LBE_OK;
+}
+
+lbe_status lbe_set_tile(lbe_handle* h, int32_t tile_id, int32_t grid_ctas) {
+  if (!h) return fail(nullptr, LBE_EINVAL, "handle is NULL");
+  if (!tile_available(h->storage, tile_id))
+    return fail(h, LBE_EINVAL, "tile %d is not built for this storage", tile_id);
+  if (grid_ctas < -1) return fail(h, LBE_EINVAL, "grid_ctas must be >= -1");
+  lbe_status st = wait(h);
+  if (st) return st;
+  h->tile = tile_id;
+  h->grid_req = grid_ctas;
+  return setup_tiles(h);
+}
+
+int64_t lbe_steps_done(const lbe_handle* h) { return h ? h->steps : -1; }
+void* lbe_stream(const lbe_handle* h) { return h ? (void*)h->stream : nullptr; }
+int32_t lbe_num_instances(const lbe_handle* h) { return h ? h->n : 0; }
+int64_t lbe_state_bytes(const lbe_handle* h) {
+  if (!h) return 0;
+  int64_t b = 0;
+  for (auto& H : h->inst) b += 2 * (int64_t)H.buf_bytes;
+  return b;
+}
+
+void lbe_destroy(lbe_handle* h) {
+  if (!h) return;
+  if (h->stream) wait(h);  // bounded; the buffers are freed either way
+  free_handle(h);
+}
+
+const char* lbe_last_error(const lbe_handle* h) {
+  return h ? h->err.c_str() : g_thread_err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,267 @@
+// Auxiliary kernels: initial state, state conversion (push / pull between the
+// pre-collision form and a storage buffer), FP64 reductions, dtype casts,
+// and the storage dispatch of the step / field launchers.
+#include "lbe_launch.h"
+#include "lbe_tile.cuh"
+
+namespace lbe {
+
+// ------------------------------------------------------------------ dispatch
+bool tile_available(int storage, int tile) {
+  if (tile < 0 || tile >= NUM_TILES) return false;
+  if (storage == ST_F64) return tile == 0;
+  return true;
+}
+
+cudaError_t launch_step(int storage, int tile, const InstDev* d, int n, int64_t total, int parity,
+                        int grid, cudaStream_t s) {
+  switch (storage) {
+    case ST_F64: return launch_step_f64(tile, d, n, total, parity, grid, s);
+    case ST_F32: return launch_step_f32(tile, d, n, total, parity, grid, s);
+    case ST_F16DEV: return launch_step_f16(tile, d, n, total, parity, grid, s);
+    case ST_BF16DEV: return launch_step_bf16(tile, d, n, total, parity, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+int step_occupancy(int storage, int tile) {
+  switch (storage) {
+    case ST_F64: return occupancy_f64(tile);
+    case ST_F32: return occupancy_f32(tile);
+    case ST_F16DEV: return occupancy_f16(tile);
+    case ST_BF16DEV: return occupancy_bf16(tile);
+  }
+  return 0;
+}
+
+cudaError_t launch_fields(int storage, const InstDev* d, int64_t tiles, int parity, double* out,
+                          cudaStream_t s) {
+  switch (storage) {
+    case ST_F64: return fields_f64(d, tiles, parity, out, s);
+    case ST_F32: return fields_f32(d, tiles, parity, out, s);
+    case ST_F16DEV: return fields_f16(d, tiles, parity, out, s);
+    case ST_BF16DEV: return fields_bf16(d, tiles, parity, out, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------- initial state
+// At rest (u = 0, p = 0): f_i = f_eq(0, 0) = 0; g_i = g_eq(c0, mu0, 0) with
+// mu0 = 2 beta c0 (c0-1)(2c0-1) - eps^2 lap c0 (Eq. 21-22), lap c0 by the
+// isotropic stencil with mirrored ghost rows; hbar_i = w_i rho c_v T0
+// (Eq. aEq9 at u = 0).
+__global__ void init_state_kernel(const InstDev* __restrict__ d, int nx, int ny,
+                                  const double* __restrict__ c0, const double* __restrict__ T0,
+                                  double* __restrict__ pre) {
+  const int64_t N = (int64_t)nx * ny;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(k % nx), y = (int)(k / nx);
+    const InstDev& I = *d;
+    auto cat = [&](int xx, int yy) -> double {
+      xx = (xx % nx + nx) % nx;
+      if (yy < 0) yy = -1 - yy;
+      if (yy >= ny) yy = 2 * ny - 1 - yy;
+      return c0[(int64_t)yy * nx + xx];
+    };
+    const double v0 = c0[k];
+    const double ax = (cat(x + 1, y) + cat(x - 1, y)) + (cat(x, y + 1) + cat(x, y - 1));
+    const double dg = (cat(x + 1, y + 1) + cat(x - 1, y + 1)) + (cat(x + 1, y - 1) + cat(x - 1, y - 1));
+    const double lap = (4.0 * ax + dg - 20.0 * v0) * (1.0 / 6.0);
+    const double mu = I.beta2 * v0 * (v0 - 1.0) * (2.0 * v0 - 1.0) - I.eps2 * lap;
+    const double Gmu = I.Gm3 * mu;
+    for (int i = 0; i < 9; i++) {
+      const double w = WGT<double>(i);
+      pre[(int64_t)i * N + k] = 0.0;
+      pre[(int64_t)(9 + i) * N + k] = (i == 0) ? v0 - (1.0 - WGT<double>(0)) * Gmu : w * Gmu;
+      pre[(int64_t)(18 + i) * N + k] = w * I.rho_cv * T0[k];
+    }
+  }
+}
+
+cudaError_t launch_init_state(const InstDev* d, int nx, int ny, const double* c0,
+                              const double* T0, double* pre, cudaStream_t s) {
+  const int64_t N = (int64_t)nx * ny;
+  const int grid = (int)((N + 255) / 256 < 65535 ? (N + 255) / 256 : 65535);
+  init_state_kernel<<<grid, 256, 0, s>>>(d, nx, ny, c0, T0, pre);
+  return cudaGetLastError();
+}
+
+// -------------------------------------------------------------- push / pull
+// The pull P_i(x) = P*_i(x - xi_i) is a permutation of the buffer entries
+// (each post-collision value either streams to x + xi_i or, at a wall,
+// returns reversed to x), so it has an exact inverse, the push:
+//   P*_j(x) = P_j(x + xi_j)                 if x + xi_j is a cell,
+//   P*_j(x) = P_jbar(x)                      at a wall for f and g,
+//   P*_j(x) = 2 w_j rho c_v T_w - P_jbar(x)  at a wall for hbar.
+template <class S>
+__global__ void push_kernel(const InstDev* __restrict__ d, int nx, int ny,
+                            const double* __restrict__ pre, int parity) {
+  using C = typename S::C;
+  const InstDev& I = *d;
+  const int64_t N = (int64_t)nx * ny;
+  char* buf = I.buf[parity];
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(k % nx), y = (int)(k / nx);
+    const size_t idx = (size_t)y * I.pitch + x;
+    const C ref = (S::kind >= ST_F16DEV) ? href<S>(I, y) : C(0);
+#pragma unroll
+    for (int j = 0; j < 9; j++) {
+      const int xt = ((x + EX(j)) % nx + nx) % nx;
+      const int yt = y + EY(j);
+      const bool wall = (yt < 0) || (yt >= ny);
+      for (int kk = 0; kk < 3; kk++) {
+        double v;
+        if (!wall) {
+          v = pre[(int64_t)(kk * 9 + j) * N + (int64_t)yt * nx + xt];
+        } else {
+          const double pb = pre[(int64_t)(kk * 9 + OPP(j)) * N + k];
+          if (kk < 2) {
+            v = pb;
+          } else {
+            const double Tw = (yt < 0) ? I.Tbot[x] : I.Ttop[x];
+            v = 2.0 * WGT<double>(j) * I.rho_cv * Tw - pb;
+          }
+        }
+        S::st(I, buf, kk, j, idx, ref, (C)v);
+      }
+    }
+  }
+}
+
+template <class S>
+__global__ void pull_kernel(const InstDev* __restrict__ d, int nx, int ny, double* __restrict__ pre,
+                            int parity) {
+  using C = typename S::C;
+  const InstDev& I = *d;
+  const int64_t N = (int64_t)nx * ny;
+  const char* buf = I.buf[parity];
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(k % nx), y = (int)(k / nx);
+    const Cell<S> q = make_cell<S>(x, y, nx);
+    C v[9];
+    pull9<S, 0>(I, buf, q, v);
+    for (int i = 0; i < 9; i++) pre[(int64_t)i * N + k] = (double)v[i];
+    pull9<S, 1>(I, buf, q, v);
+    for (int i = 0; i < 9; i++) pre[(int64_t)(9 + i) * N + k] = (double)v[i];
+    pull9<S, 2>(I, buf, q, v);
+    for (int i = 0; i < 9; i++) pre[(int64_t)(18 + i) * N + k] = (double)v[i];
+  }
+}
+
+template <class S>
+static cudaError_t push_t(const InstDev* d, int nx, int ny, const double* pre, int parity,
+                          cudaStream_t s) {
+  const int64_t N = (int64_t)nx * ny;
+  const int grid = (int)((N + 255) / 256 < 65535 ? (N + 255) / 256 : 65535);
+  push_kernel<S><<<grid, 256, 0, s>>>(d, nx, ny, pre, parity);
+  return cudaGetLastError();
+}
+template <class S>
+static cudaError_t pull_t(const InstDev* d, int nx, int ny, double* pre, int parity,
+                          cudaStream_t s) {
+  const int64_t N = (int64_t)nx * ny;
+  const int grid = (int)((N + 255) / 256 < 65535 ? (N + 255) / 256 : 65535);
+  pull_kernel<S><<<grid, 256, 0, s>>>(d, nx, ny, pre, parity);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_push(int storage, const InstDev* d, int nx, int ny, const double* pre,
+                        int parity, cudaStream_t s) {
+  switch (storage) {
+    case ST_F64: return push_t<StF64>(d, nx, ny, pre, parity, s);
+    case ST_F32: return push_t<StF32>(d, nx, ny, pre, parity, s);
+    case ST_F16DEV: return push_t<StF16>(d, nx, ny, pre, parity, s);
+    case ST_BF16DEV: return push_t<StBF16>(d, nx, ny, pre, parity, s);
+  }
+  return cudaErrorInvalidValue;
+}
+cudaError_t launch_pull(int storage, const InstDev* d, int nx, int ny, double* pre, int parity,
+                        cudaStream_t s) {
+  switch (storage) {
+    case ST_F64: return pull_t<StF64>(d, nx, ny, pre, parity, s);
+    case ST_F32: return pull_t<StF32>(d, nx, ny, pre, parity, s);
+    case ST_F16DEV: return pull_t<StF16>(d, nx, ny, pre, parity, s);
+    case ST_BF16DEV: return pull_t<StBF16>(d, nx, ny, pre, parity, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------- FP64 sums
+// Two passes, fixed block count and fixed reduction order: deterministic.
+constexpr int SUM_BLOCKS = 304;
+constexpr int SUM_THREADS = 256;
+int sums_blocks() { return SUM_BLOCKS; }
+
+__device__ __forceinline__ void block_sum6(double v[6], double* sh) {
+  // sh: 6 * SUM_THREADS doubles
+  for (int j = 0; j < 6; j++) sh[j * SUM_THREADS + threadIdx.x] = v[j];
+  __syncthreads();
+  for (int st = SUM_THREADS / 2; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st)
+      for (int j = 0; j < 6; j++)
+        sh[j * SUM_THREADS + threadIdx.x] += sh[j * SUM_THREADS + threadIdx.x + st];
+    __syncthreads();
+  }
+  for (int j = 0; j < 6; j++) v[j] = sh[j * SUM_THREADS];
+}
+
+__global__ void __launch_bounds__(SUM_THREADS)
+sums_pass1(const double* __restrict__ cur, const double* __restrict__ prev, int64_t n,
+           double* __restrict__ partial) {
+  __shared__ double sh[6 * SUM_THREADS];
+  double v[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t k = blockIdx.x * (int64_t)SUM_THREADS + threadIdx.x; k < n;
+       k += (int64_t)SUM_BLOCKS * SUM_THREADS) {
+    const double c = cur[k], p = cur[n + k], ux = cur[2 * n + k], uy = cur[3 * n + k],
+                 T = cur[4 * n + k];
+    v[0] += c;
+    v[1] += p;
+    v[2] += T;
+    if (prev) {
+      const double dx = ux - prev[2 * n + k], dy = uy - prev[3 * n + k];
+      v[3] += dx * dx + dy * dy;
+    }
+    v[4] += ux * ux + uy * uy;
+    v[5] += (double)(!isfinite(c)) + (double)(!isfinite(p)) + (double)(!isfinite(ux)) +
+            (double)(!isfinite(uy)) + (double)(!isfinite(T));
+  }
+  block_sum6(v, sh);
+  if (threadIdx.x == 0)
+    for (int j = 0; j < 6; j++) partial[blockIdx.x * 6 + j] = v[j];
+}
+
+__global__ void __launch_bounds__(SUM_THREADS)
+sums_pass2(const double* __restrict__ partial, double* __restrict__ out) {
+  __shared__ double sh[6 * SUM_THREADS];
+  double v[6] = {0, 0, 0, 0, 0, 0};
+  for (int b = threadIdx.x; b < SUM_BLOCKS; b += SUM_THREADS)
+    for (int j = 0; j < 6; j++) v[j] += partial[b * 6 + j];
+  block_sum6(v, sh);
+  if (threadIdx.x == 0)
+    for (int j = 0; j < 6; j++) out[j] = v[j];
+}
+
+cudaError_t launch_sums(const double* cur, const double* prev, int64_t n, double* partial,
+                        double* out, cudaStream_t s) {
+  sums_pass1<<<SUM_BLOCKS, SUM_THREADS, 0, s>>>(cur, prev, n, partial);
+  sums_pass2<<<1, SUM_THREADS, 0, s>>>(partial, out);
+  return cudaGetLastError();
+}
+
+__global__ void f64_to_f32_kernel(const double* __restrict__ in, float* __restrict__ out,
+                                  int64_t n) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    out[k] = (float)in[k];
+}
+cudaError_t launch_f64_to_f32(const double* in, float* out, int64_t n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int grid = (int)((n + 255) / 256 < 65535 ? (n + 255) / 256 : 65535);
+  f64_to_f32_kernel<<<grid, 256, 0, s>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+}  // namespace lbe

@@ -1,0 +1,134 @@
+// Device-side definitions shared by the CUDA translation units of liblbe:
+// the D2Q9 velocity set, the per-instance descriptor and the population
+// storage codecs.
+//
+// Population layout (one "arena" per instance and buffer): planes of
+// ny rows x pitch elements, x fastest, pitch a multiple of 64 elements so
+// that every row starts on a 128-byte boundary for every element size.
+//   F64 / F32 : 27 planes, plane (k, i) at index k*9 + i (k = 0 f, 1 g, 2 hbar)
+//   F16DEV / BF16DEV : 26 planes of 16-bit deviations in the order
+//               f_0..f_8, g_1..g_8, hbar_0..hbar_8, then one FP32 plane
+//               holding g_0 at byte offset g0_off.
+// A buffer holds the post-collision populations of the previous step; the
+// step kernel pulls P_i(x) = P*_i(x - xi_i) (with the wall rules) when it
+// loads, so the two buffers ping-pong between steps.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace lbe {
+
+// D2Q9: 0 (0,0), 1 (1,0), 2 (0,1), 3 (-1,0), 4 (0,-1), 5 (1,1), 6 (-1,1),
+// 7 (-1,-1), 8 (1,-1).  constexpr so that unrolled loops fold them.
+__host__ __device__ constexpr int EX(int i) {
+  return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int EY(int i) {
+  return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+__host__ __device__ constexpr int OPP(int i) {
+  return i == 0 ? 0 : i == 1 ? 3 : i == 2 ? 4 : i == 3 ? 1 : i == 4 ? 2
+       : i == 5 ? 7 : i == 6 ? 8 : i == 7 ? 5 : 6;
+}
+// lattice weights (not listed in the paper; the standard D2Q9 set, c_s^2 = 1/3)
+template <class C>
+__host__ __device__ constexpr C WGT(int i) {
+  return i == 0 ? C(4) / C(9) : (i < 5 ? C(1) / C(9) : C(1) / C(36));
+}
+
+enum Storage { ST_F64 = 0, ST_F32 = 1, ST_F16DEV = 2, ST_BF16DEV = 3 };
+
+// Per-instance descriptor, built on the host, read by the kernels.
+struct InstDev {
+  int32_t nx, ny, pitch, tiles_x;
+  int32_t tiles_y, storage;
+  int64_t tile_begin;   // first global tile index of this instance
+  uint64_t plane_bytes; // bytes between consecutive planes
+  uint64_t g0_off;      // byte offset of the FP32 g_0 plane (deviation forms)
+  char* buf[2];         // population arenas (ping-pong)
+  const double* Tbot;   // [nx] wall temperature at y = -1/2
+  const double* Ttop;   // [nx] wall temperature at y = ny - 1/2
+  // physical constants (derived on the host in double)
+  double rho, inv_rho, rho_cv, inv_rho_cv;
+  double eta1, deta, lam1, dlam;
+  double sigma0, sigmaT, Tref;
+  double eps2, ea, beta2;  // eps^2, eps*alpha, 2 beta
+  double omega_g, Gm3;     // 1/tau_g, Gamma/c_s^2
+  double Fbx, Fby;         // rho a
+  double eta_n2;
+  // deviation codec: q = s_k (P - w_i r_k(y)), r_h(y) = rho c_v (hr0 + hr1 y)
+  float s[3], inv_s[3];
+  double hr0, hr1;
+};
+
+// ------------------------------------------------------------ storage codecs
+// ld / st take (k, i) as template-folded constants through the unrolled loops.
+
+struct StF64 {
+  using C = double;
+  static constexpr int kind = ST_F64;
+  __device__ static __forceinline__ C ld(const InstDev& I, const char* b, int k, int i,
+                                         size_t idx, C /*ref*/) {
+    return __ldg(reinterpret_cast<const double*>(b + (size_t)(k * 9 + i) * I.plane_bytes) + idx);
+  }
+  __device__ static __forceinline__ void st(const InstDev& I, char* b, int k, int i, size_t idx,
+                                            C /*ref*/, C v) {
+    reinterpret_cast<double*>(b + (size_t)(k * 9 + i) * I.plane_bytes)[idx] = v;
+  }
+};
+
+struct StF32 {
+  using C = float;
+  static constexpr int kind = ST_F32;
+  __device__ static __forceinline__ C ld(const InstDev& I, const char* b, int k, int i,
+                                         size_t idx, C /*ref*/) {
+    return __ldg(reinterpret_cast<const float*>(b + (size_t)(k * 9 + i) * I.plane_bytes) + idx);
+  }
+  __device__ static __forceinline__ void st(const InstDev& I, char* b, int k, int i, size_t idx,
+                                            C /*ref*/, C v) {
+    reinterpret_cast<float*>(b + (size_t)(k * 9 + i) * I.plane_bytes)[idx] = v;
+  }
+};
+
+__host__ __device__ constexpr int dev_plane(int k, int i) {
+  return k == 0 ? i : (k == 1 ? 8 + i : 17 + i);
+}
+
+template <class E, int KIND>
+struct StDev {
+  using C = float;
+  static constexpr int kind = KIND;
+  __device__ static __forceinline__ float cvt(__half q) { return __half2float(q); }
+  __device__ static __forceinline__ float cvt(__nv_bfloat16 q) { return __bfloat162float(q); }
+  __device__ static __forceinline__ void put(__half* p, float v) { *p = __float2half_rn(v); }
+  __device__ static __forceinline__ void put(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+  // ref: the reference r_k(y) of lattice k at this row (only used for k = 2)
+  __device__ static __forceinline__ C ld(const InstDev& I, const char* b, int k, int i,
+                                         size_t idx, C ref) {
+    if (k == 1 && i == 0)
+      return __ldg(reinterpret_cast<const float*>(b + I.g0_off) + idx);
+    const E* p = reinterpret_cast<const E*>(b + (size_t)dev_plane(k, i) * I.plane_bytes) + idx;
+    float q = cvt(*p);
+    float v = q * I.inv_s[k];
+    if (k == 2) v = fmaf(WGT<float>(i), ref, v);
+    return v;
+  }
+  __device__ static __forceinline__ void st(const InstDev& I, char* b, int k, int i, size_t idx,
+                                            C ref, C v) {
+    if (k == 1 && i == 0) {
+      reinterpret_cast<float*>(b + I.g0_off)[idx] = v;
+      return;
+    }
+    if (k == 2) v = fmaf(-WGT<float>(i), ref, v);
+    put(reinterpret_cast<E*>(b + (size_t)dev_plane(k, i) * I.plane_bytes) + idx, v * I.s[k]);
+  }
+};
+
+using StF16 = StDev<__half, ST_F16DEV>;
+using StBF16 = StDev<__nv_bfloat16, ST_BF16DEV>;
+
+}  // namespace lbe

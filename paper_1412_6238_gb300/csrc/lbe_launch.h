@@ -1,0 +1,69 @@
+// Internal interface between the host API and the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbe_common.cuh"
+
+namespace lbe {
+
+struct TileShape {
+  int tx, ty;
+};
+constexpr int NUM_TILES = 5;
+constexpr TileShape TILE_SHAPES[NUM_TILES] = {{32, 8}, {64, 4}, {32, 16}, {64, 8}, {128, 4}};
+
+// Does the step kernel of this storage exist for this tile shape?
+bool tile_available(int storage, int tile);
+
+// One step of every instance in d_inst[0..n_inst): persistent grid of `grid`
+// CTAs over total_tiles tiles; reads buf[parity], writes buf[parity ^ 1].
+cudaError_t launch_step(int storage, int tile, const InstDev* d_inst, int n_inst,
+                        int64_t total_tiles, int parity, int grid, cudaStream_t s);
+
+// Resident CTAs per SM of the step kernel (0 if unavailable).
+int step_occupancy(int storage, int tile);
+
+// Fields c, p, ux, uy, T of one instance (d_one, tiles of shape 0, whose
+// tile_begin must be 0) into out[5][ny][nx] (double).
+cudaError_t launch_fields(int storage, const InstDev* d_one, int64_t tiles, int parity,
+                          double* out, cudaStream_t s);
+
+// Per-storage entry points (defined in lbe_step_<storage>.cu).
+cudaError_t launch_step_f64(int tile, const InstDev* d, int n, int64_t total, int parity,
+                            int grid, cudaStream_t s);
+cudaError_t launch_step_f32(int tile, const InstDev* d, int n, int64_t total, int parity,
+                            int grid, cudaStream_t s);
+cudaError_t launch_step_f16(int tile, const InstDev* d, int n, int64_t total, int parity,
+                            int grid, cudaStream_t s);
+cudaError_t launch_step_bf16(int tile, const InstDev* d, int n, int64_t total, int parity,
+                             int grid, cudaStream_t s);
+int occupancy_f64(int tile);
+int occupancy_f32(int tile);
+int occupancy_f16(int tile);
+int occupancy_bf16(int tile);
+cudaError_t fields_f64(const InstDev* d, int64_t tiles, int parity, double* out, cudaStream_t s);
+cudaError_t fields_f32(const InstDev* d, int64_t tiles, int parity, double* out, cudaStream_t s);
+cudaError_t fields_f16(const InstDev* d, int64_t tiles, int parity, double* out, cudaStream_t s);
+cudaError_t fields_bf16(const InstDev* d, int64_t tiles, int parity, double* out, cudaStream_t s);
+
+// Auxiliary kernels (lbe_aux.cu).
+// Pre-collision state at rest from c0, T0 (device, [ny][nx]) into pre[27][ny][nx].
+cudaError_t launch_init_state(const InstDev* d_one, int nx, int ny, const double* c0,
+                              const double* T0, double* pre, cudaStream_t s);
+// pre[27][ny][nx] (double, pre-collision) -> buf[parity] (inverse of the pull).
+cudaError_t launch_push(int storage, const InstDev* d_one, int nx, int ny, const double* pre,
+                        int parity, cudaStream_t s);
+// buf[parity] -> pre[27][ny][nx] (the pull).
+cudaError_t launch_pull(int storage, const InstDev* d_one, int nx, int ny, double* pre,
+                        int parity, cudaStream_t s);
+// FP64 sums over cur[5][n] and prev[5][n] (or prev = nullptr): out[6] =
+// sum c, sum p, sum T, sum |u - u_prev|^2, sum |u|^2, non-finite count.
+// partial must hold 6 * sums_blocks() doubles.
+int sums_blocks();
+cudaError_t launch_sums(const double* cur, const double* prev, int64_t n, double* partial,
+                        double* out, cudaStream_t s);
+cudaError_t launch_f64_to_f32(const double* in, float* out, int64_t n, cudaStream_t s);
+
+}  // namespace lbe

@@ -1,0 +1,5 @@
+// Step and field-export kernels with StF16 population storage.
+#define LBE_ST ::lbe::StF16
+#define LBE_SUFFIX f16
+#define LBE_ALL_TILES 1
+#include "lbe_step_inst.cuh"

@@ -1,0 +1,5 @@
+// Step and field-export kernels with StF32 population storage.
+#define LBE_ST ::lbe::StF32
+#define LBE_SUFFIX f32
+#define LBE_ALL_TILES 1
+#include "lbe_step_inst.cuh"

@@ -1,0 +1,5 @@
+// Step and field-export kernels with StF64 population storage.
+#define LBE_ST ::lbe::StF64
+#define LBE_SUFFIX f64
+#define LBE_ALL_TILES 0
+#include "lbe_step_inst.cuh"

@@ -1,0 +1,66 @@
+// Instantiation of the step / field kernels for one storage type.  Included
+// by lbe_step_<storage>.cu with LBE_ST (policy), LBE_SUFFIX and LBE_ALL_TILES
+// defined.
+#include "lbe_launch.h"
+#include "lbe_tile.cuh"
+
+#define LBE_CAT2(a, b) a##b
+#define LBE_CAT(a, b) LBE_CAT2(a, b)
+
+namespace lbe {
+
+namespace {
+template <int TX, int TY>
+cudaError_t launch_one(const InstDev* d, int n, int64_t total, int parity, int grid,
+                       cudaStream_t s) {
+  if (grid <= 0) grid = 1;
+  if ((int64_t)grid > total) grid = (int)total;
+  tile_kernel<LBE_ST, TX, TY, 0><<<grid, TX * TY, 0, s>>>(d, n, total, parity, nullptr);
+  return cudaGetLastError();
+}
+template <int TX, int TY>
+int occ_one() {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, tile_kernel<LBE_ST, TX, TY, 0>, TX * TY,
+                                                    0) != cudaSuccess)
+    return 0;
+  return b;
+}
+}  // namespace
+
+cudaError_t LBE_CAT(launch_step_, LBE_SUFFIX)(int tile, const InstDev* d, int n, int64_t total,
+                                               int parity, int grid, cudaStream_t s) {
+  switch (tile) {
+    case 0: return launch_one<32, 8>(d, n, total, parity, grid, s);
+#if LBE_ALL_TILES
+    case 1: return launch_one<64, 4>(d, n, total, parity, grid, s);
+    case 2: return launch_one<32, 16>(d, n, total, parity, grid, s);
+    case 3: return launch_one<64, 8>(d, n, total, parity, grid, s);
+    case 4: return launch_one<128, 4>(d, n, total, parity, grid, s);
+#endif
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int LBE_CAT(occupancy_, LBE_SUFFIX)(int tile) {
+  switch (tile) {
+    case 0: return occ_one<32, 8>();
+#if LBE_ALL_TILES
+    case 1: return occ_one<64, 4>();
+    case 2: return occ_one<32, 16>();
+    case 3: return occ_one<64, 8>();
+    case 4: return occ_one<128, 4>();
+#endif
+    default: return 0;
+  }
+}
+
+cudaError_t LBE_CAT(fields_, LBE_SUFFIX)(const InstDev* d, int64_t tiles, int parity, double* out,
+                                          cudaStream_t s) {
+  if (tiles <= 0) return cudaSuccess;
+  const unsigned grid = (unsigned)(tiles < 2147483647 ? tiles : 2147483647);
+  tile_kernel<LBE_ST, 32, 8, 1><<<grid, 256, 0, s>>>(d, 1, tiles, parity, out);
+  return cudaGetLastError();
+}
+
+}  // namespace lbe

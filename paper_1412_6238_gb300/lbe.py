@@ -1,0 +1,251 @@
+"""ctypes binding of the C ABI in include/lbe.h (argument marshalling only).
+
+Every step of the method runs in the CUDA kernels of ``liblbe.so``; this
+module converts arguments, owns the handle, and hands torch tensors to the
+library as output buffers.  There is no CPU fallback: if the library cannot
+be built or loaded, or CUDA is unavailable, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+STORAGE = {"f64": 0, "f32": 1, "f16dev": 2, "bf16dev": 3}
+FIELD_NAMES = ("c", "p", "ux", "uy", "T")
+STATUS = {0: "LBE_OK", -1: "LBE_EINVAL", -2: "LBE_ENOMEM", -3: "LBE_ECUDA", -4: "LBE_ENAN",
+          -5: "LBE_ETIMEOUT", -6: "LBE_ESTATE"}
+PARAM_KEYS = ("rho", "cv", "eta1", "eta2", "lam1", "lam2", "sigma0", "sigmaT", "Tref", "eps",
+              "beta", "tau_g", "mobility", "ax", "ay", "eta_n")
+
+# Symbols declared in include/lbe.h (checked by the tests against the header).
+EXPORTS = ("lbe_abi_version", "lbe_init", "lbe_init_batch", "lbe_step", "lbe_synchronize",
+           "lbe_fields", "lbe_sums", "lbe_get_state", "lbe_set_state", "lbe_save", "lbe_load",
+           "lbe_num_tiles", "lbe_tile_shape", "lbe_set_tile", "lbe_steps_done", "lbe_stream",
+           "lbe_num_instances", "lbe_state_bytes", "lbe_destroy", "lbe_last_error")
+
+
+class LBEError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("%s (%d): %s" % (STATUS.get(status, "?"), status, message))
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("storage", ctypes.c_int32),
+                ("check_every", ctypes.c_int32)] + [(k, ctypes.c_double) for k in PARAM_KEYS]
+
+
+class InitFields(ctypes.Structure):
+    _fields_ = [("c0", ctypes.POINTER(ctypes.c_double)), ("T0", ctypes.POINTER(ctypes.c_double)),
+                ("Tbot", ctypes.POINTER(ctypes.c_double)),
+                ("Ttop", ctypes.POINTER(ctypes.c_double))]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library(build: bool = True) -> ctypes.CDLL:
+    """Load liblbe.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build else _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError("liblbe.so is missing (%s)" % path)
+            L = ctypes.CDLL(path)
+            H = ctypes.c_void_p
+            st = ctypes.c_int
+            dp = ctypes.POINTER(ctypes.c_double)
+            sig = {
+                "lbe_abi_version": ([], ctypes.c_int32),
+                "lbe_init": ([ctypes.POINTER(Params), ctypes.POINTER(InitFields), ctypes.c_void_p,
+                              ctypes.POINTER(H)], st),
+                "lbe_init_batch": ([ctypes.c_int32, ctypes.POINTER(Params),
+                                    ctypes.POINTER(InitFields), ctypes.c_void_p,
+                                    ctypes.POINTER(H)], st),
+                "lbe_step": ([H, ctypes.c_int64], st),
+                "lbe_synchronize": ([H], st),
+                "lbe_fields": ([H, ctypes.c_int32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p),
+                                ctypes.c_int32, ctypes.c_int32], st),
+                "lbe_sums": ([H, ctypes.c_int32, dp], st),
+                "lbe_get_state": ([H, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32], st),
+                "lbe_set_state": ([H, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32], st),
+                "lbe_save": ([H, ctypes.c_char_p], st),
+                "lbe_load": ([H, ctypes.c_char_p], st),
+                "lbe_num_tiles": ([], ctypes.c_int32),
+                "lbe_tile_shape": ([ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                    ctypes.POINTER(ctypes.c_int32)], st),
+                "lbe_set_tile": ([H, ctypes.c_int32, ctypes.c_int32], st),
+                "lbe_steps_done": ([H], ctypes.c_int64),
+                "lbe_stream": ([H], ctypes.c_void_p),
+                "lbe_num_instances": ([H], ctypes.c_int32),
+                "lbe_state_bytes": ([H], ctypes.c_int64),
+                "lbe_destroy": ([H], None),
+                "lbe_last_error": ([H], ctypes.c_char_p),
+            }
+            for name, (args, res) in sig.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def tile_shapes():
+    L = library()
+    out = []
+    for t in range(L.lbe_num_tiles()):
+        tx, ty = ctypes.c_int32(), ctypes.c_int32()
+        L.lbe_tile_shape(t, ctypes.byref(tx), ctypes.byref(ty))
+        out.append((tx.value, ty.value))
+    return out
+
+
+def _f64(a, shape):
+    a = np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64), shape))
+    return a
+
+
+def make_params(params: dict, storage: str | int, check_every: int = 0) -> Params:
+    p = Params()
+    p.nx, p.ny = int(params["nx"]), int(params["ny"])
+    p.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    p.check_every = int(check_every)
+    for k in PARAM_KEYS:
+        setattr(p, k, float(params[k]))
+    return p
+
+
+class LBE:
+    """One handle of the library: one instance, or a batch advanced together.
+
+    ``problems``: a workload (object with ``params``, ``c0``, ``T0``,
+    ``Tbot``, ``Ttop``) or a list of them.  ``stream``: a torch CUDA stream
+    (default: a new non-default stream, so that steps can be graph-captured).
+    """
+
+    def __init__(self, problems, storage: str = "f32", stream=None, check_every: int = 0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("CUDA is not available: the LBE step runs only on the GPU")
+        self._L = library()
+        probs = list(problems) if isinstance(problems, (list, tuple)) else [problems]
+        self.n = len(probs)
+        self.shapes = [(int(w.params["ny"]), int(w.params["nx"])) for w in probs]
+        self.storage = storage
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        params = (Params * self.n)()
+        inits = (InitFields * self.n)()
+        keep = []
+        for j, w in enumerate(probs):
+            ny, nx = self.shapes[j]
+            params[j] = make_params(w.params, storage, check_every)
+            arrs = [_f64(w.c0, (ny, nx)), _f64(w.T0, (ny, nx)), _f64(w.Tbot, (nx,)),
+                    _f64(w.Ttop, (nx,))]
+            keep.append(arrs)
+            dp = ctypes.POINTER(ctypes.c_double)
+            inits[j] = InitFields(*[a.ctypes.data_as(dp) for a in arrs])
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.stream.device):
+            st = self._L.lbe_init_batch(self.n, params, inits,
+                                        ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if st != 0:
+            raise LBEError(st, self._L.lbe_last_error(None).decode())
+        self._h = h
+
+    # ------------------------------------------------------------------ helpers
+    def _check(self, st):
+        if st != 0:
+            raise LBEError(st, self._L.lbe_last_error(self._h).decode())
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.lbe_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- the API
+    def step(self, n: int = 1):
+        self._check(self._L.lbe_step(self._h, int(n)))
+
+    def synchronize(self):
+        self._check(self._L.lbe_synchronize(self._h))
+
+    @property
+    def steps_done(self) -> int:
+        return int(self._L.lbe_steps_done(self._h))
+
+    @property
+    def state_bytes(self) -> int:
+        return int(self._L.lbe_state_bytes(self._h))
+
+    def set_tile(self, tile: int, grid_ctas: int = 0):
+        self._check(self._L.lbe_set_tile(self._h, int(tile), int(grid_ctas)))
+
+    def fields(self, instance: int = 0, names=FIELD_NAMES, dtype=None, device="cuda"):
+        """Dict of torch tensors (ny, nx) for the requested fields."""
+        import torch
+        dtype = torch.float64 if dtype is None else dtype
+        ny, nx = self.shapes[instance]
+        dev = torch.device(device)
+        on_dev = dev.type == "cuda"
+        out = {}
+        ptrs = (ctypes.c_void_p * 5)()
+        mask = 0
+        for k, name in enumerate(FIELD_NAMES):
+            if name in names:
+                t = torch.empty((ny, nx), dtype=dtype, device=dev,
+                                pin_memory=False)
+                out[name] = t
+                ptrs[k] = t.data_ptr()
+                mask |= 1 << k
+        self._check(self._L.lbe_fields(self._h, int(instance), mask, ptrs, int(on_dev),
+                                       0 if dtype == torch.float64 else 1))
+        return out
+
+    def sums(self, instance: int = 0) -> dict:
+        out = (ctypes.c_double * 5)()
+        self._check(self._L.lbe_sums(self._h, int(instance), out))
+        return dict(sum_c=out[0], sum_p=out[1], sum_h=out[2], residual=out[3],
+                    nonfinite=int(out[4]))
+
+    def get_state(self, instance: int = 0, device="cpu"):
+        import torch
+        ny, nx = self.shapes[instance]
+        t = torch.empty((27, ny, nx), dtype=torch.float64, device=device)
+        self._check(self._L.lbe_get_state(self._h, int(instance), ctypes.c_void_p(t.data_ptr()),
+                                          int(t.is_cuda)))
+        return t
+
+    def set_state(self, state, instance: int = 0):
+        import torch
+        ny, nx = self.shapes[instance]
+        if not torch.is_tensor(state):
+            state = torch.from_numpy(np.ascontiguousarray(np.asarray(state, dtype=np.float64)))
+        state = state.to(torch.float64).contiguous()
+        if tuple(state.shape) != (27, ny, nx):
+            raise ValueError("state must have shape (27, %d, %d)" % (ny, nx))
+        self._check(self._L.lbe_set_state(self._h, int(instance),
+                                          ctypes.c_void_p(state.data_ptr()),
+                                          int(state.is_cuda)))
+
+    def save(self, path: str):
+        self._check(self._L.lbe_save(self._h, os.fsencode(path)))
+
+    def load(self, path: str):
+        self._check(self._L.lbe_load(self._h, os.fsencode(path)))

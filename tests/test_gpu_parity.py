@@ -1,0 +1,239 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle on
+the same seeded inputs.
+
+Bounds (relative L2 over the domain, velocity as a vector):
+  FP64 storage  1e-12     FP32 storage  1e-5 (u, T)
+  FP16-deviation storage  1e-3 (u, T)   BF16-deviation: measured, 2e-2
+"""
+import numpy as np
+import pytest
+
+from paper_1412_6238_gb300 import workloads as wl
+
+from helpers import field_errors, gpu_fields, oracle_fields, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5, "f16dev": 1e-3, "bf16dev": 2e-2}
+STATE_TOL = {"f64": 1e-15, "f32": 1e-7, "f16dev": 1e-3, "bf16dev": 1e-2}
+
+
+@pytest.fixture(scope="module")
+def LBE():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1412_6238_gb300.lbe import LBE
+    return LBE
+
+
+def small_drop(nx=70, ny=45, R=9.0, steps=0, eta_r=0.5, lam_r=2.0):
+    return wl.droplet(nx, ny, R, nx / 2.0 + 3.3, ny / 2.0 - 1.7, Re=1.0, Ma=10.0, Ca=0.05,
+                      eta_m=0.2, eta_r=eta_r, lam_r=lam_r, steps=steps)
+
+
+def state_err(a, b):
+    """Max abs difference per lattice relative to the lattice's max magnitude."""
+    out = []
+    for k in range(3):
+        s = np.abs(b[9 * k:9 * k + 9]).max()
+        out.append(np.abs(a[9 * k:9 * k + 9] - b[9 * k:9 * k + 9]).max() / max(s, 1e-300))
+    return max(out)
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16dev", "bf16dev"])
+def test_initial_state_matches_oracle(LBE, orc, storage):
+    w = small_drop()
+    sim = LBE(w, storage=storage)
+    got = sim.get_state().numpy()
+    ref = orc.init(w.params, w.c0, w.T0, w.Tbot, w.Ttop)
+    assert state_err(got, ref) < STATE_TOL[storage]
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_state_roundtrip(LBE, orc, storage):
+    w = small_drop()
+    sim = LBE(w, storage=storage)
+    ref = orc.run(w.params, orc.init(w.params, w.c0, w.T0, w.Tbot, w.Ttop), w.Tbot, w.Ttop, 5)
+    sim.set_state(ref)
+    got = sim.get_state().numpy()
+    if storage == "f64":
+        assert np.array_equal(got, ref)
+    else:
+        assert np.abs(got - ref.astype(np.float32).astype(np.float64)).max() == 0
+
+
+SHAPES = [(5, 7), (4, 8), (1, 6), (2, 3), (33, 9), (100, 37), (96, 64), (130, 19)]
+
+
+@pytest.mark.parametrize("nx,ny", SHAPES)
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_one_step_from_same_state(LBE, orc, storage, nx, ny):
+    """Odd, tiny and ragged grids (several tiles plus a partial one): one
+    GPU step from the oracle's state equals one oracle step."""
+    R = max(1.5, min(nx, ny) / 4.0)
+    w = wl.droplet(nx, ny, R, nx / 2.0 + 0.3, ny / 2.0 - 0.2, Re=1.0, Ma=10.0, Ca=0.05,
+                   eta_m=0.2, eta_r=0.5, lam_r=2.0)
+    w.params["ax"] = 1e-6
+    pop0 = orc.run(w.params, orc.init(w.params, w.c0, w.T0, w.Tbot, w.Ttop), w.Tbot, w.Ttop, 3)
+    sim = LBE(w, storage=storage)
+    sim.set_state(pop0)
+    if storage == "f32":
+        pop0 = sim.get_state().numpy()  # the state the GPU actually holds
+    sim.step(1)
+    got = sim.get_state().numpy()
+    ref = orc.run(w.params, pop0, w.Tbot, w.Ttop, 1)
+    tol = 1e-14 if storage == "f64" else 2e-6
+    assert state_err(got, ref) < tol
+
+
+@pytest.mark.parametrize("tile", [0, 1, 2, 3, 4])
+def test_tile_shapes_bitwise_identical(LBE, tile):
+    """Every tile shape (and a persistent or one-CTA-per-tile grid) computes
+    the same per-cell arithmetic: results are bitwise equal."""
+    w = small_drop(150, 77)
+    a = LBE(w, storage="f32")
+    a.step(7)
+    b = LBE(w, storage="f32")
+    b.set_tile(tile, -1 if tile % 2 else 0)
+    b.step(7)
+    assert np.array_equal(a.get_state().numpy(), b.get_state().numpy())
+
+
+def test_graph_replay_equals_single_launches(LBE):
+    w = small_drop()
+    a = LBE(w, storage="f32")
+    a.step(10)  # graph replays
+    b = LBE(w, storage="f32")
+    for _ in range(10):
+        b.step(1)  # odd/even single launches
+    assert np.array_equal(a.get_state().numpy(), b.get_state().numpy())
+    assert a.steps_done == b.steps_done == 10
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16dev", "bf16dev"])
+def test_droplet_run_parity(LBE, orc, storage):
+    """300 steps of a migrating drop (viscosity ratio 0.5, conductivity ratio
+    2) on a 70 x 45 grid: fields within the storage's bound."""
+    w = small_drop()
+    n = 300
+    sim = LBE(w, storage=storage)
+    sim.step(n)
+    F = gpu_fields(sim)
+    G = oracle_fields(orc, w, orc.run(w.params, orc.init(w.params, w.c0, w.T0, w.Tbot, w.Ttop),
+                                      w.Tbot, w.Ttop, n))
+    e = field_errors(F, G)
+    tol = TOL[storage]
+    assert e["u"] < tol and e["T"] < tol and e["c"] < tol, e
+
+
+def test_layered_poiseuille_f64_full_run(LBE, orc):
+    """4 x 101 two-layer thermal Poiseuille flow in FP64, 20000 steps."""
+    w = wl.layered_poiseuille()
+    sim = LBE(w, storage="f64")
+    sim.step(w.steps)
+    F = gpu_fields(sim)
+    G = oracle_fields(orc, w, orc.run(w.params, orc.init(w.params, w.c0, w.T0, w.Tbot, w.Ttop),
+                                      w.Tbot, w.Ttop, w.steps))
+    e = field_errors(F, G)
+    assert max(e.values()) < 1e-12, e
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_planar_marangoni_parity(LBE, orc, storage):
+    """The 512 x 256 planar Marangoni problem, 1000 steps."""
+    w = wl.planar_marangoni()
+    n = 1000
+    sim = LBE(w, storage=storage)
+    sim.step(n)
+    F = gpu_fields(sim)
+    G = oracle_fields(orc, w, orc.run(w.params, orc.init(w.params, w.c0, w.T0, w.Tbot, w.Ttop),
+                                      w.Tbot, w.Ttop, n))
+    e = field_errors(F, G)
+    assert e["u"] < TOL[storage] and e["T"] < TOL[storage], e
+
+
+def test_fields_f32_and_device_outputs(LBE, orc):
+    import torch
+    w = small_drop()
+    sim = LBE(w, storage="f64")
+    sim.step(20)
+    F64 = sim.fields(device="cpu")
+    F32 = sim.fields(dtype=torch.float32, device="cpu")
+    Fd = sim.fields(device="cuda")
+    for k in F64:
+        assert torch.equal(F64[k].float(), F32[k])
+        assert torch.equal(F64[k], Fd[k].cpu())
+    part = sim.fields(names=("T",), device="cpu")
+    assert list(part) == ["T"] and torch.equal(part["T"], F64["T"])
+
+
+def test_sums_mass_conservation_and_residual(LBE, orc):
+    w = small_drop()
+    sim = LBE(w, storage="f64")
+    s0 = sim.sums()
+    assert s0["residual"] == 0.0 and s0["nonfinite"] == 0
+    sim.step(50)
+    s1 = sim.sums()
+    assert abs(s1["sum_c"] - s0["sum_c"]) < 1e-12 * s0["sum_c"]
+    assert abs(s1["sum_c"] - w.c0.sum()) < 1e-11 * w.c0.sum()
+    pop49 = orc.run(w.params, orc.init(w.params, w.c0, w.T0, w.Tbot, w.Ttop), w.Tbot, w.Ttop, 49)
+    pop50 = orc.run(w.params, pop49, w.Tbot, w.Ttop, 1)
+    A = oracle_fields(orc, w, pop49)
+    B = oracle_fields(orc, w, pop50)
+    du = np.sqrt(((B["ux"] - A["ux"]) ** 2 + (B["uy"] - A["uy"]) ** 2).sum())
+    un = np.sqrt((B["ux"] ** 2 + B["uy"] ** 2).sum())
+    assert s1["residual"] == pytest.approx(du / un, rel=1e-9)
+    assert s1["sum_h"] == pytest.approx(pop50[18:27].sum(), rel=1e-13)
+
+
+def test_nan_detection_and_recovery(LBE, orc):
+    w = small_drop()
+    sim = LBE(w, storage="f32", check_every=5)
+    sim.step(10)
+    st = sim.get_state().numpy().copy()
+    st[20, 10, 10] = np.nan  # planted on the host
+    sim.set_state(st)
+    from paper_1412_6238_gb300.lbe import LBEError
+    with pytest.raises(LBEError) as ei:
+        sim.step(10)
+    assert ei.value.status == -4
+    with pytest.raises(LBEError) as ei2:
+        sim.step(1)
+    assert ei2.value.status == -6
+    good = orc.init(w.params, w.c0, w.T0, w.Tbot, w.Ttop)
+    sim.set_state(good)
+    sim.step(5)
+    assert sim.sums()["nonfinite"] == 0
+
+
+def test_checkpoint_roundtrip(LBE, tmp_path):
+    w = small_drop()
+    a = LBE(w, storage="f32")
+    a.step(13)
+    path = str(tmp_path / "ck.bin")
+    a.save(path)
+    ref = a.get_state().numpy()
+    a.step(5)
+    after = a.get_state().numpy()
+    b = LBE(w, storage="f32")
+    b.load(path)
+    assert b.steps_done == 13
+    assert np.array_equal(b.get_state().numpy(), ref)
+    b.step(5)
+    assert np.array_equal(b.get_state().numpy(), after)
+
+
+def test_batch_of_uneven_instances_matches_each_alone(LBE, orc):
+    """Instances of different sizes and parameters advanced by one persistent
+    launch per step equal the oracle run of each alone."""
+    ws = wl.batch_sweep(n=5, seed=3, grids=((40, 80), (24, 48), (64, 128)))
+    n = 60
+    sim = LBE(ws, storage="f64")
+    sim.step(n)
+    for j, w in enumerate(ws):
+        F = gpu_fields(sim, j)
+        G = oracle_fields(orc, w, orc.run(w.params, orc.init(w.params, w.c0, w.T0, w.Tbot,
+                                                              w.Ttop), w.Tbot, w.Ttop, n))
+        e = field_errors(F, G)
+        assert max(e["u"], e["T"], e["c"]) < 1e-12, (j, e)
