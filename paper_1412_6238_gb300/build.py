@@ -1,7 +1,8 @@
 """Build liblbe.so (the CUDA C-ABI library) in-tree with nvcc for sm_103a.
 
-Each translation unit compiles in parallel; the FP64 step kernel is compiled
-without FMA contraction so that it rounds like the FP64 CPU reference.
+Each translation unit compiles in parallel; the FP64 step kernel and the
+state kernels are compiled without FMA contraction, so that FP64 mode rounds
+operation by operation like the FP64 CPU reference.
 """
 from __future__ import annotations
 
@@ -22,8 +23,8 @@ UNITS = {
     "lbe_step_f32.cu": [],
     "lbe_step_f16.cu": [],
     "lbe_step_bf16.cu": [],
-    "lbe_aux.cu": [],
-    "lbe_api.cu": [],
+    "lbe_aux.cu": ["-fmad=false"],
+    "lbe_api.cu": ["-Xcompiler", "-ffp-contract=off"],
 }
 
 

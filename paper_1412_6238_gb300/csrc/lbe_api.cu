@@ -154,7 +154,10 @@ void fill_desc(lbe_handle* h, int j, InstDev& D) {
   D.Ttop = H.walls + H.nx;
   D.rho = p.rho;
   D.inv_rho = 1.0 / p.rho;
+  D.cv = p.cv;
   D.rho_cv = p.rho * p.cv;
+  D.rcs2 = p.rho * (1.0 / 3.0);
+  D.rcvcs2 = (p.rho * p.cv) * (1.0 / 3.0);
   D.inv_rho_cv = 1.0 / (p.rho * p.cv);
   D.eta1 = p.eta1;
   D.deta = p.eta2 - p.eta1;
@@ -164,10 +167,10 @@ void fill_desc(lbe_handle* h, int j, InstDev& D) {
   D.sigmaT = p.sigmaT;
   D.Tref = p.Tref;
   D.eps2 = p.eps * p.eps;
-  D.ea = p.eps * 6.0 * std::sqrt(2.0);  // alpha = 6 sqrt 2 (Sec. II)
+  D.ea = p.eps * (6.0 * std::sqrt(2.0));  // alpha = 6 sqrt 2 (Sec. II)
   D.beta2 = 2.0 * p.beta;
   D.omega_g = 1.0 / p.tau_g;
-  D.Gm3 = 3.0 * p.mobility / (p.tau_g - 0.5);
+  D.Gm = p.mobility / (p.tau_g - 0.5);
   D.Fbx = p.rho * p.ax;
   D.Fby = p.rho * p.ay;
   D.eta_n2 = p.eta_n * p.eta_n;

@@ -65,16 +65,28 @@ __global__ void init_state_kernel(const InstDev* __restrict__ d, int nx, int ny,
       return c0[(int64_t)yy * nx + xx];
     };
     const double v0 = c0[k];
-    const double ax = (cat(x + 1, y) + cat(x - 1, y)) + (cat(x, y + 1) + cat(x, y - 1));
-    const double dg = (cat(x + 1, y + 1) + cat(x - 1, y + 1)) + (cat(x + 1, y - 1) + cat(x - 1, y - 1));
-    const double lap = (4.0 * ax + dg - 20.0 * v0) * (1.0 / 6.0);
+    // Laplacian (2/c_s^2) sum_i w_i (c(x + xi_i) - c(x)), terms in index order
+    const double wa = WGT<double>(1), wd = WGT<double>(5);
+    double t = wa * (cat(x + 1, y) - v0);
+    t = t + wa * (cat(x, y + 1) - v0);
+    t = t + wa * (cat(x - 1, y) - v0);
+    t = t + wa * (cat(x, y - 1) - v0);
+    t = t + wd * (cat(x + 1, y + 1) - v0);
+    t = t + wd * (cat(x - 1, y + 1) - v0);
+    t = t + wd * (cat(x - 1, y - 1) - v0);
+    t = t + wd * (cat(x + 1, y - 1) - v0);
+    const double cs2 = 1.0 / 3.0;
+    const double lap = 2.0 * t / cs2;
     const double mu = I.beta2 * v0 * (v0 - 1.0) * (2.0 * v0 - 1.0) - I.eps2 * lap;
-    const double Gmu = I.Gm3 * mu;
+    const double W0 = WGT<double>(0);
+    const double H0 = (v0 - (1.0 - W0) * I.Gm * mu / cs2) / W0;
+    const double Hi = I.Gm * mu / cs2;
+    const double rcvT = I.rho * I.cv * T0[k];
     for (int i = 0; i < 9; i++) {
       const double w = WGT<double>(i);
       pre[(int64_t)i * N + k] = 0.0;
-      pre[(int64_t)(9 + i) * N + k] = (i == 0) ? v0 - (1.0 - WGT<double>(0)) * Gmu : w * Gmu;
-      pre[(int64_t)(18 + i) * N + k] = w * I.rho_cv * T0[k];
+      pre[(int64_t)(9 + i) * N + k] = w * (i == 0 ? H0 : Hi);
+      pre[(int64_t)(18 + i) * N + k] = rcvT * w;
     }
   }
 }
@@ -121,7 +133,7 @@ __global__ void push_kernel(const InstDev* __restrict__ d, int nx, int ny,
             v = pb;
           } else {
             const double Tw = (yt < 0) ? I.Tbot[x] : I.Ttop[x];
-            v = 2.0 * WGT<double>(j) * I.rho_cv * Tw - pb;
+            v = 2.0 * WGT<double>(j) * I.rho * I.cv * Tw - pb;
           }
         }
         S::st(I, buf, kk, j, idx, ref, (C)v);

@@ -53,11 +53,12 @@ struct InstDev {
   const double* Tbot;   // [nx] wall temperature at y = -1/2
   const double* Ttop;   // [nx] wall temperature at y = ny - 1/2
   // physical constants (derived on the host in double)
-  double rho, inv_rho, rho_cv, inv_rho_cv;
+  double rho, inv_rho, cv, rho_cv, inv_rho_cv;
+  double rcs2, rcvcs2;     // rho c_s^2, rho c_v c_s^2
   double eta1, deta, lam1, dlam;
   double sigma0, sigmaT, Tref;
   double eps2, ea, beta2;  // eps^2, eps*alpha, 2 beta
-  double omega_g, Gm3;     // 1/tau_g, Gamma/c_s^2
+  double omega_g, Gm;      // 1/tau_g, Gamma = M/(tau_g - 1/2)
   double Fbx, Fby;         // rho a
   double eta_n2;
   // deviation codec: q = s_k (P - w_i r_k(y)), r_h(y) = rho c_v (hr0 + hr1 y)

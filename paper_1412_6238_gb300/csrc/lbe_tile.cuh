@@ -63,7 +63,7 @@ __device__ __forceinline__ void pull9(const InstDev& I, const char* __restrict__
   if (K == 2 && (wb || wt)) Tw = C(wb ? I.Tbot[q.x] : I.Ttop[q.x]);
   auto bb = [&](int i) -> C {
     C v = S::ld(I, src, K, OPP(i), r0 + q.x, ref0);
-    if (K == 2) return -v + C(2) * WGT<C>(i) * C(I.rho_cv) * Tw;
+    if (K == 2) return -v + C(2) * WGT<C>(i) * C(I.rho) * C(I.cv) * Tw;
     return v;
   };
   out[0] = S::ld(I, src, K, 0, r0 + q.x, ref0);
@@ -91,10 +91,24 @@ __device__ __forceinline__ void pull9(const InstDev& I, const char* __restrict__
   }
 }
 
+// Sum over i = 0..8 in index order (the order the moments of Eq. 13, Eq. 28
+// and Eq. aEq13 are accumulated in FP64 parity mode as well).
 template <class C>
 __device__ __forceinline__ C sum9(const C v[9]) {
-  return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
+  C s = v[0];
+#pragma unroll
+  for (int i = 1; i < 9; i++) s += v[i];
+  return s;
 }
+
+// a / b: a true division in FP64 (parity mode rounds like the FP64
+// reference); a product with the precomputed reciprocal in FP32.
+__device__ __forceinline__ double dv(double a, double b, double) { return a / b; }
+__device__ __forceinline__ float dv(float a, float, float inv_b) { return a * inv_b; }
+
+// c_s^2 = 1/3 of D2Q9
+template <class C>
+__device__ __forceinline__ C cs2() { return C(1.0 / 3.0); }
 
 __device__ __forceinline__ int wrapx(int gx, int nx) {
   int x = gx % nx;
@@ -136,7 +150,7 @@ __device__ __forceinline__ void region_values(const InstDev& I, const char* __re
     pull9<S, 0>(I, src, q, v);
     p = sum9(v);
     pull9<S, 2>(I, src, q, v);
-    T = sum9(v) * C(I.inv_rho_cv);
+    T = dv(sum9(v), C(I.rho_cv), C(I.inv_rho_cv));
     if (ghost != 0) {
       const C Tw = C(ghost < 0 ? I.Tbot[q.x] : I.Ttop[q.x]);
       T = C(2) * Tw - T;
@@ -147,30 +161,46 @@ __device__ __forceinline__ void region_values(const InstDev& I, const char* __re
   }
 }
 
-// Isotropic gradient (1/c_s^2) sum_i w_i xi_i phi(x + xi_i) and Laplacian
-// (2/c_s^2) sum_i w_i (phi(x + xi_i) - phi(x)) of a shared-memory array of
-// row width WD at (rx, ry).
+// Isotropic gradient (1/c_s^2) sum_{i>=1} w_i xi_i phi(x + xi_i) and Laplacian
+// (2/c_s^2) sum_{i>=1} w_i (phi(x + xi_i) - phi(x)) of a shared-memory array
+// of row width WD at (rx, ry); the terms are summed in index order
+// i = 1 (E), 2 (N), 3 (W), 4 (S), 5 (NE), 6 (NW), 7 (SW), 8 (SE), terms with
+// xi_ia = 0 being exact zeros.
 template <class C, int WD>
 __device__ __forceinline__ void grad_iso(const C* s, int rx, int ry, C& gx, C& gy) {
   const C* r0 = s + ry * WD + rx;
   const C vE = r0[1], vW = r0[-1], vN = r0[WD], vS = r0[-WD];
   const C vNE = r0[WD + 1], vNW = r0[WD - 1], vSE = r0[-WD + 1], vSW = r0[-WD - 1];
-  gx = C(1) / C(3) * (vE - vW) + C(1) / C(12) * ((vNE - vSW) + (vSE - vNW));
-  gy = C(1) / C(3) * (vN - vS) + C(1) / C(12) * ((vNE - vSW) + (vNW - vSE));
+  const C wa = WGT<C>(1), wd = WGT<C>(5);
+  C sx = wa * vE;
+  sx = sx - wa * vW;
+  sx = sx + wd * vNE;
+  sx = sx - wd * vNW;
+  sx = sx - wd * vSW;
+  sx = sx + wd * vSE;
+  C sy = wa * vN;
+  sy = sy - wa * vS;
+  sy = sy + wd * vNE;
+  sy = sy + wd * vNW;
+  sy = sy - wd * vSW;
+  sy = sy - wd * vSE;
+  gx = dv(sx, cs2<C>(), C(3));
+  gy = dv(sy, cs2<C>(), C(3));
 }
 template <class C, int WD>
 __device__ __forceinline__ C lap_iso(const C* s, int rx, int ry) {
   const C* r0 = s + ry * WD + rx;
-  const C ax = (r0[1] + r0[-1]) + (r0[WD] + r0[-WD]);
-  const C dg = (r0[WD + 1] + r0[WD - 1]) + (r0[-WD + 1] + r0[-WD - 1]);
-  return (C(4) * ax + dg - C(20) * r0[0]) * (C(1) / C(6));
-}
-
-// Gamma_i(u) of Eq. 6.
-template <class C>
-__device__ __forceinline__ C gamma_i(int i, C ux, C uy, C usq15) {
-  const C xu = C(EX(i)) * ux + C(EY(i)) * uy;
-  return WGT<C>(i) * (C(1) + C(3) * xu + C(4.5) * xu * xu - usq15);
+  const C v0 = r0[0];
+  const C wa = WGT<C>(1), wd = WGT<C>(5);
+  C t = wa * (r0[1] - v0);
+  t = t + wa * (r0[WD] - v0);
+  t = t + wa * (r0[-1] - v0);
+  t = t + wa * (r0[-WD] - v0);
+  t = t + wd * (r0[WD + 1] - v0);
+  t = t + wd * (r0[WD - 1] - v0);
+  t = t + wd * (r0[-WD - 1] - v0);
+  t = t + wd * (r0[-WD + 1] - v0);
+  return dv(C(2) * t, cs2<C>(), C(3));
 }
 
 // Tile work.  MODE 0: full step (collide and store into the other buffer).
@@ -212,7 +242,7 @@ struct Tile {
       pull9<S, 2>(I, src, q, h);
       cc = sum9(g);
       pp = sum9(f);
-      TT = sum9(h) * C(I.inv_rho_cv);
+      TT = dv(sum9(h), C(I.rho_cv), C(I.inv_rho_cv));
     } else if (gy <= ny + 1) {
       region_values<S>(I, src, gx, gy, true, cc, pp, TT);
     }
@@ -281,12 +311,25 @@ struct Tile {
       const C Fx = cap * gcx + mar * (g2 * gTx - cdT * gcx) + C(I.Fbx);
       const C Fy = cap * gcy + mar * (g2 * gTy - cdT * gcy) + C(I.Fby);
 
-      // S6
-      const C jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-      const C jy = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
+      // S6 (Eq. 13): first moments summed in index order
+      const C f0 = f[0];
+      (void)f0;
+      C jx = f[1] - f[3];
+      jx = jx + f[5];
+      jx = jx - f[6];
+      jx = jx - f[7];
+      jx = jx + f[8];
+      C jy = f[2] - f[4];
+      jy = jy + f[5];
+      jy = jy + f[6];
+      jy = jy - f[7];
+      jy = jy - f[8];
+      const C rho = C(I.rho);
       const C inv_rho = C(I.inv_rho);
-      const C ux = C(3) * jx * inv_rho + C(0.5) * Fx * inv_rho;
-      const C uy = C(3) * jy * inv_rho + C(0.5) * Fy * inv_rho;
+      const C rcs2 = C(I.rcs2);          // rho c_s^2
+      const C inv_rcs2 = C(3) * inv_rho;
+      const C ux = dv(jx, rcs2, inv_rcs2) + dv(C(0.5) * Fx, rho, inv_rho);
+      const C uy = dv(jy, rcs2, inv_rcs2) + dv(C(0.5) * Fy, rho, inv_rho);
 
       if (MODE == 1) {
         const size_t N = (size_t)nx * ny, k = (size_t)gy * nx + gx;
@@ -298,44 +341,49 @@ struct Tile {
         return;
       }
 
-      // S3
-      const C rho = C(I.rho);
+      // S3: properties, linear in c
       const C eta = C(I.eta1) + cc * C(I.deta);
       const C lam = C(I.lam1) + cc * C(I.dlam);
-      const C omega_f = C(1) / (C(3) * eta * inv_rho + C(0.5));
-      const C tau_h = C(3) * lam * C(I.inv_rho_cv);
+      const C tau_f = dv(eta, rcs2, inv_rcs2) + C(0.5);
+      const C omega_f = C(1) / tau_f;
+      const C tau_h = dv(lam, C(I.rcvcs2), C(3) * C(I.inv_rho_cv));
       const C omega_T = C(2) / (C(2) * tau_h + C(1));
       const C omega_g = C(I.omega_g);
       const C af = C(1) - C(0.5) * omega_f;
       const C ag = C(1) - C(0.5) * omega_g;
       const C aT = C(1) - C(0.5) * omega_T;
-      const C usq15 = C(1.5) * (ux * ux + uy * uy);
-      const C rcs2 = rho * (C(1) / C(3));
-      const C Gmu = C(I.Gm3) * mu;  // Gamma mu / c_s^2
+      // Gamma_i(u) = w_i (1 + xi.u/c_s^2 + ((xi.u/c_s^2)^2 - u^2/c_s^2)/2) (Eq. 6)
+      const C uu = dv(ux * ux + uy * uy, cs2<C>(), C(3));
+      const C Gm = C(I.Gm);
+      // H_i of Eq. 22
+      const C Hi = dv(Gm * mu, cs2<C>(), C(3));
+      const C H0 = dv(cc - dv((C(1) - WGT<C>(0)) * Gm * mu, cs2<C>(), C(3)), WGT<C>(0),
+                      C(9) / C(4));
       const C Gx = Fx - gpx, Gy = Fy - gpy;  // F - grad p (= Fbar, uniform rho)
-      const C sg = cc * C(3) * inv_rho;      // c / (rho c_s^2)
-      const C sh = C(3) * inv_rho;           // 1 / (rho c_s^2)
-      const C rcvT = C(I.rho_cv) * TT;
+      const C rcvT = C(I.rho) * C(I.cv) * TT;
 
       char* __restrict__ dst = I.buf[parity ^ 1];
       const size_t idx = (size_t)gy * I.pitch + gx;
       const C ref = (S::kind >= ST_F16DEV) ? href<S>(I, gy) : C(0);
 #pragma unroll
       for (int i = 0; i < 9; i++) {
-        const C G = gamma_i<C>(i, ux, uy, usq15);
+        const C W = WGT<C>(i);
+        const C xu = dv(C(EX(i)) * ux + C(EY(i)) * uy, cs2<C>(), C(3));
+        const C hq = C(0.5) * (xu * xu - uu);
+        const C G = W * (C(1) + xu + hq);
+        const C q = xu + hq;  // velocity part, without the cancelling w_i
         const C dx = C(EX(i)) - ux, dy = C(EY(i)) - uy;
-        // f (Eq. 12, Eq. 5)
-        const C feq = WGT<C>(i) * pp + rcs2 * (G - WGT<C>(i));
+        // f (Eq. 12 with Eq. 5)
+        const C feq = W * (pp + rcs2 * q);
         const C fs = (Fx * dx + Fy * dy) * G;
         const C fn = f[i] - omega_f * (f[i] - feq) + af * fs;
-        // g (Eq. 27, Eq. 21-22)
-        C geq = cc * (G - WGT<C>(i));
-        geq += (i == 0) ? cc - (C(1) - WGT<C>(0)) * Gmu : WGT<C>(i) * Gmu;
-        const C gs = sg * (dx * Gx + dy * Gy) * G;
+        // g (Eq. 27 with Eq. 21-22)
+        const C geq = W * ((i == 0 ? H0 : Hi) + cc * q);
+        const C gs = dv(cc * (dx * Gx + dy * Gy), rcs2, inv_rcs2) * G;
         const C gn = g[i] - omega_g * (g[i] - geq) + ag * gs;
-        // hbar (Eq. aEq12, Eq. aEq9)
+        // hbar (Eq. aEq12 with Eq. aEq9)
         const C heq = rcvT * G;
-        const C hs = sh * (Gx * dx + Gy * dy) * heq;
+        const C hs = dv(Gx * dx + Gy * dy, rcs2, inv_rcs2) * heq;
         const C hn = h[i] - omega_T * (h[i] - heq) + aT * hs;
         S::st(I, dst, 0, i, idx, ref, fn);
         S::st(I, dst, 1, i, idx, ref, gn);
