@@ -596,29 +596,34 @@ lbe_status lbe_set_state(lbe_handle* h, int32_t instance, const double* pops, in
   return LBE_OK;
 }
 
-// checkpoint format: "LBECKPT1", int32 n, int32 storage, int64 steps, then per
-// instance: lbe_params, Tbot[nx], Ttop[nx], state[27][ny][nx] (double)
+// checkpoint format: "LBECKPT2", int32 n, int32 storage, int64 steps, then per
+// instance: lbe_params, Tbot[nx], Ttop[nx], uint64 nbytes, the raw bytes of the
+// buffer the next step reads (so a restart continues bit for bit)
 lbe_status lbe_save(lbe_handle* h, const char* path) {
   if (!h || !path) return fail(h, LBE_EINVAL, "handle or path is NULL");
+  lbe_status st = wait(h);
+  if (st) return st;
   FILE* fp = fopen(path, "wb");
   if (!fp) return fail(h, LBE_EINVAL, "cannot open %s for writing", path);
-  const char magic[8] = {'L', 'B', 'E', 'C', 'K', 'P', 'T', '1'};
+  const char magic[8] = {'L', 'B', 'E', 'C', 'K', 'P', 'T', '2'};
   const int32_t hdr[2] = {h->n, h->storage};
   const int64_t steps = h->steps;
   bool ok = fwrite(magic, 1, 8, fp) == 8 && fwrite(hdr, sizeof hdr, 1, fp) == 1 &&
             fwrite(&steps, sizeof steps, 1, fp) == 1;
   for (int j = 0; ok && j < h->n; j++) {
     const InstHost& H = h->inst[j];
-    std::vector<double> s((size_t)27 * H.nx * H.ny);
-    lbe_status st = lbe_get_state(h, j, s.data(), 0);
-    if (st) {
+    std::vector<char> raw(H.buf_bytes);
+    cudaError_t e = cudaMemcpy(raw.data(), H.arena + (size_t)h->parity * H.buf_bytes,
+                               H.buf_bytes, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
       fclose(fp);
-      return st;
+      return fail(h, LBE_ECUDA, "save copy: %s", cudaGetErrorString(e));
     }
+    const uint64_t nb = H.buf_bytes;
     ok = fwrite(&H.p, sizeof H.p, 1, fp) == 1 &&
          fwrite(H.Tbot.data(), sizeof(double), H.nx, fp) == (size_t)H.nx &&
          fwrite(H.Ttop.data(), sizeof(double), H.nx, fp) == (size_t)H.nx &&
-         fwrite(s.data(), sizeof(double), s.size(), fp) == s.size();
+         fwrite(&nb, sizeof nb, 1, fp) == 1 && fwrite(raw.data(), 1, nb, fp) == nb;
   }
   if (fclose(fp) != 0) ok = false;
   return ok ? LBE_OK : fail(h, LBE_EINVAL, "short write to %s", path);
@@ -626,25 +631,33 @@ lbe_status lbe_save(lbe_handle* h, const char* path) {
 
 lbe_status lbe_load(lbe_handle* h, const char* path) {
   if (!h || !path) return fail(h, LBE_EINVAL, "handle or path is NULL");
+  lbe_status st = wait(h);
+  if (st) return st;
   FILE* fp = fopen(path, "rb");
   if (!fp) return fail(h, LBE_EINVAL, "cannot open %s", path);
   char magic[8];
   int32_t hdr[2];
   int64_t steps;
-  bool ok = fread(magic, 1, 8, fp) == 8 && memcmp(magic, "LBECKPT1", 8) == 0 &&
+  bool ok = fread(magic, 1, 8, fp) == 8 && memcmp(magic, "LBECKPT2", 8) == 0 &&
             fread(hdr, sizeof hdr, 1, fp) == 1 && fread(&steps, sizeof steps, 1, fp) == 1;
   if (!ok || hdr[0] != h->n || hdr[1] != h->storage) {
     fclose(fp);
     return fail(h, LBE_EINVAL, "%s: not a checkpoint of this handle's layout", path);
   }
+  std::vector<std::vector<char>> raws(h->n);
   for (int j = 0; j < h->n; j++) {
     InstHost& H = h->inst[j];
     lbe_params p;
-    std::vector<double> tb(H.nx), tt(H.nx), s((size_t)27 * H.nx * H.ny);
+    uint64_t nb = 0;
+    std::vector<double> tb(H.nx), tt(H.nx);
     ok = fread(&p, sizeof p, 1, fp) == 1 && p.nx == H.nx && p.ny == H.ny &&
          fread(tb.data(), sizeof(double), H.nx, fp) == (size_t)H.nx &&
          fread(tt.data(), sizeof(double), H.nx, fp) == (size_t)H.nx &&
-         fread(s.data(), sizeof(double), s.size(), fp) == s.size();
+         fread(&nb, sizeof nb, 1, fp) == 1 && nb == H.buf_bytes;
+    if (ok) {
+      raws[j].resize(nb);
+      ok = fread(raws[j].data(), 1, nb, fp) == nb;
+    }
     if (!ok) {
       fclose(fp);
       return fail(h, LBE_EINVAL, "%s: truncated or mismatched instance %d", path, j);
@@ -653,14 +666,16 @@ lbe_status lbe_load(lbe_handle* h, const char* path) {
       fclose(fp);
       return fail(h, LBE_EINVAL, "%s: instance %d has other parameters or walls", path, j);
     }
-    lbe_status st = lbe_set_state(h, j, s.data(), 0);
-    if (st) {
-      fclose(fp);
-      return st;
-    }
   }
   fclose(fp);
+  for (int j = 0; j < h->n; j++) {
+    InstHost& H = h->inst[j];
+    CU(h, cudaMemcpy(H.arena + (size_t)h->parity * H.buf_bytes, raws[j].data(), H.buf_bytes,
+                     cudaMemcpyHostToDevice));
+  }
   h->steps = steps;
+  h->bad = false;
+  h->prev_valid = false;
   return LBE_OK;
 }
 

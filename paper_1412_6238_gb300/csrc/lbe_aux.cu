@@ -117,7 +117,8 @@ __global__ void push_kernel(const InstDev* __restrict__ d, int nx, int ny,
        k += (int64_t)gridDim.x * blockDim.x) {
     const int x = (int)(k % nx), y = (int)(k / nx);
     const size_t idx = (size_t)y * I.pitch + x;
-    const C ref = (S::kind >= ST_F16DEV) ? href<S>(I, y) : C(0);
+    // hbar deviation reference of this row (storage forms other than FP64)
+    const double rref = dev_h<S>() ? I.rho * I.cv * (I.hr0 + I.hr1 * y) : 0.0;
 #pragma unroll
     for (int j = 0; j < 9; j++) {
       const int xt = ((x + EX(j)) % nx + nx) % nx;
@@ -136,7 +137,8 @@ __global__ void push_kernel(const InstDev* __restrict__ d, int nx, int ny,
             v = 2.0 * WGT<double>(j) * I.rho * I.cv * Tw - pb;
           }
         }
-        S::st(I, buf, kk, j, idx, ref, (C)v);
+        if (kk == 2) v -= WGT<double>(j) * rref;
+        S::st(I, buf, kk, j, idx, (C)v);
       }
     }
   }
@@ -159,7 +161,9 @@ __global__ void pull_kernel(const InstDev* __restrict__ d, int nx, int ny, doubl
     pull9<S, 1>(I, buf, q, v);
     for (int i = 0; i < 9; i++) pre[(int64_t)(9 + i) * N + k] = (double)v[i];
     pull9<S, 2>(I, buf, q, v);
-    for (int i = 0; i < 9; i++) pre[(int64_t)(18 + i) * N + k] = (double)v[i];
+    const double rref = dev_h<S>() ? I.rho * I.cv * (I.hr0 + I.hr1 * y) : 0.0;
+    for (int i = 0; i < 9; i++)
+      pre[(int64_t)(18 + i) * N + k] = (double)v[i] + WGT<double>(i) * rref;
   }
 }
 

@@ -61,23 +61,28 @@ struct InstDev {
   double omega_g, Gm;      // 1/tau_g, Gamma = M/(tau_g - 1/2)
   double Fbx, Fby;         // rho a
   double eta_n2;
-  // deviation codec: q = s_k (P - w_i r_k(y)), r_h(y) = rho c_v (hr0 + hr1 y)
+  // hbar deviation reference T_r(y) = hr0 + hr1 y (the linear conduction
+  // profile between the mean wall temperatures) and 16-bit scales s_k
   float s[3], inv_s[3];
   double hr0, hr1;
 };
 
 // ------------------------------------------------------------ storage codecs
 // ld / st take (k, i) as template-folded constants through the unrolled loops.
+// FP64 stores the populations as they are (parity mode).  The other forms
+// store hbar as the deviation hbar_i - w_i rho c_v T_r(y) from the linear
+// conduction profile T_r of the row the value is stored in; the kernels work
+// with that deviation directly (the codec does not add the reference back).
 
 struct StF64 {
   using C = double;
   static constexpr int kind = ST_F64;
   __device__ static __forceinline__ C ld(const InstDev& I, const char* b, int k, int i,
-                                         size_t idx, C /*ref*/) {
+                                         size_t idx) {
     return __ldg(reinterpret_cast<const double*>(b + (size_t)(k * 9 + i) * I.plane_bytes) + idx);
   }
   __device__ static __forceinline__ void st(const InstDev& I, char* b, int k, int i, size_t idx,
-                                            C /*ref*/, C v) {
+                                            C v) {
     reinterpret_cast<double*>(b + (size_t)(k * 9 + i) * I.plane_bytes)[idx] = v;
   }
 };
@@ -86,11 +91,11 @@ struct StF32 {
   using C = float;
   static constexpr int kind = ST_F32;
   __device__ static __forceinline__ C ld(const InstDev& I, const char* b, int k, int i,
-                                         size_t idx, C /*ref*/) {
+                                         size_t idx) {
     return __ldg(reinterpret_cast<const float*>(b + (size_t)(k * 9 + i) * I.plane_bytes) + idx);
   }
   __device__ static __forceinline__ void st(const InstDev& I, char* b, int k, int i, size_t idx,
-                                            C /*ref*/, C v) {
+                                            C v) {
     reinterpret_cast<float*>(b + (size_t)(k * 9 + i) * I.plane_bytes)[idx] = v;
   }
 };
@@ -99,6 +104,8 @@ __host__ __device__ constexpr int dev_plane(int k, int i) {
   return k == 0 ? i : (k == 1 ? 8 + i : 17 + i);
 }
 
+// 16-bit forms: q = s_k v in fp16 / bf16 (v the value or, for hbar, the
+// deviation); g_0 in FP32.
 template <class E, int KIND>
 struct StDev {
   using C = float;
@@ -107,24 +114,19 @@ struct StDev {
   __device__ static __forceinline__ float cvt(__nv_bfloat16 q) { return __bfloat162float(q); }
   __device__ static __forceinline__ void put(__half* p, float v) { *p = __float2half_rn(v); }
   __device__ static __forceinline__ void put(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
-  // ref: the reference r_k(y) of lattice k at this row (only used for k = 2)
   __device__ static __forceinline__ C ld(const InstDev& I, const char* b, int k, int i,
-                                         size_t idx, C ref) {
+                                         size_t idx) {
     if (k == 1 && i == 0)
       return __ldg(reinterpret_cast<const float*>(b + I.g0_off) + idx);
     const E* p = reinterpret_cast<const E*>(b + (size_t)dev_plane(k, i) * I.plane_bytes) + idx;
-    float q = cvt(*p);
-    float v = q * I.inv_s[k];
-    if (k == 2) v = fmaf(WGT<float>(i), ref, v);
-    return v;
+    return cvt(*p) * I.inv_s[k];
   }
   __device__ static __forceinline__ void st(const InstDev& I, char* b, int k, int i, size_t idx,
-                                            C ref, C v) {
+                                            C v) {
     if (k == 1 && i == 0) {
       reinterpret_cast<float*>(b + I.g0_off)[idx] = v;
       return;
     }
-    if (k == 2) v = fmaf(-WGT<float>(i), ref, v);
     put(reinterpret_cast<E*>(b + (size_t)dev_plane(k, i) * I.plane_bytes) + idx, v * I.s[k]);
   }
 };

@@ -41,43 +41,53 @@ struct Cell {
   int x, xm, xp, y;  // wrapped column, its neighbours, row (0 <= y < ny)
 };
 
-// Reference value r_h(y) of the hbar deviation codec at row y.
+// hbar is handled as the deviation hbar_i - w_i rho c_v T_r(y) from the linear
+// conduction profile T_r(y) = hr0 + hr1 y in every storage but FP64 (which
+// keeps the full populations, like the FP64 reference).
 template <class S>
-__device__ __forceinline__ typename S::C href(const InstDev& I, int y) {
-  using C = typename S::C;
-  return C(I.rho_cv) * (C(I.hr0) + C(I.hr1) * C(y));
-}
+__device__ __forceinline__ constexpr bool dev_h() { return S::kind != ST_F64; }
 
-// Pull the 9 pre-collision populations of lattice K at (x, y).
+// Pull the 9 pre-collision populations of lattice K at (x, y).  For hbar in
+// deviation form the result is relative to T_r of row y: a value pulled from
+// row y - xi_iy was stored relative to T_r(y - xi_iy), which differs by
+// w_i rho c_v hr1 xi_iy; at a wall the anti-bounce-back reads
+// -P*_ibar + 2 w_i rho c_v (T_w - T_r(y)).
 template <class S, int K>
 __device__ __forceinline__ void pull9(const InstDev& I, const char* __restrict__ src,
                                       const Cell<S>& q, typename S::C out[9]) {
   using C = typename S::C;
+  constexpr bool DEV = (K == 2) && dev_h<S>();
   const size_t pitch = (size_t)I.pitch;
   const size_t r0 = (size_t)q.y * pitch;
   const bool wb = (q.y == 0), wt = (q.y == I.ny - 1);
-  const C ref0 = (K == 2) ? href<S>(I, q.y) : C(0);
-  const C refm = (K == 2 && !wb) ? href<S>(I, q.y - 1) : C(0);
-  const C refp = (K == 2 && !wt) ? href<S>(I, q.y + 1) : C(0);
   C Tw = C(0);
-  if (K == 2 && (wb || wt)) Tw = C(wb ? I.Tbot[q.x] : I.Ttop[q.x]);
+  if (K == 2 && (wb || wt)) {
+    const double tw = wb ? I.Tbot[q.x] : I.Ttop[q.x];
+    Tw = DEV ? C(tw - (I.hr0 + I.hr1 * q.y)) : C(tw);
+  }
+  const C dh = DEV ? C(I.rho_cv * I.hr1) : C(0);  // rho c_v (T_r(y) - T_r(y-1))
   auto bb = [&](int i) -> C {
-    C v = S::ld(I, src, K, OPP(i), r0 + q.x, ref0);
+    C v = S::ld(I, src, K, OPP(i), r0 + q.x);
     if (K == 2) return -v + C(2) * WGT<C>(i) * C(I.rho) * C(I.cv) * Tw;
     return v;
   };
-  out[0] = S::ld(I, src, K, 0, r0 + q.x, ref0);
-  out[1] = S::ld(I, src, K, 1, r0 + q.xm, ref0);
-  out[3] = S::ld(I, src, K, 3, r0 + q.xp, ref0);
+  out[0] = S::ld(I, src, K, 0, r0 + q.x);
+  out[1] = S::ld(I, src, K, 1, r0 + q.xm);
+  out[3] = S::ld(I, src, K, 3, r0 + q.xp);
   if (wb) {
     out[2] = bb(2);
     out[5] = bb(5);
     out[6] = bb(6);
   } else {
     const size_t rm = r0 - pitch;
-    out[2] = S::ld(I, src, K, 2, rm + q.x, refm);
-    out[5] = S::ld(I, src, K, 5, rm + q.xm, refm);
-    out[6] = S::ld(I, src, K, 6, rm + q.xp, refm);
+    out[2] = S::ld(I, src, K, 2, rm + q.x);
+    out[5] = S::ld(I, src, K, 5, rm + q.xm);
+    out[6] = S::ld(I, src, K, 6, rm + q.xp);
+    if (DEV) {
+      out[2] -= WGT<C>(2) * dh;
+      out[5] -= WGT<C>(5) * dh;
+      out[6] -= WGT<C>(6) * dh;
+    }
   }
   if (wt) {
     out[4] = bb(4);
@@ -85,9 +95,14 @@ __device__ __forceinline__ void pull9(const InstDev& I, const char* __restrict__
     out[8] = bb(8);
   } else {
     const size_t rp = r0 + pitch;
-    out[4] = S::ld(I, src, K, 4, rp + q.x, refp);
-    out[7] = S::ld(I, src, K, 7, rp + q.xp, refp);
-    out[8] = S::ld(I, src, K, 8, rp + q.xm, refp);
+    out[4] = S::ld(I, src, K, 4, rp + q.x);
+    out[7] = S::ld(I, src, K, 7, rp + q.xp);
+    out[8] = S::ld(I, src, K, 8, rp + q.xm);
+    if (DEV) {
+      out[4] += WGT<C>(4) * dh;
+      out[7] += WGT<C>(7) * dh;
+      out[8] += WGT<C>(8) * dh;
+    }
   }
 }
 
@@ -152,7 +167,11 @@ __device__ __forceinline__ void region_values(const InstDev& I, const char* __re
     pull9<S, 2>(I, src, q, v);
     T = dv(sum9(v), C(I.rho_cv), C(I.inv_rho_cv));
     if (ghost != 0) {
-      const C Tw = C(ghost < 0 ? I.Tbot[q.x] : I.Ttop[q.x]);
+      // T(-1-j) = 2 T_w - T(j); in deviation form T_r is linear, so
+      // T'(-1-j) = 2 (T_w - T_r(wall)) - T'(j), T_r(wall) = T_r(-1/2) or T_r(ny-1/2)
+      const double tw = ghost < 0 ? I.Tbot[q.x] : I.Ttop[q.x];
+      const C Tw = dev_h<S>() ? C(tw - (I.hr0 + I.hr1 * (ghost < 0 ? -0.5 : ny - 0.5)))
+                              : C(tw);
       T = C(2) * Tw - T;
     }
   } else {
@@ -294,6 +313,10 @@ struct Tile {
       grad_iso<C, RW>(sm.c, tx + 2, ty + 2, gcx, gcy);
       const C lapc = lap_iso<C, RW>(sm.c, tx + 2, ty + 2);
       grad_iso<C, QW>(sm.T, tx + 1, ty + 1, gTx, gTy);
+      // deviation form: T = T' + T_r(y), grad T = grad T' + (0, hr1) (the
+      // isotropic gradient of a linear profile is exact)
+      const C Trow = dev_h<S>() ? C(I.hr0 + I.hr1 * gy) : C(0);
+      if (dev_h<S>()) gTy += C(I.hr1);
       grad_iso<C, QW>(sm.p, tx + 1, ty + 1, gpx, gpy);
       grad_iso<C, QW>(sm.nx, tx + 1, ty + 1, d1, dum);
       grad_iso<C, QW>(sm.ny, tx + 1, ty + 1, dum, d2);
@@ -301,7 +324,8 @@ struct Tile {
 
       // S4, S5
       const C mu = C(I.beta2) * cc * (cc - C(1)) * (C(2) * cc - C(1)) - C(I.eps2) * lapc;
-      const C sigma = C(I.sigma0) - C(I.sigmaT) * (TT - C(I.Tref));
+      const C sigma = dev_h<S>() ? C(I.sigma0) - C(I.sigmaT) * (TT + C(I.hr0 + I.hr1 * gy - I.Tref))
+                                 : C(I.sigma0) - C(I.sigmaT) * (TT - C(I.Tref));
       const C g2 = gcx * gcx + gcy * gcy;
       const C gabs = sqrt(g2);
       const C cdT = gcx * gTx + gcy * gTy;
@@ -337,7 +361,7 @@ struct Tile {
         out[N + k] = (double)pp;
         out[2 * N + k] = (double)ux;
         out[3 * N + k] = (double)uy;
-        out[4 * N + k] = (double)TT;
+        out[4 * N + k] = dev_h<S>() ? (double)TT + (I.hr0 + I.hr1 * gy) : (double)TT;
         return;
       }
 
@@ -360,11 +384,12 @@ struct Tile {
       const C H0 = dv(cc - dv((C(1) - WGT<C>(0)) * Gm * mu, cs2<C>(), C(3)), WGT<C>(0),
                       C(9) / C(4));
       const C Gx = Fx - gpx, Gy = Fy - gpy;  // F - grad p (= Fbar, uniform rho)
-      const C rcvT = C(I.rho) * C(I.cv) * TT;
+      const C rcvT = C(I.rho) * C(I.cv) * (TT + Trow);  // rho c_v T (full T)
+      const C rcvTr = C(I.rho_cv) * Trow;                // rho c_v T_r(y)
+      const C rcvTd = C(I.rho_cv) * TT;                  // rho c_v T'
 
       char* __restrict__ dst = I.buf[parity ^ 1];
       const size_t idx = (size_t)gy * I.pitch + gx;
-      const C ref = (S::kind >= ST_F16DEV) ? href<S>(I, gy) : C(0);
 #pragma unroll
       for (int i = 0; i < 9; i++) {
         const C W = WGT<C>(i);
@@ -384,10 +409,12 @@ struct Tile {
         // hbar (Eq. aEq12 with Eq. aEq9)
         const C heq = rcvT * G;
         const C hs = dv(Gx * dx + Gy * dy, rcs2, inv_rcs2) * heq;
-        const C hn = h[i] - omega_T * (h[i] - heq) + aT * hs;
-        S::st(I, dst, 0, i, idx, ref, fn);
-        S::st(I, dst, 1, i, idx, ref, gn);
-        S::st(I, dst, 2, i, idx, ref, hn);
+        // deviation form: h_eq - w_i rho c_v T_r = rho c_v (T' Gamma_i + T_r w_i q_i)
+        const C heqd = dev_h<S>() ? rcvTd * G + rcvTr * (W * q) : heq;
+        const C hn = h[i] - omega_T * (h[i] - heqd) + aT * hs;
+        S::st(I, dst, 0, i, idx, fn);
+        S::st(I, dst, 1, i, idx, gn);
+        S::st(I, dst, 2, i, idx, hn);
       }
     }
   }
