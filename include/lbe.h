@@ -181,6 +181,30 @@ int64_t lbe_state_bytes(const lbe_handle* h); /* both population buffers */
 
 void lbe_destroy(lbe_handle* h);
 
+/* Allocation-free FP64 sums.  The paper has no counterpart: this is a library
+ * service for callers that cannot let the library allocate device memory (a
+ * framework whose caching allocator owns the device memory, a per-step
+ * monitoring loop where cudaMalloc/cudaFree would synchronize the device, a
+ * process with a fixed device-memory budget).  It computes what lbe_sums
+ * computes, but from caller-provided fields and without a handle:
+ *   cur[0..4]  device pointers to c, p, ux, uy, T of one state, n values each
+ *   prev       NULL, or device pointers whose [2] and [3] (ux, uy) are the
+ *              previous step's velocity (for the residual; other entries unused)
+ *   rho_cv     rho * c_v, so that out[2] = rho c_v sum T = sum of hbar
+ *   out        device pointer to 5 doubles: sum c, sum p, sum hbar, residual
+ *              ||u - u_prev|| / ||u|| (0 without prev), non-finite count
+ *   stream     cudaStream_t the two kernels are enqueued on (asynchronous).
+ * Its only scratch is a static 384 KiB device array inside the library, held
+ * by every GPU that loads it until the process exits; n must be at most
+ * 33,554,432 (LBE_EINVAL otherwise, message from lbe_last_error(NULL)).  No
+ * call allocates or frees memory.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current, so
+ * make that first call before any stream capture.  All calls on a device
+ * share the array: calls that overlap on the GPU (other streams, other
+ * threads) race and must be serialized by the caller. */
+lbe_status lbe_sums_fields_noalloc(const double* const cur[5], const double* const prev[5],
+                                   int64_t n, double rho_cv, double* out, void* stream);
+
 /* Last error message of the handle (or of this thread if h is NULL). */
 const char* lbe_last_error(const lbe_handle* h);
 

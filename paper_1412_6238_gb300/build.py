@@ -25,6 +25,7 @@ UNITS = {
     "lbe_step_bf16.cu": [],
     "lbe_aux.cu": ["-fmad=false"],
     "lbe_api.cu": ["-Xcompiler", "-ffp-contract=off"],
+    "lbe_noalloc.cu": ["-fmad=false"],
 }
 
 

@@ -458,6 +458,8 @@ lbe_status check_handle(lbe_handle* h, int32_t instance) {
 
 }  // namespace
 
+void lbe::set_thread_error(const char* msg) { g_thread_err = msg ? msg : ""; }
+
 extern "C" {
 
 int32_t lbe_abi_version(void) { return LBE_ABI_VERSION; }

@@ -66,4 +66,7 @@ cudaError_t launch_sums(const double* cur, const double* prev, int64_t n, double
                         double* out, cudaStream_t s);
 cudaError_t launch_f64_to_f32(const double* in, float* out, int64_t n, cudaStream_t s);
 
+// Sets the message lbe_last_error(NULL) returns on this thread (lbe_api.cu).
+void set_thread_error(const char* msg);
+
 }  // namespace lbe
