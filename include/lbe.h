@@ -165,13 +165,19 @@ lbe_status lbe_set_state(lbe_handle* h, int32_t instance, const double* pops,
 lbe_status lbe_save(lbe_handle* h, const char* path);
 lbe_status lbe_load(lbe_handle* h, const char* path);
 
-/* Tile shape of the step kernel (autotuner hook).  lbe_num_tiles() shapes
- * exist; lbe_tile_shape() gives the cells of one CTA tile.  Setting a shape
- * the handle's storage does not provide returns LBE_EINVAL.  grid_ctas sets
- * the persistent grid size (0 = 2 x the SM count x resident CTAs/SM). */
+/* Step-kernel choice (autotuner hook).  Kernel ids 0 .. lbe_num_tiles()-1:
+ * ids whose shape has ty > 0 are the tile kernel with TX x TY cells per CTA
+ * (any storage; FP64 provides id 0 only); ids with ty == 0 are the strip
+ * kernel with TX columns per CTA marching over rows with TMA-staged rows
+ * (16/32-bit storages, every instance at least 4 columns wide; the default
+ * there).  grid_ctas: persistent grid size (0 = resident CTAs x SMs, -1 = one
+ * CTA per work item).  seg_rows: rows per strip work item (0 = about two
+ * items per resident CTA).  LBE_EINVAL for a kernel the handle cannot use.
+ * lbe_get_tile() reports {kernel id, grid CTAs, seg rows, work items}. */
 int32_t lbe_num_tiles(void);
 lbe_status lbe_tile_shape(int32_t tile_id, int32_t* tx, int32_t* ty);
-lbe_status lbe_set_tile(lbe_handle* h, int32_t tile_id, int32_t grid_ctas);
+lbe_status lbe_set_tile(lbe_handle* h, int32_t tile_id, int32_t grid_ctas, int32_t seg_rows);
+lbe_status lbe_get_tile(const lbe_handle* h, int32_t out[4]);
 
 /* Introspection. */
 int64_t lbe_steps_done(const lbe_handle* h);

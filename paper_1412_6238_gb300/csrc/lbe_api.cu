@@ -11,8 +11,12 @@
 #include <thread>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "../../include/lbe.h"
 #include "lbe_launch.h"
+#include "lbe_strip.cuh"
 
 using namespace lbe;
 
@@ -45,6 +49,10 @@ struct lbe_handle {
   int tile = 0;
   int grid_req = 0;              // 0 = auto, -1 = one CTA per tile, >0 = CTAs
   int grid = 0;
+  int seg_req = 0;               // strip kernel: rows per work item (0 = auto)
+  int seg = 0;
+  TmapSet* d_maps = nullptr;     // [n] tensor maps for the strip kernel
+  int* d_err = nullptr;          // device error word (strip kernel wait time-outs)
   int64_t total_tiles = 0;
   int parity = 0;
   int64_t steps = 0;
@@ -115,6 +123,17 @@ lbe_status wait(lbe_handle* h) {
 }
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+// Bounded wait, then the device error word of the strip kernel.
+lbe_status wait_checked(lbe_handle* h) {
+  lbe_status st = wait(h);
+  if (st || !h->d_err) return st;
+  int e = 0;
+  CU(h, cudaMemcpyAsync(&e, h->d_err, sizeof e, cudaMemcpyDeviceToHost, h->stream));
+  if ((st = wait(h))) return st;
+  if (e) return fail(h, LBE_ECUDA, "a strip-kernel copy wait timed out (device error word %d)", e);
+  return LBE_OK;
+}
 
 lbe_status check_params(const lbe_params& p, int index) {
   auto bad = [&](const char* what) {
@@ -210,6 +229,8 @@ void free_handle(lbe_handle* h) {
     if (H.walls) cudaFree(H.walls);
   }
   if (h->d_inst) cudaFree(h->d_inst);
+  if (h->d_maps) cudaFree(h->d_maps);
+  if (h->d_err) cudaFree(h->d_err);
   if (h->d_finst) cudaFree(h->d_finst);
   if (h->scratch) cudaFree(h->scratch);
   if (h->d_partial) cudaFree(h->d_partial);
@@ -219,8 +240,102 @@ void free_handle(lbe_handle* h) {
   delete h;
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// Tensor maps of instance j for the strip kernel with NC columns: box of
+// NC + 2 XG elements in x, one row, all population planes.
+lbe_status encode_maps(lbe_handle* h, int j, int nc, TmapSet& T) {
+  auto enc = encode_fn();
+  if (!enc) return fail(h, LBE_ECUDA, "cuTensorMapEncodeTiled is not available");
+  const InstHost& H = h->inst[j];
+  const cuuint32_t bw = (cuuint32_t)(nc + 2 * XG);
+  memset(&T, 0, sizeof T);
+  for (int b = 0; b < 2; b++) {
+    char* base = H.arena + (size_t)b * H.buf_bytes;
+    const bool dev = h->storage >= LBE_F16DEV;
+    const CUtensorMapDataType dt =
+        h->storage == LBE_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+        : (h->storage == LBE_F16DEV ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                    : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+    const cuuint64_t esz = dev ? 2 : 4;
+    const cuuint64_t dims[3] = {(cuuint64_t)H.pitch, (cuuint64_t)H.ny, dev ? 26u : 27u};
+    const cuuint64_t strides[2] = {(cuuint64_t)H.pitch * esz, (cuuint64_t)H.plane_bytes};
+    const cuuint32_t box[3] = {bw, 1, dev ? 26u : 27u};
+    const cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = enc(&T.m[b][0], dt, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(h, LBE_ECUDA, "tensor map (planes) encode failed: %d", (int)r);
+    if (dev) {
+      const cuuint64_t d2[2] = {(cuuint64_t)H.pitch, (cuuint64_t)H.ny};
+      const cuuint64_t s2[1] = {(cuuint64_t)H.pitch * 4};
+      const cuuint32_t b2[2] = {bw, 1};
+      r = enc(&T.m[b][1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base + H.g0_off, d2, s2, b2, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return fail(h, LBE_ECUDA, "tensor map (g0) encode failed: %d", (int)r);
+    }
+  }
+  return LBE_OK;
+}
+
 // (Re)build the step descriptors for the current tile shape and upload them.
 lbe_status setup_tiles(lbe_handle* h) {
+  if (is_strip(h->tile)) {
+    const int nc = TILE_SHAPES[h->tile].tx;
+    const int occ = strip_occupancy(h->storage, h->tile - STRIP_FIRST);
+    if (occ <= 0) return fail(h, LBE_ECUDA, "strip kernel %d cannot be resident", h->tile);
+    h->grid = h->grid_req > 0 ? h->grid_req : occ * h->num_sms;
+    int64_t rowstrips = 0;
+    int max_ny = 1;
+    for (auto& H : h->inst) {
+      rowstrips += (int64_t)((H.nx + nc - 1) / nc) * H.ny;
+      max_ny = std::max(max_ny, H.ny);
+    }
+    if (h->seg_req > 0) {
+      h->seg = h->seg_req;
+    } else {
+      // about two work items per resident CTA
+      const int64_t target = 2 * (int64_t)(h->grid_req == -1 ? occ * h->num_sms : h->grid);
+      int64_t seg = (rowstrips + target - 1) / target;
+      h->seg = (int)std::min<int64_t>(std::max<int64_t>(seg, 8), max_ny);
+    }
+    std::vector<TmapSet> maps(h->n);
+    int64_t begin = 0;
+    for (int j = 0; j < h->n; j++) {
+      InstDev& D = h->idev[j];
+      D.tiles_x = (D.nx + nc - 1) / nc;
+      D.tiles_y = (D.ny + h->seg - 1) / h->seg;
+      D.tile_begin = begin;
+      begin += (int64_t)D.tiles_x * D.tiles_y;
+      lbe_status st = encode_maps(h, j, nc, maps[j]);
+      if (st) return st;
+    }
+    h->total_tiles = begin;
+    if (h->grid_req == -1) h->grid = (int)std::min<int64_t>(begin, 2147483647);
+    if (!h->d_maps) CU(h, cudaMalloc(&h->d_maps, sizeof(TmapSet) * h->n));
+    CU(h, cudaMemcpyAsync(h->d_maps, maps.data(), sizeof(TmapSet) * h->n, cudaMemcpyHostToDevice,
+                          h->stream));
+    CU(h, cudaMemcpyAsync(h->d_inst, h->idev.data(), sizeof(InstDev) * h->n,
+                          cudaMemcpyHostToDevice, h->stream));
+    if (h->gexec) {
+      cudaGraphExecDestroy(h->gexec);
+      h->gexec = nullptr;
+    }
+    h->graph_failed = false;
+    return wait(h);
+  }
   const TileShape ts = TILE_SHAPES[h->tile];
   int64_t begin = 0;
   for (int j = 0; j < h->n; j++) {
@@ -249,10 +364,17 @@ lbe_status setup_tiles(lbe_handle* h) {
   return wait(h);
 }
 
+cudaError_t launch_one_step(lbe_handle* h, int parity) {
+  if (is_strip(h->tile))
+    return launch_strip(h->storage, h->tile - STRIP_FIRST, h->d_inst, h->d_maps, h->n,
+                        h->total_tiles, h->seg, parity, h->grid, h->d_err, h->stream);
+  return launch_step(h->storage, h->tile, h->d_inst, h->n, h->total_tiles, parity, h->grid,
+                     h->stream);
+}
+
 lbe_status launch_steps_direct(lbe_handle* h, int64_t k) {
   for (int64_t s = 0; s < k; s++) {
-    cudaError_t e = launch_step(h->storage, h->tile, h->d_inst, h->n, h->total_tiles,
-                                h->parity, h->grid, h->stream);
+    cudaError_t e = launch_one_step(h, h->parity);
     if (e != cudaSuccess) return fail(h, LBE_ECUDA, "step launch: %s", cudaGetErrorString(e));
     h->parity ^= 1;
     h->steps++;
@@ -270,10 +392,8 @@ void ensure_graph(lbe_handle* h) {
     h->graph_failed = true;
     return;
   }
-  cudaError_t e1 = launch_step(h->storage, h->tile, h->d_inst, h->n, h->total_tiles, 0, h->grid,
-                               h->stream);
-  cudaError_t e2 = launch_step(h->storage, h->tile, h->d_inst, h->n, h->total_tiles, 1, h->grid,
-                               h->stream);
+  cudaError_t e1 = launch_one_step(h, 0);
+  cudaError_t e2 = launch_one_step(h, 1);
   cudaError_t e3 = cudaStreamEndCapture(h->stream, &g);
   if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || !g ||
       cudaGraphInstantiate(&h->gexec, g, 0) != cudaSuccess) {
@@ -385,7 +505,7 @@ lbe_status create(int32_t n, const lbe_params* params, const lbe_init_fields* in
     H.p = params[j];
     H.nx = params[j].nx;
     H.ny = params[j].ny;
-    H.pitch = round_up(H.nx, 64);
+    H.pitch = round_up(H.nx + 2 * XG, 64);  // periodic ghost columns on both sides
     H.plane_bytes = ((uint64_t)H.ny * H.pitch * esz + 255) / 256 * 256;
     if (st >= LBE_F16DEV) {
       H.g0_off = 26 * H.plane_bytes;
@@ -442,7 +562,15 @@ lbe_status create(int32_t n, const lbe_params* params, const lbe_init_fields* in
     CUB(e);
     CUB(es);
   }
-  h->tile = 0;
+  CUB(cudaMalloc(&h->d_err, sizeof(int)));
+  CUB(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
+  {
+    // default kernel: the strip kernel where it applies (16/32-bit storage,
+    // every instance at least XG columns wide), else the tile kernel
+    int min_nx = 1 << 30;
+    for (auto& H : h->inst) min_nx = std::min(min_nx, H.nx);
+    h->tile = (h->storage != LBE_F64 && min_nx >= XG) ? STRIP_FIRST : 0;
+  }
   lbe_status s2 = setup_tiles(h);
   if (s2) return bail(s2);
   *out = h;
@@ -504,7 +632,7 @@ lbe_status lbe_step(lbe_handle* h, int64_t nsteps) {
 
 lbe_status lbe_synchronize(lbe_handle* h) {
   if (!h) return fail(nullptr, LBE_EINVAL, "handle is NULL");
-  return wait(h);
+  return wait_checked(h);
 }
 
 lbe_status lbe_fields(lbe_handle* h, int32_t instance, uint32_t mask, void* const dst[5],
@@ -538,7 +666,7 @@ lbe_status lbe_fields(lbe_handle* h, int32_t instance, uint32_t mask, void* cons
       if ((st = wait(h))) return st;  // tmp32 is reused by the next field
     }
   }
-  return wait(h);
+  return wait_checked(h);
 }
 
 lbe_status lbe_sums(lbe_handle* h, int32_t instance, double out[5]) {
@@ -691,16 +819,30 @@ lbe_status lbe_tile_shape(int32_t tile_id, int32_t* tx, int32_t* ty) {
   return LBE_OK;
 }
 
-lbe_status lbe_set_tile(lbe_handle* h, int32_t tile_id, int32_t grid_ctas) {
+lbe_status lbe_set_tile(lbe_handle* h, int32_t tile_id, int32_t grid_ctas, int32_t seg_rows) {
   if (!h) return fail(nullptr, LBE_EINVAL, "handle is NULL");
   if (!tile_available(h->storage, tile_id))
-    return fail(h, LBE_EINVAL, "tile %d is not built for this storage", tile_id);
+    return fail(h, LBE_EINVAL, "kernel %d is not built for this storage", tile_id);
+  if (is_strip(tile_id))
+    for (auto& H : h->inst)
+      if (H.nx < XG) return fail(h, LBE_EINVAL, "the strip kernel needs nx >= %d", XG);
   if (grid_ctas < -1) return fail(h, LBE_EINVAL, "grid_ctas must be >= -1");
+  if (seg_rows < 0) return fail(h, LBE_EINVAL, "seg_rows must be >= 0");
   lbe_status st = wait(h);
   if (st) return st;
   h->tile = tile_id;
   h->grid_req = grid_ctas;
+  h->seg_req = seg_rows;
   return setup_tiles(h);
+}
+
+lbe_status lbe_get_tile(const lbe_handle* h, int32_t out[4]) {
+  if (!h || !out) return fail(nullptr, LBE_EINVAL, "handle or out is NULL");
+  out[0] = h->tile;
+  out[1] = h->grid;
+  out[2] = is_strip(h->tile) ? h->seg : 0;
+  out[3] = (int32_t)std::min<int64_t>(h->total_tiles, 2147483647);
+  return LBE_OK;
 }
 
 int64_t lbe_steps_done(const lbe_handle* h) { return h ? h->steps : -1; }

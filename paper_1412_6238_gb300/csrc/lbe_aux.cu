@@ -13,6 +13,26 @@ bool tile_available(int storage, int tile) {
   return true;
 }
 
+cudaError_t launch_strip(int storage, int variant, const InstDev* d, const TmapSet* maps, int n,
+                         int64_t items, int seg, int parity, int grid, int* err, cudaStream_t s) {
+  switch (storage) {
+    case ST_F32: return launch_strip_f32(variant, d, maps, n, items, seg, parity, grid, err, s);
+    case ST_F16DEV: return launch_strip_f16(variant, d, maps, n, items, seg, parity, grid, err, s);
+    case ST_BF16DEV:
+      return launch_strip_bf16(variant, d, maps, n, items, seg, parity, grid, err, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+int strip_occupancy(int storage, int variant) {
+  switch (storage) {
+    case ST_F32: return strip_occupancy_f32(variant);
+    case ST_F16DEV: return strip_occupancy_f16(variant);
+    case ST_BF16DEV: return strip_occupancy_bf16(variant);
+  }
+  return 0;
+}
+
 cudaError_t launch_step(int storage, int tile, const InstDev* d, int n, int64_t total, int parity,
                         int grid, cudaStream_t s) {
   switch (storage) {
@@ -116,7 +136,7 @@ __global__ void push_kernel(const InstDev* __restrict__ d, int nx, int ny,
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int x = (int)(k % nx), y = (int)(k / nx);
-    const size_t idx = (size_t)y * I.pitch + x;
+    const size_t rowbase = (size_t)y * I.pitch;
     // hbar deviation reference of this row (storage forms other than FP64)
     const double rref = dev_h<S>() ? I.rho * I.cv * (I.hr0 + I.hr1 * y) : 0.0;
 #pragma unroll
@@ -138,7 +158,7 @@ __global__ void push_kernel(const InstDev* __restrict__ d, int nx, int ny,
           }
         }
         if (kk == 2) v -= WGT<double>(j) * rref;
-        S::st(I, buf, kk, j, idx, (C)v);
+        st_cell<S>(I, buf, kk, j, rowbase, x, (C)v);
       }
     }
   }

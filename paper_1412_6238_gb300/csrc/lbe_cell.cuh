@@ -1,0 +1,212 @@
+// Per-cell arithmetic of the fused step, shared by the tile kernel and the
+// strip kernel: isotropic stencils, chemical potential, CSF + Marangoni force,
+// velocity and the three forced BGK collisions (steps S2-S9).  Expressions are
+// evaluated in the operation order of the FP64 CPU reference; divisions are
+// true divisions in FP64 and products with a reciprocal in FP32 (dv()).
+#pragma once
+
+#include "lbe_common.cuh"
+
+namespace lbe {
+
+// a / b: a true division in FP64 (parity mode rounds like the FP64
+// reference); a product with the precomputed reciprocal in FP32.
+__device__ __forceinline__ double dv(double a, double b, double) { return a / b; }
+__device__ __forceinline__ float dv(float a, float, float inv_b) { return a * inv_b; }
+
+// c_s^2 = 1/3 of D2Q9
+template <class C>
+__device__ __forceinline__ C cs2() { return C(1.0 / 3.0); }
+
+// Sum over i = 0..8 in index order (the order the moments of Eq. 13, Eq. 28
+// and Eq. aEq13 are accumulated in FP64 parity mode as well).
+template <class C>
+__device__ __forceinline__ C sum9(const C v[9]) {
+  C s = v[0];
+#pragma unroll
+  for (int i = 1; i < 9; i++) s += v[i];
+  return s;
+}
+
+// hbar is handled as the deviation hbar_i - w_i rho c_v T_r(y) from the linear
+// conduction profile T_r(y) = hr0 + hr1 y in every storage but FP64 (which
+// keeps the full populations, like the FP64 reference).
+template <class S>
+__device__ __forceinline__ constexpr bool dev_h() { return S::kind != ST_F64; }
+
+// Isotropic gradient (1/c_s^2) sum_{i>=1} w_i xi_i phi(x + xi_i) and Laplacian
+// (2/c_s^2) sum_{i>=1} w_i (phi(x + xi_i) - phi(x)) from three rows (south,
+// centre, north) at column x; the terms are summed in index order
+// i = 1 (E), 2 (N), 3 (W), 4 (S), 5 (NE), 6 (NW), 7 (SW), 8 (SE), terms with
+// xi_ia = 0 being exact zeros.
+template <class C>
+__device__ __forceinline__ void grad3(const C* rs, const C* rc, const C* rn, int x, C& gx, C& gy) {
+  const C vE = rc[x + 1], vW = rc[x - 1], vN = rn[x], vS = rs[x];
+  const C vNE = rn[x + 1], vNW = rn[x - 1], vSE = rs[x + 1], vSW = rs[x - 1];
+  const C wa = WGT<C>(1), wd = WGT<C>(5);
+  C sx = wa * vE;
+  sx = sx - wa * vW;
+  sx = sx + wd * vNE;
+  sx = sx - wd * vNW;
+  sx = sx - wd * vSW;
+  sx = sx + wd * vSE;
+  C sy = wa * vN;
+  sy = sy - wa * vS;
+  sy = sy + wd * vNE;
+  sy = sy + wd * vNW;
+  sy = sy - wd * vSW;
+  sy = sy - wd * vSE;
+  gx = dv(sx, cs2<C>(), C(3));
+  gy = dv(sy, cs2<C>(), C(3));
+}
+
+template <class C>
+__device__ __forceinline__ C lap3(const C* rs, const C* rc, const C* rn, int x) {
+  const C v0 = rc[x];
+  const C wa = WGT<C>(1), wd = WGT<C>(5);
+  C t = wa * (rc[x + 1] - v0);
+  t = t + wa * (rn[x] - v0);
+  t = t + wa * (rc[x - 1] - v0);
+  t = t + wa * (rs[x] - v0);
+  t = t + wd * (rn[x + 1] - v0);
+  t = t + wd * (rn[x - 1] - v0);
+  t = t + wd * (rs[x - 1] - v0);
+  t = t + wd * (rs[x + 1] - v0);
+  return dv(C(2) * t, cs2<C>(), C(3));
+}
+
+// Unit normal n = grad c / sqrt(|grad c|^2 + eta_n^2) (Eq. 3).
+template <class C>
+__device__ __forceinline__ void normal3(const C* rs, const C* rc, const C* rn, int x, C en2, C& nx,
+                                        C& ny) {
+  C gx, gy;
+  grad3(rs, rc, rn, x, gx, gy);
+  const C inv = C(1) / sqrt(gx * gx + gy * gy + en2);
+  nx = gx * inv;
+  ny = gy * inv;
+}
+
+// Stencil results at one cell.
+template <class C>
+struct Stencils {
+  C gcx, gcy, lapc, gTx, gTy, gpx, gpy, kappa;
+};
+
+// Force, chemical potential and velocity (S4-S6).  TT is T, or T' = T - T_r(y)
+// in the deviation forms (then gTy already includes dT_r/dy).
+template <class S>
+struct Drive {
+  using C = typename S::C;
+  C mu, Fx, Fy, ux, uy, Trow;
+};
+
+template <class S>
+__device__ __forceinline__ Drive<S> drive(const InstDev& I, int gy, const typename S::C f[9],
+                                          typename S::C cc, typename S::C TT,
+                                          const Stencils<typename S::C>& s) {
+  using C = typename S::C;
+  Drive<S> d;
+  d.Trow = dev_h<S>() ? C(I.hr0 + I.hr1 * gy) : C(0);
+  // S4: mu = 2 beta c (c-1)(2c-1) - eps^2 lap c
+  d.mu = C(I.beta2) * cc * (cc - C(1)) * (C(2) * cc - C(1)) - C(I.eps2) * s.lapc;
+  // S5: sigma(T) (Eq. aEq3) and F (Eq. 3)
+  const C sigma = dev_h<S>() ? C(I.sigma0) - C(I.sigmaT) * (TT + C(I.hr0 + I.hr1 * gy - I.Tref))
+                             : C(I.sigma0) - C(I.sigmaT) * (TT - C(I.Tref));
+  const C g2 = s.gcx * s.gcx + s.gcy * s.gcy;
+  const C gabs = sqrt(g2);
+  const C cdT = s.gcx * s.gTx + s.gcy * s.gTy;
+  const C ea = C(I.ea);
+  const C cap = -sigma * s.kappa * ea * gabs;
+  const C mar = -C(I.sigmaT) * ea;
+  d.Fx = cap * s.gcx + mar * (g2 * s.gTx - cdT * s.gcx) + C(I.Fbx);
+  d.Fy = cap * s.gcy + mar * (g2 * s.gTy - cdT * s.gcy) + C(I.Fby);
+  // S6 (Eq. 13): first moments summed in index order
+  C jx = f[1] - f[3];
+  jx = jx + f[5];
+  jx = jx - f[6];
+  jx = jx - f[7];
+  jx = jx + f[8];
+  C jy = f[2] - f[4];
+  jy = jy + f[5];
+  jy = jy + f[6];
+  jy = jy - f[7];
+  jy = jy - f[8];
+  const C rho = C(I.rho), inv_rho = C(I.inv_rho);
+  const C rcs2 = C(I.rcs2), inv_rcs2 = C(3) * inv_rho;
+  d.ux = dv(jx, rcs2, inv_rcs2) + dv(C(0.5) * d.Fx, rho, inv_rho);
+  d.uy = dv(jy, rcs2, inv_rcs2) + dv(C(0.5) * d.Fy, rho, inv_rho);
+  return d;
+}
+
+// S3, S7-S9: the three forced BGK collisions.  out(k, i, value) receives the
+// post-collision value of population (k, i) (hbar as a deviation in the
+// deviation forms).
+template <class S, class Out>
+__device__ __forceinline__ void collide(const InstDev& I, const typename S::C f[9],
+                                        const typename S::C g[9], const typename S::C h[9],
+                                        typename S::C cc, typename S::C pp, typename S::C TT,
+                                        typename S::C gpx, typename S::C gpy, const Drive<S>& d,
+                                        Out&& out) {
+  using C = typename S::C;
+  const C inv_rho = C(I.inv_rho);
+  const C rcs2 = C(I.rcs2), inv_rcs2 = C(3) * inv_rho;
+  // S3: properties, linear in c
+  const C eta = C(I.eta1) + cc * C(I.deta);
+  const C lam = C(I.lam1) + cc * C(I.dlam);
+  const C tau_f = dv(eta, rcs2, inv_rcs2) + C(0.5);
+  const C omega_f = C(1) / tau_f;
+  const C tau_h = dv(lam, C(I.rcvcs2), C(3) * C(I.inv_rho_cv));
+  const C omega_T = C(2) / (C(2) * tau_h + C(1));
+  const C omega_g = C(I.omega_g);
+  const C af = C(1) - C(0.5) * omega_f;
+  const C ag = C(1) - C(0.5) * omega_g;
+  const C aT = C(1) - C(0.5) * omega_T;
+  const C ux = d.ux, uy = d.uy, Fx = d.Fx, Fy = d.Fy;
+  // Gamma_i(u) = w_i (1 + xi.u/c_s^2 + ((xi.u/c_s^2)^2 - u^2/c_s^2)/2) (Eq. 6)
+  const C uu = dv(ux * ux + uy * uy, cs2<C>(), C(3));
+  const C Gm = C(I.Gm);
+  // H_i of Eq. 22
+  const C Hi = dv(Gm * d.mu, cs2<C>(), C(3));
+  const C H0 = dv(cc - dv((C(1) - WGT<C>(0)) * Gm * d.mu, cs2<C>(), C(3)), WGT<C>(0),
+                  C(9) / C(4));
+  const C Gx = Fx - gpx, Gy = Fy - gpy;  // F - grad p (= Fbar, uniform rho)
+  const C rcvT = C(I.rho) * C(I.cv) * (TT + d.Trow);  // rho c_v T (full T)
+  const C rcvTr = C(I.rho_cv) * d.Trow;               // rho c_v T_r(y)
+  const C rcvTd = C(I.rho_cv) * TT;                   // rho c_v T'
+#pragma unroll
+  for (int i = 0; i < 9; i++) {
+    const C W = WGT<C>(i);
+    const C xu = dv(C(EX(i)) * ux + C(EY(i)) * uy, cs2<C>(), C(3));
+    const C hq = C(0.5) * (xu * xu - uu);
+    const C G = W * (C(1) + xu + hq);
+    const C q = xu + hq;  // velocity part, without the cancelling w_i
+    const C dx = C(EX(i)) - ux, dy = C(EY(i)) - uy;
+    // f (Eq. 12 with Eq. 5)
+    const C feq = W * (pp + rcs2 * q);
+    const C fs = (Fx * dx + Fy * dy) * G;
+    out(0, i, f[i] - omega_f * (f[i] - feq) + af * fs);
+    // g (Eq. 27 with Eq. 21-22)
+    const C geq = W * ((i == 0 ? H0 : Hi) + cc * q);
+    const C gs = dv(cc * (dx * Gx + dy * Gy), rcs2, inv_rcs2) * G;
+    out(1, i, g[i] - omega_g * (g[i] - geq) + ag * gs);
+    // hbar (Eq. aEq12 with Eq. aEq9); deviation form:
+    // h_eq - w_i rho c_v T_r = rho c_v (T' Gamma_i + T_r w_i q_i)
+    const C heq = rcvT * G;
+    const C hs = dv(Gx * dx + Gy * dy, rcs2, inv_rcs2) * heq;
+    const C heqd = dev_h<S>() ? rcvTd * G + rcvTr * (W * q) : heq;
+    out(2, i, h[i] - omega_T * (h[i] - heqd) + aT * hs);
+  }
+}
+
+// Store one population of cell x (row base offset rowbase) and its periodic
+// ghost copies: element XG + x holds cell x; elements 0..XG-1 repeat cells
+// nx-XG..nx-1 and elements nx+XG..nx+2XG-1 repeat cells 0..XG-1.
+template <class S>
+__device__ __forceinline__ void st_cell(const InstDev& I, char* dst, int k, int i, size_t rowbase,
+                                        int x, typename S::C v) {
+  S::st(I, dst, k, i, rowbase + XG + x, v);
+  if (x < XG) S::st(I, dst, k, i, rowbase + XG + x + I.nx, v);
+  if (x >= I.nx - XG) S::st(I, dst, k, i, rowbase + XG + x - I.nx, v);
+}
+
+}  // namespace lbe

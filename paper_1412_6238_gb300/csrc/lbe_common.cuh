@@ -4,7 +4,11 @@
 //
 // Population layout (one "arena" per instance and buffer): planes of
 // ny rows x pitch elements, x fastest, pitch a multiple of 64 elements so
-// that every row starts on a 128-byte boundary for every element size.
+// that every row starts on a 128-byte boundary for every element size.  In a
+// row, element XG + x holds cell x; the XG elements on either side are
+// periodic ghost copies (cells nx-XG..nx-1 on the left, 0..XG-1 on the right)
+// written with every store, so that a row segment [x0-XG, x0+w+XG) can be
+// copied in one piece (TMA) for any strip start x0.
 //   F64 / F32 : 27 planes, plane (k, i) at index k*9 + i (k = 0 f, 1 g, 2 hbar)
 //   F16DEV / BF16DEV : 26 planes of 16-bit deviations in the order
 //               f_0..f_8, g_1..g_8, hbar_0..hbar_8, then one FP32 plane
@@ -41,6 +45,8 @@ __host__ __device__ constexpr C WGT(int i) {
 }
 
 enum Storage { ST_F64 = 0, ST_F32 = 1, ST_F16DEV = 2, ST_BF16DEV = 3 };
+
+constexpr int XG = 4;  // periodic ghost columns on each side of a row
 
 // Per-instance descriptor, built on the host, read by the kernels.
 struct InstDev {

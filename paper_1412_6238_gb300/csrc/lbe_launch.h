@@ -11,11 +11,36 @@ namespace lbe {
 struct TileShape {
   int tx, ty;
 };
-constexpr int NUM_TILES = 5;
-constexpr TileShape TILE_SHAPES[NUM_TILES] = {{32, 8}, {64, 4}, {32, 16}, {64, 8}, {128, 4}};
+// Kernel ids: 0..4 tile kernel with these tile shapes; 5, 6 strip kernel with
+// 128 / 64 columns per strip (ty = 0: a strip marches over its rows).
+constexpr int NUM_TILE_SHAPES = 5;
+constexpr int NUM_TILES = 7;
+constexpr int STRIP_FIRST = 5;
+constexpr TileShape TILE_SHAPES[NUM_TILES] = {{32, 8},  {64, 4}, {32, 16}, {64, 8},
+                                              {128, 4}, {128, 0}, {64, 0}};
+inline bool is_strip(int tile) { return tile >= STRIP_FIRST && tile < NUM_TILES; }
 
-// Does the step kernel of this storage exist for this tile shape?
+struct TmapSet;  // lbe_strip.cuh
+
+// Does the step kernel of this storage exist for this kernel id?
 bool tile_available(int storage, int tile);
+
+// Strip kernel (16/32-bit storages): variant 0 = 128 columns, 1 = 64.
+cudaError_t launch_strip(int storage, int variant, const InstDev* d, const TmapSet* maps, int n,
+                         int64_t items, int seg, int parity, int grid, int* err, cudaStream_t s);
+int strip_occupancy(int storage, int variant);
+cudaError_t launch_strip_f32(int variant, const InstDev* d, const TmapSet* maps, int n,
+                             int64_t items, int seg, int parity, int grid, int* err,
+                             cudaStream_t s);
+cudaError_t launch_strip_f16(int variant, const InstDev* d, const TmapSet* maps, int n,
+                             int64_t items, int seg, int parity, int grid, int* err,
+                             cudaStream_t s);
+cudaError_t launch_strip_bf16(int variant, const InstDev* d, const TmapSet* maps, int n,
+                              int64_t items, int seg, int parity, int grid, int* err,
+                              cudaStream_t s);
+int strip_occupancy_f32(int variant);
+int strip_occupancy_f16(int variant);
+int strip_occupancy_bf16(int variant);
 
 // One step of every instance in d_inst[0..n_inst): persistent grid of `grid`
 // CTAs over total_tiles tiles; reads buf[parity], writes buf[parity ^ 1].

@@ -2,4 +2,5 @@
 #define LBE_ST ::lbe::StF64
 #define LBE_SUFFIX f64
 #define LBE_ALL_TILES 0
+#define LBE_STRIP 0
 #include "lbe_step_inst.cuh"

@@ -25,7 +25,7 @@ PARAM_KEYS = ("rho", "cv", "eta1", "eta2", "lam1", "lam2", "sigma0", "sigmaT", "
 # Symbols declared in include/lbe.h (checked by the tests against the header).
 EXPORTS = ("lbe_abi_version", "lbe_init", "lbe_init_batch", "lbe_step", "lbe_synchronize",
            "lbe_fields", "lbe_sums", "lbe_get_state", "lbe_set_state", "lbe_save", "lbe_load",
-           "lbe_num_tiles", "lbe_tile_shape", "lbe_set_tile", "lbe_steps_done", "lbe_stream",
+           "lbe_num_tiles", "lbe_tile_shape", "lbe_set_tile", "lbe_get_tile", "lbe_steps_done", "lbe_stream",
            "lbe_num_instances", "lbe_state_bytes", "lbe_destroy", "lbe_last_error")
 
 
@@ -81,7 +81,8 @@ def library(build: bool = True) -> ctypes.CDLL:
                 "lbe_num_tiles": ([], ctypes.c_int32),
                 "lbe_tile_shape": ([ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                     ctypes.POINTER(ctypes.c_int32)], st),
-                "lbe_set_tile": ([H, ctypes.c_int32, ctypes.c_int32], st),
+                "lbe_set_tile": ([H, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], st),
+                "lbe_get_tile": ([H, ctypes.POINTER(ctypes.c_int32)], st),
                 "lbe_steps_done": ([H], ctypes.c_int64),
                 "lbe_stream": ([H], ctypes.c_void_p),
                 "lbe_num_instances": ([H], ctypes.c_int32),
@@ -194,8 +195,14 @@ class LBE:
     def state_bytes(self) -> int:
         return int(self._L.lbe_state_bytes(self._h))
 
-    def set_tile(self, tile: int, grid_ctas: int = 0):
-        self._check(self._L.lbe_set_tile(self._h, int(tile), int(grid_ctas)))
+    def set_tile(self, tile: int, grid_ctas: int = 0, seg_rows: int = 0):
+        """Choose the step kernel (see lbe_set_tile in include/lbe.h)."""
+        self._check(self._L.lbe_set_tile(self._h, int(tile), int(grid_ctas), int(seg_rows)))
+
+    def get_tile(self) -> dict:
+        out = (ctypes.c_int32 * 4)()
+        self._check(self._L.lbe_get_tile(self._h, out))
+        return dict(kernel=out[0], grid=out[1], seg_rows=out[2], items=out[3])
 
     def fields(self, instance: int = 0, names=FIELD_NAMES, dtype=None, device="cuda"):
         """Dict of torch tensors (ny, nx) for the requested fields."""

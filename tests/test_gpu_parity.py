@@ -97,17 +97,56 @@ def test_one_step_from_same_state(LBE, orc, storage, nx, ny):
     assert state_err(got, ref) < tol
 
 
-@pytest.mark.parametrize("tile", [0, 1, 2, 3, 4])
-def test_tile_shapes_bitwise_identical(LBE, tile):
-    """Every tile shape (and a persistent or one-CTA-per-tile grid) computes
-    the same per-cell arithmetic: results are bitwise equal."""
+@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5, 6])
+def test_kernels_bitwise_identical(LBE, tile):
+    """Every tile shape and both strip kernels (TMA-staged rows) compute the
+    same per-cell arithmetic: results are bitwise equal to tile kernel 0."""
     w = small_drop(150, 77)
     a = LBE(w, storage="f32")
+    a.set_tile(0)
     a.step(7)
     b = LBE(w, storage="f32")
     b.set_tile(tile, -1 if tile % 2 else 0)
     b.step(7)
     assert np.array_equal(a.get_state().numpy(), b.get_state().numpy())
+
+
+STRIP_SHAPES = [(4, 8), (5, 3), (7, 40), (64, 17), (130, 19), (200, 33), (257, 70)]
+
+
+@pytest.mark.parametrize("nx,ny", STRIP_SHAPES)
+@pytest.mark.parametrize("storage", ["f32", "f16dev", "bf16dev"])
+@pytest.mark.parametrize("seg", [1, 3, 0])
+def test_strip_kernel_equals_tile_kernel(LBE, storage, nx, ny, seg):
+    """The strip kernel on narrow, ragged and partial strips, with segments of
+    1, 3 and automatic rows (segment seams, bottom and top ghost rows), equals
+    the tile kernel bitwise for every 16/32-bit storage."""
+    R = max(1.5, min(nx, ny) / 4.0)
+    w = wl.droplet(nx, ny, R, nx / 2.0 + 0.3, ny / 2.0 - 0.2, Re=1.0, Ma=10.0, Ca=0.05,
+                   eta_m=0.2, eta_r=0.5, lam_r=2.0)
+    w.params["ax"] = 1e-6
+    a = LBE(w, storage=storage)
+    a.set_tile(0)
+    a.step(5)
+    for tile in (5, 6):
+        b = LBE(w, storage=storage)
+        b.set_tile(tile, 0, seg)
+        assert b.get_tile()["kernel"] == tile
+        b.step(5)
+        assert np.array_equal(a.get_state().numpy(), b.get_state().numpy()), tile
+
+
+def test_strip_is_default_and_rejects_narrow(LBE):
+    from paper_1412_6238_gb300.lbe import LBEError
+    w = small_drop()
+    assert LBE(w, storage="f32").get_tile()["kernel"] == 5
+    assert LBE(w, storage="f64").get_tile()["kernel"] == 0
+    narrow = wl.droplet(3, 20, 1.5, 1.5, 10.0, Re=1.0, Ma=10.0, Ca=0.05, eta_m=0.2, eta_r=1.0,
+                        lam_r=1.0)
+    s = LBE(narrow, storage="f32")
+    assert s.get_tile()["kernel"] == 0
+    with pytest.raises(LBEError):
+        s.set_tile(5)
 
 
 def test_graph_replay_equals_single_launches(LBE):
