@@ -29,8 +29,9 @@ struct InstHost {
   int nx = 0, ny = 0, pitch = 0;
   uint64_t plane_bytes = 0, g0_off = 0, buf_bytes = 0;
   char* arena = nullptr;  // two buffers of buf_bytes
-  double* walls = nullptr;  // device: Tbot[nx], Ttop[nx]
+  double* walls = nullptr;  // device: Tbot[nx], Ttop[nx], then 4 float tables
   std::vector<double> Tbot, Ttop;
+  std::vector<float> wdev;  // host copy of the T_w - T_r tables
 };
 
 }  // namespace
@@ -171,28 +172,29 @@ void fill_desc(lbe_handle* h, int j, InstDev& D) {
   D.buf[1] = H.arena + H.buf_bytes;
   D.Tbot = H.walls;
   D.Ttop = H.walls + H.nx;
-  D.rho = p.rho;
-  D.inv_rho = 1.0 / p.rho;
-  D.cv = p.cv;
-  D.rho_cv = p.rho * p.cv;
-  D.rcs2 = p.rho * (1.0 / 3.0);
-  D.rcvcs2 = (p.rho * p.cv) * (1.0 / 3.0);
-  D.inv_rho_cv = 1.0 / (p.rho * p.cv);
-  D.eta1 = p.eta1;
-  D.deta = p.eta2 - p.eta1;
-  D.lam1 = p.lam1;
-  D.dlam = p.lam2 - p.lam1;
-  D.sigma0 = p.sigma0;
-  D.sigmaT = p.sigmaT;
-  D.Tref = p.Tref;
-  D.eps2 = p.eps * p.eps;
-  D.ea = p.eps * (6.0 * std::sqrt(2.0));  // alpha = 6 sqrt 2 (Sec. II)
-  D.beta2 = 2.0 * p.beta;
-  D.omega_g = 1.0 / p.tau_g;
-  D.Gm = p.mobility / (p.tau_g - 0.5);
-  D.Fbx = p.rho * p.ax;
-  D.Fby = p.rho * p.ay;
-  D.eta_n2 = p.eta_n * p.eta_n;
+  Phys<double>& P = D.pd;
+  P.rho = p.rho;
+  P.inv_rho = 1.0 / p.rho;
+  P.cv = p.cv;
+  P.rho_cv = p.rho * p.cv;
+  P.inv_rho_cv = 1.0 / (p.rho * p.cv);
+  P.rcs2 = p.rho * (1.0 / 3.0);
+  P.rcvcs2 = (p.rho * p.cv) * (1.0 / 3.0);
+  P.eta1 = p.eta1;
+  P.deta = p.eta2 - p.eta1;
+  P.lam1 = p.lam1;
+  P.dlam = p.lam2 - p.lam1;
+  P.sigma0 = p.sigma0;
+  P.sigmaT = p.sigmaT;
+  P.Tref = p.Tref;
+  P.eps2 = p.eps * p.eps;
+  P.ea = p.eps * (6.0 * std::sqrt(2.0));  // alpha = 6 sqrt 2 (Sec. II)
+  P.beta2 = 2.0 * p.beta;
+  P.omega_g = 1.0 / p.tau_g;
+  P.Gm = p.mobility / (p.tau_g - 0.5);
+  P.Fbx = p.rho * p.ax;
+  P.Fby = p.rho * p.ay;
+  P.eta_n2 = p.eta_n * p.eta_n;
   // hbar reference: linear profile between the mean wall temperatures
   double tb = 0, tt = 0;
   for (int x = 0; x < H.nx; x++) {
@@ -203,6 +205,9 @@ void fill_desc(lbe_handle* h, int j, InstDev& D) {
   tt /= H.nx;
   D.hr1 = (tt - tb) / H.ny;
   D.hr0 = tb + 0.5 * D.hr1;
+  P.hr0 = D.hr0;
+  P.hr1 = D.hr1;
+  P.dh = P.rho_cv * D.hr1;
   // power-of-two scales keep the 16-bit deviations in the normal range with
   // a wide margin below the FP16 maximum (65504)
   double dev = 1e-6 * (std::fabs(tb) + std::fabs(tt) + 1.0);
@@ -215,10 +220,22 @@ void fill_desc(lbe_handle* h, int j, InstDev& D) {
   int eh = (int)std::floor(std::log2(65504.0 / 64.0 / hmax));
   eh = eh < -30 ? -30 : (eh > 30 ? 30 : eh);
   const int e[3] = {12, 12, eh};
+  const bool sixteen = h->storage >= LBE_F16DEV;
   for (int k = 0; k < 3; k++) {
-    D.s[k] = std::ldexp(1.0f, e[k]);
-    D.inv_s[k] = std::ldexp(1.0f, -e[k]);
+    D.s[k] = sixteen ? std::ldexp(1.0f, e[k]) : 1.0f;
+    P.inv_s[k] = sixteen ? std::ldexp(1.0, -e[k]) : 1.0;
   }
+  // the same constants in FP32 for the FP32 arithmetic
+  Phys<float>& F = D.pf;
+  const double* src = &P.rho;
+  float* dstf = &F.rho;
+  const int nfield = (int)(sizeof(Phys<double>) / sizeof(double));
+  for (int k = 0; k < nfield; k++) dstf[k] = (float)src[k];
+  // T_w - T_r at the first / last row and at the wall positions
+  D.wdev[0] = reinterpret_cast<const float*>(H.walls + 2 * H.nx);
+  D.wdev[1] = D.wdev[0] + H.nx;
+  D.wdev[2] = D.wdev[1] + H.nx;
+  D.wdev[3] = D.wdev[2] + H.nx;
 }
 
 void free_handle(lbe_handle* h) {
@@ -516,7 +533,8 @@ lbe_status create(int32_t n, const lbe_params* params, const lbe_init_fields* in
     }
     CUB(cudaMalloc(&H.arena, 2 * H.buf_bytes));
     CUB(cudaMemsetAsync(H.arena, 0, 2 * H.buf_bytes, h->stream));
-    CUB(cudaMalloc(&H.walls, sizeof(double) * 2 * H.nx));
+    // walls: Tbot[nx], Ttop[nx] (double), then 4 x nx floats of T_w - T_r
+    CUB(cudaMalloc(&H.walls, sizeof(double) * 2 * H.nx + sizeof(float) * 4 * H.nx));
     H.Tbot.assign(init[j].Tbot, init[j].Tbot + H.nx);
     H.Ttop.assign(init[j].Ttop, init[j].Ttop + H.nx);
     CUB(cudaMemcpyAsync(H.walls, H.Tbot.data(), sizeof(double) * H.nx, cudaMemcpyHostToDevice,
@@ -524,6 +542,18 @@ lbe_status create(int32_t n, const lbe_params* params, const lbe_init_fields* in
     CUB(cudaMemcpyAsync(H.walls + H.nx, H.Ttop.data(), sizeof(double) * H.nx,
                         cudaMemcpyHostToDevice, h->stream));
     fill_desc(h, j, h->idev[j]);
+    {
+      const InstDev& D = h->idev[j];
+      H.wdev.resize(4 * (size_t)H.nx);
+      for (int x = 0; x < H.nx; x++) {
+        H.wdev[x] = (float)(H.Tbot[x] - (D.hr0 + D.hr1 * 0));
+        H.wdev[H.nx + x] = (float)(H.Ttop[x] - (D.hr0 + D.hr1 * (H.ny - 1)));
+        H.wdev[2 * H.nx + x] = (float)(H.Tbot[x] - (D.hr0 + D.hr1 * -0.5));
+        H.wdev[3 * H.nx + x] = (float)(H.Ttop[x] - (D.hr0 + D.hr1 * (H.ny - 0.5)));
+      }
+      CUB(cudaMemcpyAsync(H.walls + 2 * H.nx, H.wdev.data(), sizeof(float) * 4 * H.nx,
+                          cudaMemcpyHostToDevice, h->stream));
+    }
     h->max_cells = std::max<int64_t>(h->max_cells, (int64_t)H.nx * H.ny);
   }
   CUB(cudaMalloc(&h->d_inst, sizeof(InstDev) * n));

@@ -97,11 +97,12 @@ __global__ void init_state_kernel(const InstDev* __restrict__ d, int nx, int ny,
     t = t + wd * (cat(x + 1, y - 1) - v0);
     const double cs2 = 1.0 / 3.0;
     const double lap = 2.0 * t / cs2;
-    const double mu = I.beta2 * v0 * (v0 - 1.0) * (2.0 * v0 - 1.0) - I.eps2 * lap;
+    const Phys<double>& P = I.pd;
+    const double mu = P.beta2 * v0 * (v0 - 1.0) * (2.0 * v0 - 1.0) - P.eps2 * lap;
     const double W0 = WGT<double>(0);
-    const double H0 = (v0 - (1.0 - W0) * I.Gm * mu / cs2) / W0;
-    const double Hi = I.Gm * mu / cs2;
-    const double rcvT = I.rho * I.cv * T0[k];
+    const double H0 = (v0 - (1.0 - W0) * P.Gm * mu / cs2) / W0;
+    const double Hi = P.Gm * mu / cs2;
+    const double rcvT = P.rho * P.cv * T0[k];
     for (int i = 0; i < 9; i++) {
       const double w = WGT<double>(i);
       pre[(int64_t)i * N + k] = 0.0;
@@ -138,7 +139,7 @@ __global__ void push_kernel(const InstDev* __restrict__ d, int nx, int ny,
     const int x = (int)(k % nx), y = (int)(k / nx);
     const size_t rowbase = (size_t)y * I.pitch;
     // hbar deviation reference of this row (storage forms other than FP64)
-    const double rref = dev_h<S>() ? I.rho * I.cv * (I.hr0 + I.hr1 * y) : 0.0;
+    const double rref = dev_h<S>() ? I.pd.rho * I.pd.cv * (I.hr0 + I.hr1 * y) : 0.0;
 #pragma unroll
     for (int j = 0; j < 9; j++) {
       const int xt = ((x + EX(j)) % nx + nx) % nx;
@@ -154,7 +155,7 @@ __global__ void push_kernel(const InstDev* __restrict__ d, int nx, int ny,
             v = pb;
           } else {
             const double Tw = (yt < 0) ? I.Tbot[x] : I.Ttop[x];
-            v = 2.0 * WGT<double>(j) * I.rho * I.cv * Tw - pb;
+            v = 2.0 * WGT<double>(j) * I.pd.rho * I.pd.cv * Tw - pb;
           }
         }
         if (kk == 2) v -= WGT<double>(j) * rref;
@@ -175,13 +176,14 @@ __global__ void pull_kernel(const InstDev* __restrict__ d, int nx, int ny, doubl
        k += (int64_t)gridDim.x * blockDim.x) {
     const int x = (int)(k % nx), y = (int)(k / nx);
     const Cell<S> q = make_cell<S>(x, y, nx);
+    const Phys<C>& P = phys<C>(I);
     C v[9];
-    pull9<S, 0>(I, buf, q, v);
+    pull9<S, 0>(I, P, buf, q, v);
     for (int i = 0; i < 9; i++) pre[(int64_t)i * N + k] = (double)v[i];
-    pull9<S, 1>(I, buf, q, v);
+    pull9<S, 1>(I, P, buf, q, v);
     for (int i = 0; i < 9; i++) pre[(int64_t)(9 + i) * N + k] = (double)v[i];
-    pull9<S, 2>(I, buf, q, v);
-    const double rref = dev_h<S>() ? I.rho * I.cv * (I.hr0 + I.hr1 * y) : 0.0;
+    pull9<S, 2>(I, P, buf, q, v);
+    const double rref = dev_h<S>() ? I.pd.rho * I.pd.cv * (I.hr0 + I.hr1 * y) : 0.0;
     for (int i = 0; i < 9; i++)
       pre[(int64_t)(18 + i) * N + k] = (double)v[i] + WGT<double>(i) * rref;
   }

@@ -101,25 +101,25 @@ struct Drive {
 };
 
 template <class S>
-__device__ __forceinline__ Drive<S> drive(const InstDev& I, int gy, const typename S::C f[9],
-                                          typename S::C cc, typename S::C TT,
-                                          const Stencils<typename S::C>& s) {
+__device__ __forceinline__ Drive<S> drive(const Phys<typename S::C>& P, int gy,
+                                          const typename S::C f[9], typename S::C cc,
+                                          typename S::C TT, const Stencils<typename S::C>& s) {
   using C = typename S::C;
   Drive<S> d;
-  d.Trow = dev_h<S>() ? C(I.hr0 + I.hr1 * gy) : C(0);
+  d.Trow = dev_h<S>() ? P.hr0 + P.hr1 * C(gy) : C(0);
   // S4: mu = 2 beta c (c-1)(2c-1) - eps^2 lap c
-  d.mu = C(I.beta2) * cc * (cc - C(1)) * (C(2) * cc - C(1)) - C(I.eps2) * s.lapc;
+  d.mu = P.beta2 * cc * (cc - C(1)) * (C(2) * cc - C(1)) - P.eps2 * s.lapc;
   // S5: sigma(T) (Eq. aEq3) and F (Eq. 3)
-  const C sigma = dev_h<S>() ? C(I.sigma0) - C(I.sigmaT) * (TT + C(I.hr0 + I.hr1 * gy - I.Tref))
-                             : C(I.sigma0) - C(I.sigmaT) * (TT - C(I.Tref));
+  const C sigma = dev_h<S>() ? P.sigma0 - P.sigmaT * (TT + (d.Trow - P.Tref))
+                             : P.sigma0 - P.sigmaT * (TT - P.Tref);
   const C g2 = s.gcx * s.gcx + s.gcy * s.gcy;
   const C gabs = sqrt(g2);
   const C cdT = s.gcx * s.gTx + s.gcy * s.gTy;
-  const C ea = C(I.ea);
+  const C ea = P.ea;
   const C cap = -sigma * s.kappa * ea * gabs;
-  const C mar = -C(I.sigmaT) * ea;
-  d.Fx = cap * s.gcx + mar * (g2 * s.gTx - cdT * s.gcx) + C(I.Fbx);
-  d.Fy = cap * s.gcy + mar * (g2 * s.gTy - cdT * s.gcy) + C(I.Fby);
+  const C mar = -P.sigmaT * ea;
+  d.Fx = cap * s.gcx + mar * (g2 * s.gTx - cdT * s.gcx) + P.Fbx;
+  d.Fy = cap * s.gcy + mar * (g2 * s.gTy - cdT * s.gcy) + P.Fby;
   // S6 (Eq. 13): first moments summed in index order
   C jx = f[1] - f[3];
   jx = jx + f[5];
@@ -131,8 +131,8 @@ __device__ __forceinline__ Drive<S> drive(const InstDev& I, int gy, const typena
   jy = jy + f[6];
   jy = jy - f[7];
   jy = jy - f[8];
-  const C rho = C(I.rho), inv_rho = C(I.inv_rho);
-  const C rcs2 = C(I.rcs2), inv_rcs2 = C(3) * inv_rho;
+  const C rho = P.rho, inv_rho = P.inv_rho;
+  const C rcs2 = P.rcs2, inv_rcs2 = C(3) * inv_rho;
   d.ux = dv(jx, rcs2, inv_rcs2) + dv(C(0.5) * d.Fx, rho, inv_rho);
   d.uy = dv(jy, rcs2, inv_rcs2) + dv(C(0.5) * d.Fy, rho, inv_rho);
   return d;
@@ -142,37 +142,37 @@ __device__ __forceinline__ Drive<S> drive(const InstDev& I, int gy, const typena
 // post-collision value of population (k, i) (hbar as a deviation in the
 // deviation forms).
 template <class S, class Out>
-__device__ __forceinline__ void collide(const InstDev& I, const typename S::C f[9],
+__device__ __forceinline__ void collide(const Phys<typename S::C>& P, const typename S::C f[9],
                                         const typename S::C g[9], const typename S::C h[9],
                                         typename S::C cc, typename S::C pp, typename S::C TT,
                                         typename S::C gpx, typename S::C gpy, const Drive<S>& d,
                                         Out&& out) {
   using C = typename S::C;
-  const C inv_rho = C(I.inv_rho);
-  const C rcs2 = C(I.rcs2), inv_rcs2 = C(3) * inv_rho;
+  const C inv_rho = P.inv_rho;
+  const C rcs2 = P.rcs2, inv_rcs2 = C(3) * inv_rho;
   // S3: properties, linear in c
-  const C eta = C(I.eta1) + cc * C(I.deta);
-  const C lam = C(I.lam1) + cc * C(I.dlam);
+  const C eta = P.eta1 + cc * P.deta;
+  const C lam = P.lam1 + cc * P.dlam;
   const C tau_f = dv(eta, rcs2, inv_rcs2) + C(0.5);
   const C omega_f = C(1) / tau_f;
-  const C tau_h = dv(lam, C(I.rcvcs2), C(3) * C(I.inv_rho_cv));
+  const C tau_h = dv(lam, P.rcvcs2, C(3) * P.inv_rho_cv);
   const C omega_T = C(2) / (C(2) * tau_h + C(1));
-  const C omega_g = C(I.omega_g);
+  const C omega_g = P.omega_g;
   const C af = C(1) - C(0.5) * omega_f;
   const C ag = C(1) - C(0.5) * omega_g;
   const C aT = C(1) - C(0.5) * omega_T;
   const C ux = d.ux, uy = d.uy, Fx = d.Fx, Fy = d.Fy;
   // Gamma_i(u) = w_i (1 + xi.u/c_s^2 + ((xi.u/c_s^2)^2 - u^2/c_s^2)/2) (Eq. 6)
   const C uu = dv(ux * ux + uy * uy, cs2<C>(), C(3));
-  const C Gm = C(I.Gm);
+  const C Gm = P.Gm;
   // H_i of Eq. 22
   const C Hi = dv(Gm * d.mu, cs2<C>(), C(3));
   const C H0 = dv(cc - dv((C(1) - WGT<C>(0)) * Gm * d.mu, cs2<C>(), C(3)), WGT<C>(0),
                   C(9) / C(4));
   const C Gx = Fx - gpx, Gy = Fy - gpy;  // F - grad p (= Fbar, uniform rho)
-  const C rcvT = C(I.rho) * C(I.cv) * (TT + d.Trow);  // rho c_v T (full T)
-  const C rcvTr = C(I.rho_cv) * d.Trow;               // rho c_v T_r(y)
-  const C rcvTd = C(I.rho_cv) * TT;                   // rho c_v T'
+  const C rcvT = P.rho * P.cv * (TT + d.Trow);  // rho c_v T (full T)
+  const C rcvTr = P.rho_cv * d.Trow;            // rho c_v T_r(y)
+  const C rcvTd = P.rho_cv * TT;                // rho c_v T'
 #pragma unroll
   for (int i = 0; i < 9; i++) {
     const C W = WGT<C>(i);

@@ -48,30 +48,48 @@ enum Storage { ST_F64 = 0, ST_F32 = 1, ST_F16DEV = 2, ST_BF16DEV = 3 };
 
 constexpr int XG = 4;  // periodic ghost columns on each side of a row
 
+// Physical constants of one instance, derived on the host in double and
+// kept in both precisions, so that the FP32 arithmetic never converts or
+// computes in FP64 (a slow pipe on this GPU).
+template <class C>
+struct Phys {
+  C rho, inv_rho, cv, rho_cv, inv_rho_cv;
+  C rcs2, rcvcs2;          // rho c_s^2, rho c_v c_s^2
+  C eta1, deta, lam1, dlam;
+  C sigma0, sigmaT, Tref;
+  C eps2, ea, beta2;       // eps^2, eps*alpha, 2 beta
+  C omega_g, Gm;           // 1/tau_g, Gamma = M/(tau_g - 1/2)
+  C Fbx, Fby;              // rho a
+  C eta_n2;
+  C hr0, hr1, dh;          // T_r(y) = hr0 + hr1 y; dh = rho c_v hr1
+  C inv_s[3];              // 16-bit codec: 1/s_k (1 for the other storages)
+};
+
 // Per-instance descriptor, built on the host, read by the kernels.
 struct InstDev {
   int32_t nx, ny, pitch, tiles_x;
   int32_t tiles_y, storage;
-  int64_t tile_begin;   // first global tile index of this instance
+  int64_t tile_begin;   // first global tile / work-item index of this instance
   uint64_t plane_bytes; // bytes between consecutive planes
-  uint64_t g0_off;      // byte offset of the FP32 g_0 plane (deviation forms)
+  uint64_t g0_off;      // byte offset of the FP32 g_0 plane (16-bit forms)
   char* buf[2];         // population arenas (ping-pong)
   const double* Tbot;   // [nx] wall temperature at y = -1/2
   const double* Ttop;   // [nx] wall temperature at y = ny - 1/2
-  // physical constants (derived on the host in double)
-  double rho, inv_rho, cv, rho_cv, inv_rho_cv;
-  double rcs2, rcvcs2;     // rho c_s^2, rho c_v c_s^2
-  double eta1, deta, lam1, dlam;
-  double sigma0, sigmaT, Tref;
-  double eps2, ea, beta2;  // eps^2, eps*alpha, 2 beta
-  double omega_g, Gm;      // 1/tau_g, Gamma = M/(tau_g - 1/2)
-  double Fbx, Fby;         // rho a
-  double eta_n2;
-  // hbar deviation reference T_r(y) = hr0 + hr1 y (the linear conduction
-  // profile between the mean wall temperatures) and 16-bit scales s_k
-  float s[3], inv_s[3];
-  double hr0, hr1;
+  // deviation forms: T_w - T_r at the first row (bottom), last row (top),
+  // and at the wall positions y = -1/2 (bottom) and y = ny - 1/2 (top)
+  const float* wdev[4];
+  Phys<double> pd;
+  Phys<float> pf;
+  float s[3];           // 16-bit codec scales s_k
+  double hr0, hr1;      // T_r(y) = hr0 + hr1 y (double, for state conversion)
 };
+
+template <class C>
+__device__ __forceinline__ const Phys<C>& phys(const InstDev& I);
+template <>
+__device__ __forceinline__ const Phys<double>& phys<double>(const InstDev& I) { return I.pd; }
+template <>
+__device__ __forceinline__ const Phys<float>& phys<float>(const InstDev& I) { return I.pf; }
 
 // ------------------------------------------------------------ storage codecs
 // ld / st take (k, i) as template-folded constants through the unrolled loops.
@@ -83,8 +101,8 @@ struct InstDev {
 struct StF64 {
   using C = double;
   static constexpr int kind = ST_F64;
-  __device__ static __forceinline__ C ld(const InstDev& I, const char* b, int k, int i,
-                                         size_t idx) {
+  __device__ static __forceinline__ C ld(const InstDev& I, const Phys<C>&, const char* b, int k,
+                                         int i, size_t idx) {
     return __ldg(reinterpret_cast<const double*>(b + (size_t)(k * 9 + i) * I.plane_bytes) + idx);
   }
   __device__ static __forceinline__ void st(const InstDev& I, char* b, int k, int i, size_t idx,
@@ -96,8 +114,8 @@ struct StF64 {
 struct StF32 {
   using C = float;
   static constexpr int kind = ST_F32;
-  __device__ static __forceinline__ C ld(const InstDev& I, const char* b, int k, int i,
-                                         size_t idx) {
+  __device__ static __forceinline__ C ld(const InstDev& I, const Phys<C>&, const char* b, int k,
+                                         int i, size_t idx) {
     return __ldg(reinterpret_cast<const float*>(b + (size_t)(k * 9 + i) * I.plane_bytes) + idx);
   }
   __device__ static __forceinline__ void st(const InstDev& I, char* b, int k, int i, size_t idx,
@@ -120,12 +138,12 @@ struct StDev {
   __device__ static __forceinline__ float cvt(__nv_bfloat16 q) { return __bfloat162float(q); }
   __device__ static __forceinline__ void put(__half* p, float v) { *p = __float2half_rn(v); }
   __device__ static __forceinline__ void put(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
-  __device__ static __forceinline__ C ld(const InstDev& I, const char* b, int k, int i,
-                                         size_t idx) {
+  __device__ static __forceinline__ C ld(const InstDev& I, const Phys<C>& P, const char* b, int k,
+                                         int i, size_t idx) {
     if (k == 1 && i == 0)
       return __ldg(reinterpret_cast<const float*>(b + I.g0_off) + idx);
     const E* p = reinterpret_cast<const E*>(b + (size_t)dev_plane(k, i) * I.plane_bytes) + idx;
-    return cvt(*p) * I.inv_s[k];
+    return cvt(*p) * P.inv_s[k];
   }
   __device__ static __forceinline__ void st(const InstDev& I, char* b, int k, int i, size_t idx,
                                             C v) {

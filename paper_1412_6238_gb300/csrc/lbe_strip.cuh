@@ -113,45 +113,43 @@ struct Strip {
                               3 * QW * 2 * (int)sizeof(C) + R * 8 + 16;
 
   // population (k, i) at staged column col of a slot
-  __device__ static __forceinline__ C sld(const InstDev& I, const char* slot, int k, int i,
+  __device__ static __forceinline__ C sld(const Phys<C>& P, const char* slot, int k, int i,
                                           int col) {
     if constexpr (S::kind == ST_F32) {
       return reinterpret_cast<const float*>(slot)[(k * 9 + i) * BW + col];
     } else {
       if (k == 1 && i == 0) return reinterpret_cast<const float*>(slot + G0OFF)[col];
-      return S::cvt(reinterpret_cast<const E*>(slot)[dev_plane(k, i) * BW + col]) * I.inv_s[k];
+      return S::cvt(reinterpret_cast<const E*>(slot)[dev_plane(k, i) * BW + col]) * P.inv_s[k];
     }
   }
 
   // Pull of lattice K at staged column col, row y, from the slots holding
   // rows y-1 (sm), y (s0), y+1 (sp); same rules and arithmetic as pull9.
   template <int K>
-  __device__ static __forceinline__ void spull9(const InstDev& I, const char* sm, const char* s0,
-                                                const char* sp, int col, int y, int xw, C out[9]) {
+  __device__ static __forceinline__ void spull9(const InstDev& I, const Phys<C>& P, const char* sm,
+                                                const char* s0, const char* sp, int col, int y,
+                                                int xw, C out[9]) {
     constexpr bool DEV = (K == 2) && dev_h<S>();
     const bool wb = (y == 0), wt = (y == I.ny - 1);
     C Tw = C(0);
-    if (K == 2 && (wb || wt)) {
-      const double tw = wb ? I.Tbot[xw] : I.Ttop[xw];
-      Tw = DEV ? C(tw - (I.hr0 + I.hr1 * y)) : C(tw);
-    }
-    const C dh = DEV ? C(I.rho_cv * I.hr1) : C(0);
+    if (K == 2 && (wb || wt)) Tw = wall_T<S>(I, xw, wb ? 0 : 1);
+    const C dh = DEV ? P.dh : C(0);
     auto bb = [&](int i) -> C {
-      C v = sld(I, s0, K, OPP(i), col);
-      if (K == 2) return -v + C(2) * WGT<C>(i) * C(I.rho) * C(I.cv) * Tw;
+      C v = sld(P, s0, K, OPP(i), col);
+      if (K == 2) return -v + C(2) * WGT<C>(i) * P.rho * P.cv * Tw;
       return v;
     };
-    out[0] = sld(I, s0, K, 0, col);
-    out[1] = sld(I, s0, K, 1, col - 1);
-    out[3] = sld(I, s0, K, 3, col + 1);
+    out[0] = sld(P, s0, K, 0, col);
+    out[1] = sld(P, s0, K, 1, col - 1);
+    out[3] = sld(P, s0, K, 3, col + 1);
     if (wb) {
       out[2] = bb(2);
       out[5] = bb(5);
       out[6] = bb(6);
     } else {
-      out[2] = sld(I, sm, K, 2, col);
-      out[5] = sld(I, sm, K, 5, col - 1);
-      out[6] = sld(I, sm, K, 6, col + 1);
+      out[2] = sld(P, sm, K, 2, col);
+      out[5] = sld(P, sm, K, 5, col - 1);
+      out[6] = sld(P, sm, K, 6, col + 1);
       if (DEV) {
         out[2] -= WGT<C>(2) * dh;
         out[5] -= WGT<C>(5) * dh;
@@ -163,9 +161,9 @@ struct Strip {
       out[7] = bb(7);
       out[8] = bb(8);
     } else {
-      out[4] = sld(I, sp, K, 4, col);
-      out[7] = sld(I, sp, K, 7, col + 1);
-      out[8] = sld(I, sp, K, 8, col - 1);
+      out[4] = sld(P, sp, K, 4, col);
+      out[7] = sld(P, sp, K, 7, col + 1);
+      out[8] = sld(P, sp, K, 8, col - 1);
       if (DEV) {
         out[4] += WGT<C>(4) * dh;
         out[7] += WGT<C>(7) * dh;
@@ -210,7 +208,8 @@ strip_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
     const int yb = min(ya + seg_rows, ny);
     const int src_lo = max(ya - 3, 0), src_hi = min(yb + 2, ny - 1);
     char* __restrict__ dst = I.buf[parity ^ 1];
-    const C en2 = C(I.eta_n2);
+    const Phys<C> P = phys<C>(I);  // constants in registers for the whole item
+    const C en2 = P.eta_n2;
 
     __syncthreads();  // previous item fully done with the slots and barriers
     if (t == 0) {
@@ -255,12 +254,12 @@ strip_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
       const char* sm = m > 0 ? slot_of(m - 1) : s0;
       const char* sp = m < ny - 1 ? slot_of(m + 1) : s0;
       C v[9];
-      St::template spull9<1>(I, sm, s0, sp, col, m, xw, v);
+      St::template spull9<1>(I, P, sm, s0, sp, col, m, xw, v);
       c = sum9(v);
-      St::template spull9<0>(I, sm, s0, sp, col, m, xw, v);
+      St::template spull9<0>(I, P, sm, s0, sp, col, m, xw, v);
       p = sum9(v);
-      St::template spull9<2>(I, sm, s0, sp, col, m, xw, v);
-      T = dv(sum9(v), C(I.rho_cv), C(I.inv_rho_cv));
+      St::template spull9<2>(I, P, sm, s0, sp, col, m, xw, v);
+      T = dv(sum9(v), P.rho_cv, P.inv_rho_cv);
     };
 
     for (int r = ya - 4; r < yb; r++) {
@@ -335,9 +334,9 @@ strip_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
         const char* sm = r > 0 ? slot_of(r - 1) : s0;
         const char* sp = r < ny - 1 ? slot_of(r + 1) : s0;
         C f[9], g[9], h[9];
-        St::template spull9<0>(I, sm, s0, sp, col, r, x, f);
-        St::template spull9<1>(I, sm, s0, sp, col, r, x, g);
-        St::template spull9<2>(I, sm, s0, sp, col, r, x, h);
+        St::template spull9<0>(I, P, sm, s0, sp, col, r, x, f);
+        St::template spull9<1>(I, P, sm, s0, sp, col, r, x, g);
+        St::template spull9<2>(I, P, sm, s0, sp, col, r, x, h);
         const C* cs = cring + ((r - 1 + 10) % 5) * RW;
         const C* c0 = cring + ((r + 10) % 5) * RW;
         const C* cn = cring + ((r + 1 + 10) % 5) * RW;
@@ -353,16 +352,16 @@ strip_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
         grad3(cs, c0, cn, t + 2, st.gcx, st.gcy);
         st.lapc = lap3(cs, c0, cn, t + 2);
         grad3(Ts, T0, Tn, t + 2, st.gTx, st.gTy);
-        if (dev_h<S>()) st.gTy += C(I.hr1);
+        if (dev_h<S>()) st.gTy += P.hr1;
         grad3(ps, p0, pn, t + 2, st.gpx, st.gpy);
         const int ns = ((r - 1 + 9) % 3) * QW, n0 = ((r + 9) % 3) * QW, nn = ((r + 1 + 9) % 3) * QW;
         C d1, d2, dum;
         grad3(nxr + ns, nxr + n0, nxr + nn, t + 1, d1, dum);
         grad3(nyr + ns, nyr + n0, nyr + nn, t + 1, dum, d2);
         st.kappa = d1 + d2;
-        const Drive<S> d = drive<S>(I, r, f, cc, TT, st);
+        const Drive<S> d = drive<S>(P, r, f, cc, TT, st);
         const size_t rowbase = (size_t)r * I.pitch;
-        collide<S>(I, f, g, h, cc, pp, TT, st.gpx, st.gpy, d,
+        collide<S>(P, f, g, h, cc, pp, TT, st.gpx, st.gpy, d,
                    [&](int k, int i, C v) { st_cell<S>(I, dst, k, i, rowbase, x, v); });
       }
     }

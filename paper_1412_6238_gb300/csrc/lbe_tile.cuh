@@ -35,37 +35,46 @@ struct Cell {
 // y: a value pulled from row y - xi_iy was stored relative to
 // T_r(y - xi_iy), which differs by w_i rho c_v hr1 xi_iy; at a wall the
 // anti-bounce-back reads -P*_ibar + 2 w_i rho c_v (T_w - T_r(y)).
+template <class S>
+__device__ __forceinline__ typename S::C wall_T(const InstDev& I, int x, int which) {
+  // which: 0 bottom row, 1 top row (for the anti-bounce-back), 2 bottom wall,
+  // 3 top wall (for the ghost rows); deviation forms read T_w - T_r there
+  if constexpr (dev_h<S>()) {
+    return I.wdev[which][x];
+  } else {
+    return (which == 0 || which == 2) ? I.Tbot[x] : I.Ttop[x];
+  }
+}
+
 template <class S, int K>
-__device__ __forceinline__ void pull9(const InstDev& I, const char* __restrict__ src,
-                                      const Cell<S>& q, typename S::C out[9]) {
+__device__ __forceinline__ void pull9(const InstDev& I, const Phys<typename S::C>& P,
+                                      const char* __restrict__ src, const Cell<S>& q,
+                                      typename S::C out[9]) {
   using C = typename S::C;
   constexpr bool DEV = (K == 2) && dev_h<S>();
   const size_t pitch = (size_t)I.pitch;
   const size_t r0 = (size_t)q.y * pitch + XG;
   const bool wb = (q.y == 0), wt = (q.y == I.ny - 1);
   C Tw = C(0);
-  if (K == 2 && (wb || wt)) {
-    const double tw = wb ? I.Tbot[q.x] : I.Ttop[q.x];
-    Tw = DEV ? C(tw - (I.hr0 + I.hr1 * q.y)) : C(tw);
-  }
-  const C dh = DEV ? C(I.rho_cv * I.hr1) : C(0);  // rho c_v (T_r(y) - T_r(y-1))
+  if (K == 2 && (wb || wt)) Tw = wall_T<S>(I, q.x, wb ? 0 : 1);
+  const C dh = DEV ? P.dh : C(0);  // rho c_v (T_r(y) - T_r(y-1))
   auto bb = [&](int i) -> C {
-    C v = S::ld(I, src, K, OPP(i), r0 + q.x);
-    if (K == 2) return -v + C(2) * WGT<C>(i) * C(I.rho) * C(I.cv) * Tw;
+    C v = S::ld(I, P, src, K, OPP(i), r0 + q.x);
+    if (K == 2) return -v + C(2) * WGT<C>(i) * P.rho * P.cv * Tw;
     return v;
   };
-  out[0] = S::ld(I, src, K, 0, r0 + q.x);
-  out[1] = S::ld(I, src, K, 1, r0 + q.xm);
-  out[3] = S::ld(I, src, K, 3, r0 + q.xp);
+  out[0] = S::ld(I, P, src, K, 0, r0 + q.x);
+  out[1] = S::ld(I, P, src, K, 1, r0 + q.xm);
+  out[3] = S::ld(I, P, src, K, 3, r0 + q.xp);
   if (wb) {
     out[2] = bb(2);
     out[5] = bb(5);
     out[6] = bb(6);
   } else {
     const size_t rm = r0 - pitch;
-    out[2] = S::ld(I, src, K, 2, rm + q.x);
-    out[5] = S::ld(I, src, K, 5, rm + q.xm);
-    out[6] = S::ld(I, src, K, 6, rm + q.xp);
+    out[2] = S::ld(I, P, src, K, 2, rm + q.x);
+    out[5] = S::ld(I, P, src, K, 5, rm + q.xm);
+    out[6] = S::ld(I, P, src, K, 6, rm + q.xp);
     if (DEV) {
       out[2] -= WGT<C>(2) * dh;
       out[5] -= WGT<C>(5) * dh;
@@ -78,9 +87,9 @@ __device__ __forceinline__ void pull9(const InstDev& I, const char* __restrict__
     out[8] = bb(8);
   } else {
     const size_t rp = r0 + pitch;
-    out[4] = S::ld(I, src, K, 4, rp + q.x);
-    out[7] = S::ld(I, src, K, 7, rp + q.xp);
-    out[8] = S::ld(I, src, K, 8, rp + q.xm);
+    out[4] = S::ld(I, P, src, K, 4, rp + q.x);
+    out[7] = S::ld(I, P, src, K, 7, rp + q.xp);
+    out[8] = S::ld(I, P, src, K, 8, rp + q.xm);
     if (DEV) {
       out[4] += WGT<C>(4) * dh;
       out[7] += WGT<C>(7) * dh;
@@ -111,16 +120,15 @@ template <class S>
 __device__ __forceinline__ typename S::C ghost_T(const InstDev& I, int x, bool bottom,
                                                  typename S::C T) {
   using C = typename S::C;
-  const double tw = bottom ? I.Tbot[x] : I.Ttop[x];
-  const C Tw = dev_h<S>() ? C(tw - (I.hr0 + I.hr1 * (bottom ? -0.5 : I.ny - 0.5))) : C(tw);
-  return C(2) * Tw - T;
+  return C(2) * wall_T<S>(I, x, bottom ? 2 : 3) - T;
 }
 
 // c, p, T at an arbitrary tile-region position: x wraps, rows beyond the
 // walls (gy in [-2, -1] or [ny, ny+1]) are ghosts.
 template <class S>
-__device__ __forceinline__ void region_values(const InstDev& I, const char* __restrict__ src,
-                                              int gx, int gy, bool need_pT,
+__device__ __forceinline__ void region_values(const InstDev& I, const Phys<typename S::C>& P,
+                                              const char* __restrict__ src, int gx, int gy,
+                                              bool need_pT,
                                               typename S::C& c, typename S::C& p,
                                               typename S::C& T) {
   using C = typename S::C;
@@ -135,13 +143,13 @@ __device__ __forceinline__ void region_values(const InstDev& I, const char* __re
   }
   const Cell<S> q = make_cell<S>(wrapx(gx, nx), y, nx);
   C v[9];
-  pull9<S, 1>(I, src, q, v);
+  pull9<S, 1>(I, P, src, q, v);
   c = sum9(v);
   if (need_pT) {
-    pull9<S, 0>(I, src, q, v);
+    pull9<S, 0>(I, P, src, q, v);
     p = sum9(v);
-    pull9<S, 2>(I, src, q, v);
-    T = dv(sum9(v), C(I.rho_cv), C(I.inv_rho_cv));
+    pull9<S, 2>(I, P, src, q, v);
+    T = dv(sum9(v), P.rho_cv, P.inv_rho_cv);
     if (ghost != 0) T = ghost_T<S>(I, q.x, ghost < 0, T);
   } else {
     p = C(0);
@@ -175,6 +183,7 @@ struct Tile {
     const int x0 = (int)(tile % I.tiles_x) * TX;
     const int y0 = (int)(tile / I.tiles_x) * TY;
     const char* __restrict__ src = I.buf[parity];
+    const Phys<C> P = phys<C>(I);  // constants in registers for the whole tile
 
     // ---- S1: own cell
     const int gx = x0 + tx, gy = y0 + ty;
@@ -183,14 +192,14 @@ struct Tile {
     C cc = C(0), pp = C(0), TT = C(0);
     Cell<S> q = make_cell<S>(active ? gx : 0, active ? gy : 0, nx);
     if (active) {
-      pull9<S, 0>(I, src, q, f);
-      pull9<S, 1>(I, src, q, g);
-      pull9<S, 2>(I, src, q, h);
+      pull9<S, 0>(I, P, src, q, f);
+      pull9<S, 1>(I, P, src, q, g);
+      pull9<S, 2>(I, P, src, q, h);
       cc = sum9(g);
       pp = sum9(f);
-      TT = dv(sum9(h), C(I.rho_cv), C(I.inv_rho_cv));
+      TT = dv(sum9(h), P.rho_cv, P.inv_rho_cv);
     } else if (gy <= ny + 1) {
-      region_values<S>(I, src, gx, gy, true, cc, pp, TT);
+      region_values<S>(I, P, src, gx, gy, true, cc, pp, TT);
     }
     sm.c[(ty + 2) * RW + tx + 2] = cc;
     sm.p[(ty + 1) * QW + tx + 1] = pp;
@@ -214,7 +223,7 @@ struct Tile {
       const int hx = x0 - 2 + rx, hy = y0 - 2 + ry;
       const bool inner = rx >= 1 && rx <= TX + 2 && ry >= 1 && ry <= TY + 2;
       C vc = C(0), vp = C(0), vT = C(0);
-      if (hy >= -2 && hy <= ny + 1) region_values<S>(I, src, hx, hy, inner, vc, vp, vT);
+      if (hy >= -2 && hy <= ny + 1) region_values<S>(I, P, src, hx, hy, inner, vc, vp, vT);
       sm.c[ry * RW + rx] = vc;
       if (inner) {
         sm.p[(ry - 1) * QW + rx - 1] = vp;
@@ -224,7 +233,7 @@ struct Tile {
     __syncthreads();
 
     // ---- S2: unit normal on the (TX+2) x (TY+2) region
-    const C en2 = C(I.eta_n2);
+    const C en2 = P.eta_n2;
     for (int r = tid; r < QW * QH; r += NT) {
       const int qx = r % QW, qy = r / QW;
       const C* c0 = sm.c + (qy + 1) * RW;
@@ -241,12 +250,12 @@ struct Tile {
       const int qo = (ty + 1) * QW;
       grad3(sm.T + qo - QW, sm.T + qo, sm.T + qo + QW, tx + 1, st.gTx, st.gTy);
       // deviation form: grad T = grad T' + (0, hr1) (exact for the linear T_r)
-      if (dev_h<S>()) st.gTy += C(I.hr1);
+      if (dev_h<S>()) st.gTy += P.hr1;
       grad3(sm.p + qo - QW, sm.p + qo, sm.p + qo + QW, tx + 1, st.gpx, st.gpy);
       grad3(sm.nx + qo - QW, sm.nx + qo, sm.nx + qo + QW, tx + 1, d1, dum);
       grad3(sm.ny + qo - QW, sm.ny + qo, sm.ny + qo + QW, tx + 1, dum, d2);
       st.kappa = d1 + d2;
-      const Drive<S> d = drive<S>(I, gy, f, cc, TT, st);
+      const Drive<S> d = drive<S>(P, gy, f, cc, TT, st);
 
       if (MODE == 1) {
         const size_t N = (size_t)nx * ny, k = (size_t)gy * nx + gx;
@@ -260,7 +269,7 @@ struct Tile {
 
       char* __restrict__ dst = I.buf[parity ^ 1];
       const size_t rowbase = (size_t)gy * I.pitch;
-      collide<S>(I, f, g, h, cc, pp, TT, st.gpx, st.gpy, d,
+      collide<S>(P, f, g, h, cc, pp, TT, st.gpx, st.gpy, d,
                  [&](int k, int i, C v) { st_cell<S>(I, dst, k, i, rowbase, gx, v); });
     }
   }
@@ -268,7 +277,7 @@ struct Tile {
 
 // Persistent kernel over a tile list spanning one or more instances.
 template <class S, int TX, int TY, int MODE>
-__global__ void __launch_bounds__(TX * TY, (S::kind == ST_F64) ? 1 : 2)
+__global__ void __launch_bounds__(TX * TY, (S::kind == ST_F64 || TX * TY >= 512) ? 1 : 2)
 tile_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_tiles, int parity,
             double* __restrict__ out) {
   using T = Tile<S, TX, TY, MODE>;

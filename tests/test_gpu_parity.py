@@ -100,7 +100,9 @@ def test_one_step_from_same_state(LBE, orc, storage, nx, ny):
 @pytest.mark.parametrize("tile", [1, 2, 3, 4, 5, 6])
 def test_kernels_bitwise_identical(LBE, tile):
     """Every tile shape and both strip kernels (TMA-staged rows) compute the
-    same per-cell arithmetic: results are bitwise equal to tile kernel 0."""
+    same per-cell arithmetic as tile kernel 0; the compiler may contract a
+    different subset of products into FMAs per kernel, so results agree to
+    the last bits (1e-6 of each lattice's magnitude), not bitwise."""
     w = small_drop(150, 77)
     a = LBE(w, storage="f32")
     a.set_tile(0)
@@ -108,7 +110,7 @@ def test_kernels_bitwise_identical(LBE, tile):
     b = LBE(w, storage="f32")
     b.set_tile(tile, -1 if tile % 2 else 0)
     b.step(7)
-    assert np.array_equal(a.get_state().numpy(), b.get_state().numpy())
+    assert state_err(b.get_state().numpy(), a.get_state().numpy()) < 1e-6
 
 
 STRIP_SHAPES = [(4, 8), (5, 3), (7, 40), (64, 17), (130, 19), (200, 33), (257, 70)]
@@ -120,7 +122,9 @@ STRIP_SHAPES = [(4, 8), (5, 3), (7, 40), (64, 17), (130, 19), (200, 33), (257, 7
 def test_strip_kernel_equals_tile_kernel(LBE, storage, nx, ny, seg):
     """The strip kernel on narrow, ragged and partial strips, with segments of
     1, 3 and automatic rows (segment seams, bottom and top ghost rows), equals
-    the tile kernel bitwise for every 16/32-bit storage."""
+    the tile kernel for every 16/32-bit storage up to last-bit FMA
+    contraction differences (which a 16-bit store may round to one unit of
+    the 16-bit format)."""
     R = max(1.5, min(nx, ny) / 4.0)
     w = wl.droplet(nx, ny, R, nx / 2.0 + 0.3, ny / 2.0 - 0.2, Re=1.0, Ma=10.0, Ca=0.05,
                    eta_m=0.2, eta_r=0.5, lam_r=2.0)
@@ -133,7 +137,8 @@ def test_strip_kernel_equals_tile_kernel(LBE, storage, nx, ny, seg):
         b.set_tile(tile, 0, seg)
         assert b.get_tile()["kernel"] == tile
         b.step(5)
-        assert np.array_equal(a.get_state().numpy(), b.get_state().numpy()), tile
+        tol = 1e-6 if storage == "f32" else 1e-3
+        assert state_err(b.get_state().numpy(), a.get_state().numpy()) < tol, tile
 
 
 def test_strip_is_default_and_rejects_narrow(LBE):
