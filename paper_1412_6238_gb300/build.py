@@ -20,9 +20,11 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 UNITS = {
     "lbe_step_f64.cu": ["-fmad=false"],
-    "lbe_step_f32.cu": [],
-    "lbe_step_f16.cu": [],
-    "lbe_step_bf16.cu": [],
+    # FP32 arithmetic: division and square root to within 2 ulp (a few
+    # instructions instead of the IEEE-rounded sequences)
+    "lbe_step_f32.cu": ["-prec-div=false", "-prec-sqrt=false"],
+    "lbe_step_f16.cu": ["-prec-div=false", "-prec-sqrt=false"],
+    "lbe_step_bf16.cu": ["-prec-div=false", "-prec-sqrt=false"],
     "lbe_aux.cu": ["-fmad=false"],
     "lbe_api.cu": ["-Xcompiler", "-ffp-contract=off"],
     "lbe_noalloc.cu": ["-fmad=false"],

@@ -246,9 +246,15 @@ strip_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
       }
       return true;
     };
-    auto slot_of = [&](int q) -> const char* { return slots + ((q - src_lo) % R) * St::SLOT; };
+    auto slot_of = [&](int q) -> const char* {
+      int d = (q - src_lo) % R;
+      if (d < 0) d += R;
+      return slots + d * St::SLOT;
+    };
+    auto ring5 = [](int m) { return ((m % 5) + 5) % 5; };
+    auto ring3 = [](int m) { return ((m % 3) + 3) % 3; };
 
-    // moments of row m (0 <= m < ny) at staged column col into ring row ridx
+    // moments c, p, T of row m (0 <= m < ny) at staged column col
     auto moments = [&](int m, int col, int xw, C& c, C& p, C& T) {
       const char* s0 = slot_of(m);
       const char* sm = m > 0 ? slot_of(m - 1) : s0;
@@ -262,6 +268,24 @@ strip_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
       T = dv(sum9(v), P.rho_cv, P.inv_rho_cv);
     };
 
+    // per-thread constants of the item: own column and the halo columns the
+    // edge threads also compute
+    const int x = x0 + t;
+    const bool own_active = x < nx;
+    const bool edge_ghost = own_active && (x < XG || x >= nx - XG);
+    int rcs[3], nrc = 0;
+    rcs[nrc++] = t + 2;
+    if (t == 0) {
+      rcs[nrc++] = 0;
+      rcs[nrc++] = 1;
+    } else if (t == NC - 1) {
+      rcs[nrc++] = NC + 2;
+      rcs[nrc++] = NC + 3;
+    }
+    int xws[3];
+    for (int j = 0; j < nrc; j++) xws[j] = wrapx(x0 - 2 + rcs[j], nx);
+    const size_t pitch = (size_t)I.pitch;
+
     for (int r = ya - 4; r < yb; r++) {
       __syncthreads();
       if (s_abort) break;
@@ -270,42 +294,28 @@ strip_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
       // ---- moments of row m = r + 2 at ring columns t+2 (+ halo columns)
       const int m = r + 2;
       if (m <= yb + 1) {
-        const int ridx = (m + 10) % 5;
+        const int ridx = ring5(m) * RW;
         if (m < ny) {
           const int mr = m >= 0 ? m : -1 - m;  // bottom ghost rows: the mirror row
-          const bool ok = wait_upto(mr + 1);
-          if (ok) {
-            // own column (ring column t+2) and, for the edge threads, the two
-            // halo columns on their side
-            int rcs[3], nrc = 0;
-            rcs[nrc++] = t + 2;
-            if (t == 0) {
-              rcs[nrc++] = 0;
-              rcs[nrc++] = 1;
-            } else if (t == NC - 1) {
-              rcs[nrc++] = NC + 2;
-              rcs[nrc++] = NC + 3;
-            }
+          if (wait_upto(mr + 1)) {
             for (int j = 0; j < nrc; j++) {
               const int rc = rcs[j];
-              const int xw = wrapx(x0 - 2 + rc, nx);
               C c, p, T;
-              moments(mr, rc - 2 + XG, xw, c, p, T);
-              if (m < 0) T = ghost_T<S>(I, xw, true, T);
-              cring[ridx * RW + rc] = c;
-              pring[ridx * RW + rc] = p;
-              Tring[ridx * RW + rc] = T;
+              moments(mr, rc - 2 + XG, xws[j], c, p, T);
+              if (m < 0) T = ghost_T<S>(I, xws[j], true, T);
+              cring[ridx + rc] = c;
+              pring[ridx + rc] = p;
+              Tring[ridx + rc] = T;
             }
           }
         } else {
           // top ghost rows from the mirror rows still in the ring
-          const int mr = 2 * ny - 1 - m;
-          const int sidx = (mr + 10) % 5;
+          const int sidx = ring5(2 * ny - 1 - m) * RW;
           for (int rc = t; rc < RW; rc += NC) {
             const int xw = wrapx(x0 - 2 + rc, nx);
-            cring[ridx * RW + rc] = cring[sidx * RW + rc];
-            pring[ridx * RW + rc] = pring[sidx * RW + rc];
-            Tring[ridx * RW + rc] = ghost_T<S>(I, xw, false, Tring[sidx * RW + rc]);
+            cring[ridx + rc] = cring[sidx + rc];
+            pring[ridx + rc] = pring[sidx + rc];
+            Tring[ridx + rc] = ghost_T<S>(I, xw, false, Tring[sidx + rc]);
           }
         }
       }
@@ -315,10 +325,10 @@ strip_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
       // ---- unit normal of row r + 1 at normal-ring columns t+1 (+ halo)
       const int mn = r + 1;
       if (mn >= ya - 1 && mn <= yb) {
-        const C* cs = cring + ((mn - 1 + 10) % 5) * RW;
-        const C* c0 = cring + ((mn + 10) % 5) * RW;
-        const C* cn = cring + ((mn + 1 + 10) % 5) * RW;
-        const int nidx = ((mn + 9) % 3) * QW;
+        const C* cs = cring + ring5(mn - 1) * RW;
+        const C* c0 = cring + ring5(mn) * RW;
+        const C* cn = cring + ring5(mn + 1) * RW;
+        const int nidx = ring3(mn) * QW;
         normal3(cs, c0, cn, t + 2, en2, nxr[nidx + t + 1], nyr[nidx + t + 1]);
         if (t == 0) normal3(cs, c0, cn, 1, en2, nxr[nidx], nyr[nidx]);
         if (t == NC - 1) normal3(cs, c0, cn, NC + 2, en2, nxr[nidx + NC + 1], nyr[nidx + NC + 1]);
@@ -327,8 +337,7 @@ strip_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
       if (s_abort) break;
 
       // ---- collide row r at column x0 + t
-      const int x = x0 + t;
-      if (r >= ya && x < nx) {
+      if (r >= ya && own_active) {
         const int col = t + XG;
         const char* s0 = slot_of(r);
         const char* sm = r > 0 ? slot_of(r - 1) : s0;
@@ -337,32 +346,42 @@ strip_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
         St::template spull9<0>(I, P, sm, s0, sp, col, r, x, f);
         St::template spull9<1>(I, P, sm, s0, sp, col, r, x, g);
         St::template spull9<2>(I, P, sm, s0, sp, col, r, x, h);
-        const C* cs = cring + ((r - 1 + 10) % 5) * RW;
-        const C* c0 = cring + ((r + 10) % 5) * RW;
-        const C* cn = cring + ((r + 1 + 10) % 5) * RW;
+        const int rs5 = ring5(r - 1) * RW, r05 = ring5(r) * RW, rn5 = ring5(r + 1) * RW;
+        const C* cs = cring + rs5;
+        const C* c0 = cring + r05;
+        const C* cn = cring + rn5;
         const C cc = c0[t + 2];
-        const C* ps = pring + ((r - 1 + 10) % 5) * RW;
-        const C* p0 = pring + ((r + 10) % 5) * RW;
-        const C* pn = pring + ((r + 1 + 10) % 5) * RW;
-        const C* Ts = Tring + ((r - 1 + 10) % 5) * RW;
-        const C* T0 = Tring + ((r + 10) % 5) * RW;
-        const C* Tn = Tring + ((r + 1 + 10) % 5) * RW;
-        const C pp = p0[t + 2], TT = T0[t + 2];
+        const C pp = pring[r05 + t + 2], TT = Tring[r05 + t + 2];
         Stencils<C> st;
         grad3(cs, c0, cn, t + 2, st.gcx, st.gcy);
         st.lapc = lap3(cs, c0, cn, t + 2);
-        grad3(Ts, T0, Tn, t + 2, st.gTx, st.gTy);
+        grad3(Tring + rs5, Tring + r05, Tring + rn5, t + 2, st.gTx, st.gTy);
         if (dev_h<S>()) st.gTy += P.hr1;
-        grad3(ps, p0, pn, t + 2, st.gpx, st.gpy);
-        const int ns = ((r - 1 + 9) % 3) * QW, n0 = ((r + 9) % 3) * QW, nn = ((r + 1 + 9) % 3) * QW;
+        grad3(pring + rs5, pring + r05, pring + rn5, t + 2, st.gpx, st.gpy);
+        const int ns = ring3(r - 1) * QW, n0 = ring3(r) * QW, nn = ring3(r + 1) * QW;
         C d1, d2, dum;
         grad3(nxr + ns, nxr + n0, nxr + nn, t + 1, d1, dum);
         grad3(nyr + ns, nyr + n0, nyr + nn, t + 1, dum, d2);
         st.kappa = d1 + d2;
         const Drive<S> d = drive<S>(P, r, f, cc, TT, st);
-        const size_t rowbase = (size_t)r * I.pitch;
+        C o[27];
         collide<S>(P, f, g, h, cc, pp, TT, st.gpx, st.gpy, d,
-                   [&](int k, int i, C v) { st_cell<S>(I, dst, k, i, rowbase, x, v); });
+                   [&](int k, int i, C v) { o[k * 9 + i] = v; });
+        const size_t e0 = (size_t)r * pitch + XG + x;
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+#pragma unroll
+          for (int i = 0; i < 9; i++) S::st(I, dst, k, i, e0, o[k * 9 + i]);
+        if (edge_ghost) {
+          // periodic ghost copies of the first / last XG cells of the row
+#pragma unroll
+          for (int k = 0; k < 3; k++)
+#pragma unroll
+            for (int i = 0; i < 9; i++) {
+              if (x < XG) S::st(I, dst, k, i, e0 + nx, o[k * 9 + i]);
+              if (x >= nx - XG) S::st(I, dst, k, i, e0 - nx, o[k * 9 + i]);
+            }
+        }
       }
     }
     __syncthreads();
