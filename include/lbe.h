@@ -168,7 +168,7 @@ lbe_status lbe_load(lbe_handle* h, const char* path);
 /* Step-kernel choice (autotuner hook).  Kernel ids 0 .. lbe_num_tiles()-1:
  * ids whose shape has ty > 0 are the tile kernel with TX x TY cells per CTA
  * (any storage; FP64 provides id 0 only); ids with ty == 0 are the strip
- * kernel with TX columns per CTA marching over rows with TMA-staged rows
+ * kernel with TX output columns per CTA marching over rows with TMA-staged rows
  * (16/32-bit storages, every instance at least 4 columns wide; the default
  * there).  grid_ctas: persistent grid size (0 = resident CTAs x SMs, -1 = one
  * CTA per work item).  seg_rows: rows per strip work item (0 = about two

@@ -270,13 +270,13 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// Tensor maps of instance j for the strip kernel with NC columns: box of
-// NC + 2 XG elements in x, one row, all population planes.
+// Tensor maps of instance j for the strip kernel with nc threads: box of
+// strip_bw(nc) elements in x, one row, all population planes.
 lbe_status encode_maps(lbe_handle* h, int j, int nc, TmapSet& T) {
   auto enc = encode_fn();
   if (!enc) return fail(h, LBE_ECUDA, "cuTensorMapEncodeTiled is not available");
   const InstHost& H = h->inst[j];
-  const cuuint32_t bw = (cuuint32_t)(nc + 2 * XG);
+  const cuuint32_t bw = (cuuint32_t)strip_bw(nc, h->storage >= LBE_F16DEV ? 2 : 4);
   memset(&T, 0, sizeof T);
   for (int b = 0; b < 2; b++) {
     char* base = H.arena + (size_t)b * H.buf_bytes;
@@ -310,23 +310,33 @@ lbe_status encode_maps(lbe_handle* h, int j, int nc, TmapSet& T) {
 // (Re)build the step descriptors for the current tile shape and upload them.
 lbe_status setup_tiles(lbe_handle* h) {
   if (is_strip(h->tile)) {
-    const int nc = TILE_SHAPES[h->tile].tx;
+    const int nc = TILE_SHAPES[h->tile].tx;  // output columns per strip
+    const int threads = nc + 4;
     const int occ = strip_occupancy(h->storage, h->tile - STRIP_FIRST);
     if (occ <= 0) return fail(h, LBE_ECUDA, "strip kernel %d cannot be resident", h->tile);
     h->grid = h->grid_req > 0 ? h->grid_req : occ * h->num_sms;
-    int64_t rowstrips = 0;
     int max_ny = 1;
-    for (auto& H : h->inst) {
-      rowstrips += (int64_t)((H.nx + nc - 1) / nc) * H.ny;
-      max_ny = std::max(max_ny, H.ny);
-    }
+    for (auto& H : h->inst) max_ny = std::max(max_ny, H.ny);
     if (h->seg_req > 0) {
       h->seg = h->seg_req;
     } else {
-      // about two work items per resident CTA
-      const int64_t target = 2 * (int64_t)(h->grid_req == -1 ? occ * h->num_sms : h->grid);
-      int64_t seg = (rowstrips + target - 1) / target;
-      h->seg = (int)std::min<int64_t>(std::max<int64_t>(seg, 8), max_ny);
+      // rows per work item: minimise (waves of the persistent grid) x (rows
+      // per item + the 4 warm-up rows every item recomputes)
+      const int64_t slots = h->grid_req == -1 ? (int64_t)occ * h->num_sms : h->grid;
+      double best = 1e300;
+      int best_seg = max_ny;
+      for (int seg = 8; seg <= max_ny; seg++) {
+        int64_t items = 0;
+        for (auto& H : h->inst)
+          items += (int64_t)((H.nx + nc - 1) / nc) * ((H.ny + seg - 1) / seg);
+        const double waves = (double)((items + slots - 1) / slots);
+        const double cost = waves * (seg + 4);
+        if (cost < best * (1 - 1e-9)) {
+          best = cost;
+          best_seg = seg;
+        }
+      }
+      h->seg = best_seg;
     }
     std::vector<TmapSet> maps(h->n);
     int64_t begin = 0;
@@ -336,7 +346,7 @@ lbe_status setup_tiles(lbe_handle* h) {
       D.tiles_y = (D.ny + h->seg - 1) / h->seg;
       D.tile_begin = begin;
       begin += (int64_t)D.tiles_x * D.tiles_y;
-      lbe_status st = encode_maps(h, j, nc, maps[j]);
+      lbe_status st = encode_maps(h, j, threads, maps[j]);
       if (st) return st;
     }
     h->total_tiles = begin;

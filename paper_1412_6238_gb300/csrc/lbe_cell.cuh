@@ -18,14 +18,16 @@ __device__ __forceinline__ float dv(float a, float, float inv_b) { return a * in
 template <class C>
 __device__ __forceinline__ C cs2() { return C(1.0 / 3.0); }
 
-// Sum over i = 0..8 in index order (the order the moments of Eq. 13, Eq. 28
-// and Eq. aEq13 are accumulated in FP64 parity mode as well).
-template <class C>
-__device__ __forceinline__ C sum9(const C v[9]) {
-  C s = v[0];
+// Sum over i = 0..8: in index order in FP64 (the order of the FP64
+// reference), as a pairwise tree in FP32 (shorter dependency chains).
+__device__ __forceinline__ double sum9(const double v[9]) {
+  double s = v[0];
 #pragma unroll
   for (int i = 1; i < 9; i++) s += v[i];
   return s;
+}
+__device__ __forceinline__ float sum9(const float v[9]) {
+  return (((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]))) + v[8];
 }
 
 // hbar is handled as the deviation hbar_i - w_i rho c_v T_r(y) from the linear
@@ -173,28 +175,66 @@ __device__ __forceinline__ void collide(const Phys<typename S::C>& P, const type
   const C rcvT = P.rho * P.cv * (TT + d.Trow);  // rho c_v T (full T)
   const C rcvTr = P.rho_cv * d.Trow;            // rho c_v T_r(y)
   const C rcvTd = P.rho_cv * TT;                // rho c_v T'
+  if constexpr (sizeof(C) == 4) {
+    // FP32: the same terms regrouped.  With a = xi_i.u/c_s^2 and
+    // q = a + ((a^2 - u^2/c_s^2)/2), Gamma_i = w_i (1 + q); opposite
+    // directions share (a^2 - u^2/c_s^2)/2; F.(xi_i - u) = F.xi_i - F.u.
+    const C Fdu = Fx * ux + Fy * uy, Gdu = Gx * ux + Gy * uy;
+    const C sg = cc * inv_rcs2;  // c / (rho c_s^2)
+    const C ux3 = C(3) * ux, uy3 = C(3) * uy;
+    auto dir = [&](int i, C W, C a, C hq, C Fxi, C Gxi) {
+      const C q = a + hq;
+      const C G = W + W * q;
+      const C feq = W * (pp + rcs2 * q);
+      out(0, i, f[i] + omega_f * (feq - f[i]) + af * ((Fxi - Fdu) * G));
+      const C gdot = Gxi - Gdu;
+      const C geq = W * ((i == 0 ? H0 : Hi) + cc * q);
+      out(1, i, g[i] + omega_g * (geq - g[i]) + ag * (sg * gdot) * G);
+      const C heqd = dev_h<S>() ? rcvTd * G + rcvTr * (W * q) : rcvT * G;
+      out(2, i, h[i] + omega_T * (heqd - h[i]) + aT * (inv_rcs2 * gdot) * (rcvT * G));
+    };
+    const C wa = WGT<C>(1), wd = WGT<C>(5);
+    const C hu = C(-0.5) * uu;
+    dir(0, WGT<C>(0), C(0), hu, C(0), C(0));
+    C a = ux3, hq = C(0.5) * (a * a - uu);
+    dir(1, wa, a, hq, Fx, Gx);
+    dir(3, wa, -a, hq, -Fx, -Gx);
+    a = uy3;
+    hq = C(0.5) * (a * a - uu);
+    dir(2, wa, a, hq, Fy, Gy);
+    dir(4, wa, -a, hq, -Fy, -Gy);
+    a = ux3 + uy3;
+    hq = C(0.5) * (a * a - uu);
+    dir(5, wd, a, hq, Fx + Fy, Gx + Gy);
+    dir(7, wd, -a, hq, -(Fx + Fy), -(Gx + Gy));
+    a = uy3 - ux3;
+    hq = C(0.5) * (a * a - uu);
+    dir(6, wd, a, hq, Fy - Fx, Gy - Gx);
+    dir(8, wd, -a, hq, Fx - Fy, Gx - Gy);
+  } else {
 #pragma unroll
-  for (int i = 0; i < 9; i++) {
-    const C W = WGT<C>(i);
-    const C xu = dv(C(EX(i)) * ux + C(EY(i)) * uy, cs2<C>(), C(3));
-    const C hq = C(0.5) * (xu * xu - uu);
-    const C G = W * (C(1) + xu + hq);
-    const C q = xu + hq;  // velocity part, without the cancelling w_i
-    const C dx = C(EX(i)) - ux, dy = C(EY(i)) - uy;
-    // f (Eq. 12 with Eq. 5)
-    const C feq = W * (pp + rcs2 * q);
-    const C fs = (Fx * dx + Fy * dy) * G;
-    out(0, i, f[i] - omega_f * (f[i] - feq) + af * fs);
-    // g (Eq. 27 with Eq. 21-22)
-    const C geq = W * ((i == 0 ? H0 : Hi) + cc * q);
-    const C gs = dv(cc * (dx * Gx + dy * Gy), rcs2, inv_rcs2) * G;
-    out(1, i, g[i] - omega_g * (g[i] - geq) + ag * gs);
-    // hbar (Eq. aEq12 with Eq. aEq9); deviation form:
-    // h_eq - w_i rho c_v T_r = rho c_v (T' Gamma_i + T_r w_i q_i)
-    const C heq = rcvT * G;
-    const C hs = dv(Gx * dx + Gy * dy, rcs2, inv_rcs2) * heq;
-    const C heqd = dev_h<S>() ? rcvTd * G + rcvTr * (W * q) : heq;
-    out(2, i, h[i] - omega_T * (h[i] - heqd) + aT * hs);
+    for (int i = 0; i < 9; i++) {
+      const C W = WGT<C>(i);
+      const C xu = dv(C(EX(i)) * ux + C(EY(i)) * uy, cs2<C>(), C(3));
+      const C hq = C(0.5) * (xu * xu - uu);
+      const C G = W * (C(1) + xu + hq);
+      const C q = xu + hq;  // velocity part, without the cancelling w_i
+      const C dx = C(EX(i)) - ux, dy = C(EY(i)) - uy;
+      // f (Eq. 12 with Eq. 5)
+      const C feq = W * (pp + rcs2 * q);
+      const C fs = (Fx * dx + Fy * dy) * G;
+      out(0, i, f[i] - omega_f * (f[i] - feq) + af * fs);
+      // g (Eq. 27 with Eq. 21-22)
+      const C geq = W * ((i == 0 ? H0 : Hi) + cc * q);
+      const C gs = dv(cc * (dx * Gx + dy * Gy), rcs2, inv_rcs2) * G;
+      out(1, i, g[i] - omega_g * (g[i] - geq) + ag * gs);
+      // hbar (Eq. aEq12 with Eq. aEq9); deviation form:
+      // h_eq - w_i rho c_v T_r = rho c_v (T' Gamma_i + T_r w_i q_i)
+      const C heq = rcvT * G;
+      const C hs = dv(Gx * dx + Gy * dy, rcs2, inv_rcs2) * heq;
+      const C heqd = dev_h<S>() ? rcvTd * G + rcvTr * (W * q) : heq;
+      out(2, i, h[i] - omega_T * (h[i] - heqd) + aT * hs);
+    }
   }
 }
 

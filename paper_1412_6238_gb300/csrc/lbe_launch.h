@@ -12,12 +12,13 @@ struct TileShape {
   int tx, ty;
 };
 // Kernel ids: 0..4 tile kernel with these tile shapes; 5, 6 strip kernel with
-// 128 / 64 columns per strip (ty = 0: a strip marches over its rows).
+// 124 / 60 output columns per strip (128 / 64 threads; ty = 0: a strip
+// marches over its rows).
 constexpr int NUM_TILE_SHAPES = 5;
 constexpr int NUM_TILES = 7;
 constexpr int STRIP_FIRST = 5;
 constexpr TileShape TILE_SHAPES[NUM_TILES] = {{32, 8},  {64, 4}, {32, 16}, {64, 8},
-                                              {128, 4}, {128, 0}, {64, 0}};
+                                              {128, 4}, {124, 0}, {60, 0}};
 inline bool is_strip(int tile) { return tile >= STRIP_FIRST && tile < NUM_TILES; }
 
 struct TmapSet;  // lbe_strip.cuh

@@ -3,6 +3,6 @@
 #define LBE_SUFFIX f16
 #define LBE_ALL_TILES 1
 #define LBE_STRIP 1
-#define LBE_R128 8  // staged-row ring depth of the 128-column strip kernel
-#define LBE_R64 12   // and of the 64-column one
+#define LBE_R128 7  // staged-row ring depth of the 128-column strip kernel
+#define LBE_R64 11   // and of the 64-column one
 #include "lbe_step_inst.cuh"

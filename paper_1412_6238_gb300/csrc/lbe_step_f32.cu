@@ -3,6 +3,6 @@
 #define LBE_SUFFIX f32
 #define LBE_ALL_TILES 1
 #define LBE_STRIP 1
-#define LBE_R128 6  // staged-row ring depth of the 128-column strip kernel
-#define LBE_R64 8   // and of the 64-column one
+#define LBE_R128 7  // staged-row ring depth of the 128-column strip kernel
+#define LBE_R64 9   // and of the 64-column one
 #include "lbe_step_inst.cuh"

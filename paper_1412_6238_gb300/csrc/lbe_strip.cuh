@@ -1,22 +1,24 @@
 // The fused step as a column-strip marching kernel with TMA row staging.
 //
-// A work item is a strip of NC columns [x0, x0+NC) and a segment of rows
-// [ya, yb) of one instance.  One CTA of NC threads (one column each) marches
-// up the rows.  The source rows it needs (all 27 population planes of row q,
-// columns x0-XG .. x0+NC+XG) are copied into a ring of R shared-memory slots
-// by one TMA tiled load per row (cp.async.bulk.tensor, completion on an
-// mbarrier per slot), issued up to two rows ahead of use.  Per output row r:
-//   1. moments c, p, T of row r+2 (S1), pulled from the staged rows r+1..r+3
-//      (rows beyond a wall are ghosts: mirror for c and p, 2 T_w - T for T);
-//      a ring of the last 5 moment rows feeds the stencils;
-//   2. unit normal of row r+1 (S2) into a ring of 3 rows;
-//   3. the stencils, force, velocity and three collisions of row r (S2-S9,
-//      lbe_cell.cuh) from the staged rows r-1..r+1 and the rings, and the 27
-//      stores of the post-collision values with their periodic ghost copies.
-// Every moment and normal is computed once per strip (only 4 halo columns are
-// recomputed by the neighbouring strip), every population is read from HBM
-// once per step, and the per-cell arithmetic is that of the tile kernel, so
-// the two kernels produce bitwise-equal results.
+// A work item is a strip of NC - 4 output columns [x0, x0 + NC - 4) and a
+// segment of rows [ya, yb) of one instance.  One CTA of NC threads marches up
+// the rows; thread t owns column x0 - 2 + t, so the two halo columns on each
+// side that the stencils need are ordinary threads (no divergent halo work).
+// The source rows (all population planes of row q, columns x0-3 .. x0+NC-2)
+// are copied into a ring of R shared-memory slots by one TMA tiled load per
+// row (cp.async.bulk.tensor, completion on an mbarrier per slot), issued
+// R - 6 rows ahead of use.  Iteration i has two phases separated by a
+// barrier:
+//   phase 1, two independent pieces of work the compiler interleaves:
+//     - every thread: moments c, p, T of row i+2 at its column (S1), pulled
+//       from the staged rows i+1..i+3 (rows beyond a wall are ghosts: mirror
+//       for c and p, 2 T_w - T for T) into rings of the last moment rows;
+//     - threads 2..NC-3: stencils, force, velocity and the three collisions
+//       of row i-1 (S2-S9, lbe_cell.cuh) from the staged rows i-2..i and the
+//       rings, and the 27 stores (plus periodic ghost copies at row ends);
+//   phase 2, threads 1..NC-2: unit normal of row i+1 (S2) into a ring.
+// Every population is read from HBM once per step; moments and normals are
+// computed once per strip column (4 halo columns overlap the neighbour).
 //
 // Every mbarrier wait is bounded; on time-out the kernel sets *err, waits
 // (bounded) for its own copies in flight and returns.
@@ -34,6 +36,12 @@ namespace lbe {
 struct alignas(64) TmapSet {
   CUtensorMap m[2][2];
 };
+
+// Staged row width (elements) of a strip kernel with nc threads: cells
+// x0-3 .. x0+nc-2 from a start element rounded down to 16 bytes.
+__host__ __device__ constexpr int strip_bw(int nc, int esz) {
+  return ((nc + 2 + 16 / esz - 1) + 16 / esz - 1) / (16 / esz) * (16 / esz);
+}
 
 template <class S>
 struct RowFmt;
@@ -102,15 +110,18 @@ struct Strip {
   using C = typename S::C;
   using F = RowFmt<S>;
   using E = typename F::E;
-  static constexpr int BW = NC + 2 * XG;  // staged columns x0-XG .. x0+NC+XG-1
+  static constexpr int NCO = NC - 4;                       // output columns
+  static constexpr int A = 16 / (int)sizeof(E);            // TMA x alignment (elements)
+  static constexpr int BW = strip_bw(NC, (int)sizeof(E));  // staged columns
   static constexpr int MAIN = F::planes * BW * (int)sizeof(E);
   static constexpr int G0OFF = (MAIN + 127) / 128 * 128;
   static constexpr int ROW_BYTES = MAIN + (F::g0 ? BW * 4 : 0);  // TMA bytes per row
   static constexpr int SLOT = (G0OFF + (F::g0 ? BW * 4 : 0) + 127) / 128 * 128;
-  static constexpr int RW = NC + 4;  // moment ring columns x0-2 .. x0+NC+1
-  static constexpr int QW = NC + 2;  // normal ring columns x0-1 .. x0+NC
-  static constexpr int SMEM = R * SLOT + 5 * RW * 3 * (int)sizeof(C) +
-                              3 * QW * 2 * (int)sizeof(C) + R * 8 + 16;
+  // rings of moment rows (c: 6, p and T: 5) and normal rows (4)
+  static constexpr int CR = 6, PR = 5, NR = 4;
+  static constexpr int SMEM = R * SLOT + (CR + 2 * PR) * NC * (int)sizeof(C) +
+                              NR * NC * 2 * (int)sizeof(C) + R * 8 + 16;
+  static_assert(R >= 7, "the ring holds rows i-2..i+3 plus at least one prefetched row");
 
   // population (k, i) at staged column col of a slot
   __device__ static __forceinline__ C sld(const Phys<C>& P, const char* slot, int k, int i,
@@ -124,13 +135,13 @@ struct Strip {
   }
 
   // Pull of lattice K at staged column col, row y, from the slots holding
-  // rows y-1 (sm), y (s0), y+1 (sp); same rules and arithmetic as pull9.
+  // rows y-1 (sm), y (s0), y+1 (sp); same rules as pull9 (lbe_tile.cuh).
   template <int K>
   __device__ static __forceinline__ void spull9(const InstDev& I, const Phys<C>& P, const char* sm,
                                                 const char* s0, const char* sp, int col, int y,
-                                                int xw, C out[9]) {
+                                                int ny, int xw, C out[9]) {
     constexpr bool DEV = (K == 2) && dev_h<S>();
-    const bool wb = (y == 0), wt = (y == I.ny - 1);
+    const bool wb = (y == 0), wt = (y == ny - 1);
     C Tw = C(0);
     if (K == 2 && (wb || wt)) Tw = wall_T<S>(I, xw, wb ? 0 : 1);
     const C dh = DEV ? P.dh : C(0);
@@ -181,16 +192,15 @@ strip_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
   using C = typename S::C;
   extern __shared__ __align__(128) char smem[];
   char* slots = smem;
-  C* cring = reinterpret_cast<C*>(smem + R * St::SLOT);  // [5][RW]
-  C* pring = cring + 5 * St::RW;
-  C* Tring = pring + 5 * St::RW;
-  C* nxr = Tring + 5 * St::RW;  // [3][QW]
-  C* nyr = nxr + 3 * St::QW;
+  C* cring = reinterpret_cast<C*>(smem + R * St::SLOT);  // [CR][NC]
+  C* pring = cring + St::CR * NC;                           // [PR][NC]
+  C* Tring = pring + St::PR * NC;                           // [PR][NC]
+  C* nxr = Tring + St::PR * NC;                             // [NR][NC]
+  C* nyr = nxr + St::NR * NC;
   uint64_t* bars = reinterpret_cast<uint64_t*>(
-      (reinterpret_cast<uintptr_t>(nyr + 3 * St::QW) + 15) & ~uintptr_t(15));
+      (reinterpret_cast<uintptr_t>(nyr + St::NR * NC) + 15) & ~uintptr_t(15));
   __shared__ int s_abort;
   const int t = threadIdx.x;
-  constexpr int RW = St::RW, QW = St::QW;
 
   for (int64_t item = blockIdx.x; item < total_items; item += gridDim.x) {
     int lo = 0, hi = n_inst - 1;
@@ -203,13 +213,21 @@ strip_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
     const CUtensorMap* map1 = &maps[lo].m[parity][1];
     const int64_t local = item - I.tile_begin;
     const int nx = I.nx, ny = I.ny;
-    const int x0 = (int)(local % I.tiles_x) * NC;
+    const int x0 = (int)(local % I.tiles_x) * St::NCO;
     const int ya = (int)(local / I.tiles_x) * seg_rows;
     const int yb = min(ya + seg_rows, ny);
     const int src_lo = max(ya - 3, 0), src_hi = min(yb + 2, ny - 1);
+    // staged row: elements e0 .. e0+BW-1 (element XG + c holds cell c)
+    const int e0 = (x0 + 1) / St::A * St::A;
+    const int col = (x0 + 1 - e0) + 1 + t;  // staged column of this thread's cell
     char* __restrict__ dst = I.buf[parity ^ 1];
     const Phys<C> P = phys<C>(I);  // constants in registers for the whole item
     const C en2 = P.eta_n2;
+    const size_t pitch = (size_t)I.pitch;
+    const int x = x0 - 2 + t;
+    const int xw = wrapx(x, nx);
+    const bool collides = t >= 2 && t < NC - 2 && x < nx;
+    const bool edge_ghost = collides && (x < XG || x >= nx - XG);
 
     __syncthreads();  // previous item fully done with the slots and barriers
     if (t == 0) {
@@ -220,8 +238,8 @@ strip_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
     }
     __syncthreads();
 
-    int next = src_lo;          // next source row to issue (thread 0)
-    int waited = src_lo - 1;    // highest source row waited for
+    int next = src_lo;        // next source row to issue (thread 0)
+    int waited = src_lo - 1;  // highest source row waited for
     auto issue_upto = [&](int lim) {
       if (t != 0) return;
       lim = min(lim, src_hi);
@@ -230,8 +248,8 @@ strip_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
         const uint32_t bar = smem_u32(&bars[s]);
         const uint32_t dsts = smem_u32(slots + s * St::SLOT);
         mbar_expect_tx(bar, St::ROW_BYTES);
-        tma_load_3d(dsts, map0, x0, next, 0, bar);
-        if (RowFmt<S>::g0) tma_load_2d(dsts + St::G0OFF, map1, x0, next, bar);
+        tma_load_3d(dsts, map0, e0, next, 0, bar);
+        if (RowFmt<S>::g0) tma_load_2d(dsts + St::G0OFF, map1, e0, next, bar);
       }
     };
     auto wait_upto = [&](int y) -> bool {
@@ -251,137 +269,101 @@ strip_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
       if (d < 0) d += R;
       return slots + d * St::SLOT;
     };
-    auto ring5 = [](int m) { return ((m % 5) + 5) % 5; };
-    auto ring3 = [](int m) { return ((m % 3) + 3) % 3; };
+    auto cr = [](int m) { return (((m % St::CR) + St::CR) % St::CR) * NC; };
+    auto pr = [](int m) { return (((m % St::PR) + St::PR) % St::PR) * NC; };
+    auto nr = [](int m) { return (m & (St::NR - 1)) * NC; };
 
-    // moments c, p, T of row m (0 <= m < ny) at staged column col
-    auto moments = [&](int m, int col, int xw, C& c, C& p, C& T) {
-      const char* s0 = slot_of(m);
-      const char* sm = m > 0 ? slot_of(m - 1) : s0;
-      const char* sp = m < ny - 1 ? slot_of(m + 1) : s0;
-      C v[9];
-      St::template spull9<1>(I, P, sm, s0, sp, col, m, xw, v);
-      c = sum9(v);
-      St::template spull9<0>(I, P, sm, s0, sp, col, m, xw, v);
-      p = sum9(v);
-      St::template spull9<2>(I, P, sm, s0, sp, col, m, xw, v);
-      T = dv(sum9(v), P.rho_cv, P.inv_rho_cv);
-    };
-
-    // per-thread constants of the item: own column and the halo columns the
-    // edge threads also compute
-    const int x = x0 + t;
-    const bool own_active = x < nx;
-    const bool edge_ghost = own_active && (x < XG || x >= nx - XG);
-    int rcs[3], nrc = 0;
-    rcs[nrc++] = t + 2;
-    if (t == 0) {
-      rcs[nrc++] = 0;
-      rcs[nrc++] = 1;
-    } else if (t == NC - 1) {
-      rcs[nrc++] = NC + 2;
-      rcs[nrc++] = NC + 3;
-    }
-    int xws[3];
-    for (int j = 0; j < nrc; j++) xws[j] = wrapx(x0 - 2 + rcs[j], nx);
-    const size_t pitch = (size_t)I.pitch;
-
-    for (int r = ya - 4; r < yb; r++) {
+    for (int i = ya - 4; i <= yb; i++) {
       __syncthreads();
       if (s_abort) break;
-      issue_upto(max(r - 2, src_lo - 1) + R);
+      // rows <= i-3 are done (the collision of row i-2 used rows i-3..i-1)
+      issue_upto(max(i - 3, src_lo - 1) + R);
 
-      // ---- moments of row m = r + 2 at ring columns t+2 (+ halo columns)
-      const int m = r + 2;
+      // ---- phase 1a: moments of row m = i + 2 at this thread's column
+      const int m = i + 2;
       if (m <= yb + 1) {
-        const int ridx = ring5(m) * RW;
+        const int ci = cr(m) + t, pi = pr(m) + t;
         if (m < ny) {
           const int mr = m >= 0 ? m : -1 - m;  // bottom ghost rows: the mirror row
           if (wait_upto(mr + 1)) {
-            for (int j = 0; j < nrc; j++) {
-              const int rc = rcs[j];
-              C c, p, T;
-              moments(mr, rc - 2 + XG, xws[j], c, p, T);
-              if (m < 0) T = ghost_T<S>(I, xws[j], true, T);
-              cring[ridx + rc] = c;
-              pring[ridx + rc] = p;
-              Tring[ridx + rc] = T;
-            }
+            const char* s0 = slot_of(mr);
+            const char* sm = mr > 0 ? slot_of(mr - 1) : s0;
+            const char* sp = mr < ny - 1 ? slot_of(mr + 1) : s0;
+            C v[9];
+            St::template spull9<1>(I, P, sm, s0, sp, col, mr, ny, xw, v);
+            cring[ci] = sum9(v);
+            St::template spull9<0>(I, P, sm, s0, sp, col, mr, ny, xw, v);
+            pring[pi] = sum9(v);
+            St::template spull9<2>(I, P, sm, s0, sp, col, mr, ny, xw, v);
+            C T = dv(sum9(v), P.rho_cv, P.inv_rho_cv);
+            if (m < 0) T = ghost_T<S>(I, xw, true, T);
+            Tring[pi] = T;
           }
         } else {
-          // top ghost rows from the mirror rows still in the ring
-          const int sidx = ring5(2 * ny - 1 - m) * RW;
-          for (int rc = t; rc < RW; rc += NC) {
-            const int xw = wrapx(x0 - 2 + rc, nx);
-            cring[ridx + rc] = cring[sidx + rc];
-            pring[ridx + rc] = pring[sidx + rc];
-            Tring[ridx + rc] = ghost_T<S>(I, xw, false, Tring[sidx + rc]);
-          }
+          // top ghost rows from the mirror rows still in the rings
+          const int mm = 2 * ny - 1 - m;
+          cring[ci] = cring[cr(mm) + t];
+          pring[pi] = pring[pr(mm) + t];
+          Tring[pi] = ghost_T<S>(I, xw, false, Tring[pr(mm) + t]);
         }
       }
-      __syncthreads();
-      if (s_abort) break;
 
-      // ---- unit normal of row r + 1 at normal-ring columns t+1 (+ halo)
-      const int mn = r + 1;
-      if (mn >= ya - 1 && mn <= yb) {
-        const C* cs = cring + ring5(mn - 1) * RW;
-        const C* c0 = cring + ring5(mn) * RW;
-        const C* cn = cring + ring5(mn + 1) * RW;
-        const int nidx = ring3(mn) * QW;
-        normal3(cs, c0, cn, t + 2, en2, nxr[nidx + t + 1], nyr[nidx + t + 1]);
-        if (t == 0) normal3(cs, c0, cn, 1, en2, nxr[nidx], nyr[nidx]);
-        if (t == NC - 1) normal3(cs, c0, cn, NC + 2, en2, nxr[nidx + NC + 1], nyr[nidx + NC + 1]);
-      }
-      __syncthreads();
-      if (s_abort) break;
-
-      // ---- collide row r at column x0 + t
-      if (r >= ya && own_active) {
-        const int col = t + XG;
+      // ---- phase 1b: collide row r = i - 1
+      const int r = i - 1;
+      if (r >= ya && r < yb && collides) {
         const char* s0 = slot_of(r);
         const char* sm = r > 0 ? slot_of(r - 1) : s0;
         const char* sp = r < ny - 1 ? slot_of(r + 1) : s0;
         C f[9], g[9], h[9];
-        St::template spull9<0>(I, P, sm, s0, sp, col, r, x, f);
-        St::template spull9<1>(I, P, sm, s0, sp, col, r, x, g);
-        St::template spull9<2>(I, P, sm, s0, sp, col, r, x, h);
-        const int rs5 = ring5(r - 1) * RW, r05 = ring5(r) * RW, rn5 = ring5(r + 1) * RW;
-        const C* cs = cring + rs5;
-        const C* c0 = cring + r05;
-        const C* cn = cring + rn5;
-        const C cc = c0[t + 2];
-        const C pp = pring[r05 + t + 2], TT = Tring[r05 + t + 2];
+        St::template spull9<0>(I, P, sm, s0, sp, col, r, ny, x, f);
+        St::template spull9<1>(I, P, sm, s0, sp, col, r, ny, x, g);
+        St::template spull9<2>(I, P, sm, s0, sp, col, r, ny, x, h);
+        const C* cs = cring + cr(r - 1);
+        const C* c0 = cring + cr(r);
+        const C* cn = cring + cr(r + 1);
+        const int ps = pr(r - 1), p0 = pr(r), pn = pr(r + 1);
+        const C cc = c0[t];
+        const C pp = pring[p0 + t], TT = Tring[p0 + t];
         Stencils<C> st;
-        grad3(cs, c0, cn, t + 2, st.gcx, st.gcy);
-        st.lapc = lap3(cs, c0, cn, t + 2);
-        grad3(Tring + rs5, Tring + r05, Tring + rn5, t + 2, st.gTx, st.gTy);
+        grad3(cs, c0, cn, t, st.gcx, st.gcy);
+        st.lapc = lap3(cs, c0, cn, t);
+        grad3(Tring + ps, Tring + p0, Tring + pn, t, st.gTx, st.gTy);
         if (dev_h<S>()) st.gTy += P.hr1;
-        grad3(pring + rs5, pring + r05, pring + rn5, t + 2, st.gpx, st.gpy);
-        const int ns = ring3(r - 1) * QW, n0 = ring3(r) * QW, nn = ring3(r + 1) * QW;
+        grad3(pring + ps, pring + p0, pring + pn, t, st.gpx, st.gpy);
+        const int ns = nr(r - 1), n0 = nr(r), nn = nr(r + 1);
         C d1, d2, dum;
-        grad3(nxr + ns, nxr + n0, nxr + nn, t + 1, d1, dum);
-        grad3(nyr + ns, nyr + n0, nyr + nn, t + 1, dum, d2);
+        grad3(nxr + ns, nxr + n0, nxr + nn, t, d1, dum);
+        grad3(nyr + ns, nyr + n0, nyr + nn, t, dum, d2);
         st.kappa = d1 + d2;
         const Drive<S> d = drive<S>(P, r, f, cc, TT, st);
         C o[27];
         collide<S>(P, f, g, h, cc, pp, TT, st.gpx, st.gpy, d,
-                   [&](int k, int i, C v) { o[k * 9 + i] = v; });
-        const size_t e0 = (size_t)r * pitch + XG + x;
+                   [&](int k, int ii, C v) { o[k * 9 + ii] = v; });
+        const size_t e = (size_t)r * pitch + XG + x;
 #pragma unroll
         for (int k = 0; k < 3; k++)
 #pragma unroll
-          for (int i = 0; i < 9; i++) S::st(I, dst, k, i, e0, o[k * 9 + i]);
+          for (int ii = 0; ii < 9; ii++) S::st(I, dst, k, ii, e, o[k * 9 + ii]);
         if (edge_ghost) {
           // periodic ghost copies of the first / last XG cells of the row
 #pragma unroll
           for (int k = 0; k < 3; k++)
 #pragma unroll
-            for (int i = 0; i < 9; i++) {
-              if (x < XG) S::st(I, dst, k, i, e0 + nx, o[k * 9 + i]);
-              if (x >= nx - XG) S::st(I, dst, k, i, e0 - nx, o[k * 9 + i]);
+            for (int ii = 0; ii < 9; ii++) {
+              if (x < XG) S::st(I, dst, k, ii, e + nx, o[k * 9 + ii]);
+              if (x >= nx - XG) S::st(I, dst, k, ii, e - nx, o[k * 9 + ii]);
             }
         }
+      }
+      __syncthreads();
+      if (s_abort) break;
+
+      // ---- phase 2: unit normal of row i + 1
+      const int mn = i + 1;
+      if (mn >= ya - 1 && mn <= yb && t >= 1 && t < NC - 1) {
+        const C* c0 = cring + cr(mn);
+        const int ni = nr(mn) + t;
+        normal3(cring + cr(mn - 1), c0, cring + cr(mn + 1), t, en2, nxr[ni], nyr[ni]);
       }
     }
     __syncthreads();
