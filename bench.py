@@ -49,6 +49,9 @@ def parse_args():
     ap.add_argument("--storage", default="f32", choices=list(BYTES_PER_CELL))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the 16-bit storage and batched-sweep measurements")
+    ap.add_argument("--batch-steps", type=int, default=50)
     return ap.parse_args()
 
 
@@ -244,8 +247,15 @@ def run_ours(args, ws, rank, local):
     peak, peak_kind = hbm_peak()
     traffic = profiled_traffic() if (args.storage == "f32" and args.nx == NX and args.ny == NY) else None
     fin = sim.sums()
+    ref_fields = sim.fields(device="cuda") if not args.no_variants else None
     del sim
     torch.cuda.empty_cache()
+
+    variants = None
+    if not args.no_variants and ws == 1:
+        variants = measure_variants(args, w, ref_fields)
+        del ref_fields
+        torch.cuda.empty_cache()
 
     # end to end through the public API, host buffers in and out
     e2e = None
@@ -295,10 +305,84 @@ def run_ours(args, ws, rank, local):
                              "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                              "peak_kind": peak_kind,
                              "algorithmic_bytes_per_launch": algo_bytes},
-                "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "variants": variants,
                 "gpu_launches": args.steps,
                 "check": {"sum_c": fin["sum_c"], "nonfinite": fin["nonfinite"]}}
         print(json.dumps(line), flush=True)
+
+
+def _timed(sim, steps):
+    import torch
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    sim.synchronize()
+    t0.record(sim.stream)
+    sim.step(steps)
+    t1.record(sim.stream)
+    t1.synchronize()
+    return t0.elapsed_time(t1)
+
+
+def measure_variants(args, w, ref_fields):
+    """The same workload with 16-bit deviation storage (timed like the main
+    line; fields compared with the FP32 run after the same steps), and the
+    batched parameter sweep of 64 drops of uneven size in one persistent
+    launch per step against 64 sequential FP32 runs."""
+    import numpy as np
+    import torch
+
+    from paper_1412_6238_gb300 import workloads as wl
+    from paper_1412_6238_gb300.lbe import LBE
+    out = {}
+    peak, _ = hbm_peak()
+
+    def rel(F, G, keys):
+        a = torch.stack([F[k] for k in keys])
+        b = torch.stack([G[k] for k in keys])
+        return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+
+    for st in ("f16dev", "bf16dev"):
+        sim = LBE(w, storage=st)
+        sim.step(args.warmup)
+        ms = _timed(sim, args.steps)
+        F = sim.fields(device="cuda")
+        del sim
+        launch_ms = ms / args.steps
+        mlups = w.cells * args.steps / (ms / 1e3) / 1e6
+        bytes_launch = w.cells * BYTES_PER_CELL[st]
+        out[st] = {"value": mlups, "unit": UNIT, "ms_per_step": launch_ms,
+                   "hbm_frac": bytes_launch / (launch_ms / 1e3) / 1e9 / peak,
+                   "bytes_per_cell": BYTES_PER_CELL[st],
+                   "rel_l2_vs_f32": {"u": rel(F, ref_fields, ("ux", "uy")),
+                                     "T": rel(F, ref_fields, ("T",)),
+                                     "c": rel(F, ref_fields, ("c",))},
+                   "steps_compared": args.warmup + args.steps}
+        del F
+        torch.cuda.empty_cache()
+
+    # batched sweep (64 drops, grids 128x256 .. 768x1536, seed 0)
+    sweep = wl.batch_sweep(64, seed=0)
+    cells = sum(x.cells for x in sweep)
+    K = args.batch_steps
+    res = {"instances": len(sweep), "cells": cells, "steps": K}
+    for st in ("f16dev", "f32"):
+        sim = LBE(sweep, storage=st)
+        sim.step(3)
+        ms = _timed(sim, K)
+        res["batched_" + st] = cells * K / (ms / 1e3) / 1e6
+        del sim
+        torch.cuda.empty_cache()
+    seq_ms = 0.0
+    for x in sweep:
+        sim = LBE(x, storage="f32")
+        sim.step(3)
+        seq_ms += _timed(sim, K)
+        del sim
+    res["sequential_f32"] = cells * K / (seq_ms / 1e3) / 1e6
+    res["speedup_batched_f16dev_vs_sequential_f32"] = res["batched_f16dev"] / res["sequential_f32"]
+    res["unit"] = UNIT
+    out["batch64"] = res
+    return out
 
 
 def main():
