@@ -63,8 +63,9 @@ def dist_init():
     if ws > 1:
         import torch
         import torch.distributed as dist
-        backend = "nccl" if torch.cuda.is_available() else "gloo"
-        if torch.cuda.is_available():
+        backend = os.environ.get("BENCH_DIST_BACKEND") or (
+            "nccl" if torch.cuda.is_available() else "gloo")
+        if backend == "nccl":
             torch.cuda.set_device(local)
         dist.init_process_group(backend=backend)
     return ws, rank, local
@@ -81,10 +82,18 @@ def allmax(ws, v: float) -> float:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64,
-                     device="cuda" if torch.cuda.is_available() else "cpu")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate(ws, ms: float, cells: int, steps: int):
+    """(max-over-ranks time in ms, whole-job MLUPS): every rank advances its
+    own replica of the problem, so the job updates ws * cells * steps cells
+    in the slowest rank's time."""
+    ms_max = allmax(ws, ms)
+    return ms_max, cells * steps * ws / (ms_max / 1e3) / 1e6
 
 
 # ------------------------------------------------------------ measurement aids
@@ -141,11 +150,15 @@ def hbm_peak():
 
 
 def kernel_source_sha() -> str:
+    """Hash of the sources and flags that make the FP32 step kernel (the
+    traffic figure of the committed ncu summary is valid while it matches)."""
+    from paper_1412_6238_gb300 import build as _b
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1412_6238_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in ("lbe_common.cuh", "lbe_cell.cuh", "lbe_tile.cuh", "lbe_strip.cuh",
+              "lbe_step_inst.cuh", "lbe_step_f32.cu"):
+        h.update(open(os.path.join(d, f), "rb").read())
+    h.update(repr(_b.UNITS["lbe_step_f32.cu"]).encode())
     return h.hexdigest()[:16]
 
 
@@ -239,8 +252,7 @@ def run_ours(args, ws, rank, local):
     clocks = clk.stop()
     barrier(ws)
     ms = t0.elapsed_time(t1)
-    ms_max = allmax(ws, ms)
-    value = cells * args.steps * ws / (ms_max / 1e3) / 1e6
+    ms_max, value = aggregate(ws, ms, cells, args.steps)
     launch_ms = ms / args.steps
     algo_bytes = cells * BYTES_PER_CELL[args.storage]
     achieved = algo_bytes / (launch_ms / 1e3) / 1e9

@@ -179,6 +179,59 @@ lbe_status lbe_tile_shape(int32_t tile_id, int32_t* tx, int32_t* ty);
 lbe_status lbe_set_tile(lbe_handle* h, int32_t tile_id, int32_t grid_ctas, int32_t seg_rows);
 lbe_status lbe_get_tile(const lbe_handle* h, int32_t out[4]);
 
+/* ---- Discrete adjoint (gradients of a drop-migration observable).
+ *
+ * The observable of a state Q is the phase-1 centroid velocity of the
+ * migration problem (Sec. IV.C):
+ *   l(Q) = sum_x c(x) u_y(x) / sum_x c(x)
+ * with c, u_y the fields of Q as lbe_fields computes them (u includes the
+ * half-step force, Eq. 13).  The loss of a run of N steps from Q_0 is the mean
+ * of l over the last `window` states:  L = (1/W) sum_{n=N-W+1..N} l(Q_n).
+ * The gradient is the discrete adjoint of the FP64 step: the transposed
+ * streaming (bounce-back and anti-bounce-back included), the transposed
+ * collision of all three lattices (Eq. 12, 27, aEq12) with the force of Eq. 3
+ * and sigma(T) of Eq. aEq3, and the transposed isotropic stencils with their
+ * ghost-row rules, propagated backward over the run.  Parameters:
+ *   theta = (sigmaT, eta2/eta1, lam2/lam1), the ratios varied with eta1 and
+ *   lam1 fixed.  The initial state is the equilibrium of lbe_init at u = 0, so
+ *   hbar_i(x, 0) = w_i rho c_v T0(x) and dL/dT0(x) = rho c_v sum_i w_i
+ *   dL/dhbar_i(x, 0). */
+typedef struct {
+  int64_t steps;       /* N >= 1 steps from the handle's current state      */
+  int64_t window;      /* 1 <= W <= N: states averaged into the loss          */
+  int64_t ckpt_every;  /* k >= 1: spacing of the stored checkpoints; the
+                          backward recomputes each segment of k steps from
+                          its checkpoint and keeps k + 1 FP64 states          */
+} lbe_adjoint_spec;
+
+/* Forward N steps from the handle's current state (the handle's storage and
+ * kernel; checkpoints of the raw storage every k steps), then the backward
+ * sweep in FP64 over the recomputed states.  Outputs (each may be NULL):
+ *   loss     host double: L
+ *   grad     host double[3]: dL/dsigmaT, dL/d(eta2/eta1), dL/d(lam2/lam1)
+ *   dT0      [ny][nx] doubles: dL/dT0
+ *   dQ0      [27][ny][nx] doubles: dL/dQ_0 (adjoint of the starting state)
+ * dT0 and dQ0 are device pointers if on_device, else host.  The handle must
+ * hold one instance.  On return the handle holds the state after the N steps
+ * (steps_done advanced by N).  Device memory used during the call:
+ * about (k + 1 + 2) * 27 + 30 doubles per cell plus N/k raw checkpoints; it is
+ * allocated and freed inside the call (LBE_ENOMEM if it does not fit).
+ * Waits. */
+lbe_status lbe_adjoint(lbe_handle* h, const lbe_adjoint_spec* spec, double* loss,
+                       double grad[3], double* dT0, double* dQ0, int32_t on_device);
+
+/* One adjoint step at an explicit state, for tests and custom losses.  With
+ * Q = Q_n ([27][ny][nx] device doubles, instance 0's parameters) and
+ * a_next = dL/dQ_{n+1} (device, same layout):
+ *   a_out = (dQ_{n+1}/dQ_n)^T a_next + wl * dl/dQ_n          (device)
+ *   grad[0..2] += a_next^T dQ_{n+1}/dtheta + wl * dl/dtheta  (host)
+ * a_next may be NULL (taken as zero: the last state of a run).  Waits. */
+lbe_status lbe_adjoint_step(lbe_handle* h, const double* Q, const double* a_next, double wl,
+                            double* a_out, double grad[3]);
+
+/* l(Q) of a [27][ny][nx] device state with instance 0's parameters.  Waits. */
+lbe_status lbe_observable(lbe_handle* h, const double* Q, double* out);
+
 /* Introspection. */
 int64_t lbe_steps_done(const lbe_handle* h);
 void* lbe_stream(const lbe_handle* h);         /* the cudaStream_t used   */

@@ -186,3 +186,33 @@ def cell_terms(params: dict, c, p, T, mu, ux, uy, Fx, Fy, gpx, gpy) -> dict:
                          Fy, gpx, gpy, *[_d(arrs[k]) for k in
                                          ("feq", "geq", "heq", "fsrc", "gsrc", "hsrc")])
     return arrs
+
+
+# ---------------------------------------------------------------- migration
+def centroid_velocity(params: dict, pop, Tbot, Ttop) -> float:
+    """Phase-1 centroid velocity of a state: sum c u_y / sum c over the cells
+    (the migration velocity of the drop, Sec. IV.C; c is the drop's order
+    parameter, u the velocity of Eq. 13 with the half-step force)."""
+    F = fields(params, pop, Tbot, Ttop)
+    return float((F["c"] * F["uy"]).sum() / F["c"].sum())
+
+
+def migration_loss(params: dict, c0, T0, Tbot, Ttop, steps: int, window: int) -> float:
+    """Mean centroid velocity over the states n = steps-window+1 .. steps of
+    the run that starts from the rest state of (c0, T0)."""
+    if not 1 <= window <= steps:
+        raise ValueError("window must be in [1, steps]")
+    pop = init(params, c0, T0, Tbot, Ttop)
+    pop = run(params, pop, Tbot, Ttop, steps - window)
+    total = 0.0
+    for _ in range(window):
+        pop = run(params, pop, Tbot, Ttop, 1)
+        total += centroid_velocity(params, pop, Tbot, Ttop)
+    return total / window
+
+
+def migration_centroid(params: dict, pop, Tbot, Ttop) -> float:
+    """Phase-1 centroid height sum c y / sum c (cell centres y = 0..ny-1)."""
+    F = fields(params, pop, Tbot, Ttop)
+    y = np.arange(F["c"].shape[0], dtype=np.float64)[:, None]
+    return float((F["c"] * y).sum() / F["c"].sum())

@@ -28,6 +28,7 @@ UNITS = {
     "lbe_aux.cu": ["-fmad=false"],
     "lbe_api.cu": ["-Xcompiler", "-ffp-contract=off"],
     "lbe_noalloc.cu": ["-fmad=false"],
+    "lbe_adjoint.cu": [],
 }
 
 

@@ -1,0 +1,577 @@
+// Discrete adjoint (vector-Jacobian product) of one FP64 step, and the
+// drop-migration observable.
+//
+// The step maps the pre-collision state Q_n (27 planes, [27][ny][nx]) to
+// Q_{n+1} = Pull(Post(Q_n; theta)); Post is the collision of every cell,
+// which reads its own populations and, through the stencils, c at distance
+// <= 2 and p, T at distance 1 (with the wall ghost rows).  Given
+// a = dL/dQ_{n+1} the adjoint step returns
+//   dL/dQ_n = Post'(Q_n)^T Pull^T a + w dl/dQ_n
+// and adds a^T dQ_{n+1}/dtheta (+ w dl/dtheta) to the gradient of
+// theta = (sigmaT, eta ratio eta2/eta1, conductivity ratio lam2/lam1), where
+// l(Q) = sum_x c u_y / sum_x c is the centroid velocity of phase 1 (the
+// migration velocity of Sec. IV.C without the c >= 0.5 threshold) and w the
+// loss weight of step n.  Passes, all deterministic gathers:
+//   M   c, p, T of every cell                      (moments, Eq. 13/28/aEq13)
+//   N   n = grad c / |grad c|_eta on cells and the ghost rows -1, ny (Eq. 3)
+//   P   b = Pull^T a (the transpose of streaming with bounce-back /
+//       anti-bounce-back: a permutation with signs)
+//   A   per cell: recompute the forward step (stencils, mu, F, u, the three
+//       collisions) and back-propagate b through it; writes the direct
+//       population adjoints, the adjoints of the stencil outputs
+//       (grad c, lap c, grad T, grad p, kappa) and of the cell's own c, p, T,
+//       and per-block theta partials
+//   B   kappa-bar -> n-bar (transposed divergence) -> grad-c-bar through the
+//       normalisation, on cells and ghost rows
+//   CD  per cell: transposed stencils (ghost images folded back: mirror for
+//       c and p, sign flip for T) give c-bar, p-bar, T-bar, added to g, f,
+//       hbar adjoints.
+#include <cstdio>
+
+#include "../../include/lbe.h"
+#include "lbe_launch.h"
+
+namespace lbe {
+namespace adj {
+
+constexpr int TPB = 256;
+constexpr int RBLK = 304;  // blocks of the deterministic reductions
+constexpr double CS2 = 1.0 / 3.0;
+
+struct Geo {
+  int nx, ny;
+  int64_t N;  // nx * ny
+};
+
+__device__ __forceinline__ int wrap(int x, int nx) {
+  x %= nx;
+  return x < 0 ? x + nx : x;
+}
+
+// c with mirrored ghost rows (depth 2), p mirrored (depth 1), T antisymmetric
+// about the wall temperature (depth 1)
+__device__ __forceinline__ double cget(const double* c, const Geo& G, int x, int y) {
+  if (y < 0) y = -1 - y;
+  else if (y >= G.ny) y = 2 * G.ny - 1 - y;
+  return c[(int64_t)y * G.nx + wrap(x, G.nx)];
+}
+__device__ __forceinline__ double Tget(const double* T, const Geo& G, const InstDev& I, int x,
+                                       int y) {
+  x = wrap(x, G.nx);
+  if (y < 0) return 2.0 * I.Tbot[x] - T[x];
+  if (y >= G.ny) return 2.0 * I.Ttop[x] - T[(int64_t)(G.ny - 1) * G.nx + x];
+  return T[(int64_t)y * G.nx + x];
+}
+// ext arrays hold rows -1..ny (ny + 2 rows)
+__device__ __forceinline__ double eget(const double* e, const Geo& G, int x, int y) {
+  return e[(int64_t)(y + 1) * G.nx + wrap(x, G.nx)];
+}
+
+// isotropic gradient, index order i = 1..8, of a field given by an accessor
+template <class Fn>
+__device__ __forceinline__ void grad_at(Fn v, int x, int y, double& gx, double& gy) {
+  double sx = 0.0, sy = 0.0;
+  for (int i = 1; i < 9; i++) {
+    const double a = v(x + EX(i), y + EY(i));
+    sx += WGT<double>(i) * EX(i) * a;
+    sy += WGT<double>(i) * EY(i) * a;
+  }
+  gx = sx / CS2;
+  gy = sy / CS2;
+}
+template <class Fn>
+__device__ __forceinline__ double lap_at(Fn v, int x, int y) {
+  const double v0 = v(x, y);
+  double s = 0.0;
+  for (int i = 1; i < 9; i++) s += WGT<double>(i) * (v(x + EX(i), y + EY(i)) - v0);
+  return 2.0 * s / CS2;
+}
+
+// ---------------------------------------------------------------- M, N, P
+__global__ void pass_M(Geo G, const InstDev* __restrict__ d, const double* __restrict__ Q,
+                       double* __restrict__ C, double* __restrict__ Pp, double* __restrict__ T) {
+  const InstDev& I = *d;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < G.N;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    double sf = 0, sg = 0, sh = 0;
+    for (int i = 0; i < 9; i++) {
+      sf += Q[(int64_t)i * G.N + k];
+      sg += Q[(int64_t)(9 + i) * G.N + k];
+      sh += Q[(int64_t)(18 + i) * G.N + k];
+    }
+    C[k] = sg;
+    Pp[k] = sf;
+    T[k] = sh / (I.pd.rho * I.pd.cv);
+  }
+}
+
+__global__ void pass_N(Geo G, const InstDev* __restrict__ d, const double* __restrict__ C,
+                       double* __restrict__ NX, double* __restrict__ NY) {
+  const InstDev& I = *d;
+  const int64_t NE = (int64_t)(G.ny + 2) * G.nx;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < NE;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(k % G.nx), y = (int)(k / G.nx) - 1;
+    double gx, gy;
+    grad_at([&](int a, int b) { return cget(C, G, a, b); }, x, y, gx, gy);
+    const double inv = 1.0 / sqrt(gx * gx + gy * gy + I.pd.eta_n2);
+    NX[k] = gx * inv;
+    NY[k] = gy * inv;
+  }
+}
+
+// b_j(x) = a_j(x + xi_j), or +-a_jbar(x) where x + xi_j is beyond a wall
+__global__ void pass_P(Geo G, const double* __restrict__ a, double* __restrict__ b) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < G.N;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(k % G.nx), y = (int)(k / G.nx);
+    for (int j = 0; j < 9; j++) {
+      const int yt = y + EY(j);
+      const bool wall = yt < 0 || yt >= G.ny;
+      const int64_t kt = wall ? k : (int64_t)yt * G.nx + wrap(x + EX(j), G.nx);
+      const int js = wall ? OPP(j) : j;
+      for (int l = 0; l < 3; l++) {
+        const double v = a[(int64_t)(l * 9 + js) * G.N + kt];
+        b[(int64_t)(l * 9 + j) * G.N + k] = (wall && l == 2) ? -v : v;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- A
+// Stencil-output adjoint planes written by pass A.
+enum { S_GCX = 0, S_GCY, S_LAP, S_GTX, S_GTY, S_GPX, S_GPY, S_KAP, S_C, S_P, S_T, S_NUM };
+
+__device__ __forceinline__ void block_sum(double v[4], double* sh) {
+  for (int j = 0; j < 4; j++) sh[j * TPB + threadIdx.x] = v[j];
+  __syncthreads();
+  for (int s = TPB / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s)
+      for (int j = 0; j < 4; j++) sh[j * TPB + threadIdx.x] += sh[j * TPB + threadIdx.x + s];
+    __syncthreads();
+  }
+  for (int j = 0; j < 4; j++) v[j] = sh[j * TPB];
+}
+
+// MODE 0: observable partials (sum c u_y, sum c) into part[blk][4].
+// MODE 1: adjoint of the step at this state.
+template <int MODE>
+__global__ void __launch_bounds__(TPB)
+pass_A(Geo G, const InstDev* __restrict__ d, const double* __restrict__ Q,
+       const double* __restrict__ C, const double* __restrict__ Pp, const double* __restrict__ T,
+       const double* __restrict__ NX, const double* __restrict__ NY, const double* __restrict__ b,
+       const double* __restrict__ obs, double wl, double* __restrict__ aout,
+       double* __restrict__ S, double* __restrict__ part) {
+  __shared__ double sh[4 * TPB];
+  const InstDev& I = *d;
+  const Phys<double>& P = I.pd;
+  double acc[4] = {0, 0, 0, 0};
+  for (int64_t k = blockIdx.x * (int64_t)TPB + threadIdx.x; k < G.N;
+       k += (int64_t)RBLK * TPB) {
+    const int x = (int)(k % G.nx), y = (int)(k / G.nx);
+    double f[9], g[9], h[9];
+    for (int i = 0; i < 9; i++) {
+      f[i] = Q[(int64_t)i * G.N + k];
+      g[i] = Q[(int64_t)(9 + i) * G.N + k];
+      h[i] = Q[(int64_t)(18 + i) * G.N + k];
+    }
+    const double cc = C[k], pp = Pp[k], TT = T[k];
+    auto cf = [&](int a, int bb) { return cget(C, G, a, bb); };
+    auto pf = [&](int a, int bb) { return cget(Pp, G, a, bb); };
+    auto Tf = [&](int a, int bb) { return Tget(T, G, I, a, bb); };
+    double gcx, gcy, gTx, gTy, gpx, gpy, d1, d2, dum;
+    grad_at(cf, x, y, gcx, gcy);
+    const double lapc = lap_at(cf, x, y);
+    grad_at(Tf, x, y, gTx, gTy);
+    grad_at(pf, x, y, gpx, gpy);
+    grad_at([&](int a, int bb) { return eget(NX, G, a, bb); }, x, y, d1, dum);
+    grad_at([&](int a, int bb) { return eget(NY, G, a, bb); }, x, y, dum, d2);
+    const double kappa = d1 + d2;
+    // forward (same expressions as the FP64 step)
+    const double mu = P.beta2 * cc * (cc - 1.0) * (2.0 * cc - 1.0) - P.eps2 * lapc;
+    const double sigma = P.sigma0 - P.sigmaT * (TT - P.Tref);
+    const double g2 = gcx * gcx + gcy * gcy;
+    const double gabs = sqrt(g2);
+    const double cdT = gcx * gTx + gcy * gTy;
+    const double ea = P.ea;
+    const double cap = -sigma * kappa * ea * gabs;
+    const double mar = -P.sigmaT * ea;
+    const double Fx = cap * gcx + mar * (g2 * gTx - cdT * gcx) + P.Fbx;
+    const double Fy = cap * gcy + mar * (g2 * gTy - cdT * gcy) + P.Fby;
+    double jx = f[1] - f[3];
+    jx = jx + f[5];
+    jx = jx - f[6];
+    jx = jx - f[7];
+    jx = jx + f[8];
+    double jy = f[2] - f[4];
+    jy = jy + f[5];
+    jy = jy + f[6];
+    jy = jy - f[7];
+    jy = jy - f[8];
+    const double rho = P.rho, rcs2 = P.rcs2;
+    const double ux = jx / rcs2 + 0.5 * Fx / rho;
+    const double uy = jy / rcs2 + 0.5 * Fy / rho;
+    if (MODE == 0) {
+      acc[0] += cc * uy;
+      acc[1] += cc;
+      continue;
+    }
+    const double eta = P.eta1 + cc * P.deta;
+    const double lam = P.lam1 + cc * P.dlam;
+    const double tau_f = eta / rcs2 + 0.5;
+    const double omega_f = 1.0 / tau_f;
+    const double tau_h = lam / P.rcvcs2;
+    const double omega_T = 2.0 / (2.0 * tau_h + 1.0);
+    const double omega_g = P.omega_g;
+    const double af = 1.0 - 0.5 * omega_f, ag = 1.0 - 0.5 * omega_g, aT = 1.0 - 0.5 * omega_T;
+    const double uu = (ux * ux + uy * uy) / CS2;
+    const double Gm = P.Gm;
+    const double W0 = WGT<double>(0);
+    const double Hi = Gm * mu / CS2;
+    const double H0 = (cc - (1.0 - W0) * Gm * mu / CS2) / W0;
+    const double Gx = Fx - gpx, Gy = Fy - gpy;
+    const double rcvT = P.rho * P.cv * TT;
+
+    // ---- reverse through the collisions
+    double fb[9], gbr[9], hb[9];
+    double cb = 0, pb = 0, Tb = 0, uxb = 0, uyb = 0, Fxb = 0, Fyb = 0, Gxb = 0, Gyb = 0;
+    double uub = 0, Hib = 0, H0b = 0, rcvTb = 0, wfb = 0, wTb = 0, afb = 0, aTb = 0;
+    for (int i = 0; i < 9; i++) {
+      const double W = WGT<double>(i);
+      const double xu = (EX(i) * ux + EY(i) * uy) / CS2;
+      const double hq = 0.5 * (xu * xu - uu);
+      const double Gam = W * (1.0 + xu + hq);
+      const double q = xu + hq;
+      const double dx = EX(i) - ux, dy = EY(i) - uy;
+      const double feq = W * (pp + rcs2 * q);
+      const double fsd = Fx * dx + Fy * dy;
+      const double fs = fsd * Gam;
+      const double Hx = (i == 0 ? H0 : Hi);
+      const double geq = W * (Hx + cc * q);
+      const double gdot = dx * Gx + dy * Gy;
+      const double sgv = cc * gdot / rcs2;
+      const double heq = rcvT * Gam;
+      const double shv = (Gx * dx + Gy * dy) / rcs2;
+      const double hs = shv * heq;
+      const double bf = b[(int64_t)i * G.N + k], bg = b[(int64_t)(9 + i) * G.N + k],
+                   bh = b[(int64_t)(18 + i) * G.N + k];
+      double Gamb = 0, qb = 0, dxb = 0, dyb = 0, xub = 0, hqb = 0;
+      // h: ho = h - wT (h - heq) + aT hs
+      hb[i] = bh * (1.0 - omega_T);
+      wTb += bh * (heq - h[i]);
+      double heqb = bh * omega_T;
+      const double hsb = bh * aT;
+      aTb += bh * hs;
+      const double shb = hsb * heq;
+      heqb += hsb * shv;
+      Gxb += shb * dx / rcs2;
+      Gyb += shb * dy / rcs2;
+      dxb += shb * Gx / rcs2;
+      dyb += shb * Gy / rcs2;
+      rcvTb += heqb * Gam;
+      Gamb += heqb * rcvT;
+      // g: go = g - wg (g - geq) + ag gs, gs = (c gdot / rcs2) Gam
+      gbr[i] = bg * (1.0 - omega_g);
+      const double geqb = bg * omega_g;
+      const double gsb = bg * ag;
+      const double sgb = gsb * Gam;
+      Gamb += gsb * sgv;
+      cb += sgb * gdot / rcs2;
+      Gxb += sgb * cc * dx / rcs2;
+      Gyb += sgb * cc * dy / rcs2;
+      dxb += sgb * cc * Gx / rcs2;
+      dyb += sgb * cc * Gy / rcs2;
+      if (i == 0) H0b += geqb * W; else Hib += geqb * W;
+      cb += geqb * W * q;
+      qb += geqb * W * cc;
+      // f: fo = f - wf (f - feq) + af fs, fs = (F.(xi - u)) Gam
+      fb[i] = bf * (1.0 - omega_f);
+      wfb += bf * (feq - f[i]);
+      const double feqb = bf * omega_f;
+      const double fsb = bf * af;
+      afb += bf * fs;
+      Fxb += fsb * Gam * dx;
+      Fyb += fsb * Gam * dy;
+      dxb += fsb * Gam * Fx;
+      dyb += fsb * Gam * Fy;
+      Gamb += fsb * fsd;
+      pb += feqb * W;
+      qb += feqb * W * rcs2;
+      // dx = EX - ux
+      uxb -= dxb;
+      uyb -= dyb;
+      // Gam = W (1 + xu + hq), q = xu + hq, hq = (xu^2 - uu)/2
+      xub += Gamb * W + qb;
+      hqb += Gamb * W + qb;
+      xub += hqb * xu;
+      uub -= 0.5 * hqb;
+      uxb += xub * EX(i) / CS2;
+      uyb += xub * EY(i) / CS2;
+    }
+    Tb += rcvTb * P.rho * P.cv;
+    Fxb += Gxb;
+    Fyb += Gyb;
+    double gpxb = -Gxb, gpyb = -Gyb;
+    double mub = Hib * Gm / CS2;
+    cb += H0b / W0;
+    mub -= H0b * (1.0 - W0) * Gm / (CS2 * W0);
+    uxb += uub * 2.0 * ux / CS2;
+    uyb += uub * 2.0 * uy / CS2;
+    wTb -= 0.5 * aTb;
+    wfb -= 0.5 * afb;
+    const double tauhb = -wTb * omega_T * omega_T;
+    const double lamb = tauhb / P.rcvcs2;
+    const double taufb = -wfb * omega_f * omega_f;
+    const double etab = taufb / rcs2;
+    cb += etab * P.deta + lamb * P.dlam;
+    double th_eta = etab * cc * P.eta1;  // d eta / d (eta2/eta1) = c eta1
+    double th_lam = lamb * cc * P.lam1;
+    // the observable at this step: l = A/B, dl/dc = u_y/B - A/B^2, dl/du_y = c/B
+    if (wl != 0.0) {
+      const double A = obs[0], B = obs[1];
+      cb += wl * (uy / B - A / (B * B));
+      uyb += wl * cc / B;
+    }
+    // u = j/(rho cs2) + F/(2 rho)
+    const double jxb = uxb / rcs2, jyb = uyb / rcs2;
+    Fxb += 0.5 * uxb / rho;
+    Fyb += 0.5 * uyb / rho;
+    for (int i = 0; i < 9; i++) fb[i] += EX(i) * jxb + EY(i) * jyb;
+    // F = cap gc + mar (g2 gT - cdT gc) + rho a
+    const double capb = Fxb * gcx + Fyb * gcy;
+    const double marb = Fxb * (g2 * gTx - cdT * gcx) + Fyb * (g2 * gTy - cdT * gcy);
+    double gcxb = Fxb * cap - Fxb * mar * cdT;
+    double gcyb = Fyb * cap - Fyb * mar * cdT;
+    double g2b = mar * (Fxb * gTx + Fyb * gTy);
+    double gTxb = mar * g2 * Fxb, gTyb = mar * g2 * Fyb;
+    const double cdTb = -mar * (Fxb * gcx + Fyb * gcy);
+    double th_sig = -marb * ea;
+    // cap = -sigma kappa ea gabs
+    const double sigb = -capb * kappa * ea * gabs;
+    const double kapb = -capb * sigma * ea * gabs;
+    const double gabsb = -capb * sigma * kappa * ea;
+    gcxb += cdTb * gTx;
+    gcyb += cdTb * gTy;
+    gTxb += cdTb * gcx;
+    gTyb += cdTb * gcy;
+    if (gabs > 0.0) g2b += gabsb / (2.0 * gabs);
+    gcxb += 2.0 * g2b * gcx;
+    gcyb += 2.0 * g2b * gcy;
+    // sigma = sigma0 - sigmaT (T - Tref)
+    Tb += -sigb * P.sigmaT;
+    th_sig += -sigb * (TT - P.Tref);
+    // mu = 2 beta c (c-1)(2c-1) - eps^2 lap c
+    cb += mub * P.beta2 * (6.0 * cc * cc - 6.0 * cc + 1.0);
+    const double lapb = -mub * P.eps2;
+
+    for (int i = 0; i < 9; i++) {
+      aout[(int64_t)i * G.N + k] = fb[i];
+      aout[(int64_t)(9 + i) * G.N + k] = gbr[i];
+      aout[(int64_t)(18 + i) * G.N + k] = hb[i];
+    }
+    S[(int64_t)S_GCX * G.N + k] = gcxb;
+    S[(int64_t)S_GCY * G.N + k] = gcyb;
+    S[(int64_t)S_LAP * G.N + k] = lapb;
+    S[(int64_t)S_GTX * G.N + k] = gTxb;
+    S[(int64_t)S_GTY * G.N + k] = gTyb;
+    S[(int64_t)S_GPX * G.N + k] = gpxb;
+    S[(int64_t)S_GPY * G.N + k] = gpyb;
+    S[(int64_t)S_KAP * G.N + k] = kapb;
+    S[(int64_t)S_C * G.N + k] = cb;
+    S[(int64_t)S_P * G.N + k] = pb;
+    S[(int64_t)S_T * G.N + k] = Tb;
+    acc[0] += th_sig;
+    acc[1] += th_eta;
+    acc[2] += th_lam;
+  }
+  block_sum(acc, sh);
+  if (threadIdx.x == 0)
+    for (int j = 0; j < 4; j++) part[blockIdx.x * 4 + j] = acc[j];
+}
+
+// ---------------------------------------------------------------- B
+// kappa(X) = sum_i (w_i/cs2) xi_i . n(X + xi_i)  =>  n-bar(Y) = sum_i
+// (w_i/cs2) xi_i kappa-bar(Y - xi_i) over cells Y - xi_i; then through
+// n = v / s, s = sqrt(|v|^2 + eta_n^2): v-bar = n-bar/s - v (v.n-bar)/s^3.
+__global__ void pass_B(Geo G, const InstDev* __restrict__ d, const double* __restrict__ C,
+                       const double* __restrict__ S, double* __restrict__ VX,
+                       double* __restrict__ VY) {
+  const InstDev& I = *d;
+  const int64_t NE = (int64_t)(G.ny + 2) * G.nx;
+  const double* kb = S + (int64_t)S_KAP * G.N;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < NE;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(k % G.nx), y = (int)(k / G.nx) - 1;
+    double nbx = 0, nby = 0;
+    for (int i = 1; i < 9; i++) {
+      const int yy = y - EY(i);
+      if (yy < 0 || yy >= G.ny) continue;
+      const double kv = kb[(int64_t)yy * G.nx + wrap(x - EX(i), G.nx)];
+      nbx += WGT<double>(i) * EX(i) / CS2 * kv;
+      nby += WGT<double>(i) * EY(i) / CS2 * kv;
+    }
+    double vx, vy;
+    grad_at([&](int a, int bb) { return cget(C, G, a, bb); }, x, y, vx, vy);
+    const double s2 = vx * vx + vy * vy + I.pd.eta_n2;
+    const double s = sqrt(s2);
+    const double vn = vx * nbx + vy * nby;
+    VX[k] = nbx / s - vx * vn / (s2 * s);
+    VY[k] = nby / s - vy * vn / (s2 * s);
+  }
+}
+
+// ---------------------------------------------------------------- CD
+__global__ void pass_CD(Geo G, const InstDev* __restrict__ d, const double* __restrict__ S,
+                        const double* __restrict__ VX, const double* __restrict__ VY,
+                        double* __restrict__ aout) {
+  const InstDev& I = *d;
+  const int ny = G.ny;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < G.N;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(k % G.nx), y = (int)(k / G.nx);
+    double cb = S[(int64_t)S_C * G.N + k];
+    double pb = S[(int64_t)S_P * G.N + k];
+    double Tb = S[(int64_t)S_T * G.N + k];
+    // Laplacian centre term
+    double sw = 0.0;
+    for (int i = 1; i < 9; i++) sw += WGT<double>(i);
+    cb += -2.0 * sw / CS2 * S[(int64_t)S_LAP * G.N + k];
+    // positions q holding c(x, y): the cell and its ghost images
+    int qs[5], nq = 0;
+    qs[nq++] = y;
+    const int gr[4] = {-2, -1, ny, ny + 1};
+    for (int j = 0; j < 4; j++) {
+      const int m = gr[j] < 0 ? -1 - gr[j] : 2 * ny - 1 - gr[j];
+      if (m == y) qs[nq++] = gr[j];
+    }
+    for (int jq = 0; jq < nq; jq++) {
+      const int qy = qs[jq];
+      const bool depth1 = qy >= -1 && qy <= ny;  // p, T ghosts reach one row
+      const double tsign = (qy == y) ? 1.0 : -1.0;
+      for (int i = 1; i < 9; i++) {
+        const int X = wrap(x - EX(i), G.nx), Y = qy - EY(i);
+        const double wa = WGT<double>(i) / CS2;
+        if (Y >= 0 && Y < ny) {
+          const int64_t kk = (int64_t)Y * G.nx + X;
+          cb += wa * (EX(i) * S[(int64_t)S_GCX * G.N + kk] + EY(i) * S[(int64_t)S_GCY * G.N + kk]);
+          cb += 2.0 * wa * S[(int64_t)S_LAP * G.N + kk];
+          if (depth1) {
+            pb += wa * (EX(i) * S[(int64_t)S_GPX * G.N + kk] +
+                        EY(i) * S[(int64_t)S_GPY * G.N + kk]);
+            Tb += tsign * wa *
+                  (EX(i) * S[(int64_t)S_GTX * G.N + kk] + EY(i) * S[(int64_t)S_GTY * G.N + kk]);
+          }
+        }
+        if (Y >= -1 && Y <= ny) {
+          const int64_t ke = (int64_t)(Y + 1) * G.nx + X;
+          cb += wa * (EX(i) * VX[ke] + EY(i) * VY[ke]);
+        }
+      }
+    }
+    const double Tsc = Tb / (I.pd.rho * I.pd.cv);
+    for (int i = 0; i < 9; i++) {
+      aout[(int64_t)i * G.N + k] += pb;
+      aout[(int64_t)(9 + i) * G.N + k] += cb;
+      aout[(int64_t)(18 + i) * G.N + k] += Tsc;
+    }
+  }
+}
+
+__global__ void dT0_kernel(Geo G, const InstDev* __restrict__ d, const double* __restrict__ a,
+                           double* __restrict__ out) {
+  const double rcv = d->pd.rho * d->pd.cv;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < G.N;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int i = 0; i < 9; i++) s += WGT<double>(i) * a[(int64_t)(18 + i) * G.N + k];
+    out[k] = rcv * s;
+  }
+}
+
+// final reduction of the per-block partials: into out[0..3] (overwrite) or
+// added to acc[0..3]
+__global__ void reduce_parts(const double* __restrict__ part, double* __restrict__ out,
+                             int accumulate) {
+  __shared__ double sh[4 * TPB];
+  double v[4] = {0, 0, 0, 0};
+  for (int bb = threadIdx.x; bb < RBLK; bb += TPB)
+    for (int j = 0; j < 4; j++) v[j] += part[bb * 4 + j];
+  block_sum(v, sh);
+  if (threadIdx.x == 0)
+    for (int j = 0; j < 4; j++) out[j] = accumulate ? out[j] + v[j] : v[j];
+}
+
+}  // namespace adj
+
+// Scratch doubles needed for one instance of nx x ny cells.
+int64_t adjoint_scratch_doubles(int nx, int ny) {
+  const int64_t N = (int64_t)nx * ny, NE = (int64_t)nx * (ny + 2);
+  return 27 * N + 3 * N + 2 * NE + adj::S_NUM * N + 2 * NE + 4 * adj::RBLK + 8;
+}
+
+cudaError_t launch_observable(const InstDev* d, int nx, int ny, const double* Q, double* scratch,
+                              double* out4, cudaStream_t s) {
+  using namespace adj;
+  const Geo G{nx, ny, (int64_t)nx * ny};
+  const int64_t NE = (int64_t)nx * (ny + 2);
+  double* C = scratch + 27 * G.N;
+  double* Pp = C + G.N;
+  double* T = Pp + G.N;
+  double* NX = T + G.N;
+  double* NY = NX + NE;
+  double* S = NY + NE;
+  double* part = S + S_NUM * G.N + 2 * NE;
+  const int gN = (int)((G.N + TPB - 1) / TPB < 65535 ? (G.N + TPB - 1) / TPB : 65535);
+  const int gE = (int)((NE + TPB - 1) / TPB < 65535 ? (NE + TPB - 1) / TPB : 65535);
+  pass_M<<<gN, TPB, 0, s>>>(G, d, Q, C, Pp, T);
+  pass_N<<<gE, TPB, 0, s>>>(G, d, C, NX, NY);
+  pass_A<0><<<RBLK, TPB, 0, s>>>(G, d, Q, C, Pp, T, NX, NY, nullptr, nullptr, 0.0, nullptr,
+                                 nullptr, part);
+  reduce_parts<<<1, TPB, 0, s>>>(part, out4, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_step(const InstDev* d, int nx, int ny, const double* Q,
+                                const double* a_next, double wl, const double* obs,
+                                double* a_out, double* theta_acc, double* scratch,
+                                cudaStream_t s) {
+  using namespace adj;
+  const Geo G{nx, ny, (int64_t)nx * ny};
+  const int64_t NE = (int64_t)nx * (ny + 2);
+  double* b = scratch;
+  double* C = b + 27 * G.N;
+  double* Pp = C + G.N;
+  double* T = Pp + G.N;
+  double* NX = T + G.N;
+  double* NY = NX + NE;
+  double* S = NY + NE;
+  double* VX = S + S_NUM * G.N;
+  double* VY = VX + NE;
+  double* part = VY + NE;
+  const int gN = (int)((G.N + TPB - 1) / TPB < 65535 ? (G.N + TPB - 1) / TPB : 65535);
+  const int gE = (int)((NE + TPB - 1) / TPB < 65535 ? (NE + TPB - 1) / TPB : 65535);
+  pass_M<<<gN, TPB, 0, s>>>(G, d, Q, C, Pp, T);
+  pass_N<<<gE, TPB, 0, s>>>(G, d, C, NX, NY);
+  if (a_next) {
+    pass_P<<<gN, TPB, 0, s>>>(G, a_next, b);
+  } else {
+    cudaError_t e = cudaMemsetAsync(b, 0, sizeof(double) * 27 * G.N, s);
+    if (e != cudaSuccess) return e;
+  }
+  pass_A<1><<<RBLK, TPB, 0, s>>>(G, d, Q, C, Pp, T, NX, NY, b, obs, wl, a_out, S, part);
+  reduce_parts<<<1, TPB, 0, s>>>(part, theta_acc, 1);
+  pass_B<<<gE, TPB, 0, s>>>(G, d, C, S, VX, VY);
+  pass_CD<<<gN, TPB, 0, s>>>(G, d, S, VX, VY, a_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_dT0(const InstDev* d, int nx, int ny, const double* a, double* dT0,
+                               cudaStream_t s) {
+  using namespace adj;
+  const Geo G{nx, ny, (int64_t)nx * ny};
+  const int gN = (int)((G.N + TPB - 1) / TPB < 65535 ? (G.N + TPB - 1) / TPB : 65535);
+  dT0_kernel<<<gN, TPB, 0, s>>>(G, d, a, dT0);
+  return cudaGetLastError();
+}
+
+}  // namespace lbe

@@ -624,6 +624,133 @@ lbe_status check_handle(lbe_handle* h, int32_t instance) {
   return LBE_OK;
 }
 
+// ------------------------------------------------------------------ adjoint
+// Device allocation owned by a scope (freed on every return path).
+struct DevBuf {
+  char* p = nullptr;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  double* d() const { return reinterpret_cast<double*>(p); }
+};
+
+lbe_status dalloc(lbe_handle* h, DevBuf& b, size_t bytes, const char* what) {
+  if (fault_alloc() || cudaMalloc(&b.p, bytes ? bytes : 1) != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    return fail(h, LBE_ENOMEM, "adjoint: cannot allocate %zu bytes for %s", bytes, what);
+  }
+  return LBE_OK;
+}
+
+lbe_status check_adjoint_handle(lbe_handle* h) {
+  lbe_status st = check_handle(h, 0);
+  if (st) return st;
+  if (h->n != 1) return fail(h, LBE_EINVAL, "the adjoint needs a handle of one instance (has %d)", h->n);
+  if (h->bad) return fail(h, LBE_ESTATE, "handle is in an error state; set a state or load a checkpoint");
+  return LBE_OK;
+}
+
+// Checkpointed forward + reverse sweep (see lbe_adjoint in lbe.h).
+lbe_status adjoint_run(lbe_handle* h, const lbe_adjoint_spec& sp, double* loss, double* grad,
+                       double* dT0, double* dQ0, bool on_device) {
+  InstHost& H = h->inst[0];
+  const int nx = H.nx, ny = H.ny;
+  const size_t N = (size_t)nx * ny, S27 = 27 * N;
+  const int64_t NS = sp.steps, W = sp.window, K = sp.ckpt_every;
+  const int64_t nseg = (NS + K - 1) / K;
+  const int64_t kk = K < NS ? K : NS;
+  const InstDev* d1 = h->d_finst;
+  lbe_status st;
+  DevBuf ck, states, abuf, scr, small, fin;
+  if ((st = dalloc(h, ck, (size_t)nseg * H.buf_bytes, "checkpoints"))) return st;
+  if ((st = dalloc(h, states, sizeof(double) * (size_t)(kk + 1) * S27, "segment states"))) return st;
+  if ((st = dalloc(h, abuf, sizeof(double) * 2 * S27, "adjoint states"))) return st;
+  if ((st = dalloc(h, scr, sizeof(double) * (size_t)adjoint_scratch_doubles(nx, ny), "scratch")))
+    return st;
+  if ((st = dalloc(h, small, sizeof(double) * (size_t)(4 + 4 * W), "reductions"))) return st;
+  if ((st = dalloc(h, fin, H.buf_bytes, "final state"))) return st;
+  double* theta = small.d();
+  double* obs = theta + 4;
+  CU(h, cudaMemsetAsync(theta, 0, sizeof(double) * 4, h->stream));
+  auto cur_buf = [&]() { return H.arena + (size_t)h->parity * H.buf_bytes; };
+
+  // forward: raw checkpoint at the start of every segment
+  const int64_t steps0 = h->steps;
+  for (int64_t sg = 0; sg < nseg; sg++) {
+    CU(h, cudaMemcpyAsync(ck.p + (size_t)sg * H.buf_bytes, cur_buf(), H.buf_bytes,
+                          cudaMemcpyDeviceToDevice, h->stream));
+    const int64_t len = std::min(K, NS - sg * K);
+    if ((st = run_steps(h, len))) return st;
+    if ((st = wait_checked(h))) return st;
+  }
+  const int fin_parity = h->parity;
+  CU(h, cudaMemcpyAsync(fin.p, cur_buf(), H.buf_bytes, cudaMemcpyDeviceToDevice, h->stream));
+
+  // reverse sweep over the segments; a_nxt holds dL/dQ_{n+1}
+  double* a_cur = abuf.d();
+  double* a_nxt = abuf.d() + S27;
+  bool have_next = false;
+  const int64_t first_w = NS - W + 1;
+  for (int64_t sg = nseg - 1; sg >= 0; sg--) {
+    const int64_t n0 = sg * K;
+    const int64_t n1 = (sg == nseg - 1) ? NS : n0 + K - 1;
+    CU(h, cudaMemcpyAsync(cur_buf(), ck.p + (size_t)sg * H.buf_bytes, H.buf_bytes,
+                          cudaMemcpyDeviceToDevice, h->stream));
+    cudaError_t e = launch_pull(h->storage, d1, nx, ny, states.d(), h->parity, h->stream);
+    for (int64_t t = 1; e == cudaSuccess && t <= n1 - n0; t++) {
+      if ((st = launch_steps_direct(h, 1))) return st;
+      e = launch_pull(h->storage, d1, nx, ny, states.d() + (size_t)t * S27, h->parity, h->stream);
+    }
+    for (int64_t n = n1; e == cudaSuccess && n >= n0; n--) {
+      const double* Q = states.d() + (size_t)(n - n0) * S27;
+      const double wl = n >= first_w ? 1.0 / (double)W : 0.0;
+      double* o = n >= first_w ? obs + 4 * (n - first_w) : nullptr;
+      if (o) e = launch_observable(d1, nx, ny, Q, scr.d(), o, h->stream);
+      if (e == cudaSuccess)
+        e = launch_adjoint_step(d1, nx, ny, Q, have_next ? a_nxt : nullptr, wl, o, a_cur, theta,
+                                scr.d(), h->stream);
+      std::swap(a_cur, a_nxt);
+      have_next = true;
+    }
+    if (e != cudaSuccess) return fail(h, LBE_ECUDA, "adjoint sweep: %s", cudaGetErrorString(e));
+    if ((st = wait_checked(h))) return st;
+  }
+  // a_nxt = dL/dQ_0
+  if (dT0) {
+    double* dst = on_device ? dT0 : scr.d();
+    cudaError_t e = launch_adjoint_dT0(d1, nx, ny, a_nxt, dst, h->stream);
+    if (e != cudaSuccess) return fail(h, LBE_ECUDA, "dT0 kernel: %s", cudaGetErrorString(e));
+    if (!on_device)
+      CU(h, cudaMemcpyAsync(dT0, dst, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream));
+  }
+  if (dQ0)
+    CU(h, cudaMemcpyAsync(dQ0, a_nxt, sizeof(double) * S27,
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          h->stream));
+  std::vector<double> hobs(4 * (size_t)W), hth(4);
+  CU(h, cudaMemcpyAsync(hobs.data(), obs, sizeof(double) * 4 * W, cudaMemcpyDeviceToHost,
+                        h->stream));
+  CU(h, cudaMemcpyAsync(hth.data(), theta, sizeof(double) * 4, cudaMemcpyDeviceToHost, h->stream));
+  // back to the state after the forward run
+  h->parity = fin_parity;
+  CU(h, cudaMemcpyAsync(cur_buf(), fin.p, H.buf_bytes, cudaMemcpyDeviceToDevice, h->stream));
+  h->steps = steps0 + NS;
+  h->prev_valid = false;
+  if ((st = wait_checked(h))) return st;
+  if (loss) {
+    double L = 0.0;
+    for (int64_t j = 0; j < W; j++) L += hobs[4 * j] / hobs[4 * j + 1];
+    *loss = L / (double)W;
+  }
+  if (grad)
+    for (int j = 0; j < 3; j++) grad[j] = hth[j];
+  return LBE_OK;
+}
+
 }  // namespace
 
 void lbe::set_thread_error(const char* msg) { g_thread_err = msg ? msg : ""; }
@@ -882,6 +1009,63 @@ lbe_status lbe_get_tile(const lbe_handle* h, int32_t out[4]) {
   out[1] = h->grid;
   out[2] = is_strip(h->tile) ? h->seg : 0;
   out[3] = (int32_t)std::min<int64_t>(h->total_tiles, 2147483647);
+  return LBE_OK;
+}
+
+lbe_status lbe_adjoint(lbe_handle* h, const lbe_adjoint_spec* spec, double* loss,
+                       double grad[3], double* dT0, double* dQ0, int32_t on_device) {
+  lbe_status st = check_adjoint_handle(h);
+  if (st) return st;
+  if (!spec) return fail(h, LBE_EINVAL, "spec is NULL");
+  if (spec->steps < 1) return fail(h, LBE_EINVAL, "spec.steps must be >= 1");
+  if (spec->window < 1 || spec->window > spec->steps)
+    return fail(h, LBE_EINVAL, "spec.window must be in [1, steps]");
+  if (spec->ckpt_every < 1) return fail(h, LBE_EINVAL, "spec.ckpt_every must be >= 1");
+  return adjoint_run(h, *spec, loss, grad, dT0, dQ0, on_device != 0);
+}
+
+lbe_status lbe_adjoint_step(lbe_handle* h, const double* Q, const double* a_next, double wl,
+                            double* a_out, double grad[3]) {
+  lbe_status st = check_adjoint_handle(h);
+  if (st) return st;
+  if (!Q || !a_out) return fail(h, LBE_EINVAL, "Q and a_out must be device pointers");
+  const InstHost& H = h->inst[0];
+  DevBuf scr, small;
+  if ((st = dalloc(h, scr, sizeof(double) * (size_t)adjoint_scratch_doubles(H.nx, H.ny), "scratch")))
+    return st;
+  if ((st = dalloc(h, small, sizeof(double) * 8, "reductions"))) return st;
+  double* theta = small.d();
+  double* obs = theta + 4;
+  CU(h, cudaMemsetAsync(theta, 0, sizeof(double) * 4, h->stream));
+  cudaError_t e = cudaSuccess;
+  if (wl != 0.0) e = launch_observable(h->d_finst, H.nx, H.ny, Q, scr.d(), obs, h->stream);
+  if (e == cudaSuccess)
+    e = launch_adjoint_step(h->d_finst, H.nx, H.ny, Q, a_next, wl, obs, a_out, theta, scr.d(),
+                            h->stream);
+  if (e != cudaSuccess) return fail(h, LBE_ECUDA, "adjoint step: %s", cudaGetErrorString(e));
+  double th[4];
+  CU(h, cudaMemcpyAsync(th, theta, sizeof th, cudaMemcpyDeviceToHost, h->stream));
+  if ((st = wait(h))) return st;
+  if (grad)
+    for (int j = 0; j < 3; j++) grad[j] += th[j];
+  return LBE_OK;
+}
+
+lbe_status lbe_observable(lbe_handle* h, const double* Q, double* out) {
+  lbe_status st = check_adjoint_handle(h);
+  if (st) return st;
+  if (!Q || !out) return fail(h, LBE_EINVAL, "Q (device) and out (host) must not be NULL");
+  const InstHost& H = h->inst[0];
+  DevBuf scr, small;
+  if ((st = dalloc(h, scr, sizeof(double) * (size_t)adjoint_scratch_doubles(H.nx, H.ny), "scratch")))
+    return st;
+  if ((st = dalloc(h, small, sizeof(double) * 4, "reductions"))) return st;
+  cudaError_t e = launch_observable(h->d_finst, H.nx, H.ny, Q, scr.d(), small.d(), h->stream);
+  if (e != cudaSuccess) return fail(h, LBE_ECUDA, "observable: %s", cudaGetErrorString(e));
+  double o[4];
+  CU(h, cudaMemcpyAsync(o, small.d(), sizeof o, cudaMemcpyDeviceToHost, h->stream));
+  if ((st = wait(h))) return st;
+  *out = o[0] / o[1];
   return LBE_OK;
 }
 

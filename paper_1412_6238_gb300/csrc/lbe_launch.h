@@ -92,6 +92,23 @@ cudaError_t launch_sums(const double* cur, const double* prev, int64_t n, double
                         double* out, cudaStream_t s);
 cudaError_t launch_f64_to_f32(const double* in, float* out, int64_t n, cudaStream_t s);
 
+// Adjoint kernels (lbe_adjoint.cu), FP64, one instance d_one of nx x ny.
+// Scratch: adjoint_scratch_doubles(nx, ny) doubles.
+int64_t adjoint_scratch_doubles(int nx, int ny);
+// out4[0] = sum c u_y, out4[1] = sum c of the state Q[27][ny][nx] (device).
+cudaError_t launch_observable(const InstDev* d_one, int nx, int ny, const double* Q,
+                              double* scratch, double* out4, cudaStream_t s);
+// a_out = Post'(Q)^T Pull^T a_next + wl dl/dQ with obs = {sum c u_y, sum c} of
+// Q (device, read only if wl != 0); theta_acc[0..2] (device) += the parameter
+// partials.  a_next may be nullptr (zero).
+cudaError_t launch_adjoint_step(const InstDev* d_one, int nx, int ny, const double* Q,
+                                const double* a_next, double wl, const double* obs,
+                                double* a_out, double* theta_acc, double* scratch,
+                                cudaStream_t s);
+// dT0[k] = rho c_v sum_i w_i a[18 + i][k]
+cudaError_t launch_adjoint_dT0(const InstDev* d_one, int nx, int ny, const double* a,
+                               double* dT0, cudaStream_t s);
+
 // Sets the message lbe_last_error(NULL) returns on this thread (lbe_api.cu).
 void set_thread_error(const char* msg);
 

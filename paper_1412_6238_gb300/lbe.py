@@ -26,7 +26,8 @@ PARAM_KEYS = ("rho", "cv", "eta1", "eta2", "lam1", "lam2", "sigma0", "sigmaT", "
 EXPORTS = ("lbe_abi_version", "lbe_init", "lbe_init_batch", "lbe_step", "lbe_synchronize",
            "lbe_fields", "lbe_sums", "lbe_get_state", "lbe_set_state", "lbe_save", "lbe_load",
            "lbe_num_tiles", "lbe_tile_shape", "lbe_set_tile", "lbe_get_tile", "lbe_steps_done", "lbe_stream",
-           "lbe_num_instances", "lbe_state_bytes", "lbe_destroy", "lbe_last_error")
+           "lbe_num_instances", "lbe_state_bytes", "lbe_destroy", "lbe_last_error",
+           "lbe_adjoint", "lbe_adjoint_step", "lbe_observable")
 
 
 class LBEError(RuntimeError):
@@ -44,6 +45,11 @@ class InitFields(ctypes.Structure):
     _fields_ = [("c0", ctypes.POINTER(ctypes.c_double)), ("T0", ctypes.POINTER(ctypes.c_double)),
                 ("Tbot", ctypes.POINTER(ctypes.c_double)),
                 ("Ttop", ctypes.POINTER(ctypes.c_double))]
+
+
+class AdjointSpec(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("window", ctypes.c_int64),
+                ("ckpt_every", ctypes.c_int64)]
 
 
 _lock = threading.Lock()
@@ -89,6 +95,11 @@ def library(build: bool = True) -> ctypes.CDLL:
                 "lbe_state_bytes": ([H], ctypes.c_int64),
                 "lbe_destroy": ([H], None),
                 "lbe_last_error": ([H], ctypes.c_char_p),
+                "lbe_adjoint": ([H, ctypes.POINTER(AdjointSpec), dp, dp, ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.c_int32], st),
+                "lbe_adjoint_step": ([H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                                      ctypes.c_void_p, dp], st),
+                "lbe_observable": ([H, ctypes.c_void_p, dp], st),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -247,6 +258,8 @@ class LBE:
         state = state.to(torch.float64).contiguous()
         if tuple(state.shape) != (27, ny, nx):
             raise ValueError("state must have shape (27, %d, %d)" % (ny, nx))
+        if state.is_cuda:
+            self._order_after_torch()
         self._check(self._L.lbe_set_state(self._h, int(instance),
                                           ctypes.c_void_p(state.data_ptr()),
                                           int(state.is_cuda)))
@@ -256,3 +269,62 @@ class LBE:
 
     def load(self, path: str):
         self._check(self._L.lbe_load(self._h, os.fsencode(path)))
+
+    # ---- discrete adjoint (single-instance handles)
+    def adjoint(self, steps: int, window: int, ckpt_every: int = 100, want_dT0: bool = True,
+                want_dQ0: bool = False) -> dict:
+        """Run ``steps`` steps from the current state and the reverse sweep.
+        Returns {loss, grad (sigmaT, eta ratio, lam ratio), dT0, dQ0} with the
+        field gradients as float64 CUDA tensors (None when not requested)."""
+        import torch
+        ny, nx = self.shapes[0]
+        dev = self.stream.device
+        dT0 = torch.empty((ny, nx), dtype=torch.float64, device=dev) if want_dT0 else None
+        dQ0 = torch.empty((27, ny, nx), dtype=torch.float64, device=dev) if want_dQ0 else None
+        spec = AdjointSpec(int(steps), int(window), int(ckpt_every))
+        loss = ctypes.c_double()
+        grad = (ctypes.c_double * 3)()
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr() if t is not None else 0)  # noqa: E731
+        self._check(self._L.lbe_adjoint(self._h, ctypes.byref(spec), ctypes.byref(loss), grad,
+                                        ptr(dT0), ptr(dQ0), 1))
+        return dict(loss=loss.value, grad=tuple(grad), dT0=dT0, dQ0=dQ0)
+
+    def adjoint_step(self, Q, a_next=None, wl: float = 0.0):
+        """(a_out, grad[3]) of one adjoint step at the state Q (CUDA float64
+        tensor [27, ny, nx]); a_next = dL/dQ_{n+1} or None (zero)."""
+        import torch
+        ny, nx = self.shapes[0]
+        Q = self._dev_state(Q)
+        an = self._dev_state(a_next) if a_next is not None else None
+        out = torch.empty_like(Q)
+        grad = (ctypes.c_double * 3)(0.0, 0.0, 0.0)
+        self._check(self._L.lbe_adjoint_step(
+            self._h, ctypes.c_void_p(Q.data_ptr()),
+            ctypes.c_void_p(an.data_ptr() if an is not None else 0), float(wl),
+            ctypes.c_void_p(out.data_ptr()), grad))
+        return out, tuple(grad)
+
+    def observable(self, Q) -> float:
+        """Phase-1 centroid velocity sum(c u_y) / sum(c) of the state Q."""
+        Q = self._dev_state(Q)
+        out = ctypes.c_double()
+        self._check(self._L.lbe_observable(self._h, ctypes.c_void_p(Q.data_ptr()),
+                                           ctypes.byref(out)))
+        return out.value
+
+    def _dev_state(self, t):
+        import torch
+        ny, nx = self.shapes[0]
+        if not torch.is_tensor(t):
+            t = torch.from_numpy(np.ascontiguousarray(np.asarray(t, dtype=np.float64)))
+        t = t.to(device=self.stream.device, dtype=torch.float64).contiguous()
+        if tuple(t.shape) != (27, ny, nx):
+            raise ValueError("state must have shape (27, %d, %d)" % (ny, nx))
+        self._order_after_torch()
+        return t
+
+    def _order_after_torch(self):
+        """Make the handle's stream wait for work torch queued on its current
+        stream (copies that produced an input tensor)."""
+        import torch
+        self.stream.wait_stream(torch.cuda.current_stream(self.stream.device))
