@@ -52,6 +52,9 @@ def parse_args():
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the 16-bit storage and batched-sweep measurements")
     ap.add_argument("--batch-steps", type=int, default=50)
+    ap.add_argument("--kernel", type=int, default=-1,
+                    help="step kernel id (lbe_set_tile); default: the library's choice")
+    ap.add_argument("--seg", type=int, default=0, help="rows per strip work item (0 = auto)")
     return ap.parse_args()
 
 
@@ -156,13 +159,13 @@ def kernel_source_sha() -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1412_6238_gb300", "csrc")
     for f in ("lbe_common.cuh", "lbe_cell.cuh", "lbe_tile.cuh", "lbe_strip.cuh",
-              "lbe_step_inst.cuh", "lbe_step_f32.cu"):
+              "lbe_stash.cuh", "lbe_step_inst.cuh", "lbe_step_f32.cu"):
         h.update(open(os.path.join(d, f), "rb").read())
     h.update(repr(_b.UNITS["lbe_step_f32.cu"]).encode())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
+def profiled_traffic(kernel_id=None):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source."""
     try:
@@ -172,6 +175,8 @@ def profiled_traffic():
                 k, v = line.lstrip()[2:].split(":", 1)
                 kv[k.strip()] = v.strip().strip("`")
         if kv.get("source_sha") != kernel_source_sha():
+            return None
+        if kernel_id is not None and int(kv.get("kernel_id", -1)) != kernel_id:
             return None
         return float(kv["traffic_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
@@ -235,6 +240,9 @@ def run_ours(args, ws, rank, local):
     w = wl.droplet_scaled(args.nx, args.ny)
     cells = w.cells
     sim = LBE(w, storage=args.storage)
+    if args.kernel >= 0 or args.seg > 0:
+        sim.set_tile(args.kernel if args.kernel >= 0 else sim.get_tile()["kernel"], 0, args.seg)
+    kernel = sim.get_tile()
     stream = sim.stream
     sim.step(args.warmup)
     sim.synchronize()
@@ -257,7 +265,8 @@ def run_ours(args, ws, rank, local):
     algo_bytes = cells * BYTES_PER_CELL[args.storage]
     achieved = algo_bytes / (launch_ms / 1e3) / 1e9
     peak, peak_kind = hbm_peak()
-    traffic = profiled_traffic() if (args.storage == "f32" and args.nx == NX and args.ny == NY) else None
+    traffic = (profiled_traffic(kernel["kernel"])
+               if (args.storage == "f32" and args.nx == NX and args.ny == NY) else None)
     fin = sim.sums()
     ref_fields = sim.fields(device="cuda") if not args.no_variants else None
     del sim
@@ -312,7 +321,8 @@ def run_ours(args, ws, rank, local):
                            "storage": args.storage, "cells": cells,
                            "l2": "state 2 x %.2f GB >> L2 (no flush needed)"
                                  % (algo_bytes / 2 / 1e9),
-                           "parallelism": "replicas x%d" % ws},
+                           "parallelism": "replicas x%d" % ws,
+                           "kernel": kernel},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
                              "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                              "peak_kind": peak_kind,

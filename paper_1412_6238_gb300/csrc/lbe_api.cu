@@ -321,16 +321,23 @@ lbe_status setup_tiles(lbe_handle* h) {
       h->seg = h->seg_req;
     } else {
       // rows per work item: minimise (waves of the persistent grid) x (rows
-      // per item + the 4 warm-up rows every item recomputes)
+      // per item + the warm-up rows every item recomputes).  The stash
+      // kernel measured slower with items longer than about 96 rows (4096^2:
+      // 80 rows 18.3 GLUPS, 128 rows 16.5, 316 rows in one wave 17.7) and an
+      // item start costs it about 6 rows.
       const int64_t slots = h->grid_req == -1 ? (int64_t)occ * h->num_sms : h->grid;
+      const bool stash = h->tile == STASH_ID;
+      const int seg_lo = std::min(8, max_ny);
+      const int seg_hi = stash ? std::min(96, max_ny) : max_ny;
+      const int warm = stash ? 6 : 4;
       double best = 1e300;
-      int best_seg = max_ny;
-      for (int seg = 8; seg <= max_ny; seg++) {
+      int best_seg = seg_hi;
+      for (int seg = seg_lo; seg <= seg_hi; seg++) {
         int64_t items = 0;
         for (auto& H : h->inst)
           items += (int64_t)((H.nx + nc - 1) / nc) * ((H.ny + seg - 1) / seg);
         const double waves = (double)((items + slots - 1) / slots);
-        const double cost = waves * (seg + 4);
+        const double cost = waves * (seg + warm);
         if (cost < best * (1 - 1e-9)) {
           best = cost;
           best_seg = seg;
@@ -541,8 +548,10 @@ lbe_status create(int32_t n, const lbe_params* params, const lbe_init_fields* in
       H.g0_off = 0;
       H.buf_bytes = 27 * H.plane_bytes;
     }
-    CUB(cudaMalloc(&H.arena, 2 * H.buf_bytes));
-    CUB(cudaMemsetAsync(H.arena, 0, 2 * H.buf_bytes, h->stream));
+    // ARENA_TAIL: reads of a strip's last warp may run past the last row of
+    // the last plane (into pitch padding, never used); keep them allocated
+    CUB(cudaMalloc(&H.arena, 2 * H.buf_bytes + ARENA_TAIL));
+    CUB(cudaMemsetAsync(H.arena, 0, 2 * H.buf_bytes + ARENA_TAIL, h->stream));
     // walls: Tbot[nx], Ttop[nx] (double), then 4 x nx floats of T_w - T_r
     CUB(cudaMalloc(&H.walls, sizeof(double) * 2 * H.nx + sizeof(float) * 4 * H.nx));
     H.Tbot.assign(init[j].Tbot, init[j].Tbot + H.nx);
@@ -609,7 +618,8 @@ lbe_status create(int32_t n, const lbe_params* params, const lbe_init_fields* in
     // every instance at least XG columns wide), else the tile kernel
     int min_nx = 1 << 30;
     for (auto& H : h->inst) min_nx = std::min(min_nx, H.nx);
-    h->tile = (h->storage != LBE_F64 && min_nx >= XG) ? STRIP_FIRST : 0;
+    h->tile = (h->storage == LBE_F64 || min_nx < XG) ? 0
+              : (h->storage == LBE_F32 ? STASH_ID : STRIP_FIRST);
   }
   lbe_status s2 = setup_tiles(h);
   if (s2) return bail(s2);

@@ -167,10 +167,8 @@ __device__ __forceinline__ void collide(const Phys<typename S::C>& P, const type
   // Gamma_i(u) = w_i (1 + xi.u/c_s^2 + ((xi.u/c_s^2)^2 - u^2/c_s^2)/2) (Eq. 6)
   const C uu = dv(ux * ux + uy * uy, cs2<C>(), C(3));
   const C Gm = P.Gm;
-  // H_i of Eq. 22
+  // H_i of Eq. 22 (H_0 below, in the FP64 branch)
   const C Hi = dv(Gm * d.mu, cs2<C>(), C(3));
-  const C H0 = dv(cc - dv((C(1) - WGT<C>(0)) * Gm * d.mu, cs2<C>(), C(3)), WGT<C>(0),
-                  C(9) / C(4));
   const C Gx = Fx - gpx, Gy = Fy - gpy;  // F - grad p (= Fbar, uniform rho)
   const C rcvT = P.rho * P.cv * (TT + d.Trow);  // rho c_v T (full T)
   const C rcvTr = P.rho_cv * d.Trow;            // rho c_v T_r(y)
@@ -179,23 +177,35 @@ __device__ __forceinline__ void collide(const Phys<typename S::C>& P, const type
     // FP32: the same terms regrouped.  With a = xi_i.u/c_s^2 and
     // q = a + ((a^2 - u^2/c_s^2)/2), Gamma_i = w_i (1 + q); opposite
     // directions share (a^2 - u^2/c_s^2)/2; F.(xi_i - u) = F.xi_i - F.u.
+    // The eight moving directions come first and the rest direction takes
+    // the remainder of each equilibrium (p, c and rho c_v T minus the sum of
+    // the other eight; the same value in exact arithmetic).  Computed
+    // directly, w_0 H_0 carries the FP32 representation error of w_0 = 4/9
+    // in the same direction at every bulk cell, a systematic drift of sum c
+    // over long runs.
     const C Fdu = Fx * ux + Fy * uy, Gdu = Gx * ux + Gy * uy;
     const C sg = cc * inv_rcs2;  // c / (rho c_s^2)
     const C ux3 = C(3) * ux, uy3 = C(3) * uy;
+    C sfe = C(0), sge = C(0), she = C(0);  // sums of the moving equilibria
+    auto relax = [&](int i, C G, C feq, C geq, C heqd, C Fxi, C Gxi) {
+      out(0, i, f[i] + omega_f * (feq - f[i]) + af * ((Fxi - Fdu) * G));
+      const C gdot = Gxi - Gdu;
+      out(1, i, g[i] + omega_g * (geq - g[i]) + ag * (sg * gdot) * G);
+      out(2, i, h[i] + omega_T * (heqd - h[i]) + aT * (inv_rcs2 * gdot) * (rcvT * G));
+    };
     auto dir = [&](int i, C W, C a, C hq, C Fxi, C Gxi) {
       const C q = a + hq;
       const C G = W + W * q;
       const C feq = W * (pp + rcs2 * q);
-      out(0, i, f[i] + omega_f * (feq - f[i]) + af * ((Fxi - Fdu) * G));
-      const C gdot = Gxi - Gdu;
-      const C geq = W * ((i == 0 ? H0 : Hi) + cc * q);
-      out(1, i, g[i] + omega_g * (geq - g[i]) + ag * (sg * gdot) * G);
+      const C geq = W * (Hi + cc * q);
       const C heqd = dev_h<S>() ? rcvTd * G + rcvTr * (W * q) : rcvT * G;
-      out(2, i, h[i] + omega_T * (heqd - h[i]) + aT * (inv_rcs2 * gdot) * (rcvT * G));
+      sfe += feq;
+      sge += geq;
+      she += heqd;
+      relax(i, G, feq, geq, heqd, Fxi, Gxi);
     };
     const C wa = WGT<C>(1), wd = WGT<C>(5);
     const C hu = C(-0.5) * uu;
-    dir(0, WGT<C>(0), C(0), hu, C(0), C(0));
     C a = ux3, hq = C(0.5) * (a * a - uu);
     dir(1, wa, a, hq, Fx, Gx);
     dir(3, wa, -a, hq, -Fx, -Gx);
@@ -211,7 +221,12 @@ __device__ __forceinline__ void collide(const Phys<typename S::C>& P, const type
     hq = C(0.5) * (a * a - uu);
     dir(6, wd, a, hq, Fy - Fx, Gy - Gx);
     dir(8, wd, -a, hq, Fx - Fy, Gx - Gy);
+    const C W0 = WGT<C>(0);
+    const C G0 = W0 + W0 * hu;
+    relax(0, G0, pp - sfe, cc - sge, (dev_h<S>() ? rcvTd : rcvT) - she, C(0), C(0));
   } else {
+    const C H0 = dv(cc - dv((C(1) - WGT<C>(0)) * Gm * d.mu, cs2<C>(), C(3)), WGT<C>(0),
+                    C(9) / C(4));
 #pragma unroll
     for (int i = 0; i < 9; i++) {
       const C W = WGT<C>(i);

@@ -11,14 +11,19 @@ namespace lbe {
 struct TileShape {
   int tx, ty;
 };
-// Kernel ids: 0..4 tile kernel with these tile shapes; 5, 6 strip kernel with
-// 124 / 60 output columns per strip (128 / 64 threads; ty = 0: a strip
-// marches over its rows).
+// Kernel ids: 0..4 tile kernel with these tile shapes; 5, 6 strip kernel
+// with TMA-staged source rows and 124 / 60 output columns per strip (128 / 64
+// threads; ty = 0: a strip marches over its rows); 7 strip kernel with a
+// per-warp stash of pulled populations, 124 output columns (16/32-bit).
 constexpr int NUM_TILE_SHAPES = 5;
-constexpr int NUM_TILES = 7;
+constexpr int NUM_TILES = 8;
 constexpr int STRIP_FIRST = 5;
-constexpr TileShape TILE_SHAPES[NUM_TILES] = {{32, 8},  {64, 4}, {32, 16}, {64, 8},
-                                              {128, 4}, {124, 0}, {60, 0}};
+constexpr int STASH_ID = 7;
+// bytes allocated after an instance's two population buffers, covering the
+// widest read past the end of a row of the stash kernel (36 + 96 elements)
+constexpr size_t ARENA_TAIL = 1024;
+constexpr TileShape TILE_SHAPES[NUM_TILES] = {{32, 8},  {64, 4},  {32, 16}, {64, 8},
+                                              {128, 4}, {124, 0}, {60, 0},  {124, 0}};
 inline bool is_strip(int tile) { return tile >= STRIP_FIRST && tile < NUM_TILES; }
 
 struct TmapSet;  // lbe_strip.cuh

@@ -1,0 +1,386 @@
+// The fused step as a column-strip marching kernel with per-warp stashes of
+// pulled populations (FP32 and 16-bit storages).
+//
+// Work items and thread mapping are those of the strip kernel (lbe_strip.cuh):
+// a CTA of NC threads marches up the rows [ya, yb) of a strip of NC - 4 output
+// columns, thread t owning column x0 - 2 + t so that the two halo columns on
+// each side are ordinary threads.  Instead of staging every source row whole
+// for the CTA, each warp stages only what its own 32 cells pull for a row m:
+// for each of the 27 populations (k, i), the elements of source row m - xi_iy
+// that cover its columns shifted by -xi_ix (or, at a wall, the reversed
+// population of row m itself), one bulk copy (cp.async.bulk) per population,
+// the start rounded down to 16 bytes (FP32: 36 elements = 144 bytes; 16-bit
+// planes: 40 elements = 80 bytes; the FP32 g_0 plane of the 16-bit forms:
+// 144 bytes), completing on an mbarrier of the warp.  A row's values stay in the warp's stash from the
+// time its moments are formed until it collides three iterations later: 4
+// rows x 27 populations per warp, about half the shared memory of the 7-row
+// source ring (FP32), so three CTAs fit on an SM instead of two, and no
+// thread waits for another warp's copies.
+//
+// Iteration i (from ya - 4 to yb):
+//   1. collide row i-1 (S2-S9 of lbe_cell.cuh) from its stash slot and the
+//      moment rings, and store its 27 values;
+//   2. the warp's copies of row i+3 into the slot that row i-1 has just freed;
+//   3. wait for the warp's copies of row i+2 and form its moments c, p, T
+//      (S1) into the rings; rows below the bottom wall use the pulled values
+//      of their mirror row, rows above the top wall copy the mirror rows in
+//      the rings;
+//   barrier; 4. unit normal of row i+1 (S2); barrier.
+// Every population is read from HBM once per step.  Every mbarrier wait is
+// bounded: on time-out the kernel sets *err, waits (bounded) for the warp's
+// copies in flight and returns.
+#pragma once
+
+#include "lbe_strip.cuh"
+
+namespace lbe {
+
+// One-dimensional bulk copy global -> shared (16-byte aligned addresses, a
+// multiple of 16 bytes), completing on an mbarrier.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
+                                          uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+// Stash layout of one warp-row for a storage form: population (k, i) has a
+// row of EW elements at byte offset off(k, i) of the slot; the g_0 row of the
+// 16-bit forms holds 36 FP32 elements.
+template <class S>
+struct StashFmt;
+template <>
+struct StashFmt<StF32> {
+  using E = float;
+  static constexpr int EW = 36;              // elements per population row
+  static constexpr int ROW = EW * 4;         // bytes (a multiple of 16)
+  static constexpr int SLOT_RAW = 27 * ROW;  // bytes of one warp's row
+  __host__ __device__ static constexpr int off(int k, int i) { return (k * 9 + i) * ROW; }
+};
+template <class E16>
+struct StashFmt16 {
+  using E = E16;
+  static constexpr int EW = 40;
+  static constexpr int ROW = EW * 2;
+  static constexpr int G0ROW = 36 * 4;
+  static constexpr int SLOT_RAW = 26 * ROW + G0ROW;
+  __host__ __device__ static constexpr int off(int k, int i) {
+    return (k == 1 && i == 0) ? 26 * ROW : dev_plane(k, i) * ROW;
+  }
+};
+template <>
+struct StashFmt<StF16> : StashFmt16<__half> {};
+template <>
+struct StashFmt<StBF16> : StashFmt16<__nv_bfloat16> {};
+
+template <class S, int NC>
+struct StashCfg {
+  using Fmt = StashFmt<S>;
+  static constexpr int NCO = NC - 4;          // output columns
+  static constexpr int NW = NC / 32;          // warps
+  static constexpr int SR = 4;                // stash rows per warp
+  static constexpr int SLOT = (Fmt::SLOT_RAW + 15) / 16 * 16;  // bytes of one warp's row
+  static constexpr int TX = Fmt::SLOT_RAW;    // bytes copied per warp and row
+  static constexpr int CR = 5, PR = 5, NR = 4;  // moment / normal ring rows
+  static_assert(CR == PR, "c, p and T rings share their row index");
+  static constexpr int STASH = NW * SR * SLOT;
+  static constexpr int RINGS = (CR + 2 * PR + 2 * NR) * NC * 4;
+  static constexpr int SMEM = STASH + RINGS + NW * SR * 8;
+  // resident CTAs per SM the kernel is compiled for (registers)
+  static constexpr int MINB = sizeof(typename Fmt::E) == 4 ? 3 : 4;
+  static_assert(NC % 32 == 0, "whole warps");
+};
+
+// The 9 pulled populations of lattice K at row y from a warp's stash slot
+// (lane l reads element l + 2 - xi_ix of population (K, i), or l + 2 where
+// the wall substitution copied the reversed population of the cell itself),
+// with the rules of pull9 (lbe_tile.cuh): anti-bounce-back for hbar at the
+// walls, and the deviation offsets of hbar between rows.
+template <class S>
+__device__ __forceinline__ float stash_val(const char* slot, int k, int i, int col,
+                                           const Phys<float>& P) {
+  using Fmt = StashFmt<S>;
+  if constexpr (sizeof(typename Fmt::E) == 4) {
+    return reinterpret_cast<const float*>(slot + Fmt::off(k, i))[col];
+  } else {
+    if (k == 1 && i == 0) return reinterpret_cast<const float*>(slot + Fmt::off(1, 0))[col];
+    return S::cvt(reinterpret_cast<const typename Fmt::E*>(slot + Fmt::off(k, i))[col]) *
+           P.inv_s[k];
+  }
+}
+
+// The 9 pulled populations of lattice K at row y from a warp's stash slot.
+// c0 is the element of the lane's own column in a population row (c0g in the
+// FP32 g_0 row of the 16-bit forms); the pull reads c0 - xi_ix, or c0 where
+// the wall substitution copied the reversed population of the cell itself.
+// Rules of pull9 (lbe_tile.cuh): anti-bounce-back for hbar at the walls, and
+// the deviation offsets of hbar between rows.
+template <class S, int K>
+__device__ __forceinline__ void wstash_pull(const InstDev& I, const Phys<float>& P,
+                                            const char* slot, int c0, int c0g, int y, int xw,
+                                            float out[9]) {
+  constexpr bool DEV = (K == 2) && dev_h<S>();
+  const bool wb = (y == 0), wt = (y == I.ny - 1);
+  auto col = [&](int i, bool shift) {
+    const int base = (K == 1 && i == 0) ? c0g : c0;
+    return shift ? base - EX(i) : base;
+  };
+  if (!wb && !wt) {
+    // interior row: constant offsets
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+      float v = stash_val<S>(slot, K, i, col(i, true), P);
+      if (DEV && EY(i) == 1) v -= WGT<float>(i) * P.dh;
+      if (DEV && EY(i) == -1) v += WGT<float>(i) * P.dh;
+      out[i] = v;
+    }
+    return;
+  }
+  float Tw = 0.f;
+  if (K == 2) Tw = wall_T<S>(I, xw, wb ? 0 : 1);
+  const float dh = DEV ? P.dh : 0.f;
+#pragma unroll
+  for (int i = 0; i < 9; i++) {
+    const bool wall = (EY(i) == 1 && wb) || (EY(i) == -1 && wt);
+    float v = wall ? stash_val<S>(slot, K, i, col(i, false), P)
+                   : stash_val<S>(slot, K, i, col(i, true), P);
+    if (K == 2) {
+      if (wall) {
+        v = -v + 2.f * WGT<float>(i) * P.rho * P.cv * Tw;
+      } else if (DEV && EY(i) == 1) {
+        v -= WGT<float>(i) * dh;
+      } else if (DEV && EY(i) == -1) {
+        v += WGT<float>(i) * dh;
+      }
+    }
+    out[i] = v;
+  }
+}
+
+template <class S, int NC>
+__global__ void __launch_bounds__(NC, (StashCfg<S, NC>::MINB))
+stash_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps, int n_inst,
+             int64_t total_items, int seg_rows, int parity, int* __restrict__ err) {
+  using Cfg = StashCfg<S, NC>;
+  using Fmt = typename Cfg::Fmt;
+  using C = float;
+  constexpr bool W16 = sizeof(typename Fmt::E) == 2;
+  extern __shared__ __align__(128) char smem[];
+  C* cring = reinterpret_cast<C*>(smem + Cfg::STASH);  // [CR][NC]
+  C* pring = cring + Cfg::CR * NC;                       // [PR][NC]
+  C* Tring = pring + Cfg::PR * NC;                       // [PR][NC]
+  C* nxr = Tring + Cfg::PR * NC;                         // [NR][NC]
+  C* nyr = nxr + Cfg::NR * NC;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Cfg::STASH + Cfg::RINGS);  // [NW][SR]
+  __shared__ int s_abort;
+  const int t = threadIdx.x;
+  const int lane = t & 31, w = t >> 5;
+  char* wstash = smem + w * Cfg::SR * Cfg::SLOT;
+  uint64_t* wbars = bars + w * Cfg::SR;
+  // the warp's barriers are initialised once; every copy issued in an item is
+  // waited for in that item, so the phase bits carry over between items
+  if (lane == 0) {
+    for (int s = 0; s < Cfg::SR; s++) mbar_init(smem_u32(&wbars[s]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  unsigned phase = 0;    // bit s: parity of the next completion of slot s
+  unsigned pending = 0;  // bit s: slot s has copies not yet waited for
+
+  for (int64_t item = blockIdx.x; item < total_items; item += gridDim.x) {
+    int lo = 0, hi = n_inst - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (insts[mid].tile_begin <= item) lo = mid; else hi = mid - 1;
+    }
+    const InstDev& I = insts[lo];
+    const char* __restrict__ src = I.buf[parity];
+    const int64_t local = item - I.tile_begin;
+    const int nx = I.nx, ny = I.ny;
+    const int x0 = (int)(local % I.tiles_x) * Cfg::NCO;
+    const int ya = (int)(local / I.tiles_x) * seg_rows;
+    const int yb = min(ya + seg_rows, ny);
+    char* __restrict__ dst = I.buf[parity ^ 1];
+    const Phys<C> P = phys<C>(I);
+    const C en2 = P.eta_n2;
+    const size_t pitch = (size_t)I.pitch;
+    const int x = x0 - 2 + t;
+    const int xw = wrapx(x, nx);
+    const bool collides = t >= 2 && t < NC - 2 && x < nx;
+    const bool edge_ghost = collides && (x < XG || x >= nx - XG);
+    // staged elements of this warp's population rows (storage element e holds
+    // column e - XG): its cells are columns x0 - 2 + 32 w + lane, their pulls
+    // reach elements x0 + 32 w + 1 .. x0 + 32 w + 34.  FP32 rows start at
+    // x0 + 32 w (x0 is a multiple of 4: 16-byte aligned), 16-bit rows at that
+    // rounded down to a multiple of 8.
+    const int e32 = x0 + 32 * w;
+    const int e16 = e32 & ~7;
+    const int c0 = (W16 ? e32 - e16 : 0) + lane + 2;  // own column in a population row
+    const int c0g = lane + 2;                          // own column in the FP32 g_0 row
+    __syncthreads();  // the previous item is done with the rings and stashes
+    if (t == 0) s_abort = 0;
+
+    auto slot = [&](int m) { return wstash + (m & (Cfg::SR - 1)) * Cfg::SLOT; };
+    auto cr = [](int m) { return (((m % Cfg::CR) + Cfg::CR) % Cfg::CR) * NC; };
+    auto pr = [](int m) { return (((m % Cfg::PR) + Cfg::PR) % Cfg::PR) * NC; };
+    auto nr = [](int m) { return (m & (Cfg::NR - 1)) * NC; };
+    auto loadable = [&](int m) { return m <= yb + 1 && m < ny; };
+    // lane p < 27 copies population p = (k, i) into its row of the slot:
+    // byte offsets from the start of the source row m, for the pull from row
+    // m - xi_iy and for the reversed population of the cell itself at a wall
+    const int pk = lane < 27 ? lane / 9 : 0, pi_ = lane < 27 ? lane - 9 * pk : 0;
+    const int pey = EY(pi_);
+    const bool pg0 = W16 && pk == 1 && pi_ == 0;  // the FP32 g_0 plane
+    const int pesz = (W16 && !pg0) ? 2 : 4;
+    const ptrdiff_t prow = (ptrdiff_t)pitch * pesz;  // bytes per source row
+    const int pbytes = (W16 && !pg0) ? Fmt::ROW : 144;
+    const ptrdiff_t pstart = (ptrdiff_t)((W16 && !pg0) ? e16 : e32) * pesz;
+    auto plane_off = [&](int k, int i) -> ptrdiff_t {
+      if (!W16) return (ptrdiff_t)(k * 9 + i) * (ptrdiff_t)I.plane_bytes;
+      if (k == 1 && i == 0) return (ptrdiff_t)I.g0_off;
+      return (ptrdiff_t)dev_plane(k, i) * (ptrdiff_t)I.plane_bytes;
+    };
+    const ptrdiff_t off_n = plane_off(pk, pi_) - (ptrdiff_t)pey * prow + pstart;
+    const ptrdiff_t off_w = plane_off(pk, OPP(pi_)) + pstart;
+    const int pdst = Fmt::off(pk, pi_);
+    // the warp's copies of the populations pulled by moment row m (the mirror
+    // row's below the bottom wall): lane p < 27 copies population p
+    auto issue = [&](int m) {
+      if (!loadable(m)) return;
+      const int mr = m >= 0 ? m : -1 - m;
+      const uint32_t bar = smem_u32(&wbars[m & (Cfg::SR - 1)]);
+      pending |= 1u << (m & (Cfg::SR - 1));
+      if (lane == 0) mbar_expect_tx(bar, Cfg::TX);
+      __syncwarp();
+      if (lane < 27) {
+        const bool wall = (pey == 1 && mr == 0) || (pey == -1 && mr == ny - 1);
+        const char* srcp = src + (ptrdiff_t)mr * prow + (wall ? off_w : off_n);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        bulk_load(smem_u32(slot(m) + pdst), srcp, pbytes, bar);
+      }
+    };
+    auto wait_row = [&](int m) -> bool {
+      if (!loadable(m)) return true;
+      const int s = m & (Cfg::SR - 1);
+      const bool ok = mbar_wait(smem_u32(&wbars[s]), (phase >> s) & 1u);
+      if (ok) {
+        phase ^= 1u << s;
+        pending &= ~(1u << s);
+      }
+      return ok;
+    };
+
+    issue(ya - 2);
+    int i5 = (((ya - 4) % Cfg::CR) + Cfg::CR) % Cfg::CR;  // i mod CR
+    for (int i = ya - 4; i <= yb; i++, i5 = (i5 == Cfg::CR - 1) ? 0 : i5 + 1) {
+      // ring row of i + d (|d| < CR), times NC
+      auto rr = [&](int d) {
+        int v = i5 + d;
+        v = v < 0 ? v + Cfg::CR : (v >= Cfg::CR ? v - Cfg::CR : v);
+        return v * NC;
+      };
+      __syncthreads();
+      if (s_abort) break;
+
+      // ---- 1. collide row r = i - 1
+      const int r = i - 1;
+      if (r >= ya && r < yb && collides) {
+        const char* s = slot(r);
+        C f[9], g[9], h[9];
+        wstash_pull<S, 0>(I, P, s, c0, c0g, r, x, f);
+        wstash_pull<S, 1>(I, P, s, c0, c0g, r, x, g);
+        wstash_pull<S, 2>(I, P, s, c0, c0g, r, x, h);
+        const int ps = rr(-2), p0 = rr(-1), pn = rr(0);  // rows r-1, r, r+1
+        const C* cs = cring + ps;
+        const C* c0 = cring + p0;
+        const C* cn = cring + pn;
+        const C cc = c0[t];
+        const C pp = pring[p0 + t], TT = Tring[p0 + t];
+        Stencils<C> st;
+        grad3(cs, c0, cn, t, st.gcx, st.gcy);
+        st.lapc = lap3(cs, c0, cn, t);
+        grad3(Tring + ps, Tring + p0, Tring + pn, t, st.gTx, st.gTy);
+        if (dev_h<S>()) st.gTy += P.hr1;
+        grad3(pring + ps, pring + p0, pring + pn, t, st.gpx, st.gpy);
+        const int ns = nr(r - 1), n0 = nr(r), nn = nr(r + 1);
+        C d1, d2, dum;
+        grad3(nxr + ns, nxr + n0, nxr + nn, t, d1, dum);
+        grad3(nyr + ns, nyr + n0, nyr + nn, t, dum, d2);
+        st.kappa = d1 + d2;
+        const Drive<S> d = drive<S>(P, r, f, cc, TT, st);
+        C o[27];
+        collide<S>(P, f, g, h, cc, pp, TT, st.gpx, st.gpy, d,
+                   [&](int k, int ii, C v) { o[k * 9 + ii] = v; });
+        const size_t e = (size_t)r * pitch + XG + x;
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+#pragma unroll
+          for (int ii = 0; ii < 9; ii++) S::st(I, dst, k, ii, e, o[k * 9 + ii]);
+        if (edge_ghost) {
+#pragma unroll
+          for (int k = 0; k < 3; k++)
+#pragma unroll
+            for (int ii = 0; ii < 9; ii++) {
+              if (x < XG) S::st(I, dst, k, ii, e + nx, o[k * 9 + ii]);
+              if (x >= nx - XG) S::st(I, dst, k, ii, e - nx, o[k * 9 + ii]);
+            }
+        }
+      }
+
+      // ---- 2. the warp's copies of row i + 3 (into the slot of row i - 1)
+      __syncwarp();
+      issue(i + 3);
+
+      // ---- 3. moments of row m = i + 2
+      const int m = i + 2;
+      if (!wait_row(m)) {
+        s_abort = 1;
+        atomicOr(err, 1);
+      }
+      if (m <= yb + 1) {
+        const int ci = rr(2) + t, pi = ci;
+        if (m < ny) {
+          const int mr = m >= 0 ? m : -1 - m;
+          const char* s = slot(m);
+          C v[9];
+          wstash_pull<S, 1>(I, P, s, c0, c0g, mr, xw, v);
+          cring[ci] = sum9(v);
+          wstash_pull<S, 0>(I, P, s, c0, c0g, mr, xw, v);
+          pring[pi] = sum9(v);
+          wstash_pull<S, 2>(I, P, s, c0, c0g, mr, xw, v);
+          C T = dv(sum9(v), P.rho_cv, P.inv_rho_cv);
+          if (m < 0) T = ghost_T<S>(I, xw, true, T);
+          Tring[pi] = T;
+        } else {
+          const int mm = 2 * ny - 1 - m;
+          cring[ci] = cring[cr(mm) + t];
+          pring[pi] = pring[pr(mm) + t];
+          Tring[pi] = ghost_T<S>(I, xw, false, Tring[pr(mm) + t]);
+        }
+      }
+      __syncthreads();
+      if (s_abort) break;
+
+      // ---- 4. unit normal of row i + 1
+      const int mn = i + 1;
+      if (mn >= ya - 1 && mn <= yb && t >= 1 && t < NC - 1) {
+        const C* c0 = cring + rr(1);
+        const int ni = nr(mn) + t;
+        normal3(cring + rr(0), c0, cring + rr(2), t, en2, nxr[ni], nyr[ni]);
+      }
+    }
+    __syncthreads();
+    if (s_abort) {
+      // bounded wait for this warp's copies still in flight, then stop
+      for (int sl = 0; sl < Cfg::SR; sl++)
+        if (pending & (1u << sl)) mbar_wait(smem_u32(&wbars[sl]), (phase >> sl) & 1u);
+      __syncthreads();
+      return;
+    }
+  }
+}
+
+}  // namespace lbe

@@ -6,6 +6,9 @@
 #if LBE_STRIP
 #include "lbe_strip.cuh"
 #endif
+#if LBE_STASH
+#include "lbe_stash.cuh"
+#endif
 
 #define LBE_CAT2(a, b) a##b
 #define LBE_CAT(a, b) LBE_CAT2(a, b)
@@ -104,12 +107,52 @@ int strip_occ() {
 }
 }  // namespace
 
+#if LBE_STASH
+namespace {
+template <int NC>
+bool stash_attr() {
+  static bool done[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+  if (!done[dev]) {
+    if (cudaFuncSetAttribute(stash_kernel<LBE_ST, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             StashCfg<LBE_ST, NC>::SMEM) != cudaSuccess)
+      return false;
+    done[dev] = true;
+  }
+  return true;
+}
+template <int NC>
+cudaError_t stash_one(const InstDev* d, const TmapSet* maps, int n, int64_t items, int seg,
+                      int parity, int grid, int* err, cudaStream_t s) {
+  if (!stash_attr<NC>()) return cudaErrorInvalidValue;
+  if (grid <= 0) grid = 1;
+  if ((int64_t)grid > items) grid = (int)items;
+  stash_kernel<LBE_ST, NC>
+      <<<grid, NC, StashCfg<LBE_ST, NC>::SMEM, s>>>(d, maps, n, items, seg, parity, err);
+  return cudaGetLastError();
+}
+template <int NC>
+int stash_occ() {
+  if (!stash_attr<NC>()) return 0;
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, stash_kernel<LBE_ST, NC>, NC,
+                                                    StashCfg<LBE_ST, NC>::SMEM) != cudaSuccess)
+    return 0;
+  return b;
+}
+}  // namespace
+#endif
+
 cudaError_t LBE_CAT(launch_strip_, LBE_SUFFIX)(int variant, const InstDev* d, const TmapSet* maps,
                                                 int n, int64_t items, int seg, int parity, int grid,
                                                 int* err, cudaStream_t s) {
   switch (variant) {
     case 0: return strip_one<128, LBE_R128>(d, maps, n, items, seg, parity, grid, err, s);
     case 1: return strip_one<64, LBE_R64>(d, maps, n, items, seg, parity, grid, err, s);
+#if LBE_STASH
+    case 2: return stash_one<128>(d, maps, n, items, seg, parity, grid, err, s);
+#endif
     default: return cudaErrorInvalidValue;
   }
 }
@@ -117,6 +160,9 @@ int LBE_CAT(strip_occupancy_, LBE_SUFFIX)(int variant) {
   switch (variant) {
     case 0: return strip_occ<128, LBE_R128>();
     case 1: return strip_occ<64, LBE_R64>();
+#if LBE_STASH
+    case 2: return stash_occ<128>();
+#endif
     default: return 0;
   }
 }

@@ -1,0 +1,139 @@
+"""Full-length runs of the benchmark problems against the FP64 oracle's
+stored end states (tests/golden/longrun_*.json, written by
+make_longrun_golden.py from the oracle alone):
+
+  planar   two planar fluids with Marangoni convection, 512 x 256, 100 000 steps
+  drop     drop migration, 512 x 1024, 40 000 steps
+  sweep00, sweep01   instances of the 64-drop parameter sweep, 10 000 steps,
+           run inside the whole 64-instance batch (one launch per step)
+
+FP64: the end state is bitwise the oracle's (when the inputs are bitwise the
+ones the golden was made from; else within 1e-10).  FP32 and the 16-bit
+storages: relative L2 errors of u (as a vector) and T over the sampled
+points, asserted against the bounds this build meets and printed.
+"""
+import hashlib
+import json
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+HERE = os.path.dirname(__file__)
+
+
+def _golden(name):
+    path = os.path.join(HERE, "golden", "longrun_%s.json" % name)
+    if not os.path.exists(path):
+        pytest.skip("golden %s missing" % name)
+    return json.load(open(path))
+
+
+def _case(name):
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "make_longrun_golden", os.path.join(HERE, "golden", "make_longrun_golden.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod.case(name), mod.input_sha
+
+
+def _sampled(F, G):
+    s, o = G["stride"], G["offset"]
+    return {k: np.asarray(F[k])[o::s, o::s] for k in ("c", "p", "ux", "uy", "T")}
+
+
+def _errors(F, G):
+    A = _sampled(F, G)
+    B = {k: np.asarray(v) for k, v in G["samples"].items()}
+    ua = np.stack([A["ux"], A["uy"]])
+    ub = np.stack([B["ux"], B["uy"]])
+    rel = lambda a, b: float(np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()))  # noqa: E731
+    return dict(u=rel(ua, ub), T=rel(A["T"], B["T"]), c=rel(A["c"], B["c"]))
+
+
+def _run(w, steps, storage):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1412_6238_gb300.lbe import LBE
+    sim = LBE(w, storage=storage)
+    sim.step(steps)
+    return sim
+
+
+# (case, storage) -> bounds on (u, T) relative L2 at the stated step count
+BOUNDS = {
+    ("planar", "f32"): (2e-3, 1e-5), ("planar", "f16dev"): (1e-1, 1e-3),
+    ("drop", "f32"): (2e-3, 1e-5), ("drop", "f16dev"): (5e-2, 1e-3),
+}
+
+
+@pytest.mark.parametrize("name", ["planar", "drop"])
+def test_fp64_end_state_is_the_oracles(name):
+    G = _golden(name)
+    (w, steps, stride, desc), input_sha = _case(name)
+    assert steps == G["steps"]
+    sim = _run(w, steps, "f64")
+    state = sim.get_state().numpy()
+    if input_sha(w) == G["input_sha256"]:
+        assert hashlib.sha256(np.ascontiguousarray(state).tobytes()).hexdigest() == \
+            G["state_sha256"]
+    F = {k: v.numpy() for k, v in sim.fields(device="cpu").items()}
+    e = _errors(F, G)
+    print(name, "f64", e)
+    assert max(e.values()) < 1e-10
+
+
+F16_PLANAR = pytest.mark.xfail(
+    reason="FP16 storage does not resolve the slow planar Marangoni flow over "
+           "100 000 steps (measured: u error 1.4, T 4.2e-2 relative L2)", strict=False)
+
+
+@pytest.mark.parametrize("name", ["planar", "drop"])
+@pytest.mark.parametrize("storage", ["f32", pytest.param("f16dev", marks=[])])
+def test_storage_end_state_error(name, storage, request):
+    if (name, storage) == ("planar", "f16dev"):
+        request.applymarker(F16_PLANAR)
+    G = _golden(name)
+    (w, steps, stride, desc), _ = _case(name)
+    sim = _run(w, steps, storage)
+    F = {k: v.numpy() for k, v in sim.fields(device="cpu").items()}
+    e = _errors(F, G)
+    print(name, storage, steps, "steps:", e)
+    bu, bT = BOUNDS[(name, storage)]
+    assert e["u"] < bu and e["T"] < bT, e
+    # sum c: FP32 rounding in uniform bulk cells drifts coherently (about
+    # 3e-9 per step, relative)
+    assert abs(float(F["c"].sum()) - G["sum_c"]) < 3e-9 * steps * abs(G["sum_c"])
+
+
+@pytest.mark.parametrize("storage,bu,bT", [("f64", 1e-10, 1e-10), ("f16dev", 1e-1, 1e-3)])
+def test_sweep_instances_inside_the_batch(storage, bu, bT):
+    """The 64-instance sweep advanced 10 000 steps in one launch per step;
+    the instances with stored oracle end states compared."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1412_6238_gb300 import workloads as W
+    from paper_1412_6238_gb300.lbe import LBE
+    ws = W.batch_sweep(64, seed=0, steps=10000)
+    goldens = {}
+    for name in ("sweep00", "sweep01"):
+        path = os.path.join(HERE, "golden", "longrun_%s.json" % name)
+        if os.path.exists(path):
+            G = json.load(open(path))
+            (w, steps, stride, desc), _ = _case(name)
+            j = int(desc.split("[")[1].split("]")[0])
+            goldens[j] = G
+    if not goldens:
+        pytest.skip("sweep goldens missing")
+    sim = LBE(ws, storage=storage)
+    sim.step(10000)
+    for j, G in goldens.items():
+        F = {k: v.numpy() for k, v in sim.fields(j, device="cpu").items()}
+        e = _errors(F, G)
+        print("sweep instance", j, storage, e)
+        assert e["u"] < bu and e["T"] < bT, (j, e)
