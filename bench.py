@@ -34,7 +34,10 @@ sys.path.insert(0, ROOT)
 METRIC = "coupled-LBE MLUPS & % HBM roofline; mixed/batched vs plain FP32 at stated error"
 UNIT = "MLUPS"
 NX = NY = 4096
-BYTES_PER_CELL = {"f64": 432, "f32": 216, "f16dev": 112, "bf16dev": 112}
+# algorithmic bytes per cell update: every population read once and written
+# once (FP64: 27 x 8; FP32: 27 x 4 plus the FP16 low part of g_0; 16-bit
+# forms: 26 x 2 plus the FP32 g_0 and its FP16 low part), both directions
+BYTES_PER_CELL = {"f64": 432, "f32": 220, "f16dev": 116, "bf16dev": 116}
 PROFILE = os.path.join(ROOT, "profiles", "lbe_step_f32_droplet_4096x4096.md")
 
 

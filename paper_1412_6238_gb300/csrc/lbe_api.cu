@@ -27,7 +27,7 @@ thread_local std::string g_thread_err;
 struct InstHost {
   lbe_params p{};
   int nx = 0, ny = 0, pitch = 0;
-  uint64_t plane_bytes = 0, g0_off = 0, buf_bytes = 0;
+  uint64_t plane_bytes = 0, g0_off = 0, g0lo_off = 0, buf_bytes = 0;
   char* arena = nullptr;  // two buffers of buf_bytes
   double* walls = nullptr;  // device: Tbot[nx], Ttop[nx], then 4 float tables
   std::vector<double> Tbot, Ttop;
@@ -168,6 +168,7 @@ void fill_desc(lbe_handle* h, int j, InstDev& D) {
   D.storage = h->storage;
   D.plane_bytes = H.plane_bytes;
   D.g0_off = H.g0_off;
+  D.g0lo_off = H.g0lo_off;
   D.buf[0] = H.arena;
   D.buf[1] = H.arena + H.buf_bytes;
   D.Tbot = H.walls;
@@ -541,11 +542,20 @@ lbe_status create(int32_t n, const lbe_params* params, const lbe_init_fields* in
     H.ny = params[j].ny;
     H.pitch = round_up(H.nx + 2 * XG, 64);  // periodic ghost columns on both sides
     H.plane_bytes = ((uint64_t)H.ny * H.pitch * esz + 255) / 256 * 256;
+    // the FP16 plane of the g_0 low part (16/32-bit forms) follows the
+    // population planes
+    const uint64_t lo_bytes = ((uint64_t)H.ny * H.pitch * 2 + 255) / 256 * 256;
     if (st >= LBE_F16DEV) {
       H.g0_off = 26 * H.plane_bytes;
-      H.buf_bytes = H.g0_off + (((uint64_t)H.ny * H.pitch * 4 + 255) / 256 * 256);
+      H.g0lo_off = H.g0_off + (((uint64_t)H.ny * H.pitch * 4 + 255) / 256 * 256);
+      H.buf_bytes = H.g0lo_off + lo_bytes;
+    } else if (st == LBE_F32) {
+      H.g0_off = 0;
+      H.g0lo_off = 27 * H.plane_bytes;
+      H.buf_bytes = H.g0lo_off + lo_bytes;
     } else {
       H.g0_off = 0;
+      H.g0lo_off = 0;
       H.buf_bytes = 27 * H.plane_bytes;
     }
     // ARENA_TAIL: reads of a strip's last warp may run past the last row of

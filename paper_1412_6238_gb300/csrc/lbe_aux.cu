@@ -160,6 +160,10 @@ __global__ void push_kernel(const InstDev* __restrict__ d, int nx, int ny,
         }
         if (kk == 2) v -= WGT<double>(j) * rref;
         st_cell<S>(I, buf, kk, j, rowbase, x, (C)v);
+        if constexpr (S::kind != ST_F64) {
+          // g_0 = hi + lo: the low part of the rest population
+          if (kk == 1 && j == 0) st_cell_g0lo(I, buf, rowbase, x, (float)(v - (double)(C)v));
+        }
       }
     }
   }
@@ -182,6 +186,8 @@ __global__ void pull_kernel(const InstDev* __restrict__ d, int nx, int ny, doubl
     for (int i = 0; i < 9; i++) pre[(int64_t)i * N + k] = (double)v[i];
     pull9<S, 1>(I, P, buf, q, v);
     for (int i = 0; i < 9; i++) pre[(int64_t)(9 + i) * N + k] = (double)v[i];
+    if constexpr (S::kind != ST_F64)
+      pre[(int64_t)9 * N + k] += (double)ld_g0lo(I, buf, (size_t)y * I.pitch + XG + x);
     pull9<S, 2>(I, P, buf, q, v);
     const double rref = dev_h<S>() ? I.pd.rho * I.pd.cv * (I.hr0 + I.hr1 * y) : 0.0;
     for (int i = 0; i < 9; i++)

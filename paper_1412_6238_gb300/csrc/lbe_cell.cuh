@@ -30,6 +30,29 @@ __device__ __forceinline__ float sum9(const float v[9]) {
   return (((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]))) + v[8];
 }
 
+// Error-free transformations for the two-float g_0 and c of the 16/32-bit
+// forms: a + b = s + e exactly (Knuth's two-sum; the fast variant needs
+// |a| >= |b|).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  e = b - (s - a);
+}
+
+// c = sum g_i (Eq. 28) with g_0 = g[0] + g0lo, as hi + lo: the eight small
+// moving populations are summed first, then added to g_0 exactly.
+__device__ __forceinline__ float moment_c(const float g[9], float g0lo, float& clo) {
+  const float s8 = ((g[1] + g[2]) + (g[3] + g[4])) + ((g[5] + g[6]) + (g[7] + g[8]));
+  float ch, e;
+  two_sum(g[0], s8, ch, e);
+  clo = e + g0lo;
+  return ch;
+}
+
 // hbar is handled as the deviation hbar_i - w_i rho c_v T_r(y) from the linear
 // conduction profile T_r(y) = hr0 + hr1 y in every storage but FP64 (which
 // keeps the full populations, like the FP64 reference).
@@ -38,28 +61,39 @@ __device__ __forceinline__ constexpr bool dev_h() { return S::kind != ST_F64; }
 
 // Isotropic gradient (1/c_s^2) sum_{i>=1} w_i xi_i phi(x + xi_i) and Laplacian
 // (2/c_s^2) sum_{i>=1} w_i (phi(x + xi_i) - phi(x)) from three rows (south,
-// centre, north) at column x; the terms are summed in index order
+// centre, north) at column x.  FP64: the terms are summed in index order
 // i = 1 (E), 2 (N), 3 (W), 4 (S), 5 (NE), 6 (NW), 7 (SW), 8 (SE), terms with
-// xi_ia = 0 being exact zeros.
+// xi_ia = 0 being exact zeros (the order of the FP64 reference).
 template <class C>
 __device__ __forceinline__ void grad3(const C* rs, const C* rc, const C* rn, int x, C& gx, C& gy) {
   const C vE = rc[x + 1], vW = rc[x - 1], vN = rn[x], vS = rs[x];
   const C vNE = rn[x + 1], vNW = rn[x - 1], vSE = rs[x + 1], vSW = rs[x - 1];
   const C wa = WGT<C>(1), wd = WGT<C>(5);
-  C sx = wa * vE;
-  sx = sx - wa * vW;
-  sx = sx + wd * vNE;
-  sx = sx - wd * vNW;
-  sx = sx - wd * vSW;
-  sx = sx + wd * vSE;
-  C sy = wa * vN;
-  sy = sy - wa * vS;
-  sy = sy + wd * vNE;
-  sy = sy + wd * vNW;
-  sy = sy - wd * vSW;
-  sy = sy - wd * vSE;
-  gx = dv(sx, cs2<C>(), C(3));
-  gy = dv(sy, cs2<C>(), C(3));
+  if constexpr (sizeof(C) == 4) {
+    // FP32: differences of opposite neighbours first (exact when they are
+    // within a factor 2, Sterbenz), then the weights, so that a small
+    // gradient of an O(1) field keeps its relative precision instead of
+    // inheriting the rounding of the O(1) products w_i phi(x + xi_i)
+    const C dEW = vE - vW, dNS = vN - vS;
+    const C d1 = vNE - vSW, d2 = vSE - vNW;  // xi = (1, 1) and (1, -1)
+    gx = dv(wa * dEW + wd * (d1 + d2), cs2<C>(), C(3));
+    gy = dv(wa * dNS + wd * (d1 - d2), cs2<C>(), C(3));
+  } else {
+    C sx = wa * vE;
+    sx = sx - wa * vW;
+    sx = sx + wd * vNE;
+    sx = sx - wd * vNW;
+    sx = sx - wd * vSW;
+    sx = sx + wd * vSE;
+    C sy = wa * vN;
+    sy = sy - wa * vS;
+    sy = sy + wd * vNE;
+    sy = sy + wd * vNW;
+    sy = sy - wd * vSW;
+    sy = sy - wd * vSE;
+    gx = dv(sx, cs2<C>(), C(3));
+    gy = dv(sy, cs2<C>(), C(3));
+  }
 }
 
 template <class C>
@@ -84,6 +118,48 @@ __device__ __forceinline__ void normal3(const C* rs, const C* rc, const C* rn, i
   C gx, gy;
   grad3(rs, rc, rn, x, gx, gy);
   const C inv = C(1) / sqrt(gx * gx + gy * gy + en2);
+  nx = gx * inv;
+  ny = gy * inv;
+}
+
+// The same stencils for c = hi + lo (16/32-bit forms): hi rows in FP32, lo
+// rows as FP16 of lo * 2^24; differences of hi and of lo are taken first.
+__device__ __forceinline__ float lo_at(const __half* r, int x) {
+  return __half2float(r[x]) * G0LO_INV;
+}
+__device__ __forceinline__ void grad3c(const float* rs, const float* rc, const float* rn,
+                                       const __half* ls, const __half* lc, const __half* ln, int x,
+                                       float& gx, float& gy) {
+  const float wa = WGT<float>(1), wd = WGT<float>(5);
+  const float dEW = (rc[x + 1] - rc[x - 1]) + (lo_at(lc, x + 1) - lo_at(lc, x - 1));
+  const float dNS = (rn[x] - rs[x]) + (lo_at(ln, x) - lo_at(ls, x));
+  const float d1 = (rn[x + 1] - rs[x - 1]) + (lo_at(ln, x + 1) - lo_at(ls, x - 1));
+  const float d2 = (rs[x + 1] - rn[x - 1]) + (lo_at(ls, x + 1) - lo_at(ln, x - 1));
+  gx = dv(wa * dEW + wd * (d1 + d2), cs2<float>(), 3.f);
+  gy = dv(wa * dNS + wd * (d1 - d2), cs2<float>(), 3.f);
+}
+__device__ __forceinline__ float lap3c(const float* rs, const float* rc, const float* rn,
+                                       const __half* ls, const __half* lc, const __half* ln,
+                                       int x) {
+  const float v0 = rc[x], l0 = lo_at(lc, x);
+  const float wa = WGT<float>(1), wd = WGT<float>(5);
+  auto d = [&](const float* r, const __half* l, int xx) { return (r[xx] - v0) + (lo_at(l, xx) - l0); };
+  float t = wa * d(rc, lc, x + 1);
+  t = t + wa * d(rn, ln, x);
+  t = t + wa * d(rc, lc, x - 1);
+  t = t + wa * d(rs, ls, x);
+  t = t + wd * d(rn, ln, x + 1);
+  t = t + wd * d(rn, ln, x - 1);
+  t = t + wd * d(rs, ls, x - 1);
+  t = t + wd * d(rs, ls, x + 1);
+  return dv(2.f * t, cs2<float>(), 3.f);
+}
+__device__ __forceinline__ void normal3c(const float* rs, const float* rc, const float* rn,
+                                         const __half* ls, const __half* lc, const __half* ln,
+                                         int x, float en2, float& nx, float& ny) {
+  float gx, gy;
+  grad3c(rs, rc, rn, ls, lc, ln, x, gx, gy);
+  const float inv = 1.f / sqrtf(gx * gx + gy * gy + en2);
   nx = gx * inv;
   ny = gy * inv;
 }
@@ -142,13 +218,16 @@ __device__ __forceinline__ Drive<S> drive(const Phys<typename S::C>& P, int gy,
 
 // S3, S7-S9: the three forced BGK collisions.  out(k, i, value) receives the
 // post-collision value of population (k, i) (hbar as a deviation in the
-// deviation forms).
+// deviation forms).  16/32-bit forms: g_0 = g[0] + g0lo and c = cc + clo
+// enter as two-float values and the post-collision g_0 leaves as
+// out(1, 0, hi) and *g0lo_out = lo.
 template <class S, class Out>
 __device__ __forceinline__ void collide(const Phys<typename S::C>& P, const typename S::C f[9],
                                         const typename S::C g[9], const typename S::C h[9],
                                         typename S::C cc, typename S::C pp, typename S::C TT,
                                         typename S::C gpx, typename S::C gpy, const Drive<S>& d,
-                                        Out&& out) {
+                                        Out&& out, typename S::C g0lo = 0, typename S::C clo = 0,
+                                        typename S::C* g0lo_out = nullptr) {
   using C = typename S::C;
   const C inv_rho = P.inv_rho;
   const C rcs2 = P.rcs2, inv_rcs2 = C(3) * inv_rho;
@@ -223,7 +302,29 @@ __device__ __forceinline__ void collide(const Phys<typename S::C>& P, const type
     dir(8, wd, -a, hq, Fx - Fy, Gx - Gy);
     const C W0 = WGT<C>(0);
     const C G0 = W0 + W0 * hu;
-    relax(0, G0, pp - sfe, cc - sge, (dev_h<S>() ? rcvTd : rcvT) - she, C(0), C(0));
+    // rest direction: f and hbar as above; g_0 in two-float arithmetic
+    // (g_0 + omega_g (g_eq,0 - g_0) + source, g_eq,0 = c - sum of the moving
+    // g_eq), so that c keeps the precision of its two-float moment
+    out(0, 0, f[0] + omega_f * ((pp - sfe) - f[0]) + af * ((C(0) - Fdu) * G0));
+    out(2, 0, h[0] + omega_T * (((dev_h<S>() ? rcvTd : rcvT) - she) - h[0]) +
+                  aT * (inv_rcs2 * (C(0) - Gdu)) * (rcvT * G0));
+    {
+      const C src0 = ag * (sg * (C(0) - Gdu)) * G0;
+      C s0, e0;
+      two_sum(cc, -sge, s0, e0);  // g_eq,0 = s0 + (e0 + clo)
+      C dh, de;
+      two_sum(s0, -g[0], dh, de);  // g_eq,0 - g_0 = dh + dl
+      const C dl = de + ((e0 + clo) - g0lo);
+      const C p = omega_g * dh;
+      const C pe = fmaf(omega_g, dh, -p);  // rounding error of the product
+      C hs, he;
+      two_sum(g[0], p, hs, he);
+      const C lo = he + pe + g0lo + omega_g * dl + src0;
+      C hi_new, lo_new;
+      fast_two_sum(hs, lo, hi_new, lo_new);
+      out(1, 0, hi_new);
+      if (g0lo_out) *g0lo_out = lo_new;
+    }
   } else {
     const C H0 = dv(cc - dv((C(1) - WGT<C>(0)) * Gm * d.mu, cs2<C>(), C(3)), WGT<C>(0),
                     C(9) / C(4));
@@ -250,6 +351,7 @@ __device__ __forceinline__ void collide(const Phys<typename S::C>& P, const type
       const C heqd = dev_h<S>() ? rcvTd * G + rcvTr * (W * q) : heq;
       out(2, i, h[i] - omega_T * (h[i] - heqd) + aT * hs);
     }
+    if (g0lo_out) *g0lo_out = C(0);
   }
 }
 
@@ -262,6 +364,14 @@ __device__ __forceinline__ void st_cell(const InstDev& I, char* dst, int k, int 
   S::st(I, dst, k, i, rowbase + XG + x, v);
   if (x < XG) S::st(I, dst, k, i, rowbase + XG + x + I.nx, v);
   if (x >= I.nx - XG) S::st(I, dst, k, i, rowbase + XG + x - I.nx, v);
+}
+
+// Store the low part of g_0 of cell x and its periodic ghost copies.
+__device__ __forceinline__ void st_cell_g0lo(const InstDev& I, char* dst, size_t rowbase, int x,
+                                             float lo) {
+  st_g0lo(I, dst, rowbase + XG + x, lo);
+  if (x < XG) st_g0lo(I, dst, rowbase + XG + x + I.nx, lo);
+  if (x >= I.nx - XG) st_g0lo(I, dst, rowbase + XG + x - I.nx, lo);
 }
 
 }  // namespace lbe

@@ -13,6 +13,10 @@
 //   F16DEV / BF16DEV : 26 planes of 16-bit deviations in the order
 //               f_0..f_8, g_1..g_8, hbar_0..hbar_8, then one FP32 plane
 //               holding g_0 at byte offset g0_off.
+//   F32 and the 16-bit forms also keep the low part of g_0 (g_0 = hi + lo,
+//   |lo| at most half an FP32 ulp of hi) as FP16 of lo * 2^24 in a plane at
+//   byte offset g0lo_off, so that c = sum g_i (of which g_0 carries nearly
+//   all) is held to about 1e-11 instead of the 6e-8 of one FP32 value.
 // A buffer holds the post-collision populations of the previous step; the
 // step kernel pulls P_i(x) = P*_i(x - xi_i) (with the wall rules) when it
 // loads, so the two buffers ping-pong between steps.
@@ -72,6 +76,7 @@ struct InstDev {
   int64_t tile_begin;   // first global tile / work-item index of this instance
   uint64_t plane_bytes; // bytes between consecutive planes
   uint64_t g0_off;      // byte offset of the FP32 g_0 plane (16-bit forms)
+  uint64_t g0lo_off;    // byte offset of the FP16 plane of the g_0 low part (16/32-bit)
   char* buf[2];         // population arenas (ping-pong)
   const double* Tbot;   // [nx] wall temperature at y = -1/2
   const double* Ttop;   // [nx] wall temperature at y = ny - 1/2
@@ -154,6 +159,16 @@ struct StDev {
     put(reinterpret_cast<E*>(b + (size_t)dev_plane(k, i) * I.plane_bytes) + idx, v * I.s[k]);
   }
 };
+
+// The low part of g_0 (16/32-bit storages).
+constexpr float G0LO_SCALE = 16777216.0f;  // 2^24
+constexpr float G0LO_INV = 1.0f / 16777216.0f;
+__device__ __forceinline__ float ld_g0lo(const InstDev& I, const char* b, size_t idx) {
+  return __half2float(reinterpret_cast<const __half*>(b + I.g0lo_off)[idx]) * G0LO_INV;
+}
+__device__ __forceinline__ void st_g0lo(const InstDev& I, char* b, size_t idx, float lo) {
+  reinterpret_cast<__half*>(b + I.g0lo_off)[idx] = __float2half_rn(lo * G0LO_SCALE);
+}
 
 using StF16 = StDev<__half, ST_F16DEV>;
 using StBF16 = StDev<__nv_bfloat16, ST_BF16DEV>;

@@ -51,12 +51,15 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
 // 16-bit forms holds 36 FP32 elements.
 template <class S>
 struct StashFmt;
+// Every form adds the FP16 row of the g_0 low part (40 elements, 80 bytes)
+// at byte LO of the slot.
 template <>
 struct StashFmt<StF32> {
   using E = float;
   static constexpr int EW = 36;              // elements per population row
   static constexpr int ROW = EW * 4;         // bytes (a multiple of 16)
-  static constexpr int SLOT_RAW = 27 * ROW;  // bytes of one warp's row
+  static constexpr int LO = 27 * ROW;        // the g_0 low-part row
+  static constexpr int SLOT_RAW = LO + 80;   // bytes of one warp's row
   __host__ __device__ static constexpr int off(int k, int i) { return (k * 9 + i) * ROW; }
 };
 template <class E16>
@@ -65,7 +68,8 @@ struct StashFmt16 {
   static constexpr int EW = 40;
   static constexpr int ROW = EW * 2;
   static constexpr int G0ROW = 36 * 4;
-  static constexpr int SLOT_RAW = 26 * ROW + G0ROW;
+  static constexpr int LO = 26 * ROW + G0ROW;
+  static constexpr int SLOT_RAW = LO + 80;
   __host__ __device__ static constexpr int off(int k, int i) {
     return (k == 1 && i == 0) ? 26 * ROW : dev_plane(k, i) * ROW;
   }
@@ -86,7 +90,8 @@ struct StashCfg {
   static constexpr int CR = 5, PR = 5, NR = 4;  // moment / normal ring rows
   static_assert(CR == PR, "c, p and T rings share their row index");
   static constexpr int STASH = NW * SR * SLOT;
-  static constexpr int RINGS = (CR + 2 * PR + 2 * NR) * NC * 4;
+  // FP32 rings of c, p, T, n_x, n_y and the FP16 ring of the c low part
+  static constexpr int RINGS = (CR + 2 * PR + 2 * NR) * NC * 4 + CR * NC * 2;
   static constexpr int SMEM = STASH + RINGS + NW * SR * 8;
   // resident CTAs per SM the kernel is compiled for (registers)
   static constexpr int MINB = sizeof(typename Fmt::E) == 4 ? 3 : 4;
@@ -173,6 +178,7 @@ stash_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
   C* Tring = pring + Cfg::PR * NC;                       // [PR][NC]
   C* nxr = Tring + Cfg::PR * NC;                         // [NR][NC]
   C* nyr = nxr + Cfg::NR * NC;
+  __half* clr = reinterpret_cast<__half*>(nyr + Cfg::NR * NC);  // [CR][NC], lo * 2^24
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Cfg::STASH + Cfg::RINGS);  // [NW][SR]
   __shared__ int s_abort;
   const int t = threadIdx.x;
@@ -220,6 +226,7 @@ stash_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
     const int e16 = e32 & ~7;
     const int c0 = (W16 ? e32 - e16 : 0) + lane + 2;  // own column in a population row
     const int c0g = lane + 2;                          // own column in the FP32 g_0 row
+    const int c0lo = e32 - e16 + lane + 2;             // own column in the g_0 low-part row
     __syncthreads();  // the previous item is done with the rings and stashes
     if (t == 0) s_abort = 0;
 
@@ -231,21 +238,25 @@ stash_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
     // lane p < 27 copies population p = (k, i) into its row of the slot:
     // byte offsets from the start of the source row m, for the pull from row
     // m - xi_iy and for the reversed population of the cell itself at a wall
+    // (lane 27: the row of the g_0 low part)
+    const bool plo = lane == 27;
     const int pk = lane < 27 ? lane / 9 : 0, pi_ = lane < 27 ? lane - 9 * pk : 0;
-    const int pey = EY(pi_);
-    const bool pg0 = W16 && pk == 1 && pi_ == 0;  // the FP32 g_0 plane
-    const int pesz = (W16 && !pg0) ? 2 : 4;
+    const int pey = plo ? 0 : EY(pi_);
+    const bool pg0 = W16 && pk == 1 && pi_ == 0 && !plo;  // the FP32 g_0 plane
+    const bool p16 = plo || (W16 && !pg0);                 // a 16-bit row
+    const int pesz = p16 ? 2 : 4;
     const ptrdiff_t prow = (ptrdiff_t)pitch * pesz;  // bytes per source row
-    const int pbytes = (W16 && !pg0) ? Fmt::ROW : 144;
-    const ptrdiff_t pstart = (ptrdiff_t)((W16 && !pg0) ? e16 : e32) * pesz;
+    const int pbytes = p16 ? 80 : 144;
+    const ptrdiff_t pstart = (ptrdiff_t)(p16 ? e16 : e32) * pesz;
     auto plane_off = [&](int k, int i) -> ptrdiff_t {
       if (!W16) return (ptrdiff_t)(k * 9 + i) * (ptrdiff_t)I.plane_bytes;
       if (k == 1 && i == 0) return (ptrdiff_t)I.g0_off;
       return (ptrdiff_t)dev_plane(k, i) * (ptrdiff_t)I.plane_bytes;
     };
-    const ptrdiff_t off_n = plane_off(pk, pi_) - (ptrdiff_t)pey * prow + pstart;
-    const ptrdiff_t off_w = plane_off(pk, OPP(pi_)) + pstart;
-    const int pdst = Fmt::off(pk, pi_);
+    const ptrdiff_t off_n =
+        (plo ? (ptrdiff_t)I.g0lo_off : plane_off(pk, pi_)) - (ptrdiff_t)pey * prow + pstart;
+    const ptrdiff_t off_w = plo ? off_n : plane_off(pk, OPP(pi_)) + pstart;
+    const int pdst = plo ? Fmt::LO : Fmt::off(pk, pi_);
     // the warp's copies of the populations pulled by moment row m (the mirror
     // row's below the bottom wall): lane p < 27 copies population p
     auto issue = [&](int m) {
@@ -255,7 +266,7 @@ stash_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
       pending |= 1u << (m & (Cfg::SR - 1));
       if (lane == 0) mbar_expect_tx(bar, Cfg::TX);
       __syncwarp();
-      if (lane < 27) {
+      if (lane < 28) {
         const bool wall = (pey == 1 && mr == 0) || (pey == -1 && mr == ny - 1);
         const char* srcp = src + (ptrdiff_t)mr * prow + (wall ? off_w : off_n);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -298,6 +309,9 @@ stash_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
         const C* c0 = cring + p0;
         const C* cn = cring + pn;
         const C cc = c0[t];
+        const C clo = lo_at(clr + p0, t);
+        const C g0lo = __half2float(reinterpret_cast<const __half*>(s + Fmt::LO)[c0lo]) *
+                       G0LO_INV;
         const C pp = pring[p0 + t], TT = Tring[p0 + t];
         Stencils<C> st;
         grad3(cs, c0, cn, t, st.gcx, st.gcy);
@@ -312,9 +326,11 @@ stash_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
         st.kappa = d1 + d2;
         const Drive<S> d = drive<S>(P, r, f, cc, TT, st);
         C o[27];
+        C lo_out = C(0);
         collide<S>(P, f, g, h, cc, pp, TT, st.gpx, st.gpy, d,
-                   [&](int k, int ii, C v) { o[k * 9 + ii] = v; });
+                   [&](int k, int ii, C v) { o[k * 9 + ii] = v; }, g0lo, clo, &lo_out);
         const size_t e = (size_t)r * pitch + XG + x;
+        st_cell_g0lo(I, dst, (size_t)r * pitch, x, lo_out);
 #pragma unroll
         for (int k = 0; k < 3; k++)
 #pragma unroll
@@ -347,7 +363,11 @@ stash_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
           const char* s = slot(m);
           C v[9];
           wstash_pull<S, 1>(I, P, s, c0, c0g, mr, xw, v);
-          cring[ci] = sum9(v);
+          const C g0lo =
+              __half2float(reinterpret_cast<const __half*>(s + Fmt::LO)[c0lo]) * G0LO_INV;
+          C clo;
+          cring[ci] = moment_c(v, g0lo, clo);
+          clr[ci] = __float2half_rn(clo * G0LO_SCALE);
           wstash_pull<S, 0>(I, P, s, c0, c0g, mr, xw, v);
           pring[pi] = sum9(v);
           wstash_pull<S, 2>(I, P, s, c0, c0g, mr, xw, v);
@@ -357,6 +377,7 @@ stash_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
         } else {
           const int mm = 2 * ny - 1 - m;
           cring[ci] = cring[cr(mm) + t];
+          clr[ci] = clr[cr(mm) + t];
           pring[pi] = pring[pr(mm) + t];
           Tring[pi] = ghost_T<S>(I, xw, false, Tring[pr(mm) + t]);
         }
@@ -367,9 +388,8 @@ stash_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
       // ---- 4. unit normal of row i + 1
       const int mn = i + 1;
       if (mn >= ya - 1 && mn <= yb && t >= 1 && t < NC - 1) {
-        const C* c0 = cring + rr(1);
         const int ni = nr(mn) + t;
-        normal3(cring + rr(0), c0, cring + rr(2), t, en2, nxr[ni], nyr[ni]);
+        normal3(cring + rr(0), cring + rr(1), cring + rr(2), t, en2, nxr[ni], nyr[ni]);
       }
     }
     __syncthreads();

@@ -291,7 +291,12 @@ strip_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
             const char* sp = mr < ny - 1 ? slot_of(mr + 1) : s0;
             C v[9];
             St::template spull9<1>(I, P, sm, s0, sp, col, mr, ny, xw, v);
-            cring[ci] = sum9(v);
+            {
+              // the g_0 low part is read from the buffer (it is not staged)
+              C clo_unused;
+              const C g0lo = ld_g0lo(I, I.buf[parity], (size_t)mr * pitch + XG + xw);
+              cring[ci] = moment_c(v, g0lo, clo_unused);
+            }
             St::template spull9<0>(I, P, sm, s0, sp, col, mr, ny, xw, v);
             pring[pi] = sum9(v);
             St::template spull9<2>(I, P, sm, s0, sp, col, mr, ny, xw, v);
@@ -337,9 +342,15 @@ strip_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
         st.kappa = d1 + d2;
         const Drive<S> d = drive<S>(P, r, f, cc, TT, st);
         C o[27];
+        // two-float g_0 and c of this cell (the low part read from the buffer)
+        const C g0lo = ld_g0lo(I, I.buf[parity], (size_t)r * pitch + XG + x);
+        C clo;
+        (void)moment_c(g, g0lo, clo);
+        C lo_out = C(0);
         collide<S>(P, f, g, h, cc, pp, TT, st.gpx, st.gpy, d,
-                   [&](int k, int ii, C v) { o[k * 9 + ii] = v; });
+                   [&](int k, int ii, C v) { o[k * 9 + ii] = v; }, g0lo, clo, &lo_out);
         const size_t e = (size_t)r * pitch + XG + x;
+        st_cell_g0lo(I, dst, (size_t)r * pitch, x, lo_out);
 #pragma unroll
         for (int k = 0; k < 3; k++)
 #pragma unroll

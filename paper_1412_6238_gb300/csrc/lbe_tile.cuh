@@ -190,12 +190,18 @@ struct Tile {
     const bool active = (gx < nx) && (gy < ny);
     C f[9], g[9], h[9];
     C cc = C(0), pp = C(0), TT = C(0);
+    C g0lo = C(0), clo = C(0);  // low parts of g_0 and c (16/32-bit forms)
     Cell<S> q = make_cell<S>(active ? gx : 0, active ? gy : 0, nx);
     if (active) {
       pull9<S, 0>(I, P, src, q, f);
       pull9<S, 1>(I, P, src, q, g);
       pull9<S, 2>(I, P, src, q, h);
-      cc = sum9(g);
+      if constexpr (S::kind != ST_F64) {
+        g0lo = ld_g0lo(I, src, (size_t)gy * I.pitch + XG + gx);
+        cc = moment_c(g, g0lo, clo);
+      } else {
+        cc = sum9(g);
+      }
       pp = sum9(f);
       TT = dv(sum9(h), P.rho_cv, P.inv_rho_cv);
     } else if (gy <= ny + 1) {
@@ -259,7 +265,7 @@ struct Tile {
 
       if (MODE == 1) {
         const size_t N = (size_t)nx * ny, k = (size_t)gy * nx + gx;
-        out[k] = (double)cc;
+        out[k] = (double)cc + (double)clo;
         out[N + k] = (double)pp;
         out[2 * N + k] = (double)d.ux;
         out[3 * N + k] = (double)d.uy;
@@ -269,8 +275,11 @@ struct Tile {
 
       char* __restrict__ dst = I.buf[parity ^ 1];
       const size_t rowbase = (size_t)gy * I.pitch;
+      C lo_out = C(0);
       collide<S>(P, f, g, h, cc, pp, TT, st.gpx, st.gpy, d,
-                 [&](int k, int i, C v) { st_cell<S>(I, dst, k, i, rowbase, gx, v); });
+                 [&](int k, int i, C v) { st_cell<S>(I, dst, k, i, rowbase, gx, v); }, g0lo,
+                 clo, &lo_out);
+      if constexpr (S::kind != ST_F64) st_cell_g0lo(I, dst, rowbase, gx, (float)lo_out);
     }
   }
 };

@@ -66,8 +66,8 @@ def _run(w, steps, storage):
 
 # (case, storage) -> bounds on (u, T) relative L2 at the stated step count
 BOUNDS = {
-    ("planar", "f32"): (2e-3, 1e-5), ("planar", "f16dev"): (1e-1, 1e-3),
-    ("drop", "f32"): (2e-3, 1e-5), ("drop", "f16dev"): (5e-2, 1e-3),
+    ("planar", "f32"): (1e-4, 1e-5), ("planar", "f16dev"): (1e-1, 1e-3),
+    ("drop", "f32"): (1e-4, 1e-5), ("drop", "f16dev"): (5e-2, 1e-3),
 }
 
 

@@ -20,8 +20,10 @@ from helpers import field_errors, gpu_fields, oracle_fields, rel_l2
 
 pytestmark = pytest.mark.gpu
 
+# relative L2 against the FP64 oracle: FP64 1e-12, FP32 1e-5 (u, T and c),
+# FP16 deviations 1e-3, BF16 deviations 2e-2
 TOL = {"f64": 1e-12, "f32": 1e-5, "f16dev": 1e-3, "bf16dev": 2e-2}
-TOL_U = dict(TOL, f32=1e-4)
+TOL_U = dict(TOL)
 STATE_TOL = {"f64": 1e-15, "f32": 1e-7, "f16dev": 1e-3, "bf16dev": 1e-2}
 
 
@@ -67,9 +69,13 @@ def test_state_roundtrip(LBE, orc, storage):
     if storage == "f64":
         assert np.array_equal(got, ref)
     else:
-        # FP32 holds f, g rounded and hbar as an FP32 deviation from the
-        # linear conduction profile
-        assert np.array_equal(got[:18], ref[:18].astype(np.float32).astype(np.float64))
+        # FP32 holds f and g_1..g_8 rounded, g_0 as an FP32 value plus its
+        # FP16-coded low part, hbar as an FP32 deviation from the linear
+        # conduction profile
+        keep = [k for k in range(18) if k != 9]
+        assert np.array_equal(got[keep], ref[keep].astype(np.float32).astype(np.float64))
+        g0, r0 = got[9], ref[9]
+        assert np.abs(g0 - r0).max() <= 2e-11 * max(1.0, np.abs(r0).max())
         assert state_err(got, ref) < 1e-7
 
 
@@ -210,7 +216,11 @@ def test_planar_marangoni_parity(LBE, orc, storage):
     G = oracle_fields(orc, w, orc.run(w.params, orc.init(w.params, w.c0, w.T0, w.Tbot, w.Ttop),
                                       w.Tbot, w.Ttop, n))
     e = field_errors(F, G)
-    assert e["u"] < TOL_U[storage] and e["T"] < TOL[storage], e
+    # FP32: the flow here is slow (Re = Ma ~ 1e-3, u ~ 1e-6) and driven by
+    # grad T along the interface, which carries the FP32 rounding of the
+    # O(1) temperature deviation: u is within 1.5e-5 after 1000 steps
+    tol_u = 2e-5 if storage == "f32" else TOL_U[storage]
+    assert e["u"] < tol_u and e["T"] < TOL[storage], e
 
 
 def test_fields_f32_and_device_outputs(LBE, orc):
