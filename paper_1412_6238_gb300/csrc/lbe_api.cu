@@ -55,6 +55,7 @@ struct lbe_handle {
   TmapSet* d_maps = nullptr;     // [n] tensor maps for the strip kernel
   int* d_err = nullptr;          // device error word (strip kernel wait time-outs)
   int64_t total_tiles = 0;
+  int max_ny = 0;                // largest ny of the instances
   int parity = 0;
   int64_t steps = 0;
   bool prev_valid = false;       // buf[parity^1] holds the previous step
@@ -318,6 +319,7 @@ lbe_status setup_tiles(lbe_handle* h) {
     h->grid = h->grid_req > 0 ? h->grid_req : occ * h->num_sms;
     int max_ny = 1;
     for (auto& H : h->inst) max_ny = std::max(max_ny, H.ny);
+    h->max_ny = max_ny;
     if (h->seg_req > 0) {
       h->seg = h->seg_req;
     } else {
@@ -400,9 +402,14 @@ lbe_status setup_tiles(lbe_handle* h) {
 }
 
 cudaError_t launch_one_step(lbe_handle* h, int parity) {
-  if (is_strip(h->tile))
-    return launch_strip(h->storage, h->tile - STRIP_FIRST, h->d_inst, h->d_maps, h->n,
-                        h->total_tiles, h->seg, parity, h->grid, h->d_err, h->stream);
+  if (is_strip(h->tile)) {
+    cudaError_t e = launch_strip(h->storage, h->tile - STRIP_FIRST, h->d_inst, h->d_maps, h->n,
+                                 h->total_tiles, h->seg, parity, h->grid, h->d_err, h->stream);
+    // the stash kernel leaves the periodic ghost columns to ghost_kernel
+    if (e == cudaSuccess && h->tile == STASH_ID)
+      e = launch_ghosts(h->d_inst, h->n, h->max_ny, parity ^ 1, h->stream);
+    return e;
+  }
   return launch_step(h->storage, h->tile, h->d_inst, h->n, h->total_tiles, parity, h->grid,
                      h->stream);
 }
@@ -624,12 +631,11 @@ lbe_status create(int32_t n, const lbe_params* params, const lbe_init_fields* in
   CUB(cudaMalloc(&h->d_err, sizeof(int)));
   CUB(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
   {
-    // default kernel: the strip kernel where it applies (16/32-bit storage,
-    // every instance at least XG columns wide), else the tile kernel
+    // default kernel: the stash strip kernel where it applies (16/32-bit
+    // storage, every instance at least XG columns wide), else the tile kernel
     int min_nx = 1 << 30;
     for (auto& H : h->inst) min_nx = std::min(min_nx, H.nx);
-    h->tile = (h->storage == LBE_F64 || min_nx < XG) ? 0
-              : (h->storage == LBE_F32 ? STASH_ID : STRIP_FIRST);
+    h->tile = (h->storage == LBE_F64 || min_nx < XG) ? 0 : STASH_ID;
   }
   lbe_status s2 = setup_tiles(h);
   if (s2) return bail(s2);

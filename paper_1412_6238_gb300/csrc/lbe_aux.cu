@@ -1,3 +1,4 @@
+#include <algorithm>
 // Auxiliary kernels: initial state, state conversion (push / pull between the
 // pre-collision form and a storage buffer), FP64 reductions, dtype casts,
 // and the storage dispatch of the step / field launchers.
@@ -238,6 +239,50 @@ cudaError_t launch_pull(int storage, const InstDev* d, int nx, int ny, double* p
 constexpr int SUM_BLOCKS = 304;
 constexpr int SUM_THREADS = 256;
 int sums_blocks() { return SUM_BLOCKS; }
+
+// ------------------------------------------------------------ ghost columns
+// Periodic ghost columns of the buffer `parity` of every instance (16/32-bit
+// storages): in a row, elements 0..XG-1 repeat cells nx-XG..nx-1 and elements
+// nx+XG..nx+2XG-1 repeat cells 0..XG-1 (element XG + x holds cell x).  Planes:
+// 27 FP32 + the FP16 g_0 low part, or 26 16-bit + the FP32 g_0 + the low part.
+// blockIdx.y: instance.
+__global__ void ghost_kernel(const InstDev* __restrict__ insts, int parity) {
+  const InstDev& I = insts[blockIdx.y];
+  char* b = I.buf[parity];
+  const int nx = I.nx, ny = I.ny;
+  const size_t pitch = (size_t)I.pitch;
+  const bool w16 = I.storage >= ST_F16DEV;
+  const int64_t total = (int64_t)28 * ny * (2 * XG);
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(t % (2 * XG));
+    const int64_t r = t / (2 * XG);
+    const int y = (int)(r % ny), p = (int)(r / ny);
+    const int dstE = j < XG ? j : nx + j;            // left ghosts, then right
+    const int srcE = j < XG ? nx + j : j;            // cells nx-XG+j, then j-XG
+    const size_t row = (size_t)y * pitch;
+    if (p == 27) {
+      uint16_t* q = reinterpret_cast<uint16_t*>(b + I.g0lo_off) + row;
+      q[dstE] = q[srcE];
+    } else if (!w16) {
+      float* q = reinterpret_cast<float*>(b + (size_t)p * I.plane_bytes) + row;
+      q[dstE] = q[srcE];
+    } else if (p == 26) {
+      float* q = reinterpret_cast<float*>(b + I.g0_off) + row;
+      q[dstE] = q[srcE];
+    } else {
+      uint16_t* q = reinterpret_cast<uint16_t*>(b + (size_t)p * I.plane_bytes) + row;
+      q[dstE] = q[srcE];
+    }
+  }
+}
+
+cudaError_t launch_ghosts(const InstDev* d, int n_inst, int max_ny, int parity, cudaStream_t s) {
+  const int64_t total = (int64_t)28 * max_ny * (2 * XG);
+  const int bx = (int)std::min<int64_t>((total + 255) / 256, 4096);
+  ghost_kernel<<<dim3(bx, n_inst), 256, 0, s>>>(d, parity);
+  return cudaGetLastError();
+}
 
 __device__ __forceinline__ void block_sum6(double v[6], double* sh) {
   // sh: 6 * SUM_THREADS doubles

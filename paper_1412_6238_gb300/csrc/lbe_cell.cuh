@@ -257,20 +257,21 @@ __device__ __forceinline__ void collide(const Phys<typename S::C>& P, const type
     // q = a + ((a^2 - u^2/c_s^2)/2), Gamma_i = w_i (1 + q); opposite
     // directions share (a^2 - u^2/c_s^2)/2; F.(xi_i - u) = F.xi_i - F.u.
     // The eight moving directions come first and the rest direction takes
-    // the remainder of each equilibrium (p, c and rho c_v T minus the sum of
-    // the other eight; the same value in exact arithmetic).  Computed
+    // the remainder of the c and rho c_v T equilibria (the moment minus the
+    // sum of the other eight; the same value in exact arithmetic).  Computed
     // directly, w_0 H_0 carries the FP32 representation error of w_0 = 4/9
     // in the same direction at every bulk cell, a systematic drift of sum c
-    // over long runs.
+    // (and of the energy) over long runs.
     const C Fdu = Fx * ux + Fy * uy, Gdu = Gx * ux + Gy * uy;
     const C sg = cc * inv_rcs2;  // c / (rho c_s^2)
+    const C agsg = ag * sg, aTi = aT * inv_rcs2;
     const C ux3 = C(3) * ux, uy3 = C(3) * uy;
-    C sfe = C(0), sge = C(0), she = C(0);  // sums of the moving equilibria
+    C sge = C(0), she = C(0);  // sums of the moving g and hbar equilibria
     auto relax = [&](int i, C G, C feq, C geq, C heqd, C Fxi, C Gxi) {
       out(0, i, f[i] + omega_f * (feq - f[i]) + af * ((Fxi - Fdu) * G));
       const C gdot = Gxi - Gdu;
-      out(1, i, g[i] + omega_g * (geq - g[i]) + ag * (sg * gdot) * G);
-      out(2, i, h[i] + omega_T * (heqd - h[i]) + aT * (inv_rcs2 * gdot) * (rcvT * G));
+      out(1, i, g[i] + omega_g * (geq - g[i]) + (agsg * gdot) * G);
+      out(2, i, h[i] + omega_T * (heqd - h[i]) + (aTi * gdot) * (rcvT * G));
     };
     auto dir = [&](int i, C W, C a, C hq, C Fxi, C Gxi) {
       const C q = a + hq;
@@ -278,7 +279,6 @@ __device__ __forceinline__ void collide(const Phys<typename S::C>& P, const type
       const C feq = W * (pp + rcs2 * q);
       const C geq = W * (Hi + cc * q);
       const C heqd = dev_h<S>() ? rcvTd * G + rcvTr * (W * q) : rcvT * G;
-      sfe += feq;
       sge += geq;
       she += heqd;
       relax(i, G, feq, geq, heqd, Fxi, Gxi);
@@ -305,13 +305,21 @@ __device__ __forceinline__ void collide(const Phys<typename S::C>& P, const type
     // rest direction: f and hbar as above; g_0 in two-float arithmetic
     // (g_0 + omega_g (g_eq,0 - g_0) + source, g_eq,0 = c - sum of the moving
     // g_eq), so that c keeps the precision of its two-float moment
-    out(0, 0, f[0] + omega_f * ((pp - sfe) - f[0]) + af * ((C(0) - Fdu) * G0));
+    out(0, 0, f[0] + omega_f * (W0 * (pp + rcs2 * hu) - f[0]) + af * ((C(0) - Fdu) * G0));
     out(2, 0, h[0] + omega_T * (((dev_h<S>() ? rcvTd : rcvT) - she) - h[0]) +
-                  aT * (inv_rcs2 * (C(0) - Gdu)) * (rcvT * G0));
+                  (aTi * (C(0) - Gdu)) * (rcvT * G0));
     {
-      const C src0 = ag * (sg * (C(0) - Gdu)) * G0;
+      const C src0 = (agsg * (C(0) - Gdu)) * G0;
       C s0, e0;
       two_sum(cc, -sge, s0, e0);  // g_eq,0 = s0 + (e0 + clo)
+      if (omega_g == C(1)) {
+        // tau_g = 1: g_0 becomes g_eq,0 + source
+        C hi_new, lo_new;
+        fast_two_sum(s0, (e0 + clo) + src0, hi_new, lo_new);
+        out(1, 0, hi_new);
+        if (g0lo_out) *g0lo_out = lo_new;
+        return;
+      }
       C dh, de;
       two_sum(s0, -g[0], dh, de);  // g_eq,0 - g_0 = dh + dl
       const C dl = de + ((e0 + clo) - g0lo);

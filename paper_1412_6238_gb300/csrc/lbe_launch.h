@@ -96,6 +96,9 @@ int sums_blocks();
 cudaError_t launch_sums(const double* cur, const double* prev, int64_t n, double* partial,
                         double* out, cudaStream_t s);
 cudaError_t launch_f64_to_f32(const double* in, float* out, int64_t n, cudaStream_t s);
+// Periodic ghost columns of buffer `parity` of n_inst instances (16/32-bit
+// storages), after a step of the stash kernel.
+cudaError_t launch_ghosts(const InstDev* d, int n_inst, int max_ny, int parity, cudaStream_t s);
 
 // Adjoint kernels (lbe_adjoint.cu), FP64, one instance d_one of nx x ny.
 // Scratch: adjoint_scratch_doubles(nx, ny) doubles.

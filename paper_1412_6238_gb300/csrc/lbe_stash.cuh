@@ -216,7 +216,6 @@ stash_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
     const int x = x0 - 2 + t;
     const int xw = wrapx(x, nx);
     const bool collides = t >= 2 && t < NC - 2 && x < nx;
-    const bool edge_ghost = collides && (x < XG || x >= nx - XG);
     // staged elements of this warp's population rows (storage element e holds
     // column e - XG): its cells are columns x0 - 2 + 32 w + lane, their pulls
     // reach elements x0 + 32 w + 1 .. x0 + 32 w + 34.  FP32 rows start at
@@ -330,20 +329,13 @@ stash_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
         collide<S>(P, f, g, h, cc, pp, TT, st.gpx, st.gpy, d,
                    [&](int k, int ii, C v) { o[k * 9 + ii] = v; }, g0lo, clo, &lo_out);
         const size_t e = (size_t)r * pitch + XG + x;
-        st_cell_g0lo(I, dst, (size_t)r * pitch, x, lo_out);
+        st_g0lo(I, dst, e, lo_out);
 #pragma unroll
         for (int k = 0; k < 3; k++)
 #pragma unroll
           for (int ii = 0; ii < 9; ii++) S::st(I, dst, k, ii, e, o[k * 9 + ii]);
-        if (edge_ghost) {
-#pragma unroll
-          for (int k = 0; k < 3; k++)
-#pragma unroll
-            for (int ii = 0; ii < 9; ii++) {
-              if (x < XG) S::st(I, dst, k, ii, e + nx, o[k * 9 + ii]);
-              if (x >= nx - XG) S::st(I, dst, k, ii, e - nx, o[k * 9 + ii]);
-            }
-        }
+        // (the periodic ghost columns are refreshed by ghost_kernel after the
+        // step, not here: the branch costs this kernel about 7 %)
       }
 
       // ---- 2. the warp's copies of row i + 3 (into the slot of row i - 1)

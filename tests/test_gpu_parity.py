@@ -154,7 +154,7 @@ def test_strip_is_default_and_rejects_narrow(LBE):
     from paper_1412_6238_gb300.lbe import LBEError
     w = small_drop()
     assert LBE(w, storage="f32").get_tile()["kernel"] == 7
-    assert LBE(w, storage="f16dev").get_tile()["kernel"] == 5
+    assert LBE(w, storage="f16dev").get_tile()["kernel"] == 7
     assert LBE(w, storage="f64").get_tile()["kernel"] == 0
     narrow = wl.droplet(3, 20, 1.5, 1.5, 10.0, Re=1.0, Ma=10.0, Ca=0.05, eta_m=0.2, eta_r=1.0,
                         lam_r=1.0)
