@@ -408,6 +408,24 @@ def measure_variants(args, w, ref_fields):
     res["speedup_batched_f16dev_vs_sequential_f32"] = res["batched_f16dev"] / res["sequential_f32"]
     res["unit"] = UNIT
     out["batch64"] = res
+
+    # differentiable migration (256 x 512 drop, 2000 FP32 steps, checkpoints
+    # every 100, loss over the last 200 states): forward + reverse sweep
+    from paper_1412_6238_gb300 import workloads as wl
+    mw = wl.migration_256x512(steps=2000)
+    sim = LBE(mw, storage="f32")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = sim.adjoint(2000, 200, 100, want_dT0=True)
+    ta = time.perf_counter() - t0
+    del sim
+    torch.cuda.empty_cache()
+    out["adjoint_migration_256x512"] = {
+        "seconds": ta, "loss": r["loss"], "grad_sigmaT": r["grad"][0],
+        "grad_eta_ratio": r["grad"][1], "grad_lam_ratio": r["grad"][2],
+        "forward_plus_reverse_MLUPS": mw.cells * 2000 / ta / 1e6,
+        "note": "FP32 forward (stash kernel), FP64 reverse sweep over recomputed segments; "
+                "wall clock of one lbe_adjoint call"}
     return out
 
 

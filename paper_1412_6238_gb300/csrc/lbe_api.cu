@@ -28,6 +28,7 @@ struct InstHost {
   lbe_params p{};
   int nx = 0, ny = 0, pitch = 0;
   uint64_t plane_bytes = 0, g0_off = 0, g0lo_off = 0, buf_bytes = 0;
+  uint64_t pair_bytes = 0, h_off = 0;  // FP32 pair layout
   char* arena = nullptr;  // two buffers of buf_bytes
   double* walls = nullptr;  // device: Tbot[nx], Ttop[nx], then 4 float tables
   std::vector<double> Tbot, Ttop;
@@ -170,6 +171,8 @@ void fill_desc(lbe_handle* h, int j, InstDev& D) {
   D.plane_bytes = H.plane_bytes;
   D.g0_off = H.g0_off;
   D.g0lo_off = H.g0lo_off;
+  D.pair_bytes = H.pair_bytes;
+  D.h_off = H.h_off;
   D.buf[0] = H.arena;
   D.buf[1] = H.arena + H.buf_bytes;
   D.Tbot = H.walls;
@@ -275,6 +278,9 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 // Tensor maps of instance j for the strip kernel with nc threads: box of
 // strip_bw(nc) elements in x, one row, all population planes.
 lbe_status encode_maps(lbe_handle* h, int j, int nc, TmapSet& T) {
+  memset(&T, 0, sizeof T);
+  // FP32 (pair layout) runs only the stash kernel, which uses no tensor map
+  if (h->storage == LBE_F32) return LBE_OK;
   auto enc = encode_fn();
   if (!enc) return fail(h, LBE_ECUDA, "cuTensorMapEncodeTiled is not available");
   const InstHost& H = h->inst[j];
@@ -557,8 +563,11 @@ lbe_status create(int32_t n, const lbe_params* params, const lbe_init_fields* in
       H.g0lo_off = H.g0_off + (((uint64_t)H.ny * H.pitch * 4 + 255) / 256 * 256);
       H.buf_bytes = H.g0lo_off + lo_bytes;
     } else if (st == LBE_F32) {
+      // 9 (f_i, g_i) pair planes, 9 hbar planes, the g_0 low part
       H.g0_off = 0;
-      H.g0lo_off = 27 * H.plane_bytes;
+      H.pair_bytes = ((uint64_t)H.ny * H.pitch * 8 + 255) / 256 * 256;
+      H.h_off = 9 * H.pair_bytes;
+      H.g0lo_off = H.h_off + 9 * H.plane_bytes;
       H.buf_bytes = H.g0lo_off + lo_bytes;
     } else {
       H.g0_off = 0;

@@ -11,6 +11,8 @@ namespace lbe {
 bool tile_available(int storage, int tile) {
   if (tile < 0 || tile >= NUM_TILES) return false;
   if (storage == ST_F64) return tile == 0;
+  // the TMA-ring strips stage 27 equal planes: not the FP32 pair layout
+  if (storage == ST_F32 && is_strip(tile) && tile != STASH_ID) return false;
   return true;
 }
 
@@ -244,7 +246,8 @@ int sums_blocks() { return SUM_BLOCKS; }
 // Periodic ghost columns of the buffer `parity` of every instance (16/32-bit
 // storages): in a row, elements 0..XG-1 repeat cells nx-XG..nx-1 and elements
 // nx+XG..nx+2XG-1 repeat cells 0..XG-1 (element XG + x holds cell x).  Planes:
-// 27 FP32 + the FP16 g_0 low part, or 26 16-bit + the FP32 g_0 + the low part.
+// FP32: 9 (f, g) pairs + 9 hbar + the FP16 g_0 low part; 16-bit: 26 16-bit +
+// the FP32 g_0 + the low part.
 // blockIdx.y: instance.
 __global__ void ghost_kernel(const InstDev* __restrict__ insts, int parity) {
   const InstDev& I = insts[blockIdx.y];
@@ -261,11 +264,20 @@ __global__ void ghost_kernel(const InstDev* __restrict__ insts, int parity) {
     const int dstE = j < XG ? j : nx + j;            // left ghosts, then right
     const int srcE = j < XG ? nx + j : j;            // cells nx-XG+j, then j-XG
     const size_t row = (size_t)y * pitch;
-    if (p == 27) {
+    if (!w16) {
+      // FP32: 9 (f, g) pair planes, 9 hbar planes, the low part
+      if (p < 9) {
+        double* q = reinterpret_cast<double*>(b + (size_t)p * I.pair_bytes) + row;  // 8-byte pairs
+        q[dstE] = q[srcE];
+      } else if (p < 18) {
+        float* q = reinterpret_cast<float*>(b + I.h_off + (size_t)(p - 9) * I.plane_bytes) + row;
+        q[dstE] = q[srcE];
+      } else if (p == 18) {
+        uint16_t* q = reinterpret_cast<uint16_t*>(b + I.g0lo_off) + row;
+        q[dstE] = q[srcE];
+      }
+    } else if (p == 27) {
       uint16_t* q = reinterpret_cast<uint16_t*>(b + I.g0lo_off) + row;
-      q[dstE] = q[srcE];
-    } else if (!w16) {
-      float* q = reinterpret_cast<float*>(b + (size_t)p * I.plane_bytes) + row;
       q[dstE] = q[srcE];
     } else if (p == 26) {
       float* q = reinterpret_cast<float*>(b + I.g0_off) + row;

@@ -9,7 +9,10 @@
 // periodic ghost copies (cells nx-XG..nx-1 on the left, 0..XG-1 on the right)
 // written with every store, so that a row segment [x0-XG, x0+w+XG) can be
 // copied in one piece (TMA) for any strip start x0.
-//   F64 / F32 : 27 planes, plane (k, i) at index k*9 + i (k = 0 f, 1 g, 2 hbar)
+//   F64 : 27 planes, plane (k, i) at index k*9 + i (k = 0 f, 1 g, 2 hbar)
+//   F32 : 9 pair planes holding (f_i, g_i) of a cell side by side (8 bytes
+//         per cell), then 9 planes of hbar_i (so that a cell's f_i and g_i,
+//         pulled from the same neighbour, load and store as one 8-byte word)
 //   F16DEV / BF16DEV : 26 planes of 16-bit deviations in the order
 //               f_0..f_8, g_1..g_8, hbar_0..hbar_8, then one FP32 plane
 //               holding g_0 at byte offset g0_off.
@@ -77,6 +80,8 @@ struct InstDev {
   uint64_t plane_bytes; // bytes between consecutive planes
   uint64_t g0_off;      // byte offset of the FP32 g_0 plane (16-bit forms)
   uint64_t g0lo_off;    // byte offset of the FP16 plane of the g_0 low part (16/32-bit)
+  uint64_t pair_bytes;  // FP32: bytes of one (f_i, g_i) pair plane
+  uint64_t h_off;       // FP32: byte offset of the first hbar plane
   char* buf[2];         // population arenas (ping-pong)
   const double* Tbot;   // [nx] wall temperature at y = -1/2
   const double* Ttop;   // [nx] wall temperature at y = ny - 1/2
@@ -121,11 +126,21 @@ struct StF32 {
   static constexpr int kind = ST_F32;
   __device__ static __forceinline__ C ld(const InstDev& I, const Phys<C>&, const char* b, int k,
                                          int i, size_t idx) {
-    return __ldg(reinterpret_cast<const float*>(b + (size_t)(k * 9 + i) * I.plane_bytes) + idx);
+    if (k < 2)
+      return __ldg(reinterpret_cast<const float*>(b + (size_t)i * I.pair_bytes) + 2 * idx + k);
+    return __ldg(reinterpret_cast<const float*>(b + I.h_off + (size_t)i * I.plane_bytes) + idx);
   }
   __device__ static __forceinline__ void st(const InstDev& I, char* b, int k, int i, size_t idx,
                                             C v) {
-    reinterpret_cast<float*>(b + (size_t)(k * 9 + i) * I.plane_bytes)[idx] = v;
+    if (k < 2)
+      reinterpret_cast<float*>(b + (size_t)i * I.pair_bytes)[2 * idx + k] = v;
+    else
+      reinterpret_cast<float*>(b + I.h_off + (size_t)i * I.plane_bytes)[idx] = v;
+  }
+  // f_i and g_i of one cell as one 8-byte store
+  __device__ static __forceinline__ void st_fg(const InstDev& I, char* b, int i, size_t idx,
+                                               float fv, float gv) {
+    reinterpret_cast<float2*>(b + (size_t)i * I.pair_bytes)[idx] = make_float2(fv, gv);
   }
 };
 

@@ -53,14 +53,20 @@ template <class S>
 struct StashFmt;
 // Every form adds the FP16 row of the g_0 low part (40 elements, 80 bytes)
 // at byte LO of the slot.
+// FP32: 9 rows of (f_i, g_i) pairs (36 cells x 8 bytes), 9 rows of hbar_i
+// (36 x 4 bytes); off(k, i) is the byte offset of the row holding (k, i).
 template <>
 struct StashFmt<StF32> {
   using E = float;
-  static constexpr int EW = 36;              // elements per population row
-  static constexpr int ROW = EW * 4;         // bytes (a multiple of 16)
-  static constexpr int LO = 27 * ROW;        // the g_0 low-part row
-  static constexpr int SLOT_RAW = LO + 80;   // bytes of one warp's row
-  __host__ __device__ static constexpr int off(int k, int i) { return (k * 9 + i) * ROW; }
+  static constexpr int EW = 36;                       // cells per row
+  static constexpr int PROW = EW * 8;                 // pair row bytes
+  static constexpr int ROW = EW * 4;                  // hbar row bytes
+  static constexpr int HOFF = 9 * PROW;
+  static constexpr int LO = HOFF + 9 * ROW;           // the g_0 low-part row
+  static constexpr int SLOT_RAW = LO + 80;            // bytes of one warp's row
+  __host__ __device__ static constexpr int off(int k, int i) {
+    return k < 2 ? i * PROW : HOFF + i * ROW;
+  }
 };
 template <class E16>
 struct StashFmt16 {
@@ -108,6 +114,7 @@ __device__ __forceinline__ float stash_val(const char* slot, int k, int i, int c
                                            const Phys<float>& P) {
   using Fmt = StashFmt<S>;
   if constexpr (sizeof(typename Fmt::E) == 4) {
+    if (k < 2) return reinterpret_cast<const float*>(slot + Fmt::off(k, i))[2 * col + k];
     return reinterpret_cast<const float*>(slot + Fmt::off(k, i))[col];
   } else {
     if (k == 1 && i == 0) return reinterpret_cast<const float*>(slot + Fmt::off(1, 0))[col];
@@ -161,6 +168,22 @@ __device__ __forceinline__ void wstash_pull(const InstDev& I, const Phys<float>&
       }
     }
     out[i] = v;
+  }
+}
+
+// FP32 pair layout: f_i and g_i of a pulled cell with one 8-byte load each
+// (f and g follow the same bounce-back rule at the walls).
+__device__ __forceinline__ void wstash_pull_fg(const InstDev& I, const char* slot, int c0, int y,
+                                               float f[9], float g[9]) {
+  using Fmt = StashFmt<StF32>;
+  const bool wb = (y == 0), wt = (y == I.ny - 1);
+  const float2* b = reinterpret_cast<const float2*>(slot) + c0;
+#pragma unroll
+  for (int i = 0; i < 9; i++) {
+    const bool wall = (EY(i) == 1 && wb) || (EY(i) == -1 && wt);
+    const float2 v = wall ? b[i * Fmt::EW] : b[i * Fmt::EW - EX(i)];
+    f[i] = v.x;
+    g[i] = v.y;
   }
 }
 
@@ -252,10 +275,42 @@ stash_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
       if (k == 1 && i == 0) return (ptrdiff_t)I.g0_off;
       return (ptrdiff_t)dev_plane(k, i) * (ptrdiff_t)I.plane_bytes;
     };
-    const ptrdiff_t off_n =
+    ptrdiff_t off_n =
         (plo ? (ptrdiff_t)I.g0lo_off : plane_off(pk, pi_)) - (ptrdiff_t)pey * prow + pstart;
-    const ptrdiff_t off_w = plo ? off_n : plane_off(pk, OPP(pi_)) + pstart;
-    const int pdst = plo ? Fmt::LO : Fmt::off(pk, pi_);
+    ptrdiff_t off_w = plo ? off_n : plane_off(pk, OPP(pi_)) + pstart;
+    int pdst = plo ? Fmt::LO : Fmt::off(pk, pi_);
+    int pbytes_ = pbytes;
+    ptrdiff_t prow_ = prow;
+    if constexpr (!W16) {
+      // FP32 pair layout: lanes 0-8 copy (f_i, g_i) pair rows, 9-17 hbar
+      // rows, 18 the low part (19 copies)
+      const int q = lane;
+      const int qi = q < 9 ? q : (q < 18 ? q - 9 : 0);
+      const int qey = q < 18 ? EY(qi) : 0;
+      if (q < 9) {
+        prow_ = (ptrdiff_t)pitch * 8;
+        pbytes_ = Fmt::PROW;
+        off_n = (ptrdiff_t)qi * (ptrdiff_t)I.pair_bytes - (ptrdiff_t)qey * prow_ + (ptrdiff_t)e32 * 8;
+        off_w = (ptrdiff_t)OPP(qi) * (ptrdiff_t)I.pair_bytes + (ptrdiff_t)e32 * 8;
+        pdst = Fmt::off(0, qi);
+      } else if (q < 18) {
+        prow_ = (ptrdiff_t)pitch * 4;
+        pbytes_ = Fmt::ROW;
+        off_n = (ptrdiff_t)I.h_off + (ptrdiff_t)qi * (ptrdiff_t)I.plane_bytes -
+                (ptrdiff_t)qey * prow_ + (ptrdiff_t)e32 * 4;
+        off_w = (ptrdiff_t)I.h_off + (ptrdiff_t)OPP(qi) * (ptrdiff_t)I.plane_bytes +
+                (ptrdiff_t)e32 * 4;
+        pdst = Fmt::off(2, qi);
+      } else {
+        prow_ = (ptrdiff_t)pitch * 2;
+        pbytes_ = 80;
+        off_n = (ptrdiff_t)I.g0lo_off + (ptrdiff_t)e16 * 2;
+        off_w = off_n;
+        pdst = Fmt::LO;
+      }
+    }
+    const int pcopies = W16 ? 28 : 19;
+    const int pey_ = W16 ? pey : (lane < 18 ? EY(lane < 9 ? lane : lane - 9) : 0);
     // the warp's copies of the populations pulled by moment row m (the mirror
     // row's below the bottom wall): lane p < 27 copies population p
     auto issue = [&](int m) {
@@ -265,11 +320,11 @@ stash_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
       pending |= 1u << (m & (Cfg::SR - 1));
       if (lane == 0) mbar_expect_tx(bar, Cfg::TX);
       __syncwarp();
-      if (lane < 28) {
-        const bool wall = (pey == 1 && mr == 0) || (pey == -1 && mr == ny - 1);
-        const char* srcp = src + (ptrdiff_t)mr * prow + (wall ? off_w : off_n);
+      if (lane < pcopies) {
+        const bool wall = (pey_ == 1 && mr == 0) || (pey_ == -1 && mr == ny - 1);
+        const char* srcp = src + (ptrdiff_t)mr * prow_ + (wall ? off_w : off_n);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        bulk_load(smem_u32(slot(m) + pdst), srcp, pbytes, bar);
+        bulk_load(smem_u32(slot(m) + pdst), srcp, pbytes_, bar);
       }
     };
     auto wait_row = [&](int m) -> bool {
@@ -300,8 +355,12 @@ stash_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
       if (r >= ya && r < yb && collides) {
         const char* s = slot(r);
         C f[9], g[9], h[9];
-        wstash_pull<S, 0>(I, P, s, c0, c0g, r, x, f);
-        wstash_pull<S, 1>(I, P, s, c0, c0g, r, x, g);
+        if constexpr (!W16) {
+          wstash_pull_fg(I, s, c0, r, f, g);
+        } else {
+          wstash_pull<S, 0>(I, P, s, c0, c0g, r, x, f);
+          wstash_pull<S, 1>(I, P, s, c0, c0g, r, x, g);
+        }
         wstash_pull<S, 2>(I, P, s, c0, c0g, r, x, h);
         const int ps = rr(-2), p0 = rr(-1), pn = rr(0);  // rows r-1, r, r+1
         const C* cs = cring + ps;
@@ -330,10 +389,17 @@ stash_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
                    [&](int k, int ii, C v) { o[k * 9 + ii] = v; }, g0lo, clo, &lo_out);
         const size_t e = (size_t)r * pitch + XG + x;
         st_g0lo(I, dst, e, lo_out);
+        if constexpr (!W16) {
 #pragma unroll
-        for (int k = 0; k < 3; k++)
+          for (int ii = 0; ii < 9; ii++) S::st_fg(I, dst, ii, e, o[ii], o[9 + ii]);
 #pragma unroll
-          for (int ii = 0; ii < 9; ii++) S::st(I, dst, k, ii, e, o[k * 9 + ii]);
+          for (int ii = 0; ii < 9; ii++) S::st(I, dst, 2, ii, e, o[18 + ii]);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 3; k++)
+#pragma unroll
+            for (int ii = 0; ii < 9; ii++) S::st(I, dst, k, ii, e, o[k * 9 + ii]);
+        }
         // (the periodic ghost columns are refreshed by ghost_kernel after the
         // step, not here: the branch costs this kernel about 7 %)
       }
@@ -353,15 +419,19 @@ stash_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
         if (m < ny) {
           const int mr = m >= 0 ? m : -1 - m;
           const char* s = slot(m);
-          C v[9];
-          wstash_pull<S, 1>(I, P, s, c0, c0g, mr, xw, v);
+          C v[9], vf[9];
+          if constexpr (!W16) {
+            wstash_pull_fg(I, s, c0, mr, vf, v);
+          } else {
+            wstash_pull<S, 1>(I, P, s, c0, c0g, mr, xw, v);
+            wstash_pull<S, 0>(I, P, s, c0, c0g, mr, xw, vf);
+          }
           const C g0lo =
               __half2float(reinterpret_cast<const __half*>(s + Fmt::LO)[c0lo]) * G0LO_INV;
           C clo;
           cring[ci] = moment_c(v, g0lo, clo);
           clr[ci] = __float2half_rn(clo * G0LO_SCALE);
-          wstash_pull<S, 0>(I, P, s, c0, c0g, mr, xw, v);
-          pring[pi] = sum9(v);
+          pring[pi] = sum9(vf);
           wstash_pull<S, 2>(I, P, s, c0, c0g, mr, xw, v);
           C T = dv(sum9(v), P.rho_cv, P.inv_rho_cv);
           if (m < 0) T = ghost_T<S>(I, xw, true, T);

@@ -4,10 +4,9 @@ the same seeded inputs.
 Bounds (relative L2 over the domain, velocity as a vector):
   FP64 storage  1e-12 (the FP64 path rounds operation by operation like the
                 oracle; it is bitwise equal in practice)
-  FP32 storage  1e-5 on T and c; 1e-4 on u: the FP32 rounding of the O(1)
-                order parameter (about 6e-8) is differentiated twice into the
-                curvature, which bounds the capillary force, and so u, at
-                ~1e-5 relative per step (measured one-step error 4.5e-6)
+  FP32 storage  1e-5 on u, T and c (c = sum g_i carried as two floats;
+                measured one-step u error 1.8e-7); 2e-5 on u for the slow
+                512 x 256 planar flow
   FP16-deviation storage  1e-3 (u, T) on the short drop run
   BF16-deviation: measured, 2e-2
 """
@@ -103,20 +102,24 @@ def test_one_step_from_same_state(LBE, orc, storage, nx, ny):
     assert state_err(got, ref) < tol
 
 
-@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5, 6, 7])
 def test_kernels_bitwise_identical(LBE, tile):
-    """Every tile shape and both strip kernels (TMA-staged rows) compute the
-    same per-cell arithmetic as tile kernel 0; the compiler may contract a
-    different subset of products into FMAs per kernel, so results agree to
-    the last bits (1e-6 of each lattice's magnitude), not bitwise."""
+    """Every tile shape and the strip kernels compute the same per-cell
+    arithmetic as tile kernel 0; the compiler may contract a different
+    subset of products into FMAs per kernel, so results agree to the last
+    bits (1e-6 of each lattice's magnitude), not bitwise.  FP32 for the tile
+    shapes and the stash kernel; FP16 deviations for the TMA-ring strips
+    (which do not run the FP32 pair layout)."""
+    storage = "f16dev" if tile in (5, 6) else "f32"
     w = small_drop(150, 77)
-    a = LBE(w, storage="f32")
+    a = LBE(w, storage=storage)
     a.set_tile(0)
     a.step(7)
-    b = LBE(w, storage="f32")
+    b = LBE(w, storage=storage)
     b.set_tile(tile, -1 if tile % 2 else 0)
     b.step(7)
-    assert state_err(b.get_state().numpy(), a.get_state().numpy()) < 1e-6
+    tol = 1e-6 if storage == "f32" else 1e-3
+    assert state_err(b.get_state().numpy(), a.get_state().numpy()) < tol
 
 
 STRIP_SHAPES = [(4, 8), (5, 3), (7, 40), (64, 17), (130, 19), (200, 33), (257, 70)]
@@ -139,7 +142,8 @@ def test_strip_kernel_equals_tile_kernel(LBE, storage, nx, ny, seg):
     a = LBE(w, storage=storage)
     a.set_tile(0)
     a.step(5)
-    for tile in (5, 6, 7):
+    # FP32 (pair layout) runs only the stash kernel among the strip kernels
+    for tile in (7,) if storage == "f32" else (5, 6, 7):
         # grid 0: as many CTAs as fit; grid 1: one CTA walks every work item
         for grid in (0, 1):
             b = LBE(w, storage=storage)
