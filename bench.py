@@ -161,8 +161,8 @@ def kernel_source_sha() -> str:
     from paper_1412_6238_gb300 import build as _b
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1412_6238_gb300", "csrc")
-    for f in ("lbe_common.cuh", "lbe_cell.cuh", "lbe_tile.cuh", "lbe_strip.cuh",
-              "lbe_stash.cuh", "lbe_step_inst.cuh", "lbe_step_f32.cu"):
+    for f in ("lbe_common.cuh", "lbe_cell.cuh", "lbe_tile.cuh", "lbe_stash.cuh",
+              "lbe_step_inst.cuh", "lbe_step_f32.cu"):
         h.update(open(os.path.join(d, f), "rb").read())
     h.update(repr(_b.UNITS["lbe_step_f32.cu"]).encode())
     return h.hexdigest()[:16]

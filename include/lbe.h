@@ -66,12 +66,14 @@ typedef enum {
 /* Population storage.  Arithmetic is FP64 for LBE_F64 and FP32 otherwise.
  * The deviation forms store f_i, g_i (i > 0) and hbar_i - w_i rho c_v T_r(y)
  * (T_r the linear conduction profile between the wall means) scaled by a
- * power of two in 16 bits; g_0 (which carries c) stays FP32. */
+ * power of two in 16 bits; g_0 (which carries c) stays FP32.  The FP32 and
+ * 16-bit forms also keep the low part of g_0 (FP16), so that c = sum g_i is
+ * carried to about 1e-11. */
 typedef enum {
-  LBE_F64 = 0,     /* 216 B per cell per buffer (parity mode)      */
-  LBE_F32 = 1,     /* 108 B per cell per buffer                    */
-  LBE_F16DEV = 2,  /* 56 B per cell per buffer (26 fp16 + 1 fp32)  */
-  LBE_BF16DEV = 3  /* 56 B per cell per buffer (26 bf16 + 1 fp32)  */
+  LBE_F64 = 0,     /* 216 B per cell per buffer (parity mode)              */
+  LBE_F32 = 1,     /* 110 B per cell per buffer (27 fp32 + fp16 low part)  */
+  LBE_F16DEV = 2,  /* 58 B per cell per buffer (26 fp16 + 1 fp32 + 1 fp16) */
+  LBE_BF16DEV = 3  /* 58 B per cell per buffer (26 bf16 + 1 fp32 + 1 fp16) */
 } lbe_storage;
 
 /* Parameters of one instance, lattice units.  Validity (LBE_EINVAL
@@ -167,12 +169,13 @@ lbe_status lbe_load(lbe_handle* h, const char* path);
 
 /* Step-kernel choice (autotuner hook).  Kernel ids 0 .. lbe_num_tiles()-1:
  * ids whose shape has ty > 0 are the tile kernel with TX x TY cells per CTA
- * (any storage; FP64 provides id 0 only); ids with ty == 0 are the strip
- * kernel with TX output columns per CTA marching over rows with TMA-staged rows
- * (16/32-bit storages, every instance at least 4 columns wide; the default
- * there).  grid_ctas: persistent grid size (0 = resident CTAs x SMs, -1 = one
- * CTA per work item).  seg_rows: rows per strip work item (0 = about two
- * items per resident CTA).  LBE_EINVAL for a kernel the handle cannot use.
+ * (any storage; FP64 provides id 0 only); id 7 (ty == 0) is the strip kernel
+ * with 124 output columns per CTA marching over rows, each warp staging its
+ * own pulled populations (16/32-bit storages, every instance at least 4
+ * columns wide; the default there); ids 5 and 6 are retired and rejected.
+ * grid_ctas: persistent grid size (0 = resident CTAs x SMs, -1 = one CTA per
+ * work item).  seg_rows: rows per strip work item (0 = chosen from the wave
+ * count, at most 96).  LBE_EINVAL for a kernel the handle cannot use.
  * lbe_get_tile() reports {kernel id, grid CTAs, seg rows, work items}. */
 int32_t lbe_num_tiles(void);
 lbe_status lbe_tile_shape(int32_t tile_id, int32_t* tx, int32_t* ty);

@@ -11,12 +11,8 @@
 #include <thread>
 #include <vector>
 
-#include <cuda.h>
-#include <cudaTypedefs.h>
-
 #include "../../include/lbe.h"
 #include "lbe_launch.h"
-#include "lbe_strip.cuh"
 
 using namespace lbe;
 
@@ -28,7 +24,7 @@ struct InstHost {
   lbe_params p{};
   int nx = 0, ny = 0, pitch = 0;
   uint64_t plane_bytes = 0, g0_off = 0, g0lo_off = 0, buf_bytes = 0;
-  uint64_t pair_bytes = 0, h_off = 0;  // FP32 pair layout
+  uint64_t pair_bytes = 0, h_off = 0, f0_off = 0;  // pair layouts
   char* arena = nullptr;  // two buffers of buf_bytes
   double* walls = nullptr;  // device: Tbot[nx], Ttop[nx], then 4 float tables
   std::vector<double> Tbot, Ttop;
@@ -53,7 +49,6 @@ struct lbe_handle {
   int grid = 0;
   int seg_req = 0;               // strip kernel: rows per work item (0 = auto)
   int seg = 0;
-  TmapSet* d_maps = nullptr;     // [n] tensor maps for the strip kernel
   int* d_err = nullptr;          // device error word (strip kernel wait time-outs)
   int64_t total_tiles = 0;
   int max_ny = 0;                // largest ny of the instances
@@ -173,6 +168,7 @@ void fill_desc(lbe_handle* h, int j, InstDev& D) {
   D.g0lo_off = H.g0lo_off;
   D.pair_bytes = H.pair_bytes;
   D.h_off = H.h_off;
+  D.f0_off = H.f0_off;
   D.buf[0] = H.arena;
   D.buf[1] = H.arena + H.buf_bytes;
   D.Tbot = H.walls;
@@ -251,7 +247,6 @@ void free_handle(lbe_handle* h) {
     if (H.walls) cudaFree(H.walls);
   }
   if (h->d_inst) cudaFree(h->d_inst);
-  if (h->d_maps) cudaFree(h->d_maps);
   if (h->d_err) cudaFree(h->d_err);
   if (h->d_finst) cudaFree(h->d_finst);
   if (h->scratch) cudaFree(h->scratch);
@@ -262,65 +257,11 @@ void free_handle(lbe_handle* h) {
   delete h;
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
-  return fn;
-}
-
-// Tensor maps of instance j for the strip kernel with nc threads: box of
-// strip_bw(nc) elements in x, one row, all population planes.
-lbe_status encode_maps(lbe_handle* h, int j, int nc, TmapSet& T) {
-  memset(&T, 0, sizeof T);
-  // FP32 (pair layout) runs only the stash kernel, which uses no tensor map
-  if (h->storage == LBE_F32) return LBE_OK;
-  auto enc = encode_fn();
-  if (!enc) return fail(h, LBE_ECUDA, "cuTensorMapEncodeTiled is not available");
-  const InstHost& H = h->inst[j];
-  const cuuint32_t bw = (cuuint32_t)strip_bw(nc, h->storage >= LBE_F16DEV ? 2 : 4);
-  memset(&T, 0, sizeof T);
-  for (int b = 0; b < 2; b++) {
-    char* base = H.arena + (size_t)b * H.buf_bytes;
-    const bool dev = h->storage >= LBE_F16DEV;
-    const CUtensorMapDataType dt =
-        h->storage == LBE_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-        : (h->storage == LBE_F16DEV ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
-                                    : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
-    const cuuint64_t esz = dev ? 2 : 4;
-    const cuuint64_t dims[3] = {(cuuint64_t)H.pitch, (cuuint64_t)H.ny, dev ? 26u : 27u};
-    const cuuint64_t strides[2] = {(cuuint64_t)H.pitch * esz, (cuuint64_t)H.plane_bytes};
-    const cuuint32_t box[3] = {bw, 1, dev ? 26u : 27u};
-    const cuuint32_t es[3] = {1, 1, 1};
-    CUresult r = enc(&T.m[b][0], dt, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return fail(h, LBE_ECUDA, "tensor map (planes) encode failed: %d", (int)r);
-    if (dev) {
-      const cuuint64_t d2[2] = {(cuuint64_t)H.pitch, (cuuint64_t)H.ny};
-      const cuuint64_t s2[1] = {(cuuint64_t)H.pitch * 4};
-      const cuuint32_t b2[2] = {bw, 1};
-      r = enc(&T.m[b][1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base + H.g0_off, d2, s2, b2, es,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-      if (r != CUDA_SUCCESS) return fail(h, LBE_ECUDA, "tensor map (g0) encode failed: %d", (int)r);
-    }
-  }
-  return LBE_OK;
-}
-
 // (Re)build the step descriptors for the current tile shape and upload them.
 lbe_status setup_tiles(lbe_handle* h) {
   if (is_strip(h->tile)) {
     const int nc = TILE_SHAPES[h->tile].tx;  // output columns per strip
-    const int threads = nc + 4;
-    const int occ = strip_occupancy(h->storage, h->tile - STRIP_FIRST);
+    const int occ = stash_occupancy(h->storage);
     if (occ <= 0) return fail(h, LBE_ECUDA, "strip kernel %d cannot be resident", h->tile);
     h->grid = h->grid_req > 0 ? h->grid_req : occ * h->num_sms;
     int max_ny = 1;
@@ -354,7 +295,6 @@ lbe_status setup_tiles(lbe_handle* h) {
       }
       h->seg = best_seg;
     }
-    std::vector<TmapSet> maps(h->n);
     int64_t begin = 0;
     for (int j = 0; j < h->n; j++) {
       InstDev& D = h->idev[j];
@@ -362,14 +302,9 @@ lbe_status setup_tiles(lbe_handle* h) {
       D.tiles_y = (D.ny + h->seg - 1) / h->seg;
       D.tile_begin = begin;
       begin += (int64_t)D.tiles_x * D.tiles_y;
-      lbe_status st = encode_maps(h, j, threads, maps[j]);
-      if (st) return st;
     }
     h->total_tiles = begin;
     if (h->grid_req == -1) h->grid = (int)std::min<int64_t>(begin, 2147483647);
-    if (!h->d_maps) CU(h, cudaMalloc(&h->d_maps, sizeof(TmapSet) * h->n));
-    CU(h, cudaMemcpyAsync(h->d_maps, maps.data(), sizeof(TmapSet) * h->n, cudaMemcpyHostToDevice,
-                          h->stream));
     CU(h, cudaMemcpyAsync(h->d_inst, h->idev.data(), sizeof(InstDev) * h->n,
                           cudaMemcpyHostToDevice, h->stream));
     if (h->gexec) {
@@ -409,11 +344,10 @@ lbe_status setup_tiles(lbe_handle* h) {
 
 cudaError_t launch_one_step(lbe_handle* h, int parity) {
   if (is_strip(h->tile)) {
-    cudaError_t e = launch_strip(h->storage, h->tile - STRIP_FIRST, h->d_inst, h->d_maps, h->n,
-                                 h->total_tiles, h->seg, parity, h->grid, h->d_err, h->stream);
+    cudaError_t e = launch_stash(h->storage, h->d_inst, h->n, h->total_tiles, h->seg, parity,
+                                 h->grid, h->d_err, h->stream);
     // the stash kernel leaves the periodic ghost columns to ghost_kernel
-    if (e == cudaSuccess && h->tile == STASH_ID)
-      e = launch_ghosts(h->d_inst, h->n, h->max_ny, parity ^ 1, h->stream);
+    if (e == cudaSuccess) e = launch_ghosts(h->d_inst, h->n, h->max_ny, parity ^ 1, h->stream);
     return e;
   }
   return launch_step(h->storage, h->tile, h->d_inst, h->n, h->total_tiles, parity, h->grid,
@@ -559,7 +493,11 @@ lbe_status create(int32_t n, const lbe_params* params, const lbe_init_fields* in
     // population planes
     const uint64_t lo_bytes = ((uint64_t)H.ny * H.pitch * 2 + 255) / 256 * 256;
     if (st >= LBE_F16DEV) {
-      H.g0_off = 26 * H.plane_bytes;
+      // 8 (f_i, g_i) pair planes (i >= 1), f_0, 9 hbar, FP32 g_0, low part
+      H.pair_bytes = ((uint64_t)H.ny * H.pitch * 4 + 255) / 256 * 256;
+      H.f0_off = 8 * H.pair_bytes;
+      H.h_off = H.f0_off + H.plane_bytes;
+      H.g0_off = H.h_off + 9 * H.plane_bytes;
       H.g0lo_off = H.g0_off + (((uint64_t)H.ny * H.pitch * 4 + 255) / 256 * 256);
       H.buf_bytes = H.g0lo_off + lo_bytes;
     } else if (st == LBE_F32) {

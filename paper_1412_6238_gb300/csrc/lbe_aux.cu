@@ -11,27 +11,26 @@ namespace lbe {
 bool tile_available(int storage, int tile) {
   if (tile < 0 || tile >= NUM_TILES) return false;
   if (storage == ST_F64) return tile == 0;
-  // the TMA-ring strips stage 27 equal planes: not the FP32 pair layout
-  if (storage == ST_F32 && is_strip(tile) && tile != STASH_ID) return false;
+  // ids 5 and 6 are retired (TMA-ring strips); the stash kernel is 16/32-bit
+  if (is_strip(tile) && tile != STASH_ID) return false;
   return true;
 }
 
-cudaError_t launch_strip(int storage, int variant, const InstDev* d, const TmapSet* maps, int n,
-                         int64_t items, int seg, int parity, int grid, int* err, cudaStream_t s) {
+cudaError_t launch_stash(int storage, const InstDev* d, int n, int64_t items, int seg, int parity,
+                         int grid, int* err, cudaStream_t s) {
   switch (storage) {
-    case ST_F32: return launch_strip_f32(variant, d, maps, n, items, seg, parity, grid, err, s);
-    case ST_F16DEV: return launch_strip_f16(variant, d, maps, n, items, seg, parity, grid, err, s);
-    case ST_BF16DEV:
-      return launch_strip_bf16(variant, d, maps, n, items, seg, parity, grid, err, s);
+    case ST_F32: return launch_stash_f32(d, n, items, seg, parity, grid, err, s);
+    case ST_F16DEV: return launch_stash_f16(d, n, items, seg, parity, grid, err, s);
+    case ST_BF16DEV: return launch_stash_bf16(d, n, items, seg, parity, grid, err, s);
   }
   return cudaErrorInvalidValue;
 }
 
-int strip_occupancy(int storage, int variant) {
+int stash_occupancy(int storage) {
   switch (storage) {
-    case ST_F32: return strip_occupancy_f32(variant);
-    case ST_F16DEV: return strip_occupancy_f16(variant);
-    case ST_BF16DEV: return strip_occupancy_bf16(variant);
+    case ST_F32: return stash_occupancy_f32();
+    case ST_F16DEV: return stash_occupancy_f16();
+    case ST_BF16DEV: return stash_occupancy_bf16();
   }
   return 0;
 }
@@ -246,8 +245,8 @@ int sums_blocks() { return SUM_BLOCKS; }
 // Periodic ghost columns of the buffer `parity` of every instance (16/32-bit
 // storages): in a row, elements 0..XG-1 repeat cells nx-XG..nx-1 and elements
 // nx+XG..nx+2XG-1 repeat cells 0..XG-1 (element XG + x holds cell x).  Planes:
-// FP32: 9 (f, g) pairs + 9 hbar + the FP16 g_0 low part; 16-bit: 26 16-bit +
-// the FP32 g_0 + the low part.
+// FP32: 9 (f, g) pairs + 9 hbar + the FP16 g_0 low part; 16-bit: 8 (f, g)
+// pairs + f_0 + 9 hbar + the FP32 g_0 + the low part.
 // blockIdx.y: instance.
 __global__ void ghost_kernel(const InstDev* __restrict__ insts, int parity) {
   const InstDev& I = insts[blockIdx.y];
@@ -255,7 +254,7 @@ __global__ void ghost_kernel(const InstDev* __restrict__ insts, int parity) {
   const int nx = I.nx, ny = I.ny;
   const size_t pitch = (size_t)I.pitch;
   const bool w16 = I.storage >= ST_F16DEV;
-  const int64_t total = (int64_t)28 * ny * (2 * XG);
+  const int64_t total = (int64_t)20 * ny * (2 * XG);
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int j = (int)(t % (2 * XG));
@@ -276,21 +275,28 @@ __global__ void ghost_kernel(const InstDev* __restrict__ insts, int parity) {
         uint16_t* q = reinterpret_cast<uint16_t*>(b + I.g0lo_off) + row;
         q[dstE] = q[srcE];
       }
-    } else if (p == 27) {
-      uint16_t* q = reinterpret_cast<uint16_t*>(b + I.g0lo_off) + row;
+    } else if (p < 8) {
+      // 16-bit: 8 (f, g) pair planes (4-byte pairs), f_0, 9 hbar, g_0, low part
+      uint32_t* q = reinterpret_cast<uint32_t*>(b + (size_t)p * I.pair_bytes) + row;
       q[dstE] = q[srcE];
-    } else if (p == 26) {
+    } else if (p == 8) {
+      uint16_t* q = reinterpret_cast<uint16_t*>(b + I.f0_off) + row;
+      q[dstE] = q[srcE];
+    } else if (p < 18) {
+      uint16_t* q = reinterpret_cast<uint16_t*>(b + I.h_off + (size_t)(p - 9) * I.plane_bytes) + row;
+      q[dstE] = q[srcE];
+    } else if (p == 18) {
       float* q = reinterpret_cast<float*>(b + I.g0_off) + row;
       q[dstE] = q[srcE];
-    } else {
-      uint16_t* q = reinterpret_cast<uint16_t*>(b + (size_t)p * I.plane_bytes) + row;
+    } else if (p == 19) {
+      uint16_t* q = reinterpret_cast<uint16_t*>(b + I.g0lo_off) + row;
       q[dstE] = q[srcE];
     }
   }
 }
 
 cudaError_t launch_ghosts(const InstDev* d, int n_inst, int max_ny, int parity, cudaStream_t s) {
-  const int64_t total = (int64_t)28 * max_ny * (2 * XG);
+  const int64_t total = (int64_t)20 * max_ny * (2 * XG);
   const int bx = (int)std::min<int64_t>((total + 255) / 256, 4096);
   ghost_kernel<<<dim3(bx, n_inst), 256, 0, s>>>(d, parity);
   return cudaGetLastError();

@@ -13,9 +13,10 @@
 //   F32 : 9 pair planes holding (f_i, g_i) of a cell side by side (8 bytes
 //         per cell), then 9 planes of hbar_i (so that a cell's f_i and g_i,
 //         pulled from the same neighbour, load and store as one 8-byte word)
-//   F16DEV / BF16DEV : 26 planes of 16-bit deviations in the order
-//               f_0..f_8, g_1..g_8, hbar_0..hbar_8, then one FP32 plane
-//               holding g_0 at byte offset g0_off.
+//   F16DEV / BF16DEV : 16-bit values (deviations, scaled): 8 pair planes
+//               holding (f_i, g_i), i = 1..8, of a cell side by side
+//               (4 bytes per cell), the f_0 plane (f0_off), 9 hbar planes
+//               (h_off), then one FP32 plane holding g_0 (g0_off).
 //   F32 and the 16-bit forms also keep the low part of g_0 (g_0 = hi + lo,
 //   |lo| at most half an FP32 ulp of hi) as FP16 of lo * 2^24 in a plane at
 //   byte offset g0lo_off, so that c = sum g_i (of which g_0 carries nearly
@@ -80,8 +81,9 @@ struct InstDev {
   uint64_t plane_bytes; // bytes between consecutive planes
   uint64_t g0_off;      // byte offset of the FP32 g_0 plane (16-bit forms)
   uint64_t g0lo_off;    // byte offset of the FP16 plane of the g_0 low part (16/32-bit)
-  uint64_t pair_bytes;  // FP32: bytes of one (f_i, g_i) pair plane
-  uint64_t h_off;       // FP32: byte offset of the first hbar plane
+  uint64_t pair_bytes;  // 16/32-bit: bytes of one (f_i, g_i) pair plane
+  uint64_t h_off;       // 16/32-bit: byte offset of the first hbar plane
+  uint64_t f0_off;      // 16-bit: byte offset of the f_0 plane
   char* buf[2];         // population arenas (ping-pong)
   const double* Tbot;   // [nx] wall temperature at y = -1/2
   const double* Ttop;   // [nx] wall temperature at y = ny - 1/2
@@ -144,12 +146,8 @@ struct StF32 {
   }
 };
 
-__host__ __device__ constexpr int dev_plane(int k, int i) {
-  return k == 0 ? i : (k == 1 ? 8 + i : 17 + i);
-}
-
 // 16-bit forms: q = s_k v in fp16 / bf16 (v the value or, for hbar, the
-// deviation); g_0 in FP32.
+// deviation); g_0 in FP32 (plus its low part, below).
 template <class E, int KIND>
 struct StDev {
   using C = float;
@@ -158,12 +156,24 @@ struct StDev {
   __device__ static __forceinline__ float cvt(__nv_bfloat16 q) { return __bfloat162float(q); }
   __device__ static __forceinline__ void put(__half* p, float v) { *p = __float2half_rn(v); }
   __device__ static __forceinline__ void put(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+  __device__ static __forceinline__ void put2(__half* p, float a, float b) {
+    *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a, b);
+  }
+  __device__ static __forceinline__ void put2(__nv_bfloat16* p, float a, float b) {
+    *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);
+  }
+  // element (k, i) of cell idx: its address in the pair / f_0 / hbar planes
+  __device__ static __forceinline__ const E* at(const InstDev& I, const char* b, int k, int i,
+                                                size_t idx) {
+    if (k == 2) return reinterpret_cast<const E*>(b + I.h_off + (size_t)i * I.plane_bytes) + idx;
+    if (i == 0) return reinterpret_cast<const E*>(b + I.f0_off) + idx;  // f_0
+    return reinterpret_cast<const E*>(b + (size_t)(i - 1) * I.pair_bytes) + 2 * idx + k;
+  }
   __device__ static __forceinline__ C ld(const InstDev& I, const Phys<C>& P, const char* b, int k,
                                          int i, size_t idx) {
     if (k == 1 && i == 0)
       return __ldg(reinterpret_cast<const float*>(b + I.g0_off) + idx);
-    const E* p = reinterpret_cast<const E*>(b + (size_t)dev_plane(k, i) * I.plane_bytes) + idx;
-    return cvt(*p) * P.inv_s[k];
+    return cvt(*at(I, b, k, i, idx)) * P.inv_s[k];
   }
   __device__ static __forceinline__ void st(const InstDev& I, char* b, int k, int i, size_t idx,
                                             C v) {
@@ -171,7 +181,13 @@ struct StDev {
       reinterpret_cast<float*>(b + I.g0_off)[idx] = v;
       return;
     }
-    put(reinterpret_cast<E*>(b + (size_t)dev_plane(k, i) * I.plane_bytes) + idx, v * I.s[k]);
+    put(const_cast<E*>(at(I, b, k, i, idx)), v * I.s[k]);
+  }
+  // f_i and g_i (i >= 1) of one cell as one 4-byte store
+  __device__ static __forceinline__ void st_fg(const InstDev& I, char* b, int i, size_t idx,
+                                               float fv, float gv) {
+    put2(reinterpret_cast<E*>(b + (size_t)(i - 1) * I.pair_bytes) + 2 * idx, fv * I.s[0],
+         gv * I.s[1]);
   }
 };
 

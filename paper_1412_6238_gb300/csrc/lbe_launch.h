@@ -11,10 +11,11 @@ namespace lbe {
 struct TileShape {
   int tx, ty;
 };
-// Kernel ids: 0..4 tile kernel with these tile shapes; 5, 6 strip kernel
-// with TMA-staged source rows and 124 / 60 output columns per strip (128 / 64
-// threads; ty = 0: a strip marches over its rows); 7 strip kernel with a
-// per-warp stash of pulled populations, 124 output columns (16/32-bit).
+// Kernel ids: 0..4 tile kernel with these tile shapes; 5, 6 retired (strip
+// kernels with a TMA ring of whole source rows, superseded by the stash
+// kernel; not built); 7 strip kernel with a per-warp stash of pulled
+// populations, 124 output columns (16/32-bit storages; ty = 0: a strip
+// marches over its rows).
 constexpr int NUM_TILE_SHAPES = 5;
 constexpr int NUM_TILES = 8;
 constexpr int STRIP_FIRST = 5;
@@ -26,27 +27,24 @@ constexpr TileShape TILE_SHAPES[NUM_TILES] = {{32, 8},  {64, 4},  {32, 16}, {64,
                                               {128, 4}, {124, 0}, {60, 0},  {124, 0}};
 inline bool is_strip(int tile) { return tile >= STRIP_FIRST && tile < NUM_TILES; }
 
-struct TmapSet;  // lbe_strip.cuh
-
 // Does the step kernel of this storage exist for this kernel id?
 bool tile_available(int storage, int tile);
 
-// Strip kernel (16/32-bit storages): variant 0 = 128 columns, 1 = 64.
-cudaError_t launch_strip(int storage, int variant, const InstDev* d, const TmapSet* maps, int n,
-                         int64_t items, int seg, int parity, int grid, int* err, cudaStream_t s);
-int strip_occupancy(int storage, int variant);
-cudaError_t launch_strip_f32(int variant, const InstDev* d, const TmapSet* maps, int n,
-                             int64_t items, int seg, int parity, int grid, int* err,
-                             cudaStream_t s);
-cudaError_t launch_strip_f16(int variant, const InstDev* d, const TmapSet* maps, int n,
-                             int64_t items, int seg, int parity, int grid, int* err,
-                             cudaStream_t s);
-cudaError_t launch_strip_bf16(int variant, const InstDev* d, const TmapSet* maps, int n,
-                              int64_t items, int seg, int parity, int grid, int* err,
-                              cudaStream_t s);
-int strip_occupancy_f32(int variant);
-int strip_occupancy_f16(int variant);
-int strip_occupancy_bf16(int variant);
+// Stash strip kernel (16/32-bit storages): one step of every instance over
+// `items` work items (strips x segments of seg rows); reads buf[parity],
+// writes buf[parity ^ 1]; *err is set if a copy wait times out.
+cudaError_t launch_stash(int storage, const InstDev* d, int n, int64_t items, int seg, int parity,
+                         int grid, int* err, cudaStream_t s);
+int stash_occupancy(int storage);
+cudaError_t launch_stash_f32(const InstDev* d, int n, int64_t items, int seg, int parity, int grid,
+                             int* err, cudaStream_t s);
+cudaError_t launch_stash_f16(const InstDev* d, int n, int64_t items, int seg, int parity, int grid,
+                             int* err, cudaStream_t s);
+cudaError_t launch_stash_bf16(const InstDev* d, int n, int64_t items, int seg, int parity,
+                              int grid, int* err, cudaStream_t s);
+int stash_occupancy_f32();
+int stash_occupancy_f16();
+int stash_occupancy_bf16();
 
 // One step of every instance in d_inst[0..n_inst): persistent grid of `grid`
 // CTAs over total_tiles tiles; reads buf[parity], writes buf[parity ^ 1].

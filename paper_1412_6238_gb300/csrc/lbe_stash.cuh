@@ -1,11 +1,12 @@
 // The fused step as a column-strip marching kernel with per-warp stashes of
 // pulled populations (FP32 and 16-bit storages).
 //
-// Work items and thread mapping are those of the strip kernel (lbe_strip.cuh):
-// a CTA of NC threads marches up the rows [ya, yb) of a strip of NC - 4 output
-// columns, thread t owning column x0 - 2 + t so that the two halo columns on
-// each side are ordinary threads.  Instead of staging every source row whole
-// for the CTA, each warp stages only what its own 32 cells pull for a row m:
+// A work item is a strip of NC - 4 output columns and a segment of rows
+// [ya, yb) of one instance: a CTA of NC threads marches up the rows, thread t
+// owning column x0 - 2 + t so that the two halo columns on each side are
+// ordinary threads.  Instead of staging every source row whole for the CTA
+// (as a TMA tiled row ring would), each warp stages only what its own 32
+// cells pull for a row m:
 // for each of the 27 populations (k, i), the elements of source row m - xi_iy
 // that cover its columns shifted by -xi_ix (or, at a wall, the reversed
 // population of row m itself), one bulk copy (cp.async.bulk) per population,
@@ -13,9 +14,9 @@
 // planes: 40 elements = 80 bytes; the FP32 g_0 plane of the 16-bit forms:
 // 144 bytes), completing on an mbarrier of the warp.  A row's values stay in the warp's stash from the
 // time its moments are formed until it collides three iterations later: 4
-// rows x 27 populations per warp, about half the shared memory of the 7-row
-// source ring (FP32), so three CTAs fit on an SM instead of two, and no
-// thread waits for another warp's copies.
+// rows x 27 populations per warp, about half the shared memory of a 7-row
+// ring of whole source rows (FP32), so three CTAs fit on an SM instead of
+// two, and no thread waits for another warp's copies.
 //
 // Iteration i (from ya - 4 to yb):
 //   1. collide row i-1 (S2-S9 of lbe_cell.cuh) from its stash slot and the
@@ -31,9 +32,34 @@
 // copies in flight and returns.
 #pragma once
 
-#include "lbe_strip.cuh"
+#include "lbe_tile.cuh"
 
 namespace lbe {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+// Bounded wait for the phase with the given parity; false on time-out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 22); ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
 
 // One-dimensional bulk copy global -> shared (16-byte aligned addresses, a
 // multiple of 16 bytes), completing on an mbarrier.
@@ -68,16 +94,21 @@ struct StashFmt<StF32> {
     return k < 2 ? i * PROW : HOFF + i * ROW;
   }
 };
+// 16-bit: 8 rows of (f_i, g_i) pairs, i = 1..8 (40 cells x 4 bytes), the
+// f_0 row, 9 hbar rows (40 x 2 bytes), the FP32 g_0 row (36 x 4 bytes).
 template <class E16>
 struct StashFmt16 {
   using E = E16;
   static constexpr int EW = 40;
+  static constexpr int PROW = EW * 4;
   static constexpr int ROW = EW * 2;
-  static constexpr int G0ROW = 36 * 4;
-  static constexpr int LO = 26 * ROW + G0ROW;
+  static constexpr int F0 = 8 * PROW;
+  static constexpr int HOFF = F0 + ROW;
+  static constexpr int G0 = HOFF + 9 * ROW;
+  static constexpr int LO = G0 + 36 * 4;
   static constexpr int SLOT_RAW = LO + 80;
   __host__ __device__ static constexpr int off(int k, int i) {
-    return (k == 1 && i == 0) ? 26 * ROW : dev_plane(k, i) * ROW;
+    return k == 2 ? HOFF + i * ROW : (i == 0 ? (k == 0 ? F0 : G0) : (i - 1) * PROW);
   }
 };
 template <>
@@ -118,8 +149,8 @@ __device__ __forceinline__ float stash_val(const char* slot, int k, int i, int c
     return reinterpret_cast<const float*>(slot + Fmt::off(k, i))[col];
   } else {
     if (k == 1 && i == 0) return reinterpret_cast<const float*>(slot + Fmt::off(1, 0))[col];
-    return S::cvt(reinterpret_cast<const typename Fmt::E*>(slot + Fmt::off(k, i))[col]) *
-           P.inv_s[k];
+    const typename Fmt::E* r = reinterpret_cast<const typename Fmt::E*>(slot + Fmt::off(k, i));
+    return S::cvt(k < 2 && i > 0 ? r[2 * col + k] : r[col]) * P.inv_s[k];
   }
 }
 
@@ -187,10 +218,31 @@ __device__ __forceinline__ void wstash_pull_fg(const InstDev& I, const char* slo
   }
 }
 
+// 16-bit pair layout: f_i and g_i (i >= 1) of a pulled cell with one 4-byte
+// load; f_0 from its row, g_0 from the FP32 row.
+template <class S>
+__device__ __forceinline__ void wstash_pull_fg16(const InstDev& I, const Phys<float>& P,
+                                                 const char* slot, int c0, int c0g, int y,
+                                                 float f[9], float g[9]) {
+  using Fmt = StashFmt<S>;
+  using E = typename Fmt::E;
+  const bool wb = (y == 0), wt = (y == I.ny - 1);
+  f[0] = S::cvt(reinterpret_cast<const E*>(slot + Fmt::F0)[c0]) * P.inv_s[0];
+  g[0] = reinterpret_cast<const float*>(slot + Fmt::G0)[c0g];
+#pragma unroll
+  for (int i = 1; i < 9; i++) {
+    const bool wall = (EY(i) == 1 && wb) || (EY(i) == -1 && wt);
+    const E* r = reinterpret_cast<const E*>(slot + (i - 1) * Fmt::PROW);
+    const int col = wall ? c0 : c0 - EX(i);
+    f[i] = S::cvt(r[2 * col]) * P.inv_s[0];
+    g[i] = S::cvt(r[2 * col + 1]) * P.inv_s[1];
+  }
+}
+
 template <class S, int NC>
 __global__ void __launch_bounds__(NC, (StashCfg<S, NC>::MINB))
-stash_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps, int n_inst,
-             int64_t total_items, int seg_rows, int parity, int* __restrict__ err) {
+stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items, int seg_rows,
+             int parity, int* __restrict__ err) {
   using Cfg = StashCfg<S, NC>;
   using Fmt = typename Cfg::Fmt;
   using C = float;
@@ -257,60 +309,72 @@ stash_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
     auto pr = [](int m) { return (((m % Cfg::PR) + Cfg::PR) % Cfg::PR) * NC; };
     auto nr = [](int m) { return (m & (Cfg::NR - 1)) * NC; };
     auto loadable = [&](int m) { return m <= yb + 1 && m < ny; };
-    // lane p < 27 copies population p = (k, i) into its row of the slot:
-    // byte offsets from the start of the source row m, for the pull from row
-    // m - xi_iy and for the reversed population of the cell itself at a wall
-    // (lane 27: the row of the g_0 low part)
-    const bool plo = lane == 27;
-    const int pk = lane < 27 ? lane / 9 : 0, pi_ = lane < 27 ? lane - 9 * pk : 0;
-    const int pey = plo ? 0 : EY(pi_);
-    const bool pg0 = W16 && pk == 1 && pi_ == 0 && !plo;  // the FP32 g_0 plane
-    const bool p16 = plo || (W16 && !pg0);                 // a 16-bit row
-    const int pesz = p16 ? 2 : 4;
-    const ptrdiff_t prow = (ptrdiff_t)pitch * pesz;  // bytes per source row
-    const int pbytes = p16 ? 80 : 144;
-    const ptrdiff_t pstart = (ptrdiff_t)(p16 ? e16 : e32) * pesz;
-    auto plane_off = [&](int k, int i) -> ptrdiff_t {
-      if (!W16) return (ptrdiff_t)(k * 9 + i) * (ptrdiff_t)I.plane_bytes;
-      if (k == 1 && i == 0) return (ptrdiff_t)I.g0_off;
-      return (ptrdiff_t)dev_plane(k, i) * (ptrdiff_t)I.plane_bytes;
-    };
-    ptrdiff_t off_n =
-        (plo ? (ptrdiff_t)I.g0lo_off : plane_off(pk, pi_)) - (ptrdiff_t)pey * prow + pstart;
-    ptrdiff_t off_w = plo ? off_n : plane_off(pk, OPP(pi_)) + pstart;
-    int pdst = plo ? Fmt::LO : Fmt::off(pk, pi_);
-    int pbytes_ = pbytes;
-    ptrdiff_t prow_ = prow;
-    if constexpr (!W16) {
-      // FP32 pair layout: lanes 0-8 copy (f_i, g_i) pair rows, 9-17 hbar
-      // rows, 18 the low part (19 copies)
-      const int q = lane;
-      const int qi = q < 9 ? q : (q < 18 ? q - 9 : 0);
-      const int qey = q < 18 ? EY(qi) : 0;
-      if (q < 9) {
-        prow_ = (ptrdiff_t)pitch * 8;
-        pbytes_ = Fmt::PROW;
-        off_n = (ptrdiff_t)qi * (ptrdiff_t)I.pair_bytes - (ptrdiff_t)qey * prow_ + (ptrdiff_t)e32 * 8;
-        off_w = (ptrdiff_t)OPP(qi) * (ptrdiff_t)I.pair_bytes + (ptrdiff_t)e32 * 8;
-        pdst = Fmt::off(0, qi);
-      } else if (q < 18) {
-        prow_ = (ptrdiff_t)pitch * 4;
-        pbytes_ = Fmt::ROW;
-        off_n = (ptrdiff_t)I.h_off + (ptrdiff_t)qi * (ptrdiff_t)I.plane_bytes -
-                (ptrdiff_t)qey * prow_ + (ptrdiff_t)e32 * 4;
-        off_w = (ptrdiff_t)I.h_off + (ptrdiff_t)OPP(qi) * (ptrdiff_t)I.plane_bytes +
-                (ptrdiff_t)e32 * 4;
-        pdst = Fmt::off(2, qi);
+    // Copy plan: one bulk copy per lane, into its row of the slot; byte
+    // offsets from the start of the source row m for the pull from row
+    // m - xi_iy (off_n) and for the reversed population of the cell itself
+    // at a wall (off_w).
+    //   FP32 (19 copies): lanes 0-8 the (f_i, g_i) pair rows, 9-17 hbar_i,
+    //     18 the g_0 low part.
+    //   16-bit (20 copies): lanes 0-7 the (f_i, g_i) pair rows, i = lane + 1,
+    //     8 f_0, 9-17 hbar_i, 18 the FP32 g_0, 19 the g_0 low part.
+    const int pcopies = W16 ? 20 : 19;
+    int pi_ = 0, pey_ = 0, pbytes_ = 80, pdst = Fmt::LO;
+    ptrdiff_t prow_ = (ptrdiff_t)pitch * 2, off_n = 0, off_w = 0;
+    {
+      const ptrdiff_t PB = (ptrdiff_t)I.plane_bytes, PP = (ptrdiff_t)I.pair_bytes;
+      if constexpr (!W16) {
+        if (lane < 9) {  // pair rows
+          pi_ = lane;
+          prow_ = (ptrdiff_t)pitch * 8;
+          pbytes_ = Fmt::PROW;
+          off_n = pi_ * PP - EY(pi_) * prow_ + (ptrdiff_t)e32 * 8;
+          off_w = OPP(pi_) * PP + (ptrdiff_t)e32 * 8;
+          pdst = Fmt::off(0, pi_);
+        } else if (lane < 18) {  // hbar rows
+          pi_ = lane - 9;
+          prow_ = (ptrdiff_t)pitch * 4;
+          pbytes_ = Fmt::ROW;
+          off_n = (ptrdiff_t)I.h_off + pi_ * PB - EY(pi_) * prow_ + (ptrdiff_t)e32 * 4;
+          off_w = (ptrdiff_t)I.h_off + OPP(pi_) * PB + (ptrdiff_t)e32 * 4;
+          pdst = Fmt::off(2, pi_);
+        }
       } else {
+        if (lane < 8) {  // pair rows, i = lane + 1
+          pi_ = lane + 1;
+          prow_ = (ptrdiff_t)pitch * 4;
+          pbytes_ = Fmt::PROW;
+          off_n = (pi_ - 1) * PP - EY(pi_) * prow_ + (ptrdiff_t)e16 * 4;
+          off_w = (OPP(pi_) - 1) * PP + (ptrdiff_t)e16 * 4;
+          pdst = Fmt::off(0, pi_);
+        } else if (lane == 8) {  // f_0
+          prow_ = (ptrdiff_t)pitch * 2;
+          pbytes_ = Fmt::ROW;
+          off_n = off_w = (ptrdiff_t)I.f0_off + (ptrdiff_t)e16 * 2;
+          pdst = Fmt::F0;
+        } else if (lane < 18) {  // hbar rows
+          pi_ = lane - 9;
+          prow_ = (ptrdiff_t)pitch * 2;
+          pbytes_ = Fmt::ROW;
+          off_n = (ptrdiff_t)I.h_off + pi_ * PB - EY(pi_) * prow_ + (ptrdiff_t)e16 * 2;
+          off_w = (ptrdiff_t)I.h_off + OPP(pi_) * PB + (ptrdiff_t)e16 * 2;
+          pdst = Fmt::off(2, pi_);
+        } else if (lane == 18) {  // FP32 g_0
+          prow_ = (ptrdiff_t)pitch * 4;
+          pbytes_ = 144;
+          off_n = off_w = (ptrdiff_t)I.g0_off + (ptrdiff_t)e32 * 4;
+          pdst = Fmt::G0;
+        }
+      }
+      const bool lo_lane = lane == pcopies - 1;
+      if (lo_lane) {  // the g_0 low part
         prow_ = (ptrdiff_t)pitch * 2;
         pbytes_ = 80;
-        off_n = (ptrdiff_t)I.g0lo_off + (ptrdiff_t)e16 * 2;
-        off_w = off_n;
+        off_n = off_w = (ptrdiff_t)I.g0lo_off + (ptrdiff_t)e16 * 2;
         pdst = Fmt::LO;
       }
+      const bool moving = lane < 18 && !(W16 && lane == 8) && !lo_lane;
+      pey_ = moving ? EY(pi_) : 0;
     }
-    const int pcopies = W16 ? 28 : 19;
-    const int pey_ = W16 ? pey : (lane < 18 ? EY(lane < 9 ? lane : lane - 9) : 0);
     // the warp's copies of the populations pulled by moment row m (the mirror
     // row's below the bottom wall): lane p < 27 copies population p
     auto issue = [&](int m) {
@@ -358,8 +422,7 @@ stash_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
         if constexpr (!W16) {
           wstash_pull_fg(I, s, c0, r, f, g);
         } else {
-          wstash_pull<S, 0>(I, P, s, c0, c0g, r, x, f);
-          wstash_pull<S, 1>(I, P, s, c0, c0g, r, x, g);
+          wstash_pull_fg16<S>(I, P, s, c0, c0g, r, f, g);
         }
         wstash_pull<S, 2>(I, P, s, c0, c0g, r, x, h);
         const int ps = rr(-2), p0 = rr(-1), pn = rr(0);  // rows r-1, r, r+1
@@ -395,10 +458,12 @@ stash_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
 #pragma unroll
           for (int ii = 0; ii < 9; ii++) S::st(I, dst, 2, ii, e, o[18 + ii]);
         } else {
+          S::st(I, dst, 0, 0, e, o[0]);
+          S::st(I, dst, 1, 0, e, o[9]);
 #pragma unroll
-          for (int k = 0; k < 3; k++)
+          for (int ii = 1; ii < 9; ii++) S::st_fg(I, dst, ii, e, o[ii], o[9 + ii]);
 #pragma unroll
-            for (int ii = 0; ii < 9; ii++) S::st(I, dst, k, ii, e, o[k * 9 + ii]);
+          for (int ii = 0; ii < 9; ii++) S::st(I, dst, 2, ii, e, o[18 + ii]);
         }
         // (the periodic ghost columns are refreshed by ghost_kernel after the
         // step, not here: the branch costs this kernel about 7 %)
@@ -423,8 +488,7 @@ stash_kernel(const InstDev* __restrict__ insts, const TmapSet* __restrict__ maps
           if constexpr (!W16) {
             wstash_pull_fg(I, s, c0, mr, vf, v);
           } else {
-            wstash_pull<S, 1>(I, P, s, c0, c0g, mr, xw, v);
-            wstash_pull<S, 0>(I, P, s, c0, c0g, mr, xw, vf);
+            wstash_pull_fg16<S>(I, P, s, c0, c0g, mr, vf, v);
           }
           const C g0lo =
               __half2float(reinterpret_cast<const __half*>(s + Fmt::LO)[c0lo]) * G0LO_INV;

@@ -3,9 +3,6 @@
 // defined.
 #include "lbe_launch.h"
 #include "lbe_tile.cuh"
-#if LBE_STRIP
-#include "lbe_strip.cuh"
-#endif
 #if LBE_STASH
 #include "lbe_stash.cuh"
 #endif
@@ -69,44 +66,6 @@ cudaError_t LBE_CAT(fields_, LBE_SUFFIX)(const InstDev* d, int64_t tiles, int pa
   return cudaGetLastError();
 }
 
-#if LBE_STRIP
-namespace {
-template <int NC, int R>
-bool strip_attr() {
-  // the dynamic shared-memory opt-in, once per device
-  static bool done[64] = {};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
-  if (!done[dev]) {
-    if (cudaFuncSetAttribute(strip_kernel<LBE_ST, NC, R>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             Strip<LBE_ST, NC, R>::SMEM) != cudaSuccess)
-      return false;
-    done[dev] = true;
-  }
-  return true;
-}
-template <int NC, int R>
-cudaError_t strip_one(const InstDev* d, const TmapSet* maps, int n, int64_t items, int seg,
-                      int parity, int grid, int* err, cudaStream_t s) {
-  if (!strip_attr<NC, R>()) return cudaErrorInvalidValue;
-  if (grid <= 0) grid = 1;
-  if ((int64_t)grid > items) grid = (int)items;
-  strip_kernel<LBE_ST, NC, R>
-      <<<grid, NC, Strip<LBE_ST, NC, R>::SMEM, s>>>(d, maps, n, items, seg, parity, err);
-  return cudaGetLastError();
-}
-template <int NC, int R>
-int strip_occ() {
-  if (!strip_attr<NC, R>()) return 0;
-  int b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, strip_kernel<LBE_ST, NC, R>, NC,
-                                                    Strip<LBE_ST, NC, R>::SMEM) != cudaSuccess)
-    return 0;
-  return b;
-}
-}  // namespace
-
 #if LBE_STASH
 namespace {
 template <int NC>
@@ -123,13 +82,13 @@ bool stash_attr() {
   return true;
 }
 template <int NC>
-cudaError_t stash_one(const InstDev* d, const TmapSet* maps, int n, int64_t items, int seg,
-                      int parity, int grid, int* err, cudaStream_t s) {
+cudaError_t stash_one(const InstDev* d, int n, int64_t items, int seg, int parity, int grid,
+                      int* err, cudaStream_t s) {
   if (!stash_attr<NC>()) return cudaErrorInvalidValue;
   if (grid <= 0) grid = 1;
   if ((int64_t)grid > items) grid = (int)items;
   stash_kernel<LBE_ST, NC>
-      <<<grid, NC, StashCfg<LBE_ST, NC>::SMEM, s>>>(d, maps, n, items, seg, parity, err);
+      <<<grid, NC, StashCfg<LBE_ST, NC>::SMEM, s>>>(d, n, items, seg, parity, err);
   return cudaGetLastError();
 }
 template <int NC>
@@ -142,30 +101,12 @@ int stash_occ() {
   return b;
 }
 }  // namespace
-#endif
 
-cudaError_t LBE_CAT(launch_strip_, LBE_SUFFIX)(int variant, const InstDev* d, const TmapSet* maps,
-                                                int n, int64_t items, int seg, int parity, int grid,
-                                                int* err, cudaStream_t s) {
-  switch (variant) {
-    case 0: return strip_one<128, LBE_R128>(d, maps, n, items, seg, parity, grid, err, s);
-    case 1: return strip_one<64, LBE_R64>(d, maps, n, items, seg, parity, grid, err, s);
-#if LBE_STASH
-    case 2: return stash_one<128>(d, maps, n, items, seg, parity, grid, err, s);
-#endif
-    default: return cudaErrorInvalidValue;
-  }
+cudaError_t LBE_CAT(launch_stash_, LBE_SUFFIX)(const InstDev* d, int n, int64_t items, int seg,
+                                                int parity, int grid, int* err, cudaStream_t s) {
+  return stash_one<128>(d, n, items, seg, parity, grid, err, s);
 }
-int LBE_CAT(strip_occupancy_, LBE_SUFFIX)(int variant) {
-  switch (variant) {
-    case 0: return strip_occ<128, LBE_R128>();
-    case 1: return strip_occ<64, LBE_R64>();
-#if LBE_STASH
-    case 2: return stash_occ<128>();
-#endif
-    default: return 0;
-  }
-}
+int LBE_CAT(stash_occupancy_, LBE_SUFFIX)() { return stash_occ<128>(); }
 #endif
 
 }  // namespace lbe
