@@ -154,6 +154,13 @@ struct StDev {
   static constexpr int kind = KIND;
   __device__ static __forceinline__ float cvt(__half q) { return __half2float(q); }
   __device__ static __forceinline__ float cvt(__nv_bfloat16 q) { return __bfloat162float(q); }
+  // two adjacent 16-bit values (4-byte aligned) to FP32
+  __device__ static __forceinline__ float2 cvt2(const __half* p) {
+    return __half22float2(*reinterpret_cast<const __half2*>(p));
+  }
+  __device__ static __forceinline__ float2 cvt2(const __nv_bfloat16* p) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+  }
   __device__ static __forceinline__ void put(__half* p, float v) { *p = __float2half_rn(v); }
   __device__ static __forceinline__ void put(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
   __device__ static __forceinline__ void put2(__half* p, float a, float b) {

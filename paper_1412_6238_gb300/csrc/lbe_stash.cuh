@@ -209,6 +209,15 @@ __device__ __forceinline__ void wstash_pull_fg(const InstDev& I, const char* slo
   using Fmt = StashFmt<StF32>;
   const bool wb = (y == 0), wt = (y == I.ny - 1);
   const float2* b = reinterpret_cast<const float2*>(slot) + c0;
+  if (!wb && !wt) {  // interior row: constant offsets
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+      const float2 v = b[i * Fmt::EW - EX(i)];
+      f[i] = v.x;
+      g[i] = v.y;
+    }
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < 9; i++) {
     const bool wall = (EY(i) == 1 && wb) || (EY(i) == -1 && wt);
@@ -229,13 +238,15 @@ __device__ __forceinline__ void wstash_pull_fg16(const InstDev& I, const Phys<fl
   const bool wb = (y == 0), wt = (y == I.ny - 1);
   f[0] = S::cvt(reinterpret_cast<const E*>(slot + Fmt::F0)[c0]) * P.inv_s[0];
   g[0] = reinterpret_cast<const float*>(slot + Fmt::G0)[c0g];
+  const bool interior = !wb && !wt;
 #pragma unroll
   for (int i = 1; i < 9; i++) {
-    const bool wall = (EY(i) == 1 && wb) || (EY(i) == -1 && wt);
+    const bool wall = !interior && ((EY(i) == 1 && wb) || (EY(i) == -1 && wt));
     const E* r = reinterpret_cast<const E*>(slot + (i - 1) * Fmt::PROW);
     const int col = wall ? c0 : c0 - EX(i);
-    f[i] = S::cvt(r[2 * col]) * P.inv_s[0];
-    g[i] = S::cvt(r[2 * col + 1]) * P.inv_s[1];
+    const float2 v = S::cvt2(r + 2 * col);
+    f[i] = v.x * P.inv_s[0];
+    g[i] = v.y * P.inv_s[1];
   }
 }
 
