@@ -267,39 +267,58 @@ __device__ __forceinline__ void collide(const Phys<typename S::C>& P, const type
     const C agsg = ag * sg, aTi = aT * inv_rcs2;
     const C ux3 = C(3) * ux, uy3 = C(3) * uy;
     C sge = C(0), she = C(0);  // sums of the moving g and hbar equilibria
-    auto relax = [&](int i, C G, C feq, C geq, C heqd, C Fxi, C Gxi) {
-      out(0, i, f[i] + omega_f * (feq - f[i]) + af * ((Fxi - Fdu) * G));
-      const C gdot = Gxi - Gdu;
-      out(1, i, g[i] + omega_g * (geq - g[i]) + (agsg * gdot) * G);
-      out(2, i, h[i] + omega_T * (heqd - h[i]) + (aTi * gdot) * (rcvT * G));
-    };
-    auto dir = [&](int i, C W, C a, C hq, C Fxi, C Gxi) {
-      const C q = a + hq;
-      const C G = W + W * q;
-      const C feq = W * (pp + rcs2 * q);
-      const C geq = W * (Hi + cc * q);
-      const C heqd = dev_h<S>() ? rcvTd * G + rcvTr * (W * q) : rcvT * G;
-      sge += geq;
-      she += heqd;
-      relax(i, G, feq, geq, heqd, Fxi, Gxi);
-    };
+    static_assert(dev_h<S>(), "the FP32 forms keep hbar as a deviation");
     const C wa = WGT<C>(1), wd = WGT<C>(5);
     const C hu = C(-0.5) * uu;
+    // The opposite directions (i, j) of a pair run as the two lanes of packed
+    // FP32 arithmetic (fma.rn.f32x2: each lane rounds like the scalar
+    // operation): q_i = a + hq, q_j = hq - a with a = xi_i.u/c_s^2.
+    const float2 rcs2v = make_float2(rcs2, rcs2), ppv = make_float2(pp, pp);
+    const float2 ccv = make_float2(cc, cc), Hiv = make_float2(Hi, Hi);
+    const float2 rTd = make_float2(rcvTd, rcvTd), rTr = make_float2(rcvTr, rcvTr);
+    const float2 rT = make_float2(rcvT, rcvT);
+    const float2 omf = make_float2(omega_f, omega_f), afv = make_float2(af, af);
+    const float2 omg = make_float2(omega_g, omega_g), omT = make_float2(omega_T, omega_T);
+    const float2 agsgv = make_float2(agsg, agsg), aTiv = make_float2(aTi, aTi);
+    const float2 m1 = make_float2(-1.f, -1.f);
+    auto dir2 = [&](int i, int j, C W, C a, C hq, C Fxi, C Gxi) {
+      const float2 Wv = make_float2(W, W);
+      const float2 q = make_float2(a + hq, hq - a);
+      const float2 G = __ffma2_rn(Wv, q, Wv);                          // Gamma_i
+      const float2 feq = __fmul2_rn(Wv, __ffma2_rn(rcs2v, q, ppv));     // Eq. 5
+      const float2 geq = __fmul2_rn(Wv, __ffma2_rn(ccv, q, Hiv));       // Eq. 21
+      const float2 heqd = __ffma2_rn(rTd, G, __fmul2_rn(rTr, __fmul2_rn(Wv, q)));
+      sge += geq.x + geq.y;
+      she += heqd.x + heqd.y;
+      const float2 fv = make_float2(f[i], f[j]);
+      const float2 gv = make_float2(g[i], g[j]);
+      const float2 hv = make_float2(h[i], h[j]);
+      const float2 Fd = make_float2(Fxi - Fdu, -Fxi - Fdu);  // F.(xi - u)
+      const float2 gd = make_float2(Gxi - Gdu, -Gxi - Gdu);  // (F - grad p).(xi - u)
+      float2 fo = __ffma2_rn(omf, __ffma2_rn(fv, m1, feq), fv);
+      fo = __ffma2_rn(afv, __fmul2_rn(Fd, G), fo);
+      float2 go = __ffma2_rn(omg, __ffma2_rn(gv, m1, geq), gv);
+      go = __ffma2_rn(__fmul2_rn(agsgv, gd), G, go);
+      float2 ho = __ffma2_rn(omT, __ffma2_rn(hv, m1, heqd), hv);
+      ho = __ffma2_rn(__fmul2_rn(aTiv, gd), __fmul2_rn(rT, G), ho);
+      out(0, i, fo.x);
+      out(0, j, fo.y);
+      out(1, i, go.x);
+      out(1, j, go.y);
+      out(2, i, ho.x);
+      out(2, j, ho.y);
+    };
     C a = ux3, hq = C(0.5) * (a * a - uu);
-    dir(1, wa, a, hq, Fx, Gx);
-    dir(3, wa, -a, hq, -Fx, -Gx);
+    dir2(1, 3, wa, a, hq, Fx, Gx);
     a = uy3;
     hq = C(0.5) * (a * a - uu);
-    dir(2, wa, a, hq, Fy, Gy);
-    dir(4, wa, -a, hq, -Fy, -Gy);
+    dir2(2, 4, wa, a, hq, Fy, Gy);
     a = ux3 + uy3;
     hq = C(0.5) * (a * a - uu);
-    dir(5, wd, a, hq, Fx + Fy, Gx + Gy);
-    dir(7, wd, -a, hq, -(Fx + Fy), -(Gx + Gy));
+    dir2(5, 7, wd, a, hq, Fx + Fy, Gx + Gy);
     a = uy3 - ux3;
     hq = C(0.5) * (a * a - uu);
-    dir(6, wd, a, hq, Fy - Fx, Gy - Gx);
-    dir(8, wd, -a, hq, Fx - Fy, Gx - Gy);
+    dir2(6, 8, wd, a, hq, Fy - Fx, Gy - Gx);
     const C W0 = WGT<C>(0);
     const C G0 = W0 + W0 * hu;
     // rest direction: f and hbar as above; g_0 in two-float arithmetic
