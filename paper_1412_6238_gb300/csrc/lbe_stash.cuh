@@ -160,7 +160,9 @@ __device__ __forceinline__ float stash_val(const char* slot, int k, int i, int c
 // the wall substitution copied the reversed population of the cell itself.
 // Rules of pull9 (lbe_tile.cuh): anti-bounce-back for hbar at the walls, and
 // the deviation offsets of hbar between rows.
-template <class S, int K>
+// SUM: the values only enter a sum over i (the moment): in an interior row
+// the hbar deviation offsets +-w_i dh then cancel exactly and are left out.
+template <class S, int K, bool SUM = false>
 __device__ __forceinline__ void wstash_pull(const InstDev& I, const Phys<float>& P,
                                             const char* slot, int c0, int c0g, int y, int xw,
                                             float out[9]) {
@@ -175,8 +177,8 @@ __device__ __forceinline__ void wstash_pull(const InstDev& I, const Phys<float>&
 #pragma unroll
     for (int i = 0; i < 9; i++) {
       float v = stash_val<S>(slot, K, i, col(i, true), P);
-      if (DEV && EY(i) == 1) v -= WGT<float>(i) * P.dh;
-      if (DEV && EY(i) == -1) v += WGT<float>(i) * P.dh;
+      if (DEV && !SUM && EY(i) == 1) v -= WGT<float>(i) * P.dh;
+      if (DEV && !SUM && EY(i) == -1) v += WGT<float>(i) * P.dh;
       out[i] = v;
     }
     return;
@@ -507,7 +509,7 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
           cring[ci] = moment_c(v, g0lo, clo);
           clr[ci] = __float2half_rn(clo * G0LO_SCALE);
           pring[pi] = sum9(vf);
-          wstash_pull<S, 2>(I, P, s, c0, c0g, mr, xw, v);
+          wstash_pull<S, 2, true>(I, P, s, c0, c0g, mr, xw, v);
           C T = dv(sum9(v), P.rho_cv, P.inv_rho_cv);
           if (m < 0) T = ghost_T<S>(I, xw, true, T);
           Tring[pi] = T;
