@@ -252,6 +252,94 @@ __device__ __forceinline__ void wstash_pull_fg16(const InstDev& I, const Phys<fl
   }
 }
 
+// True in exactly one lane of the (converged) warp.
+__device__ __forceinline__ bool elect_one() {
+  uint32_t e;
+  asm volatile(
+      "{\n .reg .b32 r;\n .reg .pred p;\n elect.sync r|p, 0xffffffff;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(e));
+  return e != 0;
+}
+
+// Warp-uniform source addresses of a warp's copies in one item: the start of
+// the warp's column window in row 0 of the first pair plane, of the first
+// hbar plane, of the f_0 and g_0 planes (16-bit forms) and of the g_0 low
+// part; the row strides in bytes (elements of 8, 4 and 2 bytes) and the
+// plane strides.  Built from values broadcast from lane 0, so that the
+// copies' operands stay in uniform registers and one elected lane issues
+// each copy as one instruction.
+struct CopyPlan {
+  const char *pair, *h, *f0, *g0, *lo;
+  int64_t row8, row4, row2, pp, pb;
+};
+__device__ __forceinline__ int64_t bcast64(int64_t v) {
+  return (int64_t)__shfl_sync(0xffffffffu, (unsigned long long)v, 0);
+}
+__device__ __forceinline__ CopyPlan copy_plan(const InstDev& I, int parity, int e32) {
+  const char* src = reinterpret_cast<const char*>(
+      __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(I.buf[parity]), 0));
+  const int64_t pitch = bcast64(I.pitch);
+  const int e16 = e32 & ~7;
+  const bool w16 = I.storage != ST_F32;
+  CopyPlan c;
+  c.row8 = pitch * 8;
+  c.row4 = pitch * 4;
+  c.row2 = pitch * 2;
+  c.pp = bcast64((int64_t)I.pair_bytes);
+  c.pb = bcast64((int64_t)I.plane_bytes);
+  c.pair = src + (w16 ? (int64_t)e16 * 4 : (int64_t)e32 * 8);
+  c.h = src + bcast64((int64_t)I.h_off) + (w16 ? (int64_t)e16 * 2 : (int64_t)e32 * 4);
+  c.f0 = src + bcast64((int64_t)I.f0_off) + (int64_t)e16 * 2;
+  c.g0 = src + bcast64((int64_t)I.g0_off) + (int64_t)e32 * 4;
+  c.lo = src + bcast64((int64_t)I.g0lo_off) + (int64_t)e16 * 2;
+  return c;
+}
+
+// The copies of one warp-row: the populations pulled by the cells of moment
+// row mr (or, at a wall, the reversed populations of row mr itself) into
+// the warp's stash slot at shared address dst, completing on bar.
+//   FP32 (19 copies): the 9 (f_i, g_i) pair rows, the 9 hbar_i rows, the
+//     g_0 low part.
+//   16-bit (20 copies): the 8 pair rows (i = 1..8), f_0, the 9 hbar_i rows,
+//     the FP32 g_0 row, the g_0 low part.
+// WALL: mr is the first or the last row (else the pulls need no wall rule).
+template <class S, bool WALL>
+__device__ __forceinline__ void issue_row(const CopyPlan& c, uint32_t dst, uint32_t bar, int mr,
+                                          int ny) {
+  using Fmt = StashFmt<S>;
+  constexpr bool W16 = sizeof(typename Fmt::E) == 2;
+  const bool wb = WALL && mr == 0, wt = WALL && mr == ny - 1;
+  // source row and plane of population i (the reversed one at a wall)
+  auto at = [&](int i, int64_t row) -> int64_t {
+    const bool wall = (EY(i) == 1 && wb) || (EY(i) == -1 && wt);
+    return wall ? (int64_t)mr * row : (int64_t)(mr - EY(i)) * row;
+  };
+  auto pl = [&](int i) {
+    const bool wall = (EY(i) == 1 && wb) || (EY(i) == -1 && wt);
+    return wall ? OPP(i) : i;
+  };
+  if constexpr (!W16) {
+#pragma unroll
+    for (int i = 0; i < 9; i++)
+      bulk_load(dst + Fmt::off(0, i), c.pair + pl(i) * c.pp + at(i, c.row8), Fmt::PROW, bar);
+#pragma unroll
+    for (int i = 0; i < 9; i++)
+      bulk_load(dst + Fmt::off(2, i), c.h + pl(i) * c.pb + at(i, c.row4), Fmt::ROW, bar);
+  } else {
+#pragma unroll
+    for (int i = 1; i < 9; i++)
+      bulk_load(dst + Fmt::off(0, i), c.pair + (pl(i) - 1) * c.pp + at(i, c.row4), Fmt::PROW,
+                bar);
+    bulk_load(dst + Fmt::F0, c.f0 + (int64_t)mr * c.row2, Fmt::ROW, bar);
+#pragma unroll
+    for (int i = 0; i < 9; i++)
+      bulk_load(dst + Fmt::off(2, i), c.h + pl(i) * c.pb + at(i, c.row2), Fmt::ROW, bar);
+    bulk_load(dst + Fmt::G0, c.g0 + (int64_t)mr * c.row4, 144, bar);
+  }
+  bulk_load(dst + Fmt::LO, c.lo + (int64_t)mr * c.row2, 80, bar);
+}
+
 template <class S, int NC>
 __global__ void __launch_bounds__(NC, (StashCfg<S, NC>::MINB))
 stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items, int seg_rows,
@@ -271,8 +359,11 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
   __shared__ int s_abort;
   const int t = threadIdx.x;
   const int lane = t & 31, w = t >> 5;
+  const int wu = __shfl_sync(0xffffffffu, w, 0);  // the warp index, warp-uniform
   char* wstash = smem + w * Cfg::SR * Cfg::SLOT;
   uint64_t* wbars = bars + w * Cfg::SR;
+  const uint32_t wst_u = smem_u32(smem) + (uint32_t)(wu * Cfg::SR * Cfg::SLOT);
+  const uint32_t bars_u = smem_u32(bars);
   // the warp's barriers are initialised once; every copy issued in an item is
   // waited for in that item, so the phase bits carry over between items
   if (lane == 0) {
@@ -291,11 +382,12 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
       if (insts[mid].tile_begin <= item) lo = mid; else hi = mid - 1;
     }
     const InstDev& I = insts[lo];
-    const char* __restrict__ src = I.buf[parity];
     const int64_t local = item - I.tile_begin;
-    const int nx = I.nx, ny = I.ny;
-    const int x0 = (int)(local % I.tiles_x) * Cfg::NCO;
-    const int ya = (int)(local / I.tiles_x) * seg_rows;
+    // the item's scalars, broadcast from lane 0 so that the compiler knows
+    // them to be warp-uniform (and so the row loop and the copy operands)
+    const int nx = I.nx, ny = __shfl_sync(0xffffffffu, I.ny, 0);
+    const int x0 = __shfl_sync(0xffffffffu, (int)(local % I.tiles_x) * Cfg::NCO, 0);
+    const int ya = __shfl_sync(0xffffffffu, (int)(local / I.tiles_x) * seg_rows, 0);
     const int yb = min(ya + seg_rows, ny);
     char* __restrict__ dst = I.buf[parity ^ 1];
     const Phys<C> P = phys<C>(I);
@@ -314,6 +406,7 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
     const int c0 = (W16 ? e32 - e16 : 0) + lane + 2;  // own column in a population row
     const int c0g = lane + 2;                          // own column in the FP32 g_0 row
     const int c0lo = e32 - e16 + lane + 2;             // own column in the g_0 low-part row
+    const CopyPlan cp = copy_plan(I, parity, x0 + 32 * wu);
     __syncthreads();  // the previous item is done with the rings and stashes
     if (t == 0) s_abort = 0;
 
@@ -322,86 +415,23 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
     auto pr = [](int m) { return (((m % Cfg::PR) + Cfg::PR) % Cfg::PR) * NC; };
     auto nr = [](int m) { return (m & (Cfg::NR - 1)) * NC; };
     auto loadable = [&](int m) { return m <= yb + 1 && m < ny; };
-    // Copy plan: one bulk copy per lane, into its row of the slot; byte
-    // offsets from the start of the source row m for the pull from row
-    // m - xi_iy (off_n) and for the reversed population of the cell itself
-    // at a wall (off_w).
-    //   FP32 (19 copies): lanes 0-8 the (f_i, g_i) pair rows, 9-17 hbar_i,
-    //     18 the g_0 low part.
-    //   16-bit (20 copies): lanes 0-7 the (f_i, g_i) pair rows, i = lane + 1,
-    //     8 f_0, 9-17 hbar_i, 18 the FP32 g_0, 19 the g_0 low part.
-    const int pcopies = W16 ? 20 : 19;
-    int pi_ = 0, pey_ = 0, pbytes_ = 80, pdst = Fmt::LO;
-    ptrdiff_t prow_ = (ptrdiff_t)pitch * 2, off_n = 0, off_w = 0;
-    {
-      const ptrdiff_t PB = (ptrdiff_t)I.plane_bytes, PP = (ptrdiff_t)I.pair_bytes;
-      if constexpr (!W16) {
-        if (lane < 9) {  // pair rows
-          pi_ = lane;
-          prow_ = (ptrdiff_t)pitch * 8;
-          pbytes_ = Fmt::PROW;
-          off_n = pi_ * PP - EY(pi_) * prow_ + (ptrdiff_t)e32 * 8;
-          off_w = OPP(pi_) * PP + (ptrdiff_t)e32 * 8;
-          pdst = Fmt::off(0, pi_);
-        } else if (lane < 18) {  // hbar rows
-          pi_ = lane - 9;
-          prow_ = (ptrdiff_t)pitch * 4;
-          pbytes_ = Fmt::ROW;
-          off_n = (ptrdiff_t)I.h_off + pi_ * PB - EY(pi_) * prow_ + (ptrdiff_t)e32 * 4;
-          off_w = (ptrdiff_t)I.h_off + OPP(pi_) * PB + (ptrdiff_t)e32 * 4;
-          pdst = Fmt::off(2, pi_);
-        }
-      } else {
-        if (lane < 8) {  // pair rows, i = lane + 1
-          pi_ = lane + 1;
-          prow_ = (ptrdiff_t)pitch * 4;
-          pbytes_ = Fmt::PROW;
-          off_n = (pi_ - 1) * PP - EY(pi_) * prow_ + (ptrdiff_t)e16 * 4;
-          off_w = (OPP(pi_) - 1) * PP + (ptrdiff_t)e16 * 4;
-          pdst = Fmt::off(0, pi_);
-        } else if (lane == 8) {  // f_0
-          prow_ = (ptrdiff_t)pitch * 2;
-          pbytes_ = Fmt::ROW;
-          off_n = off_w = (ptrdiff_t)I.f0_off + (ptrdiff_t)e16 * 2;
-          pdst = Fmt::F0;
-        } else if (lane < 18) {  // hbar rows
-          pi_ = lane - 9;
-          prow_ = (ptrdiff_t)pitch * 2;
-          pbytes_ = Fmt::ROW;
-          off_n = (ptrdiff_t)I.h_off + pi_ * PB - EY(pi_) * prow_ + (ptrdiff_t)e16 * 2;
-          off_w = (ptrdiff_t)I.h_off + OPP(pi_) * PB + (ptrdiff_t)e16 * 2;
-          pdst = Fmt::off(2, pi_);
-        } else if (lane == 18) {  // FP32 g_0
-          prow_ = (ptrdiff_t)pitch * 4;
-          pbytes_ = 144;
-          off_n = off_w = (ptrdiff_t)I.g0_off + (ptrdiff_t)e32 * 4;
-          pdst = Fmt::G0;
-        }
-      }
-      const bool lo_lane = lane == pcopies - 1;
-      if (lo_lane) {  // the g_0 low part
-        prow_ = (ptrdiff_t)pitch * 2;
-        pbytes_ = 80;
-        off_n = off_w = (ptrdiff_t)I.g0lo_off + (ptrdiff_t)e16 * 2;
-        pdst = Fmt::LO;
-      }
-      const bool moving = lane < 18 && !(W16 && lane == 8) && !lo_lane;
-      pey_ = moving ? EY(pi_) : 0;
-    }
     // the warp's copies of the populations pulled by moment row m (the mirror
-    // row's below the bottom wall): lane p < 27 copies population p
+    // row's below the bottom wall), issued by one elected lane
     auto issue = [&](int m) {
       if (!loadable(m)) return;
-      const int mr = m >= 0 ? m : -1 - m;
-      const uint32_t bar = smem_u32(&wbars[m & (Cfg::SR - 1)]);
-      pending |= 1u << (m & (Cfg::SR - 1));
-      if (lane == 0) mbar_expect_tx(bar, Cfg::TX);
-      __syncwarp();
-      if (lane < pcopies) {
-        const bool wall = (pey_ == 1 && mr == 0) || (pey_ == -1 && mr == ny - 1);
-        const char* srcp = src + (ptrdiff_t)mr * prow_ + (wall ? off_w : off_n);
+      const int sl = m & (Cfg::SR - 1);
+      pending |= 1u << sl;
+      __syncwarp();  // the lanes' reads of the slot come before the copies
+      if (elect_one()) {
+        const uint32_t bar = bars_u + (uint32_t)((wu * Cfg::SR + sl) * 8);
+        const uint32_t dstw = wst_u + (uint32_t)(sl * Cfg::SLOT);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        bulk_load(smem_u32(slot(m) + pdst), srcp, pbytes_, bar);
+        mbar_expect_tx(bar, Cfg::TX);
+        const int mr = m >= 0 ? m : -1 - m;
+        if (mr > 0 && mr < ny - 1)
+          issue_row<S, false>(cp, dstw, bar, mr, ny);
+        else
+          issue_row<S, true>(cp, dstw, bar, mr, ny);
       }
     };
     auto wait_row = [&](int m) -> bool {
