@@ -1,35 +1,32 @@
-// The fused step as a column-strip marching kernel with per-warp stashes of
-// pulled populations (FP32 and 16-bit storages).
+// The fused step as a column-strip marching kernel with a stash of pulled
+// populations (FP32 and 16-bit storages).
 //
 // A work item is a strip of NC - 4 output columns and a segment of rows
 // [ya, yb) of one instance: a CTA of NC threads marches up the rows, thread t
 // owning column x0 - 2 + t so that the two halo columns on each side are
-// ordinary threads.  Instead of staging every source row whole for the CTA
-// (as a TMA tiled row ring would), each warp stages only what its own 32
-// cells pull for a row m:
-// for each of the 27 populations (k, i), the elements of source row m - xi_iy
-// that cover its columns shifted by -xi_ix (or, at a wall, the reversed
-// population of row m itself), one bulk copy (cp.async.bulk) per population,
-// the start rounded down to 16 bytes (FP32: 36 elements = 144 bytes; 16-bit
-// planes: 40 elements = 80 bytes; the FP32 g_0 plane of the 16-bit forms:
-// 144 bytes), completing on an mbarrier of the warp.  A row's values stay in the warp's stash from the
-// time its moments are formed until it collides three iterations later: 4
-// rows x 27 populations per warp, about half the shared memory of a 7-row
-// ring of whole source rows (FP32), so three CTAs fit on an SM instead of
-// two, and no thread waits for another warp's copies.
+// ordinary threads.  Instead of staging whole source rows (as a TMA tiled
+// row ring would, 7 rows for the pull and the stencils), the CTA stages, for
+// each moment row m, what its cells pull: for each population row of the
+// layout (FP32: the 9 (f_i, g_i) pair rows, the 9 hbar_i rows and the g_0 low
+// part), the elements of source row m - xi_iy over the strip's columns and
+// the pulls' reach (or, at a wall, the reversed population of row m itself),
+// one bulk copy (cp.async.bulk, 16-byte aligned) per row, all completing on
+// the slot's mbarrier.  A row's values stay in the stash from the time its
+// moments are formed until it collides three iterations later: a 4-row
+// stash (58 KB in FP32) instead of a 7-row ring, so that three CTAs fit on
+// an SM.
 //
 // Iteration i (from ya - 4 to yb):
-//   1. collide row i-1 (S2-S9 of lbe_cell.cuh) from its stash slot and the
-//      moment rings, and store its 27 values;
-//   2. the warp's copies of row i+3 into the slot that row i-1 has just freed;
-//   3. wait for the warp's copies of row i+2 and form its moments c, p, T
-//      (S1) into the rings; rows below the bottom wall use the pulled values
-//      of their mirror row, rows above the top wall copy the mirror rows in
-//      the rings;
-//   barrier; 4. unit normal of row i+1 (S2); barrier.
+//   barrier; 1. collide row i-1 (S2-S9 of lbe_cell.cuh) from its stash slot
+//      and the moment rings, and store its 27 values;
+//   2. wait for the copies of row i+2 and form its moments c, p, T (S1) into
+//      the rings; rows below the bottom wall use the pulled values of their
+//      mirror row, rows above the top wall copy the mirror rows in the rings;
+//   barrier; 3. one elected lane issues the copies of row i+3 into the slot
+//      that row i-1 has just freed; 4. unit normal of row i+1 (S2).
 // Every population is read from HBM once per step.  Every mbarrier wait is
-// bounded: on time-out the kernel sets *err, waits (bounded) for the warp's
-// copies in flight and returns.
+// bounded: on time-out the kernel sets *err, waits (bounded) for the copies
+// in flight and returns.
 #pragma once
 
 #include "lbe_tile.cuh"
@@ -72,41 +69,48 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
       : "memory");
 }
 
-// Stash layout of one warp-row for a storage form: population (k, i) has a
-// row of EW elements at byte offset off(k, i) of the slot; the g_0 row of the
-// 16-bit forms holds 36 FP32 elements.
+// Threads (= columns, two halo columns on each side) of a strip CTA.
+constexpr int STASH_NC = 128;
+
+// Stash layout of one row for a storage form: population (k, i) has a row of
+// EW elements at byte offset off(k, i) of the slot, covering the CTA's
+// columns and the pulls' reach.  Every form adds the FP16 row of the g_0 low
+// part (NC + 8 elements from x0 rounded down to a multiple of 8) at byte LO.
 template <class S>
 struct StashFmt;
-// Every form adds the FP16 row of the g_0 low part (40 elements, 80 bytes)
-// at byte LO of the slot.
-// FP32: 9 rows of (f_i, g_i) pairs (36 cells x 8 bytes), 9 rows of hbar_i
-// (36 x 4 bytes); off(k, i) is the byte offset of the row holding (k, i).
+// FP32: 9 rows of (f_i, g_i) pairs (NC + 4 cells x 8 bytes from element x0),
+// 9 rows of hbar_i (NC + 4 x 4 bytes); off(k, i) is the byte offset of the
+// row holding (k, i).
 template <>
 struct StashFmt<StF32> {
   using E = float;
-  static constexpr int EW = 36;                       // cells per row
+  static constexpr int EW = STASH_NC + 4;             // cells per row
   static constexpr int PROW = EW * 8;                 // pair row bytes
   static constexpr int ROW = EW * 4;                  // hbar row bytes
   static constexpr int HOFF = 9 * PROW;
   static constexpr int LO = HOFF + 9 * ROW;           // the g_0 low-part row
-  static constexpr int SLOT_RAW = LO + 80;            // bytes of one warp's row
+  static constexpr int LOB = (STASH_NC + 8) * 2;      // its bytes
+  static constexpr int SLOT_RAW = LO + LOB;           // bytes of one row
   __host__ __device__ static constexpr int off(int k, int i) {
     return k < 2 ? i * PROW : HOFF + i * ROW;
   }
 };
-// 16-bit: 8 rows of (f_i, g_i) pairs, i = 1..8 (40 cells x 4 bytes), the
-// f_0 row, 9 hbar rows (40 x 2 bytes), the FP32 g_0 row (36 x 4 bytes).
+// 16-bit: 8 rows of (f_i, g_i) pairs, i = 1..8, the f_0 row and 9 hbar rows
+// (NC + 8 cells from x0 rounded down to a multiple of 8: 4 and 2 bytes per
+// cell), the FP32 g_0 row (NC + 4 x 4 bytes from x0).
 template <class E16>
 struct StashFmt16 {
   using E = E16;
-  static constexpr int EW = 40;
+  static constexpr int EW = STASH_NC + 8;
   static constexpr int PROW = EW * 4;
   static constexpr int ROW = EW * 2;
   static constexpr int F0 = 8 * PROW;
   static constexpr int HOFF = F0 + ROW;
   static constexpr int G0 = HOFF + 9 * ROW;
-  static constexpr int LO = G0 + 36 * 4;
-  static constexpr int SLOT_RAW = LO + 80;
+  static constexpr int G0B = (STASH_NC + 4) * 4;
+  static constexpr int LO = G0 + G0B;
+  static constexpr int LOB = ROW;
+  static constexpr int SLOT_RAW = LO + LOB;
   __host__ __device__ static constexpr int off(int k, int i) {
     return k == 2 ? HOFF + i * ROW : (i == 0 ? (k == 0 ? F0 : G0) : (i - 1) * PROW);
   }
@@ -119,24 +123,28 @@ struct StashFmt<StBF16> : StashFmt16<__nv_bfloat16> {};
 template <class S, int NC>
 struct StashCfg {
   using Fmt = StashFmt<S>;
+  static_assert(NC == STASH_NC, "the stash formats are laid out for STASH_NC columns");
+  static_assert(Fmt::SLOT_RAW % 16 == 0 && Fmt::PROW % 16 == 0 && Fmt::ROW % 16 == 0 &&
+                    Fmt::LOB % 16 == 0 && Fmt::LO % 16 == 0,
+                "bulk copies: 16-byte sizes and offsets");
   static constexpr int NCO = NC - 4;          // output columns
   static constexpr int NW = NC / 32;          // warps
-  static constexpr int SR = 4;                // stash rows per warp
-  static constexpr int SLOT = (Fmt::SLOT_RAW + 15) / 16 * 16;  // bytes of one warp's row
-  static constexpr int TX = Fmt::SLOT_RAW;    // bytes copied per warp and row
+  static constexpr int SR = 4;                // stash rows
+  static constexpr int SLOT = Fmt::SLOT_RAW;  // bytes of one row
+  static constexpr int TX = Fmt::SLOT_RAW;    // bytes copied per row
   static constexpr int CR = 5, PR = 5, NR = 4;  // moment / normal ring rows
   static_assert(CR == PR, "c, p and T rings share their row index");
-  static constexpr int STASH = NW * SR * SLOT;
+  static constexpr int STASH = SR * SLOT;
   // FP32 rings of c, p, T, n_x, n_y and the FP16 ring of the c low part
   static constexpr int RINGS = (CR + 2 * PR + 2 * NR) * NC * 4 + CR * NC * 2;
-  static constexpr int SMEM = STASH + RINGS + NW * SR * 8;
+  static constexpr int SMEM = STASH + RINGS + SR * 8;
   // resident CTAs per SM the kernel is compiled for (registers)
   static constexpr int MINB = sizeof(typename Fmt::E) == 4 ? 3 : 4;
   static_assert(NC % 32 == 0, "whole warps");
 };
 
-// The 9 pulled populations of lattice K at row y from a warp's stash slot
-// (lane l reads element l + 2 - xi_ix of population (K, i), or l + 2 where
+// The 9 pulled populations of lattice K at row y from a stash slot
+// (thread t reads element t + 2 - xi_ix of population (K, i), or t + 2 where
 // the wall substitution copied the reversed population of the cell itself),
 // with the rules of pull9 (lbe_tile.cuh): anti-bounce-back for hbar at the
 // walls, and the deviation offsets of hbar between rows.
@@ -154,8 +162,8 @@ __device__ __forceinline__ float stash_val(const char* slot, int k, int i, int c
   }
 }
 
-// The 9 pulled populations of lattice K at row y from a warp's stash slot.
-// c0 is the element of the lane's own column in a population row (c0g in the
+// The 9 pulled populations of lattice K at row y from a stash slot.
+// c0 is the element of the thread's own column in a population row (c0g in the
 // FP32 g_0 row of the 16-bit forms); the pull reads c0 - xi_ix, or c0 where
 // the wall substitution copied the reversed population of the cell itself.
 // Rules of pull9 (lbe_tile.cuh): anti-bounce-back for hbar at the walls, and
@@ -262,13 +270,14 @@ __device__ __forceinline__ bool elect_one() {
   return e != 0;
 }
 
-// Warp-uniform source addresses of a warp's copies in one item: the start of
-// the warp's column window in row 0 of the first pair plane, of the first
-// hbar plane, of the f_0 and g_0 planes (16-bit forms) and of the g_0 low
-// part; the row strides in bytes (elements of 8, 4 and 2 bytes) and the
-// plane strides.  Built from values broadcast from lane 0, so that the
-// copies' operands stay in uniform registers and one elected lane issues
-// each copy as one instruction.
+// Warp-uniform source addresses of a CTA's copies in one item: the start of
+// its column window (from element x0, or x0 rounded down to a multiple of 8
+// for 16-bit rows) in row 0 of the first pair plane, of the first hbar plane,
+// of the f_0 and g_0 planes (16-bit forms) and of the g_0 low part; the row
+// strides in bytes (elements of 8, 4 and 2 bytes) and the plane strides.
+// Built from values broadcast from lane 0, so that the copies' operands stay
+// in uniform registers and one elected lane issues each copy as one
+// instruction.
 struct CopyPlan {
   const char *pair, *h, *f0, *g0, *lo;
   int64_t row8, row4, row2, pp, pb;
@@ -276,11 +285,11 @@ struct CopyPlan {
 __device__ __forceinline__ int64_t bcast64(int64_t v) {
   return (int64_t)__shfl_sync(0xffffffffu, (unsigned long long)v, 0);
 }
-__device__ __forceinline__ CopyPlan copy_plan(const InstDev& I, int parity, int e32) {
+__device__ __forceinline__ CopyPlan copy_plan(const InstDev& I, int parity, int x0) {
   const char* src = reinterpret_cast<const char*>(
       __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(I.buf[parity]), 0));
   const int64_t pitch = bcast64(I.pitch);
-  const int e16 = e32 & ~7;
+  const int e16 = x0 & ~7;
   const bool w16 = I.storage != ST_F32;
   CopyPlan c;
   c.row8 = pitch * 8;
@@ -288,17 +297,17 @@ __device__ __forceinline__ CopyPlan copy_plan(const InstDev& I, int parity, int 
   c.row2 = pitch * 2;
   c.pp = bcast64((int64_t)I.pair_bytes);
   c.pb = bcast64((int64_t)I.plane_bytes);
-  c.pair = src + (w16 ? (int64_t)e16 * 4 : (int64_t)e32 * 8);
-  c.h = src + bcast64((int64_t)I.h_off) + (w16 ? (int64_t)e16 * 2 : (int64_t)e32 * 4);
+  c.pair = src + (w16 ? (int64_t)e16 * 4 : (int64_t)x0 * 8);
+  c.h = src + bcast64((int64_t)I.h_off) + (w16 ? (int64_t)e16 * 2 : (int64_t)x0 * 4);
   c.f0 = src + bcast64((int64_t)I.f0_off) + (int64_t)e16 * 2;
-  c.g0 = src + bcast64((int64_t)I.g0_off) + (int64_t)e32 * 4;
+  c.g0 = src + bcast64((int64_t)I.g0_off) + (int64_t)x0 * 4;
   c.lo = src + bcast64((int64_t)I.g0lo_off) + (int64_t)e16 * 2;
   return c;
 }
 
-// The copies of one warp-row: the populations pulled by the cells of moment
-// row mr (or, at a wall, the reversed populations of row mr itself) into
-// the warp's stash slot at shared address dst, completing on bar.
+// The copies of one row: the populations pulled by the cells of moment row
+// mr (or, at a wall, the reversed populations of row mr itself) into the
+// stash slot at shared address dst, completing on bar.
 //   FP32 (19 copies): the 9 (f_i, g_i) pair rows, the 9 hbar_i rows, the
 //     g_0 low part.
 //   16-bit (20 copies): the 8 pair rows (i = 1..8), f_0, the 9 hbar_i rows,
@@ -335,9 +344,9 @@ __device__ __forceinline__ void issue_row(const CopyPlan& c, uint32_t dst, uint3
 #pragma unroll
     for (int i = 0; i < 9; i++)
       bulk_load(dst + Fmt::off(2, i), c.h + pl(i) * c.pb + at(i, c.row2), Fmt::ROW, bar);
-    bulk_load(dst + Fmt::G0, c.g0 + (int64_t)mr * c.row4, 144, bar);
+    bulk_load(dst + Fmt::G0, c.g0 + (int64_t)mr * c.row4, Fmt::G0B, bar);
   }
-  bulk_load(dst + Fmt::LO, c.lo + (int64_t)mr * c.row2, 80, bar);
+  bulk_load(dst + Fmt::LO, c.lo + (int64_t)mr * c.row2, Fmt::LOB, bar);
 }
 
 template <class S, int NC>
@@ -355,19 +364,16 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
   C* nxr = Tring + Cfg::PR * NC;                         // [NR][NC]
   C* nyr = nxr + Cfg::NR * NC;
   __half* clr = reinterpret_cast<__half*>(nyr + Cfg::NR * NC);  // [CR][NC], lo * 2^24
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Cfg::STASH + Cfg::RINGS);  // [NW][SR]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Cfg::STASH + Cfg::RINGS);  // [SR]
   __shared__ int s_abort;
   const int t = threadIdx.x;
-  const int lane = t & 31, w = t >> 5;
-  const int wu = __shfl_sync(0xffffffffu, w, 0);  // the warp index, warp-uniform
-  char* wstash = smem + w * Cfg::SR * Cfg::SLOT;
-  uint64_t* wbars = bars + w * Cfg::SR;
-  const uint32_t wst_u = smem_u32(smem) + (uint32_t)(wu * Cfg::SR * Cfg::SLOT);
+  const int wu = __shfl_sync(0xffffffffu, t >> 5, 0);  // the warp index, warp-uniform
+  const uint32_t stash_u = smem_u32(smem);
   const uint32_t bars_u = smem_u32(bars);
-  // the warp's barriers are initialised once; every copy issued in an item is
+  // the slots' barriers are initialised once; every copy issued in an item is
   // waited for in that item, so the phase bits carry over between items
-  if (lane == 0) {
-    for (int s = 0; s < Cfg::SR; s++) mbar_init(smem_u32(&wbars[s]), 1);
+  if (t == 0) {
+    for (int s = 0; s < Cfg::SR; s++) mbar_init(bars_u + 8 * s, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -396,35 +402,36 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
     const int x = x0 - 2 + t;
     const int xw = wrapx(x, nx);
     const bool collides = t >= 2 && t < NC - 2 && x < nx;
-    // staged elements of this warp's population rows (storage element e holds
-    // column e - XG): its cells are columns x0 - 2 + 32 w + lane, their pulls
-    // reach elements x0 + 32 w + 1 .. x0 + 32 w + 34.  FP32 rows start at
-    // x0 + 32 w (x0 is a multiple of 4: 16-byte aligned), 16-bit rows at that
-    // rounded down to a multiple of 8.
-    const int e32 = x0 + 32 * w;
-    const int e16 = e32 & ~7;
-    const int c0 = (W16 ? e32 - e16 : 0) + lane + 2;  // own column in a population row
-    const int c0g = lane + 2;                          // own column in the FP32 g_0 row
-    const int c0lo = e32 - e16 + lane + 2;             // own column in the g_0 low-part row
-    const CopyPlan cp = copy_plan(I, parity, x0 + 32 * wu);
+    // staged elements of the strip's population rows (storage element e
+    // holds column e - XG): its cells are columns x0 - 2 + t, their pulls
+    // reach elements x0 + 1 .. x0 + NC + 2.  FP32 rows (and the FP32 g_0 row
+    // of the 16-bit forms) start at x0 (a multiple of 4: 16-byte aligned),
+    // 16-bit rows at x0 rounded down to a multiple of 8.
+    const int e16 = x0 & ~7;
+    const int c0 = (W16 ? x0 - e16 : 0) + t + 2;  // own column in a population row
+    const int c0g = t + 2;                         // own column in the FP32 g_0 row
+    const int c0lo = x0 - e16 + t + 2;             // own column in the g_0 low-part row
+    const CopyPlan cp = copy_plan(I, parity, x0);
     __syncthreads();  // the previous item is done with the rings and stashes
     if (t == 0) s_abort = 0;
 
-    auto slot = [&](int m) { return wstash + (m & (Cfg::SR - 1)) * Cfg::SLOT; };
+    auto slot = [&](int m) { return smem + (m & (Cfg::SR - 1)) * Cfg::SLOT; };
     auto cr = [](int m) { return (((m % Cfg::CR) + Cfg::CR) % Cfg::CR) * NC; };
     auto pr = [](int m) { return (((m % Cfg::PR) + Cfg::PR) % Cfg::PR) * NC; };
     auto nr = [](int m) { return (m & (Cfg::NR - 1)) * NC; };
     auto loadable = [&](int m) { return m <= yb + 1 && m < ny; };
-    // the warp's copies of the populations pulled by moment row m (the mirror
-    // row's below the bottom wall), issued by one elected lane
+    // the copies of the populations pulled by moment row m (the mirror row's
+    // below the bottom wall), issued by one elected lane of warp 0 after a
+    // barrier that every thread passed after its last read of the slot
     auto issue = [&](int m) {
       if (!loadable(m)) return;
       const int sl = m & (Cfg::SR - 1);
       pending |= 1u << sl;
-      __syncwarp();  // the lanes' reads of the slot come before the copies
+      if (wu != 0) return;
+      __syncwarp();
       if (elect_one()) {
-        const uint32_t bar = bars_u + (uint32_t)((wu * Cfg::SR + sl) * 8);
-        const uint32_t dstw = wst_u + (uint32_t)(sl * Cfg::SLOT);
+        const uint32_t bar = bars_u + (uint32_t)(sl * 8);
+        const uint32_t dstw = stash_u + (uint32_t)(sl * Cfg::SLOT);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(bar, Cfg::TX);
         const int mr = m >= 0 ? m : -1 - m;
@@ -437,7 +444,7 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
     auto wait_row = [&](int m) -> bool {
       if (!loadable(m)) return true;
       const int s = m & (Cfg::SR - 1);
-      const bool ok = mbar_wait(smem_u32(&wbars[s]), (phase >> s) & 1u);
+      const bool ok = mbar_wait(bars_u + 8 * s, (phase >> s) & 1u);
       if (ok) {
         phase ^= 1u << s;
         pending &= ~(1u << s);
@@ -512,11 +519,7 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
         // step, not here: the branch costs this kernel about 7 %)
       }
 
-      // ---- 2. the warp's copies of row i + 3 (into the slot of row i - 1)
-      __syncwarp();
-      issue(i + 3);
-
-      // ---- 3. moments of row m = i + 2
+      // ---- 2. moments of row m = i + 2
       const int m = i + 2;
       if (!wait_row(m)) {
         s_abort = 1;
@@ -554,6 +557,9 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
       __syncthreads();
       if (s_abort) break;
 
+      // ---- 3. the copies of row i + 3 (into the slot of row i - 1)
+      issue(i + 3);
+
       // ---- 4. unit normal of row i + 1
       const int mn = i + 1;
       if (mn >= ya - 1 && mn <= yb && t >= 1 && t < NC - 1) {
@@ -563,9 +569,9 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
     }
     __syncthreads();
     if (s_abort) {
-      // bounded wait for this warp's copies still in flight, then stop
+      // bounded wait for the copies still in flight, then stop
       for (int sl = 0; sl < Cfg::SR; sl++)
-        if (pending & (1u << sl)) mbar_wait(smem_u32(&wbars[sl]), (phase >> sl) & 1u);
+        if (pending & (1u << sl)) mbar_wait(bars_u + 8 * sl, (phase >> sl) & 1u);
       __syncthreads();
       return;
     }
