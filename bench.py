@@ -37,7 +37,7 @@ NX = NY = 4096
 # algorithmic bytes per cell update: every population read once and written
 # once (FP64: 27 x 8; FP32: 27 x 4 plus the FP16 low part of g_0; 16-bit
 # forms: 26 x 2 plus the FP32 g_0 and its FP16 low part), both directions
-BYTES_PER_CELL = {"f64": 432, "f32": 220, "f16dev": 116, "bf16dev": 116}
+BYTES_PER_CELL = {"f64": 432, "f32": 220, "f16dev": 116, "bf16dev": 116, "f16mix": 152}
 PROFILE = os.path.join(ROOT, "profiles", "lbe_step_f32_droplet_4096x4096.md")
 
 
@@ -367,7 +367,7 @@ def measure_variants(args, w, ref_fields):
         b = torch.stack([G[k] for k in keys])
         return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
 
-    for st in ("f16dev", "bf16dev"):
+    for st in ("f16mix", "f16dev", "bf16dev"):
         sim = LBE(w, storage=st)
         sim.step(args.warmup)
         ms = _timed(sim, args.steps)
@@ -391,7 +391,7 @@ def measure_variants(args, w, ref_fields):
     cells = sum(x.cells for x in sweep)
     K = args.batch_steps
     res = {"instances": len(sweep), "cells": cells, "steps": K}
-    for st in ("f16dev", "f32"):
+    for st in ("f16mix", "f16dev", "f32"):
         sim = LBE(sweep, storage=st)
         sim.step(3)
         ms = _timed(sim, K)
@@ -405,6 +405,7 @@ def measure_variants(args, w, ref_fields):
         seq_ms += _timed(sim, K)
         del sim
     res["sequential_f32"] = cells * K / (seq_ms / 1e3) / 1e6
+    res["speedup_batched_f16mix_vs_sequential_f32"] = res["batched_f16mix"] / res["sequential_f32"]
     res["speedup_batched_f16dev_vs_sequential_f32"] = res["batched_f16dev"] / res["sequential_f32"]
     res["unit"] = UNIT
     out["batch64"] = res

@@ -66,14 +66,17 @@ typedef enum {
 /* Population storage.  Arithmetic is FP64 for LBE_F64 and FP32 otherwise.
  * The deviation forms store f_i, g_i (i > 0) and hbar_i - w_i rho c_v T_r(y)
  * (T_r the linear conduction profile between the wall means) scaled by a
- * power of two in 16 bits; g_0 (which carries c) stays FP32.  The FP32 and
- * 16-bit forms also keep the low part of g_0 (FP16), so that c = sum g_i is
- * carried to about 1e-11. */
+ * power of two in 16 bits; g_0 (which carries c) stays FP32.  LBE_F16MIX
+ * keeps f (which carries the momentum, hence u) in FP32 and stores g_i
+ * (i > 0) and the hbar deviations in FP16, the three populations of a
+ * direction in one 8-byte word.  The FP32 and 16-bit forms also keep the low
+ * part of g_0 (FP16), so that c = sum g_i is carried to about 1e-11. */
 typedef enum {
   LBE_F64 = 0,     /* 216 B per cell per buffer (parity mode)              */
   LBE_F32 = 1,     /* 110 B per cell per buffer (27 fp32 + fp16 low part)  */
   LBE_F16DEV = 2,  /* 58 B per cell per buffer (26 fp16 + 1 fp32 + 1 fp16) */
-  LBE_BF16DEV = 3  /* 58 B per cell per buffer (26 bf16 + 1 fp32 + 1 fp16) */
+  LBE_BF16DEV = 3, /* 58 B per cell per buffer (26 bf16 + 1 fp32 + 1 fp16) */
+  LBE_F16MIX = 4   /* 76 B per cell per buffer (10 fp32 + 18 fp16)         */
 } lbe_storage;
 
 /* Parameters of one instance, lattice units.  Validity (LBE_EINVAL

@@ -25,6 +25,7 @@ UNITS = {
     "lbe_step_f32.cu": ["-prec-div=false", "-prec-sqrt=false"],
     "lbe_step_f16.cu": ["-prec-div=false", "-prec-sqrt=false"],
     "lbe_step_bf16.cu": ["-prec-div=false", "-prec-sqrt=false"],
+    "lbe_step_mix.cu": ["-prec-div=false", "-prec-sqrt=false"],
     "lbe_aux.cu": ["-fmad=false"],
     "lbe_api.cu": ["-Xcompiler", "-ffp-contract=off"],
     "lbe_noalloc.cu": ["-fmad=false"],

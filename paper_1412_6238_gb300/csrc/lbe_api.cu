@@ -140,7 +140,7 @@ lbe_status check_params(const lbe_params& p, int index) {
   if (p.nx < 1) return bad("nx must be >= 1");
   if (p.ny < 2) return bad("ny must be >= 2");
   if ((int64_t)p.nx * p.ny > (int64_t)1 << 31) return bad("nx*ny must be < 2^31");
-  if (p.storage < LBE_F64 || p.storage > LBE_BF16DEV) return bad("unknown storage");
+  if (p.storage < LBE_F64 || p.storage > LBE_F16MIX) return bad("unknown storage");
   if (p.check_every < 0) return bad("check_every must be >= 0");
   if (!(p.rho > 0) || !(p.cv > 0)) return bad("rho and cv must be > 0");
   if (!(p.eta1 > 0) || !(p.eta2 > 0)) return bad("eta1, eta2 must be > 0 (0 < omega_f < 2)");
@@ -221,8 +221,10 @@ void fill_desc(lbe_handle* h, int j, InstDev& D) {
   int eh = (int)std::floor(std::log2(65504.0 / 64.0 / hmax));
   eh = eh < -30 ? -30 : (eh > 30 ? 30 : eh);
   const int e[3] = {12, 12, eh};
-  const bool sixteen = h->storage >= LBE_F16DEV;
   for (int k = 0; k < 3; k++) {
+    // 16-bit values: g and hbar of F16MIX, all three lattices of F16DEV / BF16DEV
+    const bool sixteen = h->storage == LBE_F16DEV || h->storage == LBE_BF16DEV ||
+                         (h->storage == LBE_F16MIX && k > 0);
     D.s[k] = sixteen ? std::ldexp(1.0f, e[k]) : 1.0f;
     P.inv_s[k] = sixteen ? std::ldexp(1.0, -e[k]) : 1.0;
   }
@@ -481,7 +483,7 @@ lbe_status create(int32_t n, const lbe_params* params, const lbe_init_fields* in
   }
   CUB(cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming));
   const int st = h->storage;
-  const size_t esz = st == LBE_F64 ? 8 : (st == LBE_F32 ? 4 : 2);
+  const size_t esz = st == LBE_F64 ? 8 : ((st == LBE_F32 || st == LBE_F16MIX) ? 4 : 2);
   for (int j = 0; j < n; j++) {
     InstHost& H = h->inst[j];
     H.p = params[j];
@@ -492,7 +494,15 @@ lbe_status create(int32_t n, const lbe_params* params, const lbe_init_fields* in
     // the FP16 plane of the g_0 low part (16/32-bit forms) follows the
     // population planes
     const uint64_t lo_bytes = ((uint64_t)H.ny * H.pitch * 2 + 255) / 256 * 256;
-    if (st >= LBE_F16DEV) {
+    if (st == LBE_F16MIX) {
+      // 9 planes of 8-byte words (f_i FP32 and two FP16 values), FP32 g_0
+      H.pair_bytes = ((uint64_t)H.ny * H.pitch * 8 + 255) / 256 * 256;
+      H.g0_off = 9 * H.pair_bytes;
+      H.h_off = 0;
+      H.f0_off = 0;
+      H.g0lo_off = 0;  // in the words of plane 0
+      H.buf_bytes = H.g0_off + H.plane_bytes;
+    } else if (st == LBE_F16DEV || st == LBE_BF16DEV) {
       // 8 (f_i, g_i) pair planes (i >= 1), f_0, 9 hbar, FP32 g_0, low part
       H.pair_bytes = ((uint64_t)H.ny * H.pitch * 4 + 255) / 256 * 256;
       H.f0_off = 8 * H.pair_bytes;

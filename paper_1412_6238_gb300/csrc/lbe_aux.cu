@@ -22,6 +22,7 @@ cudaError_t launch_stash(int storage, const InstDev* d, int n, int64_t items, in
     case ST_F32: return launch_stash_f32(d, n, items, seg, parity, grid, err, s);
     case ST_F16DEV: return launch_stash_f16(d, n, items, seg, parity, grid, err, s);
     case ST_BF16DEV: return launch_stash_bf16(d, n, items, seg, parity, grid, err, s);
+    case ST_F16MIX: return launch_stash_mix(d, n, items, seg, parity, grid, err, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -31,6 +32,7 @@ int stash_occupancy(int storage) {
     case ST_F32: return stash_occupancy_f32();
     case ST_F16DEV: return stash_occupancy_f16();
     case ST_BF16DEV: return stash_occupancy_bf16();
+    case ST_F16MIX: return stash_occupancy_mix();
   }
   return 0;
 }
@@ -42,6 +44,7 @@ cudaError_t launch_step(int storage, int tile, const InstDev* d, int n, int64_t 
     case ST_F32: return launch_step_f32(tile, d, n, total, parity, grid, s);
     case ST_F16DEV: return launch_step_f16(tile, d, n, total, parity, grid, s);
     case ST_BF16DEV: return launch_step_bf16(tile, d, n, total, parity, grid, s);
+    case ST_F16MIX: return launch_step_mix(tile, d, n, total, parity, grid, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -52,6 +55,7 @@ int step_occupancy(int storage, int tile) {
     case ST_F32: return occupancy_f32(tile);
     case ST_F16DEV: return occupancy_f16(tile);
     case ST_BF16DEV: return occupancy_bf16(tile);
+    case ST_F16MIX: return occupancy_mix(tile);
   }
   return 0;
 }
@@ -63,6 +67,7 @@ cudaError_t launch_fields(int storage, const InstDev* d, int64_t tiles, int pari
     case ST_F32: return fields_f32(d, tiles, parity, out, s);
     case ST_F16DEV: return fields_f16(d, tiles, parity, out, s);
     case ST_BF16DEV: return fields_bf16(d, tiles, parity, out, s);
+    case ST_F16MIX: return fields_mix(d, tiles, parity, out, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -164,7 +169,7 @@ __global__ void push_kernel(const InstDev* __restrict__ d, int nx, int ny,
         st_cell<S>(I, buf, kk, j, rowbase, x, (C)v);
         if constexpr (S::kind != ST_F64) {
           // g_0 = hi + lo: the low part of the rest population
-          if (kk == 1 && j == 0) st_cell_g0lo(I, buf, rowbase, x, (float)(v - (double)(C)v));
+          if (kk == 1 && j == 0) st_cell_g0lo<S>(I, buf, rowbase, x, (float)(v - (double)(C)v));
         }
       }
     }
@@ -189,7 +194,7 @@ __global__ void pull_kernel(const InstDev* __restrict__ d, int nx, int ny, doubl
     pull9<S, 1>(I, P, buf, q, v);
     for (int i = 0; i < 9; i++) pre[(int64_t)(9 + i) * N + k] = (double)v[i];
     if constexpr (S::kind != ST_F64)
-      pre[(int64_t)9 * N + k] += (double)ld_g0lo(I, buf, (size_t)y * I.pitch + XG + x);
+      pre[(int64_t)9 * N + k] += (double)ld_g0lo<S>(I, buf, (size_t)y * I.pitch + XG + x);
     pull9<S, 2>(I, P, buf, q, v);
     const double rref = dev_h<S>() ? I.pd.rho * I.pd.cv * (I.hr0 + I.hr1 * y) : 0.0;
     for (int i = 0; i < 9; i++)
@@ -221,6 +226,7 @@ cudaError_t launch_push(int storage, const InstDev* d, int nx, int ny, const dou
     case ST_F32: return push_t<StF32>(d, nx, ny, pre, parity, s);
     case ST_F16DEV: return push_t<StF16>(d, nx, ny, pre, parity, s);
     case ST_BF16DEV: return push_t<StBF16>(d, nx, ny, pre, parity, s);
+    case ST_F16MIX: return push_t<StMix>(d, nx, ny, pre, parity, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -231,6 +237,7 @@ cudaError_t launch_pull(int storage, const InstDev* d, int nx, int ny, double* p
     case ST_F32: return pull_t<StF32>(d, nx, ny, pre, parity, s);
     case ST_F16DEV: return pull_t<StF16>(d, nx, ny, pre, parity, s);
     case ST_BF16DEV: return pull_t<StBF16>(d, nx, ny, pre, parity, s);
+    case ST_F16MIX: return pull_t<StMix>(d, nx, ny, pre, parity, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -246,14 +253,16 @@ int sums_blocks() { return SUM_BLOCKS; }
 // storages): in a row, elements 0..XG-1 repeat cells nx-XG..nx-1 and elements
 // nx+XG..nx+2XG-1 repeat cells 0..XG-1 (element XG + x holds cell x).  Planes:
 // FP32: 9 (f, g) pairs + 9 hbar + the FP16 g_0 low part; 16-bit: 8 (f, g)
-// pairs + f_0 + 9 hbar + the FP32 g_0 + the low part.
+// pairs + f_0 + 9 hbar + the FP32 g_0 + the low part; F16MIX: 9 planes of
+// 8-byte words + the FP32 g_0.
 // blockIdx.y: instance.
 __global__ void ghost_kernel(const InstDev* __restrict__ insts, int parity) {
   const InstDev& I = insts[blockIdx.y];
   char* b = I.buf[parity];
   const int nx = I.nx, ny = I.ny;
   const size_t pitch = (size_t)I.pitch;
-  const bool w16 = I.storage >= ST_F16DEV;
+  const bool w16 = I.storage == ST_F16DEV || I.storage == ST_BF16DEV;
+  const bool mix = I.storage == ST_F16MIX;
   const int64_t total = (int64_t)20 * ny * (2 * XG);
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -263,7 +272,16 @@ __global__ void ghost_kernel(const InstDev* __restrict__ insts, int parity) {
     const int dstE = j < XG ? j : nx + j;            // left ghosts, then right
     const int srcE = j < XG ? nx + j : j;            // cells nx-XG+j, then j-XG
     const size_t row = (size_t)y * pitch;
-    if (!w16) {
+    if (mix) {
+      // F16MIX: 9 planes of 8-byte words, the FP32 g_0
+      if (p < 9) {
+        double* q = reinterpret_cast<double*>(b + (size_t)p * I.pair_bytes) + row;
+        q[dstE] = q[srcE];
+      } else if (p == 9) {
+        float* q = reinterpret_cast<float*>(b + I.g0_off) + row;
+        q[dstE] = q[srcE];
+      }
+    } else if (!w16) {
       // FP32: 9 (f, g) pair planes, 9 hbar planes, the low part
       if (p < 9) {
         double* q = reinterpret_cast<double*>(b + (size_t)p * I.pair_bytes) + row;  // 8-byte pairs

@@ -394,11 +394,12 @@ __device__ __forceinline__ void st_cell(const InstDev& I, char* dst, int k, int 
 }
 
 // Store the low part of g_0 of cell x and its periodic ghost copies.
+template <class S>
 __device__ __forceinline__ void st_cell_g0lo(const InstDev& I, char* dst, size_t rowbase, int x,
                                              float lo) {
-  st_g0lo(I, dst, rowbase + XG + x, lo);
-  if (x < XG) st_g0lo(I, dst, rowbase + XG + x + I.nx, lo);
-  if (x >= I.nx - XG) st_g0lo(I, dst, rowbase + XG + x - I.nx, lo);
+  st_g0lo<S>(I, dst, rowbase + XG + x, lo);
+  if (x < XG) st_g0lo<S>(I, dst, rowbase + XG + x + I.nx, lo);
+  if (x >= I.nx - XG) st_g0lo<S>(I, dst, rowbase + XG + x - I.nx, lo);
 }
 
 }  // namespace lbe

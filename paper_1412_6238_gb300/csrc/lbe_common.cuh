@@ -17,6 +17,12 @@
 //               holding (f_i, g_i), i = 1..8, of a cell side by side
 //               (4 bytes per cell), the f_0 plane (f0_off), 9 hbar planes
 //               (h_off), then one FP32 plane holding g_0 (g0_off).
+//   F16MIX : FP32 f with 16-bit (FP16) g and hbar deviations, the three
+//               populations of a direction in one 8-byte word: 9 planes of
+//               (f_i FP32, g_i FP16, hbar_i FP16) for i >= 1 and, for i = 0,
+//               (f_0 FP32, hbar_0 FP16, the FP16 g_0 low part), then the FP32
+//               g_0 plane (g0_off).  f carries the momentum, so u keeps the
+//               precision of the FP32 form; 76 bytes per cell per buffer.
 //   F32 and the 16-bit forms also keep the low part of g_0 (g_0 = hi + lo,
 //   |lo| at most half an FP32 ulp of hi) as FP16 of lo * 2^24 in a plane at
 //   byte offset g0lo_off, so that c = sum g_i (of which g_0 carries nearly
@@ -52,7 +58,7 @@ __host__ __device__ constexpr C WGT(int i) {
   return i == 0 ? C(4) / C(9) : (i < 5 ? C(1) / C(9) : C(1) / C(36));
 }
 
-enum Storage { ST_F64 = 0, ST_F32 = 1, ST_F16DEV = 2, ST_BF16DEV = 3 };
+enum Storage { ST_F64 = 0, ST_F32 = 1, ST_F16DEV = 2, ST_BF16DEV = 3, ST_F16MIX = 4 };
 
 constexpr int XG = 4;  // periodic ghost columns on each side of a row
 
@@ -198,14 +204,57 @@ struct StDev {
   }
 };
 
+// F16MIX: direction i of cell idx is the 8-byte word at pair plane i
+// (pair_bytes apart): bytes 0-3 f_i (FP32); bytes 4-5 g_i (i >= 1) or
+// hbar_0 (i = 0); bytes 6-7 hbar_i (i >= 1) or the g_0 low part (i = 0), as
+// FP16 of s_k times the value.  g_0 itself is the FP32 plane at g0_off.
+struct StMix {
+  using C = float;
+  static constexpr int kind = ST_F16MIX;
+  __device__ static __forceinline__ const char* word(const InstDev& I, const char* b, int i,
+                                                     size_t idx) {
+    return b + (size_t)i * I.pair_bytes + 8 * idx;
+  }
+  // byte offset of (k, i) in its word (k >= 1)
+  __host__ __device__ static constexpr int half_at(int k, int i) {
+    return (k == 1 || i == 0) ? 4 : 6;
+  }
+  __device__ static __forceinline__ C ld(const InstDev& I, const Phys<C>& P, const char* b, int k,
+                                         int i, size_t idx) {
+    if (k == 0) return __ldg(reinterpret_cast<const float*>(word(I, b, i, idx)));
+    if (k == 1 && i == 0) return __ldg(reinterpret_cast<const float*>(b + I.g0_off) + idx);
+    return __half2float(*reinterpret_cast<const __half*>(word(I, b, i, idx) + half_at(k, i))) *
+           P.inv_s[k];
+  }
+  __device__ static __forceinline__ void st(const InstDev& I, char* b, int k, int i, size_t idx,
+                                            C v) {
+    char* w = const_cast<char*>(word(I, b, i, idx));
+    if (k == 0) {
+      *reinterpret_cast<float*>(w) = v;
+    } else if (k == 1 && i == 0) {
+      reinterpret_cast<float*>(b + I.g0_off)[idx] = v;
+    } else {
+      *reinterpret_cast<__half*>(w + half_at(k, i)) = __float2half_rn(v * I.s[k]);
+    }
+  }
+};
+
 // The low part of g_0 (16/32-bit storages).
 constexpr float G0LO_SCALE = 16777216.0f;  // 2^24
 constexpr float G0LO_INV = 1.0f / 16777216.0f;
+template <class S>
 __device__ __forceinline__ float ld_g0lo(const InstDev& I, const char* b, size_t idx) {
-  return __half2float(reinterpret_cast<const __half*>(b + I.g0lo_off)[idx]) * G0LO_INV;
+  if constexpr (S::kind == ST_F16MIX)
+    return __half2float(*reinterpret_cast<const __half*>(b + 8 * idx + 6)) * G0LO_INV;
+  else
+    return __half2float(reinterpret_cast<const __half*>(b + I.g0lo_off)[idx]) * G0LO_INV;
 }
+template <class S>
 __device__ __forceinline__ void st_g0lo(const InstDev& I, char* b, size_t idx, float lo) {
-  reinterpret_cast<__half*>(b + I.g0lo_off)[idx] = __float2half_rn(lo * G0LO_SCALE);
+  if constexpr (S::kind == ST_F16MIX)
+    *reinterpret_cast<__half*>(b + 8 * idx + 6) = __float2half_rn(lo * G0LO_SCALE);
+  else
+    reinterpret_cast<__half*>(b + I.g0lo_off)[idx] = __float2half_rn(lo * G0LO_SCALE);
 }
 
 using StF16 = StDev<__half, ST_F16DEV>;

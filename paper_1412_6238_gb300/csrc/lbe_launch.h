@@ -42,9 +42,12 @@ cudaError_t launch_stash_f16(const InstDev* d, int n, int64_t items, int seg, in
                              int* err, cudaStream_t s);
 cudaError_t launch_stash_bf16(const InstDev* d, int n, int64_t items, int seg, int parity,
                               int grid, int* err, cudaStream_t s);
+cudaError_t launch_stash_mix(const InstDev* d, int n, int64_t items, int seg, int parity,
+                             int grid, int* err, cudaStream_t s);
 int stash_occupancy_f32();
 int stash_occupancy_f16();
 int stash_occupancy_bf16();
+int stash_occupancy_mix();
 
 // One step of every instance in d_inst[0..n_inst): persistent grid of `grid`
 // CTAs over total_tiles tiles; reads buf[parity], writes buf[parity ^ 1].
@@ -68,14 +71,18 @@ cudaError_t launch_step_f16(int tile, const InstDev* d, int n, int64_t total, in
                             int grid, cudaStream_t s);
 cudaError_t launch_step_bf16(int tile, const InstDev* d, int n, int64_t total, int parity,
                              int grid, cudaStream_t s);
+cudaError_t launch_step_mix(int tile, const InstDev* d, int n, int64_t total, int parity,
+                            int grid, cudaStream_t s);
 int occupancy_f64(int tile);
 int occupancy_f32(int tile);
 int occupancy_f16(int tile);
 int occupancy_bf16(int tile);
+int occupancy_mix(int tile);
 cudaError_t fields_f64(const InstDev* d, int64_t tiles, int parity, double* out, cudaStream_t s);
 cudaError_t fields_f32(const InstDev* d, int64_t tiles, int parity, double* out, cudaStream_t s);
 cudaError_t fields_f16(const InstDev* d, int64_t tiles, int parity, double* out, cudaStream_t s);
 cudaError_t fields_bf16(const InstDev* d, int64_t tiles, int parity, double* out, cudaStream_t s);
+cudaError_t fields_mix(const InstDev* d, int64_t tiles, int parity, double* out, cudaStream_t s);
 
 // Auxiliary kernels (lbe_aux.cu).
 // Pre-collision state at rest from c0, T0 (device, [ny][nx]) into pre[27][ny][nx].

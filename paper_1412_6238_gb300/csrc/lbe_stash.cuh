@@ -91,9 +91,12 @@ struct StashFmt<StF32> {
   static constexpr int LO = HOFF + 9 * ROW;           // the g_0 low-part row
   static constexpr int LOB = (STASH_NC + 8) * 2;      // its bytes
   static constexpr int SLOT_RAW = LO + LOB;           // bytes of one row
+  static constexpr int MINB = 3;                      // resident CTAs per SM
   __host__ __device__ static constexpr int off(int k, int i) {
     return k < 2 ? i * PROW : HOFF + i * ROW;
   }
+  static_assert(PROW % 16 == 0 && ROW % 16 == 0 && LO % 16 == 0 && LOB % 16 == 0,
+                "bulk copies: 16-byte sizes and offsets");
 };
 // 16-bit: 8 rows of (f_i, g_i) pairs, i = 1..8, the f_0 row and 9 hbar rows
 // (NC + 8 cells from x0 rounded down to a multiple of 8: 4 and 2 bytes per
@@ -111,9 +114,27 @@ struct StashFmt16 {
   static constexpr int LO = G0 + G0B;
   static constexpr int LOB = ROW;
   static constexpr int SLOT_RAW = LO + LOB;
+  static constexpr int MINB = 4;
   __host__ __device__ static constexpr int off(int k, int i) {
     return k == 2 ? HOFF + i * ROW : (i == 0 ? (k == 0 ? F0 : G0) : (i - 1) * PROW);
   }
+  static_assert(PROW % 16 == 0 && ROW % 16 == 0 && G0 % 16 == 0 && G0B % 16 == 0 &&
+                    LO % 16 == 0,
+                "bulk copies: 16-byte sizes and offsets");
+};
+// F16MIX: 9 rows of the 8-byte direction words (f_i FP32, two FP16 values;
+// NC + 4 cells from x0) and the FP32 g_0 row (NC + 4 cells from x0); the g_0
+// low part travels in the words of row 0.
+template <>
+struct StashFmt<StMix> {
+  using E = float;
+  static constexpr int EW = STASH_NC + 4;
+  static constexpr int WROW = EW * 8;  // word row bytes
+  static constexpr int G0 = 9 * WROW;
+  static constexpr int G0B = EW * 4;
+  static constexpr int SLOT_RAW = G0 + G0B;
+  static constexpr int MINB = 4;
+  static_assert(WROW % 16 == 0 && G0B % 16 == 0, "bulk copies: 16-byte sizes and offsets");
 };
 template <>
 struct StashFmt<StF16> : StashFmt16<__half> {};
@@ -124,9 +145,7 @@ template <class S, int NC>
 struct StashCfg {
   using Fmt = StashFmt<S>;
   static_assert(NC == STASH_NC, "the stash formats are laid out for STASH_NC columns");
-  static_assert(Fmt::SLOT_RAW % 16 == 0 && Fmt::PROW % 16 == 0 && Fmt::ROW % 16 == 0 &&
-                    Fmt::LOB % 16 == 0 && Fmt::LO % 16 == 0,
-                "bulk copies: 16-byte sizes and offsets");
+  static_assert(Fmt::SLOT_RAW % 16 == 0, "16-byte slots");
   static constexpr int NCO = NC - 4;          // output columns
   static constexpr int NW = NC / 32;          // warps
   static constexpr int SR = 4;                // stash rows
@@ -139,7 +158,7 @@ struct StashCfg {
   static constexpr int RINGS = (CR + 2 * PR + 2 * NR) * NC * 4 + CR * NC * 2;
   static constexpr int SMEM = STASH + RINGS + SR * 8;
   // resident CTAs per SM the kernel is compiled for (registers)
-  static constexpr int MINB = sizeof(typename Fmt::E) == 4 ? 3 : 4;
+  static constexpr int MINB = Fmt::MINB;
   static_assert(NC % 32 == 0, "whole warps");
 };
 
@@ -260,6 +279,67 @@ __device__ __forceinline__ void wstash_pull_fg16(const InstDev& I, const Phys<fl
   }
 }
 
+// F16MIX: f_i, g_i and hbar_i of a pulled cell with one 8-byte load (the
+// three follow the same neighbour, and the same wall rule but for the
+// anti-bounce-back of hbar), with the rules of pull9 (lbe_tile.cuh) for
+// hbar; g_0 from the FP32 row and its low part from word 0.  c0: the
+// thread's own column in a row.  SUM: as in wstash_pull.
+template <bool SUM>
+__device__ __forceinline__ void wstash_pull_mix(const InstDev& I, const Phys<float>& P,
+                                                const char* slot, int c0, int y, int xw,
+                                                float f[9], float g[9], float h[9],
+                                                float& g0lo) {
+  using Fmt = StashFmt<StMix>;
+  const bool wb = (y == 0), wt = (y == I.ny - 1);
+  const uint2* b = reinterpret_cast<const uint2*>(slot) + c0;
+  const float sg = P.inv_s[1], sh = P.inv_s[2];
+  auto two = [](uint32_t u) {
+    __half2 q;
+    memcpy(&q, &u, 4);
+    return __half22float2(q);
+  };
+  {
+    const uint2 v = b[0];
+    const float2 q = two(v.y);
+    f[0] = __uint_as_float(v.x);
+    h[0] = q.x * sh;
+    g0lo = q.y * G0LO_INV;
+    g[0] = reinterpret_cast<const float*>(slot + Fmt::G0)[c0];
+  }
+  if (!wb && !wt) {  // interior row: constant offsets
+#pragma unroll
+    for (int i = 1; i < 9; i++) {
+      const uint2 v = b[i * Fmt::EW - EX(i)];
+      const float2 q = two(v.y);
+      f[i] = __uint_as_float(v.x);
+      g[i] = q.x * sg;
+      float hv = q.y * sh;
+      if (!SUM && EY(i) == 1) hv -= WGT<float>(i) * P.dh;
+      if (!SUM && EY(i) == -1) hv += WGT<float>(i) * P.dh;
+      h[i] = hv;
+    }
+    return;
+  }
+  const float Tw = wall_T<StMix>(I, xw, wb ? 0 : 1);
+#pragma unroll
+  for (int i = 1; i < 9; i++) {
+    const bool wall = (EY(i) == 1 && wb) || (EY(i) == -1 && wt);
+    const uint2 v = wall ? b[i * Fmt::EW] : b[i * Fmt::EW - EX(i)];
+    const float2 q = two(v.y);
+    f[i] = __uint_as_float(v.x);
+    g[i] = q.x * sg;
+    float hv = q.y * sh;
+    if (wall) {
+      hv = -hv + 2.f * WGT<float>(i) * P.rho * P.cv * Tw;
+    } else if (EY(i) == 1) {
+      hv -= WGT<float>(i) * P.dh;
+    } else if (EY(i) == -1) {
+      hv += WGT<float>(i) * P.dh;
+    }
+    h[i] = hv;
+  }
+}
+
 // True in exactly one lane of the (converged) warp.
 __device__ __forceinline__ bool elect_one() {
   uint32_t e;
@@ -290,7 +370,7 @@ __device__ __forceinline__ CopyPlan copy_plan(const InstDev& I, int parity, int 
       __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(I.buf[parity]), 0));
   const int64_t pitch = bcast64(I.pitch);
   const int e16 = x0 & ~7;
-  const bool w16 = I.storage != ST_F32;
+  const bool w16 = I.storage == ST_F16DEV || I.storage == ST_BF16DEV;
   CopyPlan c;
   c.row8 = pitch * 8;
   c.row4 = pitch * 4;
@@ -312,12 +392,12 @@ __device__ __forceinline__ CopyPlan copy_plan(const InstDev& I, int parity, int 
 //     g_0 low part.
 //   16-bit (20 copies): the 8 pair rows (i = 1..8), f_0, the 9 hbar_i rows,
 //     the FP32 g_0 row, the g_0 low part.
+//   F16MIX (10 copies): the 9 rows of direction words, the FP32 g_0 row.
 // WALL: mr is the first or the last row (else the pulls need no wall rule).
 template <class S, bool WALL>
 __device__ __forceinline__ void issue_row(const CopyPlan& c, uint32_t dst, uint32_t bar, int mr,
                                           int ny) {
   using Fmt = StashFmt<S>;
-  constexpr bool W16 = sizeof(typename Fmt::E) == 2;
   const bool wb = WALL && mr == 0, wt = WALL && mr == ny - 1;
   // source row and plane of population i (the reversed one at a wall)
   auto at = [&](int i, int64_t row) -> int64_t {
@@ -328,7 +408,12 @@ __device__ __forceinline__ void issue_row(const CopyPlan& c, uint32_t dst, uint3
     const bool wall = (EY(i) == 1 && wb) || (EY(i) == -1 && wt);
     return wall ? OPP(i) : i;
   };
-  if constexpr (!W16) {
+  if constexpr (S::kind == ST_F16MIX) {
+#pragma unroll
+    for (int i = 0; i < 9; i++)
+      bulk_load(dst + i * Fmt::WROW, c.pair + pl(i) * c.pp + at(i, c.row8), Fmt::WROW, bar);
+    bulk_load(dst + Fmt::G0, c.g0 + (int64_t)mr * c.row4, Fmt::G0B, bar);
+  } else if constexpr (S::kind == ST_F32) {
 #pragma unroll
     for (int i = 0; i < 9; i++)
       bulk_load(dst + Fmt::off(0, i), c.pair + pl(i) * c.pp + at(i, c.row8), Fmt::PROW, bar);
@@ -346,7 +431,8 @@ __device__ __forceinline__ void issue_row(const CopyPlan& c, uint32_t dst, uint3
       bulk_load(dst + Fmt::off(2, i), c.h + pl(i) * c.pb + at(i, c.row2), Fmt::ROW, bar);
     bulk_load(dst + Fmt::G0, c.g0 + (int64_t)mr * c.row4, Fmt::G0B, bar);
   }
-  bulk_load(dst + Fmt::LO, c.lo + (int64_t)mr * c.row2, Fmt::LOB, bar);
+  if constexpr (S::kind != ST_F16MIX)
+    bulk_load(dst + Fmt::LO, c.lo + (int64_t)mr * c.row2, Fmt::LOB, bar);
 }
 
 template <class S, int NC>
@@ -357,6 +443,7 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
   using Fmt = typename Cfg::Fmt;
   using C = float;
   constexpr bool W16 = sizeof(typename Fmt::E) == 2;
+  constexpr bool MIX = S::kind == ST_F16MIX;
   extern __shared__ __align__(128) char smem[];
   C* cring = reinterpret_cast<C*>(smem + Cfg::STASH);  // [CR][NC]
   C* pring = cring + Cfg::CR * NC;                       // [PR][NC]
@@ -468,21 +555,24 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
       const int r = i - 1;
       if (r >= ya && r < yb && collides) {
         const char* s = slot(r);
-        C f[9], g[9], h[9];
-        if constexpr (!W16) {
-          wstash_pull_fg(I, s, c0, r, f, g);
+        C f[9], g[9], h[9], g0lo;
+        if constexpr (MIX) {
+          wstash_pull_mix<false>(I, P, s, c0, r, x, f, g, h, g0lo);
         } else {
-          wstash_pull_fg16<S>(I, P, s, c0, c0g, r, f, g);
+          if constexpr (!W16) {
+            wstash_pull_fg(I, s, c0, r, f, g);
+          } else {
+            wstash_pull_fg16<S>(I, P, s, c0, c0g, r, f, g);
+          }
+          wstash_pull<S, 2>(I, P, s, c0, c0g, r, x, h);
+          g0lo = __half2float(reinterpret_cast<const __half*>(s + Fmt::LO)[c0lo]) * G0LO_INV;
         }
-        wstash_pull<S, 2>(I, P, s, c0, c0g, r, x, h);
         const int ps = rr(-2), p0 = rr(-1), pn = rr(0);  // rows r-1, r, r+1
         const C* cs = cring + ps;
         const C* c0 = cring + p0;
         const C* cn = cring + pn;
         const C cc = c0[t];
         const C clo = lo_at(clr + p0, t);
-        const C g0lo = __half2float(reinterpret_cast<const __half*>(s + Fmt::LO)[c0lo]) *
-                       G0LO_INV;
         const C pp = pring[p0 + t], TT = Tring[p0 + t];
         Stencils<C> st;
         grad3(cs, c0, cn, t, st.gcx, st.gcy);
@@ -501,13 +591,28 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
         collide<S>(P, f, g, h, cc, pp, TT, st.gpx, st.gpy, d,
                    [&](int k, int ii, C v) { o[k * 9 + ii] = v; }, g0lo, clo, &lo_out);
         const size_t e = (size_t)r * pitch + XG + x;
-        st_g0lo(I, dst, e, lo_out);
-        if constexpr (!W16) {
+        if constexpr (MIX) {
+          // word i: (f_i, g_i, hbar_i); word 0: (f_0, hbar_0, g_0 low part)
+          const float s1 = I.s[1], s2 = I.s[2];
+          auto word = [&](int ii, float fv, float a, float b) {
+            const __half2 q = __floats2half2_rn(a, b);
+            uint32_t u;
+            memcpy(&u, &q, 4);
+            reinterpret_cast<uint2*>(dst + (size_t)ii * I.pair_bytes)[e] =
+                make_uint2(__float_as_uint(fv), u);
+          };
+          word(0, o[0], o[18] * s2, lo_out * G0LO_SCALE);
+#pragma unroll
+          for (int ii = 1; ii < 9; ii++) word(ii, o[ii], o[9 + ii] * s1, o[18 + ii] * s2);
+          reinterpret_cast<float*>(dst + I.g0_off)[e] = o[9];
+        } else if constexpr (!W16) {
+          st_g0lo<S>(I, dst, e, lo_out);
 #pragma unroll
           for (int ii = 0; ii < 9; ii++) S::st_fg(I, dst, ii, e, o[ii], o[9 + ii]);
 #pragma unroll
           for (int ii = 0; ii < 9; ii++) S::st(I, dst, 2, ii, e, o[18 + ii]);
         } else {
+          st_g0lo<S>(I, dst, e, lo_out);
           S::st(I, dst, 0, 0, e, o[0]);
           S::st(I, dst, 1, 0, e, o[9]);
 #pragma unroll
@@ -531,6 +636,16 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
           const int mr = m >= 0 ? m : -1 - m;
           const char* s = slot(m);
           C v[9], vf[9];
+          if constexpr (MIX) {
+            C vh[9], g0lo, clo;
+            wstash_pull_mix<true>(I, P, s, c0, mr, xw, vf, v, vh, g0lo);
+            cring[ci] = moment_c(v, g0lo, clo);
+            clr[ci] = __float2half_rn(clo * G0LO_SCALE);
+            pring[pi] = sum9(vf);
+            C T = dv(sum9(vh), P.rho_cv, P.inv_rho_cv);
+            if (m < 0) T = ghost_T<S>(I, xw, true, T);
+            Tring[pi] = T;
+          } else {
           if constexpr (!W16) {
             wstash_pull_fg(I, s, c0, mr, vf, v);
           } else {
@@ -546,6 +661,7 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
           C T = dv(sum9(v), P.rho_cv, P.inv_rho_cv);
           if (m < 0) T = ghost_T<S>(I, xw, true, T);
           Tring[pi] = T;
+          }
         } else {
           const int mm = 2 * ny - 1 - m;
           cring[ci] = cring[cr(mm) + t];

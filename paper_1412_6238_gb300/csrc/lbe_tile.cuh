@@ -197,7 +197,7 @@ struct Tile {
       pull9<S, 1>(I, P, src, q, g);
       pull9<S, 2>(I, P, src, q, h);
       if constexpr (S::kind != ST_F64) {
-        g0lo = ld_g0lo(I, src, (size_t)gy * I.pitch + XG + gx);
+        g0lo = ld_g0lo<S>(I, src, (size_t)gy * I.pitch + XG + gx);
         cc = moment_c(g, g0lo, clo);
       } else {
         cc = sum9(g);
@@ -279,7 +279,7 @@ struct Tile {
       collide<S>(P, f, g, h, cc, pp, TT, st.gpx, st.gpy, d,
                  [&](int k, int i, C v) { st_cell<S>(I, dst, k, i, rowbase, gx, v); }, g0lo,
                  clo, &lo_out);
-      if constexpr (S::kind != ST_F64) st_cell_g0lo(I, dst, rowbase, gx, (float)lo_out);
+      if constexpr (S::kind != ST_F64) st_cell_g0lo<S>(I, dst, rowbase, gx, (float)lo_out);
     }
   }
 };

@@ -15,7 +15,7 @@ import numpy as np
 
 from . import build as _build
 
-STORAGE = {"f64": 0, "f32": 1, "f16dev": 2, "bf16dev": 3}
+STORAGE = {"f64": 0, "f32": 1, "f16dev": 2, "bf16dev": 3, "f16mix": 4}
 FIELD_NAMES = ("c", "p", "ux", "uy", "T")
 STATUS = {0: "LBE_OK", -1: "LBE_EINVAL", -2: "LBE_ENOMEM", -3: "LBE_ECUDA", -4: "LBE_ENAN",
           -5: "LBE_ETIMEOUT", -6: "LBE_ESTATE"}

@@ -65,15 +65,17 @@ def _run(w, steps, storage):
 
 
 # (case, storage) -> bounds on (u, T) relative L2 at the stated step count
-# measured on GB300: planar FP32 u 9.8e-5, T 3.2e-6; drop FP32 u 1.8e-4,
-# T 3.5e-7; drop FP16 u 3.0e-2, T 2.9e-4 (planar FP16: xfail below)
+# measured on GB300: planar FP32 u 9.3e-5, T 2.8e-6; drop FP32 u 1.9e-4,
+# T 5.0e-7; drop FP16 u 3.0e-2, T 2.9e-4; drop F16MIX u 1.0e-2, T 2.6e-4
+# (planar FP16 and F16MIX: xfail below)
 BOUNDS = {
     ("planar", "f32"): (2e-4, 1e-5), ("planar", "f16dev"): (1e-1, 1e-3),
     ("drop", "f32"): (3e-4, 1e-5), ("drop", "f16dev"): (5e-2, 1e-3),
+    ("planar", "f16mix"): (1e-1, 1e-3), ("drop", "f16mix"): (2e-2, 1e-3),
 }
 # sum c drift over the run, relative: FP32 conserves it to ~1e-9 (two-float
 # g_0); the 16-bit forms round the moving g_i to 11 (FP16) or 8 (BF16) bits
-MASS = {"f32": 1e-6, "f16dev": 1e-3}
+MASS = {"f32": 1e-6, "f16dev": 1e-3, "f16mix": 1e-3}
 
 
 @pytest.mark.parametrize("name", ["planar", "drop"])
@@ -93,14 +95,15 @@ def test_fp64_end_state_is_the_oracles(name):
 
 
 F16_PLANAR = pytest.mark.xfail(
-    reason="FP16 storage does not resolve the slow planar Marangoni flow over "
-           "100 000 steps (measured: u error 1.4, T 4.2e-2 relative L2)", strict=False)
+    reason="FP16 hbar storage does not resolve the slow planar Marangoni flow over "
+           "100 000 steps (measured, FP16DEV and F16MIX alike: u error 1.4-1.5, T 4.2e-2 "
+           "relative L2)", strict=False)
 
 
 @pytest.mark.parametrize("name", ["planar", "drop"])
-@pytest.mark.parametrize("storage", ["f32", pytest.param("f16dev", marks=[])])
+@pytest.mark.parametrize("storage", ["f32", "f16dev", "f16mix"])
 def test_storage_end_state_error(name, storage, request):
-    if (name, storage) == ("planar", "f16dev"):
+    if name == "planar" and storage in ("f16dev", "f16mix"):
         request.applymarker(F16_PLANAR)
     G = _golden(name)
     (w, steps, stride, desc), _ = _case(name)
@@ -113,7 +116,8 @@ def test_storage_end_state_error(name, storage, request):
     assert abs(float(F["c"].sum()) - G["sum_c"]) < MASS[storage] * abs(G["sum_c"])
 
 
-@pytest.mark.parametrize("storage,bu,bT", [("f64", 1e-10, 1e-10), ("f16dev", 1e-1, 1e-3)])
+@pytest.mark.parametrize("storage,bu,bT", [("f64", 1e-10, 1e-10), ("f16dev", 1e-1, 1e-3),
+                                           ("f16mix", 1e-3, 1e-3)])
 def test_sweep_instances_inside_the_batch(storage, bu, bT):
     """The 64-instance sweep advanced 10 000 steps in one launch per step;
     the instances with stored oracle end states compared."""

@@ -8,6 +8,7 @@ Bounds (relative L2 over the domain, velocity as a vector):
                 measured one-step u error 1.8e-7); 2e-5 on u for the slow
                 512 x 256 planar flow
   FP16-deviation storage  1e-3 (u, T) on the short drop run
+  F16MIX (FP32 f, FP16 g and hbar deviations)  1e-3 on T and c, 1e-4 on u
   BF16-deviation: measured, 2e-2
 """
 import numpy as np
@@ -21,9 +22,9 @@ pytestmark = pytest.mark.gpu
 
 # relative L2 against the FP64 oracle: FP64 1e-12, FP32 1e-5 (u, T and c),
 # FP16 deviations 1e-3, BF16 deviations 2e-2
-TOL = {"f64": 1e-12, "f32": 1e-5, "f16dev": 1e-3, "bf16dev": 2e-2}
-TOL_U = dict(TOL)
-STATE_TOL = {"f64": 1e-15, "f32": 1e-7, "f16dev": 1e-3, "bf16dev": 1e-2}
+TOL = {"f64": 1e-12, "f32": 1e-5, "f16dev": 1e-3, "bf16dev": 2e-2, "f16mix": 1e-3}
+TOL_U = dict(TOL, f16mix=1e-4)
+STATE_TOL = {"f64": 1e-15, "f32": 1e-7, "f16dev": 1e-3, "bf16dev": 1e-2, "f16mix": 1e-3}
 
 
 @pytest.fixture(scope="module")
@@ -49,7 +50,7 @@ def state_err(a, b):
     return max(out)
 
 
-@pytest.mark.parametrize("storage", ["f64", "f32", "f16dev", "bf16dev"])
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16dev", "bf16dev", "f16mix"])
 def test_initial_state_matches_oracle(LBE, orc, storage):
     w = small_drop()
     sim = LBE(w, storage=storage)
@@ -76,6 +77,23 @@ def test_state_roundtrip(LBE, orc, storage):
         g0, r0 = got[9], ref[9]
         assert np.abs(g0 - r0).max() <= 2e-11 * max(1.0, np.abs(r0).max())
         assert state_err(got, ref) < 1e-7
+
+
+def test_state_roundtrip_f16mix(LBE, orc):
+    """F16MIX holds f as FP32 values (bitwise the FP32 rounding), g_0 as an
+    FP32 value plus its FP16-coded low part, g_1..g_8 and the hbar
+    deviations as scaled FP16 values."""
+    w = small_drop()
+    sim = LBE(w, storage="f16mix")
+    ref = orc.run(w.params, orc.init(w.params, w.c0, w.T0, w.Tbot, w.Ttop), w.Tbot, w.Ttop, 5)
+    sim.set_state(ref)
+    got = sim.get_state().numpy()
+    assert np.array_equal(got[:9], ref[:9].astype(np.float32).astype(np.float64))
+    g0, r0 = got[9], ref[9]
+    assert np.abs(g0 - r0).max() <= 2e-11 * max(1.0, np.abs(r0).max())
+    for k in (1, 2):
+        s = np.abs(ref[9 * k:9 * k + 9]).max()
+        assert np.abs(got[9 * k:9 * k + 9] - ref[9 * k:9 * k + 9]).max() < 1e-3 * s
 
 
 SHAPES = [(5, 7), (4, 8), (1, 6), (2, 3), (33, 9), (100, 37), (96, 64), (130, 19)]
@@ -124,7 +142,7 @@ STRIP_SHAPES = [(4, 8), (5, 3), (7, 40), (64, 17), (130, 19), (200, 33), (257, 7
 
 
 @pytest.mark.parametrize("nx,ny", STRIP_SHAPES)
-@pytest.mark.parametrize("storage", ["f32", "f16dev", "bf16dev"])
+@pytest.mark.parametrize("storage", ["f32", "f16dev", "bf16dev", "f16mix"])
 @pytest.mark.parametrize("seg", [1, 3, 0])
 def test_strip_kernel_equals_tile_kernel(LBE, storage, nx, ny, seg):
     """The stash strip kernel (id 7) on
@@ -156,6 +174,7 @@ def test_strip_is_default_and_rejects_narrow(LBE):
     w = small_drop()
     assert LBE(w, storage="f32").get_tile()["kernel"] == 7
     assert LBE(w, storage="f16dev").get_tile()["kernel"] == 7
+    assert LBE(w, storage="f16mix").get_tile()["kernel"] == 7
     assert LBE(w, storage="f64").get_tile()["kernel"] == 0
     narrow = wl.droplet(3, 20, 1.5, 1.5, 10.0, Re=1.0, Ma=10.0, Ca=0.05, eta_m=0.2, eta_r=1.0,
                         lam_r=1.0)
@@ -177,7 +196,7 @@ def test_graph_replay_equals_single_launches(LBE):
     assert a.steps_done == b.steps_done == 10
 
 
-@pytest.mark.parametrize("storage", ["f64", "f32", "f16dev", "bf16dev"])
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16dev", "bf16dev", "f16mix"])
 def test_droplet_run_parity(LBE, orc, storage):
     """300 steps of a migrating drop (viscosity ratio 0.5, conductivity ratio
     2) on a 70 x 45 grid: fields within the storage's bound."""
@@ -189,6 +208,7 @@ def test_droplet_run_parity(LBE, orc, storage):
     G = oracle_fields(orc, w, orc.run(w.params, orc.init(w.params, w.c0, w.T0, w.Tbot, w.Ttop),
                                       w.Tbot, w.Ttop, n))
     e = field_errors(F, G)
+    print(storage, n, "steps:", e)
     tol = TOL[storage]
     assert e["u"] < TOL_U[storage] and e["T"] < tol and e["c"] < tol, e
 
@@ -206,7 +226,7 @@ def test_layered_poiseuille_f64_full_run(LBE, orc):
     assert max(e["u"], e["T"], e["c"]) < 1e-12, e
 
 
-@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16mix"])
 def test_planar_marangoni_parity(LBE, orc, storage):
     """The 512 x 256 planar Marangoni problem, 1000 steps."""
     w = wl.planar_marangoni()
@@ -217,11 +237,15 @@ def test_planar_marangoni_parity(LBE, orc, storage):
     G = oracle_fields(orc, w, orc.run(w.params, orc.init(w.params, w.c0, w.T0, w.Tbot, w.Ttop),
                                       w.Tbot, w.Ttop, n))
     e = field_errors(F, G)
+    print(storage, "planar", n, "steps:", e)
     # FP32: the flow here is slow (Re = Ma ~ 1e-3, u ~ 1e-6) and driven by
     # grad T along the interface, which carries the FP32 rounding of the
-    # O(1) temperature deviation: u is within 1.5e-5 after 1000 steps
-    tol_u = 2e-5 if storage == "f32" else TOL_U[storage]
-    assert e["u"] < tol_u and e["T"] < TOL[storage], e
+    # O(1) temperature deviation: u is within 1.5e-5 after 1000 steps.
+    # F16MIX keeps the hbar deviations (amplitude 4) in FP16, which this slow
+    # flow resolves only to the percent (measured: u 1.8e-2, T 2.8e-3)
+    tol_u = {"f32": 2e-5, "f16mix": 3e-2}.get(storage, TOL_U[storage])
+    tol_T = {"f16mix": 5e-3}.get(storage, TOL[storage])
+    assert e["u"] < tol_u and e["T"] < tol_T, e
 
 
 def test_fields_f32_and_device_outputs(LBE, orc):
@@ -310,7 +334,7 @@ def test_batch_of_uneven_instances_matches_each_alone(LBE, orc):
         assert max(e["u"], e["T"], e["c"]) < 1e-12, (j, e)
 
 
-@pytest.mark.parametrize("storage", ["f32", "f16dev"])
+@pytest.mark.parametrize("storage", ["f32", "f16dev", "f16mix"])
 def test_mass_drift_long_run(LBE, storage):
     """sum c over 20 000 steps of two planar fluids (128 x 64, Marangoni
     flow).  The FP64 path conserves it to rounding; in FP32 the uniform bulk
