@@ -19,11 +19,13 @@
 // Iteration i (from ya - 4 to yb):
 //   barrier; 1. collide row i-1 (S2-S9 of lbe_cell.cuh) from its stash slot
 //      and the moment rings, and store its 27 values;
+//   barrier; one elected lane issues the copies of row i+3 into the slot
+//      that row i-1 has just freed (as early as possible: the copies then
+//      have the rest of this iteration and the next collision to land);
 //   2. wait for the copies of row i+2 and form its moments c, p, T (S1) into
 //      the rings; rows below the bottom wall use the pulled values of their
 //      mirror row, rows above the top wall copy the mirror rows in the rings;
-//   barrier; 3. one elected lane issues the copies of row i+3 into the slot
-//      that row i-1 has just freed; 4. unit normal of row i+1 (S2).
+//   barrier; 4. unit normal of row i+1 (S2).
 // Every population is read from HBM once per step.  Every mbarrier wait is
 // bounded: on time-out the kernel sets *err, waits (bounded) for the copies
 // in flight and returns.
@@ -624,6 +626,10 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
         // step, not here: the branch costs this kernel about 7 %)
       }
 
+      // every thread is done with the slot of row i - 1: copies of row i + 3
+      __syncthreads();
+      issue(i + 3);
+
       // ---- 2. moments of row m = i + 2
       const int m = i + 2;
       if (!wait_row(m)) {
@@ -672,9 +678,6 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
       }
       __syncthreads();
       if (s_abort) break;
-
-      // ---- 3. the copies of row i + 3 (into the slot of row i - 1)
-      issue(i + 3);
 
       // ---- 4. unit normal of row i + 1
       const int mn = i + 1;
