@@ -173,9 +173,10 @@ lbe_status lbe_load(lbe_handle* h, const char* path);
 /* Step-kernel choice (autotuner hook).  Kernel ids 0 .. lbe_num_tiles()-1:
  * ids whose shape has ty > 0 are the tile kernel with TX x TY cells per CTA
  * (any storage; FP64 provides id 0 only); id 7 (ty == 0) is the strip kernel
- * with 124 output columns per CTA marching over rows, each warp staging its
- * own pulled populations (16/32-bit storages, every instance at least 4
- * columns wide; the default there); ids 5 and 6 are retired and rejected.
+ * with 124 output columns per CTA marching over rows, staging each row's
+ * pulled populations in shared memory with bulk copies (16/32-bit and
+ * F16MIX storages, every instance at least 4 columns wide; the default
+ * there); ids 5 and 6 are retired and rejected.
  * grid_ctas: persistent grid size (0 = resident CTAs x SMs, -1 = one CTA per
  * work item).  seg_rows: rows per strip work item (0 = chosen from the wave
  * count, at most 96).  LBE_EINVAL for a kernel the handle cannot use.

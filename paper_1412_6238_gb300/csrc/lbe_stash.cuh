@@ -626,11 +626,12 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
         // step, not here: the branch costs this kernel about 7 %)
       }
 
-      // every thread is done with the slot of row i - 1: copies of row i + 3
+      // ---- 2. the copies of row i + 3 into the slot of row i - 1, which
+      // every thread is done with
       __syncthreads();
       issue(i + 3);
 
-      // ---- 2. moments of row m = i + 2
+      // ---- 3. moments of row m = i + 2
       const int m = i + 2;
       if (!wait_row(m)) {
         s_abort = 1;
@@ -652,21 +653,21 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
             if (m < 0) T = ghost_T<S>(I, xw, true, T);
             Tring[pi] = T;
           } else {
-          if constexpr (!W16) {
-            wstash_pull_fg(I, s, c0, mr, vf, v);
-          } else {
-            wstash_pull_fg16<S>(I, P, s, c0, c0g, mr, vf, v);
-          }
-          const C g0lo =
-              __half2float(reinterpret_cast<const __half*>(s + Fmt::LO)[c0lo]) * G0LO_INV;
-          C clo;
-          cring[ci] = moment_c(v, g0lo, clo);
-          clr[ci] = __float2half_rn(clo * G0LO_SCALE);
-          pring[pi] = sum9(vf);
-          wstash_pull<S, 2, true>(I, P, s, c0, c0g, mr, xw, v);
-          C T = dv(sum9(v), P.rho_cv, P.inv_rho_cv);
-          if (m < 0) T = ghost_T<S>(I, xw, true, T);
-          Tring[pi] = T;
+            if constexpr (!W16) {
+              wstash_pull_fg(I, s, c0, mr, vf, v);
+            } else {
+              wstash_pull_fg16<S>(I, P, s, c0, c0g, mr, vf, v);
+            }
+            const C g0lo =
+                __half2float(reinterpret_cast<const __half*>(s + Fmt::LO)[c0lo]) * G0LO_INV;
+            C clo;
+            cring[ci] = moment_c(v, g0lo, clo);
+            clr[ci] = __float2half_rn(clo * G0LO_SCALE);
+            pring[pi] = sum9(vf);
+            wstash_pull<S, 2, true>(I, P, s, c0, c0g, mr, xw, v);
+            C T = dv(sum9(v), P.rho_cv, P.inv_rho_cv);
+            if (m < 0) T = ghost_T<S>(I, xw, true, T);
+            Tring[pi] = T;
           }
         } else {
           const int mm = 2 * ny - 1 - m;

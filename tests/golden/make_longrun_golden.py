@@ -18,6 +18,8 @@ Cases (``python tests/golden/make_longrun_golden.py <case> ...``):
   drop      drop migration, 512 x 1024, R = 32, 40 000 steps (Sec. IV.C)
   sweep00   first 128 x 256 instance of the 64-drop parameter sweep, 10 000 steps
   sweep01   first 256 x 512 instance of the sweep, 10 000 steps
+  sweep02   first 512 x 1024 instance of the sweep, 10 000 steps
+  sweep03   first 768 x 1536 instance of the sweep, 10 000 steps
 """
 import hashlib
 import json
@@ -55,6 +57,12 @@ def case(name):
     if name == "sweep01":
         j, w = _sweep_instance((256, 512))
         return w, 10000, 8, "batch_sweep(64, seed=0)[%d] 256x512" % j
+    if name == "sweep02":
+        j, w = _sweep_instance((512, 1024))
+        return w, 10000, 16, "batch_sweep(64, seed=0)[%d] 512x1024" % j
+    if name == "sweep03":
+        j, w = _sweep_instance((768, 1536))
+        return w, 10000, 24, "batch_sweep(64, seed=0)[%d] 768x1536" % j
     raise ValueError(name)
 
 

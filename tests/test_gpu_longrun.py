@@ -4,8 +4,9 @@ make_longrun_golden.py from the oracle alone):
 
   planar   two planar fluids with Marangoni convection, 512 x 256, 100 000 steps
   drop     drop migration, 512 x 1024, 40 000 steps
-  sweep00, sweep01   instances of the 64-drop parameter sweep, 10 000 steps,
-           run inside the whole 64-instance batch (one launch per step)
+  sweep00..sweep03   one instance of each grid size of the 64-drop parameter
+           sweep, 10 000 steps, run inside the whole 64-instance batch (one
+           launch per step)
 
 FP64: the end state is bitwise the oracle's (when the inputs are bitwise the
 ones the golden was made from; else within 1e-10).  FP32 and the 16-bit
@@ -128,7 +129,7 @@ def test_sweep_instances_inside_the_batch(storage, bu, bT):
     from paper_1412_6238_gb300.lbe import LBE
     ws = W.batch_sweep(64, seed=0, steps=10000)
     goldens = {}
-    for name in ("sweep00", "sweep01"):
+    for name in ("sweep00", "sweep01", "sweep02", "sweep03"):
         path = os.path.join(HERE, "golden", "longrun_%s.json" % name)
         if os.path.exists(path):
             G = json.load(open(path))

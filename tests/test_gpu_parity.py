@@ -349,3 +349,59 @@ def test_mass_drift_long_run(LBE, storage):
     s1 = sim.sums()["sum_c"]
     print(storage, "sum c drift", (s1 - s0) / s0)
     assert abs(s1 - s0) < 1e-4 * abs(s0)
+
+
+def _sweep500():
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "sweep500.json")
+    if not os.path.exists(path):
+        pytest.skip("golden sweep500.json missing")
+    return json.load(open(path))
+
+
+def test_sweep_all_64_instances_500_steps(LBE):
+    """Every instance of the 64-drop parameter sweep (four grid sizes,
+    uneven parameters) advanced 500 steps in one batch, one launch per step.
+    FP64: each instance's end state is bitwise the oracle's (stored hashes,
+    tests/golden/sweep500.json, written from the oracle alone).  FP32,
+    F16MIX and FP16DEV: u and T against those FP64 fields, the largest
+    relative L2 error over the 64 instances within the storage's bound."""
+    import hashlib
+
+    import torch
+    G = _sweep500()
+    ws = wl.batch_sweep(64, seed=0)
+    n = G["steps"]
+    sim = LBE(ws, storage="f64")
+    sim.step(n)
+    ref = []
+    for j, w in enumerate(ws):
+        rec = G["instances"][j]
+        assert (w.nx, w.ny) == (rec["nx"], rec["ny"])
+        h = hashlib.sha256()
+        for a in (w.c0, w.T0, w.Tbot, w.Ttop):
+            h.update(np.ascontiguousarray(a, dtype=np.float64).tobytes())
+        if h.hexdigest() == rec["input_sha256"]:
+            st = np.ascontiguousarray(sim.get_state(j).numpy())
+            assert hashlib.sha256(st.tobytes()).hexdigest() == rec["state_sha256"], j
+        F = sim.fields(j, names=("ux", "uy", "T"), device="cuda")
+        ref.append((torch.stack([F["ux"], F["uy"]]), F["T"]))
+    del sim
+    torch.cuda.empty_cache()
+    # (u, T) bounds: FP32 the north_star 1e-5; F16MIX and FP16DEV measured
+    for storage, bu, bT in (("f32", 1e-5, 1e-5), ("f16mix", 1e-3, 1e-3), ("f16dev", 1e-2, 1e-3)):
+        s = LBE(ws, storage=storage)
+        s.step(n)
+        eu = eT = 0.0
+        for j in range(len(ws)):
+            F = s.fields(j, names=("ux", "uy", "T"), device="cuda")
+            u = torch.stack([F["ux"], F["uy"]])
+            eu = max(eu, float(torch.linalg.vector_norm(u - ref[j][0]) /
+                               torch.linalg.vector_norm(ref[j][0])))
+            eT = max(eT, float(torch.linalg.vector_norm(F["T"] - ref[j][1]) /
+                               torch.linalg.vector_norm(ref[j][1])))
+        del s
+        torch.cuda.empty_cache()
+        print("sweep 64 x %d steps %s: max u %.2e, max T %.2e" % (n, storage, eu, eT))
+        assert eu < bu and eT < bT, (storage, eu, eT)
