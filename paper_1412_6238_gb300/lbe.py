@@ -215,23 +215,43 @@ class LBE:
         self._check(self._L.lbe_get_tile(self._h, out))
         return dict(kernel=out[0], grid=out[1], seg_rows=out[2], items=out[3])
 
-    def fields(self, instance: int = 0, names=FIELD_NAMES, dtype=None, device="cuda"):
-        """Dict of torch tensors (ny, nx) for the requested fields."""
+    def fields(self, instance: int = 0, names=FIELD_NAMES, dtype=None, device="cuda", out=None):
+        """Dict of torch tensors (ny, nx) for the requested fields.
+
+        out: optional dict of preallocated contiguous (ny, nx) tensors (float64
+        or float32, all of one dtype and all on the host or all on the GPU;
+        pinned host memory makes the copy a direct DMA), written in place and
+        returned; its keys are the fields to export."""
         import torch
-        dtype = torch.float64 if dtype is None else dtype
         ny, nx = self.shapes[instance]
-        dev = torch.device(device)
-        on_dev = dev.type == "cuda"
-        out = {}
         ptrs = (ctypes.c_void_p * 5)()
         mask = 0
-        for k, name in enumerate(FIELD_NAMES):
-            if name in names:
-                t = torch.empty((ny, nx), dtype=dtype, device=dev,
-                                pin_memory=False)
-                out[name] = t
-                ptrs[k] = t.data_ptr()
-                mask |= 1 << k
+        if out is not None:
+            ts = list(out.values())
+            if not ts or any(k not in FIELD_NAMES for k in out):
+                raise ValueError("out: a dict of fields among %s" % (FIELD_NAMES,))
+            dtype = ts[0].dtype
+            on_dev = ts[0].is_cuda
+            for t in ts:
+                if (tuple(t.shape) != (ny, nx) or t.dtype != dtype or t.is_cuda != on_dev
+                        or not t.is_contiguous() or dtype not in (torch.float64, torch.float32)):
+                    raise ValueError("out: contiguous (%d, %d) float64 or float32 tensors of "
+                                     "one dtype and one device kind" % (ny, nx))
+            for k, name in enumerate(FIELD_NAMES):
+                if name in out:
+                    ptrs[k] = out[name].data_ptr()
+                    mask |= 1 << k
+        else:
+            dtype = torch.float64 if dtype is None else dtype
+            dev = torch.device(device)
+            on_dev = dev.type == "cuda"
+            out = {}
+            for k, name in enumerate(FIELD_NAMES):
+                if name in names:
+                    t = torch.empty((ny, nx), dtype=dtype, device=dev)
+                    out[name] = t
+                    ptrs[k] = t.data_ptr()
+                    mask |= 1 << k
         self._check(self._L.lbe_fields(self._h, int(instance), mask, ptrs, int(on_dev),
                                        0 if dtype == torch.float64 else 1))
         return out

@@ -261,6 +261,18 @@ def test_fields_f32_and_device_outputs(LBE, orc):
         assert torch.equal(F64[k], Fd[k].cpu())
     part = sim.fields(names=("T",), device="cpu")
     assert list(part) == ["T"] and torch.equal(part["T"], F64["T"])
+    # in place: pinned host buffers and device buffers, FP64 and FP32
+    ny, nx = F64["c"].shape
+    pinned = {k: torch.empty((ny, nx), dtype=torch.float64).pin_memory() for k in ("c", "uy")}
+    assert sim.fields(out=pinned) is pinned
+    dev32 = {k: torch.empty((ny, nx), dtype=torch.float32, device="cuda") for k in ("ux", "T")}
+    sim.fields(out=dev32)
+    for k in pinned:
+        assert torch.equal(pinned[k], F64[k])
+    for k in dev32:
+        assert torch.equal(dev32[k].cpu(), F32[k])
+    with pytest.raises(ValueError):
+        sim.fields(out={"c": torch.empty((ny + 1, nx), dtype=torch.float64)})
 
 
 def test_sums_mass_conservation_and_residual(LBE, orc):
