@@ -1,5 +1,7 @@
 // Discrete adjoint (vector-Jacobian product) of one FP64 step, and the
-// drop-migration observable.
+// drop-migration observable.  (The adjoint recomputes the forward step with
+// reciprocal products where the step divides, so it differentiates the step
+// at a state equal to the FP64 one to rounding, not bitwise.)
 //
 // The step maps the pre-collision state Q_n (27 planes, [27][ny][nx]) to
 // Q_{n+1} = Pull(Post(Q_n; theta)); Post is the collision of every cell,
@@ -37,6 +39,7 @@ namespace adj {
 constexpr int TPB = 256;
 constexpr int RBLK = 304;  // blocks of the deterministic reductions
 constexpr double CS2 = 1.0 / 3.0;
+constexpr double ICS2 = 3.0;  // 1 / c_s^2: products instead of FP64 divisions
 
 struct Geo {
   int nx, ny;
@@ -76,15 +79,15 @@ __device__ __forceinline__ void grad_at(Fn v, int x, int y, double& gx, double& 
     sx += WGT<double>(i) * EX(i) * a;
     sy += WGT<double>(i) * EY(i) * a;
   }
-  gx = sx / CS2;
-  gy = sy / CS2;
+  gx = sx * ICS2;
+  gy = sy * ICS2;
 }
 template <class Fn>
 __device__ __forceinline__ double lap_at(Fn v, int x, int y) {
   const double v0 = v(x, y);
   double s = 0.0;
   for (int i = 1; i < 9; i++) s += WGT<double>(i) * (v(x + EX(i), y + EY(i)) - v0);
-  return 2.0 * s / CS2;
+  return 2.0 * s * ICS2;
 }
 
 // ---------------------------------------------------------------- M, N, P
@@ -209,8 +212,10 @@ pass_A(Geo G, const InstDev* __restrict__ d, const double* __restrict__ Q,
     jy = jy - f[7];
     jy = jy - f[8];
     const double rho = P.rho, rcs2 = P.rcs2;
-    const double ux = jx / rcs2 + 0.5 * Fx / rho;
-    const double uy = jy / rcs2 + 0.5 * Fy / rho;
+    // reciprocals once per cell: the FP64 divisions dominated this pass
+    const double irc = 1.0 / rcs2, irho = 1.0 / rho;
+    const double ux = jx * irc + 0.5 * Fx * irho;
+    const double uy = jy * irc + 0.5 * Fy * irho;
     if (MODE == 0) {
       acc[0] += cc * uy;
       acc[1] += cc;
@@ -218,17 +223,18 @@ pass_A(Geo G, const InstDev* __restrict__ d, const double* __restrict__ Q,
     }
     const double eta = P.eta1 + cc * P.deta;
     const double lam = P.lam1 + cc * P.dlam;
-    const double tau_f = eta / rcs2 + 0.5;
+    const double tau_f = eta * irc + 0.5;
     const double omega_f = 1.0 / tau_f;
-    const double tau_h = lam / P.rcvcs2;
+    const double ircv = 1.0 / P.rcvcs2;
+    const double tau_h = lam * ircv;
     const double omega_T = 2.0 / (2.0 * tau_h + 1.0);
     const double omega_g = P.omega_g;
     const double af = 1.0 - 0.5 * omega_f, ag = 1.0 - 0.5 * omega_g, aT = 1.0 - 0.5 * omega_T;
-    const double uu = (ux * ux + uy * uy) / CS2;
+    const double uu = (ux * ux + uy * uy) * ICS2;
     const double Gm = P.Gm;
     const double W0 = WGT<double>(0);
-    const double Hi = Gm * mu / CS2;
-    const double H0 = (cc - (1.0 - W0) * Gm * mu / CS2) / W0;
+    const double Hi = Gm * mu * ICS2;
+    const double H0 = (cc - (1.0 - W0) * Gm * mu * ICS2) * (1.0 / W0);
     const double Gx = Fx - gpx, Gy = Fy - gpy;
     const double rcvT = P.rho * P.cv * TT;
 
@@ -238,7 +244,7 @@ pass_A(Geo G, const InstDev* __restrict__ d, const double* __restrict__ Q,
     double uub = 0, Hib = 0, H0b = 0, rcvTb = 0, wfb = 0, wTb = 0, afb = 0, aTb = 0;
     for (int i = 0; i < 9; i++) {
       const double W = WGT<double>(i);
-      const double xu = (EX(i) * ux + EY(i) * uy) / CS2;
+      const double xu = (EX(i) * ux + EY(i) * uy) * ICS2;
       const double hq = 0.5 * (xu * xu - uu);
       const double Gam = W * (1.0 + xu + hq);
       const double q = xu + hq;
@@ -249,9 +255,9 @@ pass_A(Geo G, const InstDev* __restrict__ d, const double* __restrict__ Q,
       const double Hx = (i == 0 ? H0 : Hi);
       const double geq = W * (Hx + cc * q);
       const double gdot = dx * Gx + dy * Gy;
-      const double sgv = cc * gdot / rcs2;
+      const double sgv = cc * gdot * irc;
       const double heq = rcvT * Gam;
-      const double shv = (Gx * dx + Gy * dy) / rcs2;
+      const double shv = (Gx * dx + Gy * dy) * irc;
       const double hs = shv * heq;
       const double bf = b[(int64_t)i * G.N + k], bg = b[(int64_t)(9 + i) * G.N + k],
                    bh = b[(int64_t)(18 + i) * G.N + k];
@@ -264,10 +270,11 @@ pass_A(Geo G, const InstDev* __restrict__ d, const double* __restrict__ Q,
       aTb += bh * hs;
       const double shb = hsb * heq;
       heqb += hsb * shv;
-      Gxb += shb * dx / rcs2;
-      Gyb += shb * dy / rcs2;
-      dxb += shb * Gx / rcs2;
-      dyb += shb * Gy / rcs2;
+      const double shr = shb * irc;
+      Gxb += shr * dx;
+      Gyb += shr * dy;
+      dxb += shr * Gx;
+      dyb += shr * Gy;
       rcvTb += heqb * Gam;
       Gamb += heqb * rcvT;
       // g: go = g - wg (g - geq) + ag gs, gs = (c gdot / rcs2) Gam
@@ -276,11 +283,12 @@ pass_A(Geo G, const InstDev* __restrict__ d, const double* __restrict__ Q,
       const double gsb = bg * ag;
       const double sgb = gsb * Gam;
       Gamb += gsb * sgv;
-      cb += sgb * gdot / rcs2;
-      Gxb += sgb * cc * dx / rcs2;
-      Gyb += sgb * cc * dy / rcs2;
-      dxb += sgb * cc * Gx / rcs2;
-      dyb += sgb * cc * Gy / rcs2;
+      const double sgr = sgb * irc, sgc = sgr * cc;
+      cb += sgr * gdot;
+      Gxb += sgc * dx;
+      Gyb += sgc * dy;
+      dxb += sgc * Gx;
+      dyb += sgc * Gy;
       if (i == 0) H0b += geqb * W; else Hib += geqb * W;
       cb += geqb * W * q;
       qb += geqb * W * cc;
@@ -305,24 +313,24 @@ pass_A(Geo G, const InstDev* __restrict__ d, const double* __restrict__ Q,
       hqb += Gamb * W + qb;
       xub += hqb * xu;
       uub -= 0.5 * hqb;
-      uxb += xub * EX(i) / CS2;
-      uyb += xub * EY(i) / CS2;
+      uxb += xub * EX(i) * ICS2;
+      uyb += xub * EY(i) * ICS2;
     }
     Tb += rcvTb * P.rho * P.cv;
     Fxb += Gxb;
     Fyb += Gyb;
     double gpxb = -Gxb, gpyb = -Gyb;
-    double mub = Hib * Gm / CS2;
-    cb += H0b / W0;
-    mub -= H0b * (1.0 - W0) * Gm / (CS2 * W0);
-    uxb += uub * 2.0 * ux / CS2;
-    uyb += uub * 2.0 * uy / CS2;
+    double mub = Hib * Gm * ICS2;
+    cb += H0b * (1.0 / W0);
+    mub -= H0b * (1.0 - W0) * Gm * (ICS2 / W0);
+    uxb += uub * 2.0 * ux * ICS2;
+    uyb += uub * 2.0 * uy * ICS2;
     wTb -= 0.5 * aTb;
     wfb -= 0.5 * afb;
     const double tauhb = -wTb * omega_T * omega_T;
-    const double lamb = tauhb / P.rcvcs2;
+    const double lamb = tauhb * ircv;
     const double taufb = -wfb * omega_f * omega_f;
-    const double etab = taufb / rcs2;
+    const double etab = taufb * irc;
     cb += etab * P.deta + lamb * P.dlam;
     double th_eta = etab * cc * P.eta1;  // d eta / d (eta2/eta1) = c eta1
     double th_lam = lamb * cc * P.lam1;
@@ -333,9 +341,9 @@ pass_A(Geo G, const InstDev* __restrict__ d, const double* __restrict__ Q,
       uyb += wl * cc / B;
     }
     // u = j/(rho cs2) + F/(2 rho)
-    const double jxb = uxb / rcs2, jyb = uyb / rcs2;
-    Fxb += 0.5 * uxb / rho;
-    Fyb += 0.5 * uyb / rho;
+    const double jxb = uxb * irc, jyb = uyb * irc;
+    Fxb += 0.5 * uxb * irho;
+    Fyb += 0.5 * uyb * irho;
     for (int i = 0; i < 9; i++) fb[i] += EX(i) * jxb + EY(i) * jyb;
     // F = cap gc + mar (g2 gT - cdT gc) + rho a
     const double capb = Fxb * gcx + Fyb * gcy;
