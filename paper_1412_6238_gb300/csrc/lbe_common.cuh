@@ -211,8 +211,8 @@ struct StDev {
 struct StMix {
   using C = float;
   static constexpr int kind = ST_F16MIX;
-  __device__ static __forceinline__ const char* word(const InstDev& I, const char* b, int i,
-                                                     size_t idx) {
+  template <class B>  // const char or char
+  __device__ static __forceinline__ B* word(const InstDev& I, B* b, int i, size_t idx) {
     return b + (size_t)i * I.pair_bytes + 8 * idx;
   }
   // byte offset of (k, i) in its word (k >= 1)
@@ -228,7 +228,7 @@ struct StMix {
   }
   __device__ static __forceinline__ void st(const InstDev& I, char* b, int k, int i, size_t idx,
                                             C v) {
-    char* w = const_cast<char*>(word(I, b, i, idx));
+    char* w = word(I, b, i, idx);
     if (k == 0) {
       *reinterpret_cast<float*>(w) = v;
     } else if (k == 1 && i == 0) {

@@ -274,11 +274,12 @@ def test_adjoint_golden_reference_gradient_32x64():
         assert abs(r["grad"][j] - G[key]) <= 1e-6 * abs(G[key]), (key, r["grad"][j], G[key])
 
 
-def test_adjoint_f32_forward(orc, tiny_adjoint):
-    """FP32 storage forward (strip kernel), FP64 reverse sweep: within the
-    FP32 trajectory error of the FP64 gradient."""
+@pytest.mark.parametrize("storage", ["f32", "f16mix"])
+def test_adjoint_f32_forward(orc, tiny_adjoint, storage):
+    """FP32 (or F16MIX) storage forward (strip kernel), FP64 reverse sweep:
+    within the trajectory error of the FP64 gradient."""
     w, r, _, _ = tiny_adjoint
-    sim = _sim(w, "f32")
+    sim = _sim(w, storage)
     r32 = sim.adjoint(TINY_STEPS, TINY_WINDOW, TINY_K, want_dT0=True)
     sim.close()
     assert abs(r32["loss"] - r["loss"]) <= 1e-4 * abs(r["loss"])
