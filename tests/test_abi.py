@@ -84,3 +84,16 @@ def test_null_handle_calls():
     assert L.lbe_num_instances(None) == 0
     L.lbe_destroy(None)
     assert L.lbe_set_tile(None, 0, 0, 0) == -1
+
+
+def test_storage_names_match_the_header_enum():
+    """The binding's storage names carry the values of lbe_storage."""
+    src = open(os.path.join(ROOT, "include", "lbe.h")).read()
+    body = re.search(r"typedef enum \{(.*?)\} lbe_storage;", src, flags=re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    enum = {k: int(v) for k, v in re.findall(r"(LBE_\w+)\s*=\s*(\d+)", body)}
+    names = {"f64": "LBE_F64", "f32": "LBE_F32", "f16dev": "LBE_F16DEV",
+             "bf16dev": "LBE_BF16DEV", "f16mix": "LBE_F16MIX"}
+    assert set(lbe.STORAGE) == set(names)
+    for k, c in names.items():
+        assert lbe.STORAGE[k] == enum[c], k
