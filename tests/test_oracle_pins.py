@@ -396,6 +396,28 @@ def test_mirror_symmetry(orc):
     assert np.abs(F["uy"]).max() > 1e-6
 
 
+def test_periodic_translation_invariance(orc):
+    """Periodic x (Sec. IV): shifting every input by k columns (c0, T0 and
+    the non-uniform wall temperatures) shifts the whole run by k columns,
+    bitwise.  A wrong index in the periodic wrap of the pull or of a
+    stencil breaks it."""
+    nx, ny, k = 28, 20, 9
+    w = wl.droplet(nx, ny, 5.0, 11.3, 8.6, Re=1.0, Ma=10.0, Ca=0.05, eta_m=0.2,
+                   eta_r=0.5, lam_r=2.0)
+    x = np.arange(nx)
+    Tbot = w.Tbot + 0.01 * np.cos(2 * np.pi * x / nx)
+    Ttop = w.Ttop + 0.02 * np.sin(4 * np.pi * x / nx)
+    runs = []
+    for shift in (0, k):
+        r = lambda a: np.ascontiguousarray(np.roll(a, shift, axis=-1))  # noqa: E731
+        pop = orc.init(w.params, r(w.c0), r(w.T0), r(Tbot), r(Ttop))
+        out = orc.run(w.params, pop, r(Tbot), r(Ttop), 40)
+        runs.append(orc.fields(w.params, out, r(Tbot), r(Ttop)))
+    for f in ("c", "p", "ux", "uy", "T"):
+        assert np.array_equal(np.roll(runs[0][f], k, axis=1), runs[1][f]), f
+    assert np.abs(runs[0]["ux"]).max() > 1e-7
+
+
 def test_planar_interface_at_rest(orc):
     """A planar tanh interface (the equilibrium profile of Sec. II) at uniform
     T stays at rest (|u| < 1e-9) and settles on the scheme's discrete
