@@ -138,8 +138,12 @@ class LBE:
     """One handle of the library: one instance, or a batch advanced together.
 
     ``problems``: a workload (object with ``params``, ``c0``, ``T0``,
-    ``Tbot``, ``Ttop``) or a list of them.  ``stream``: a torch CUDA stream
-    (default: a new non-default stream, so that steps can be graph-captured).
+    ``Tbot``, ``Ttop``) or a list of them.  ``storage``: how the populations
+    are held between steps (arithmetic is FP64 for "f64", FP32 otherwise):
+    "f64" (bitwise the FP64 oracle), "f32", "f16mix" (FP32 f, FP16 g and
+    hbar deviations), "f16dev" / "bf16dev" (16-bit deviations, FP32 g_0).
+    ``stream``: a torch CUDA stream (default: a new non-default stream, so
+    that steps can be graph-captured).
     """
 
     def __init__(self, problems, storage: str = "f32", stream=None, check_every: int = 0):
