@@ -271,6 +271,32 @@ def test_conduction_linear_profile_exact(orc):
         assert np.abs(T - exact).max() < 1e-11, lam
 
 
+def test_conduction_harmonic_wall_temperature(orc):
+    """Uniform conductivity, no flow, a bottom wall temperature varying along
+    x, T_bot(x) = cos(k x), T_top = 0: the steady state is the harmonic
+    T = cos(k x) sinh(k (Y_t - y)) / sinh(k (Y_t - Y_b)) with the walls at
+    Y_b = -1/2 and Y_t = ny - 1/2 (halfway walls, wall temperature at the
+    fluid node's x: reading R9).  Second order: halving the cell size at
+    fixed k L cuts the error by about 4 (measured: 2.7e-2 at 32 x 16, 7.9e-3
+    at 64 x 32; a wall on the nodes instead would give first order)."""
+    errs = []
+    for nx, ny in ((32, 16), (64, 32)):
+        k = 2 * math.pi / nx
+        par = wl.base_params(nx, ny, lam1=0.5, lam2=0.5)
+        x = np.arange(nx, dtype=float)
+        Tb, Tt = np.cos(k * x), np.zeros(nx)
+        pop = orc.init(par, np.zeros((ny, nx)), np.zeros((ny, nx)), Tb, Tt)
+        D = 0.5  # lambda / (rho c_v)
+        pop = orc.run(par, pop, Tb, Tt, int(12 * ny * ny / D))
+        T = orc.fields(par, pop, Tb, Tt)["T"]
+        y = np.arange(ny, dtype=float)[:, None]
+        Yb, Yt = -0.5, ny - 0.5
+        exact = np.cos(k * x)[None, :] * np.sinh(k * (Yt - y)) / np.sinh(k * (Yt - Yb))
+        errs.append(float(np.sqrt(((T - exact) ** 2).sum() / (exact ** 2).sum())))
+    assert errs[0] < 3.5e-2 and errs[1] < 1e-2, errs
+    assert 3.0 < errs[0] / errs[1] < 5.0, errs
+
+
 def test_shear_wave_viscosity(orc):
     """A decaying shear wave u_y = A sin(k x) (periodic in x and y) decays at
     nu k^2 with nu = cs2 (tau_f - 1/2) (Sec. II, eta = rho cs2 (tau_f - 1/2))."""
