@@ -60,6 +60,7 @@ def _init(params, storage="f32"):
     (dict(ny=1), "ny"), (dict(nx=0), "nx"), (dict(tau_g=0.5), "tau_g"),
     (dict(eta1=0.0), "eta1"), (dict(eps=-1.0), "eps"), (dict(eta_n=0.0), "eta_n"),
     (dict(lam2=-1e-3), "lam"), (dict(rho=0.0), "rho"), (dict(sigmaT=float("nan")), "non-finite"),
+    (dict(nx=65536, ny=65537), "2^31"),
 ])
 def test_invalid_parameters_rejected(bad, msg):
     st, err, h = _init(bad)
@@ -67,8 +68,16 @@ def test_invalid_parameters_rejected(bad, msg):
 
 
 def test_invalid_storage_rejected():
-    st, err, h = _init({}, storage=7)
-    assert st == -1 and "storage" in err
+    for bad in (7, -1, 5):
+        st, err, h = _init({}, storage=bad)
+        assert st == -1 and "storage" in err, bad
+    # every named storage passes validation (no GPU here: it fails later, at
+    # the device, not as an unknown storage)
+    for name in lbe.STORAGE:
+        st, err, h = _init({}, storage=name)
+        if h.value:
+            lbe.library().lbe_destroy(h)
+        assert st == 0 or "storage" not in err, (name, err)
 
 
 def test_alloc_failure_injected_on_host(monkeypatch):
