@@ -60,3 +60,25 @@ def test_reference_arm_other_ranks_print_nothing(capsys):
     args = argparse.Namespace(steps=3, warmup=3, gpus=2)
     bench.run_reference(args, 2, 1)
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line(capsys):
+    """Rank 0 of the reference arm prints one JSON line with the keys of the
+    benchmark contract; its value is the FP64 oracle timed on the host."""
+    import argparse
+    import json
+
+    import bench
+    args = argparse.Namespace(steps=1, warmup=1, gpus=1)
+    bench.run_reference(args, 1, 0)
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+              "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
