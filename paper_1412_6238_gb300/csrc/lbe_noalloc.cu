@@ -32,7 +32,29 @@ static __device__ __align__(256) double na_partials[NA_MAX_BLOCKS * 6];
 
 constexpr int MAX_DEVICES = 64;
 std::mutex na_mutex;
-double* na_ptr[MAX_DEVICES] = {};  // device address of na_partials per device
+// device address of na_partials per device, and the context it was looked up
+// in (a caller that makes another context current on the device, through the
+// driver API, gets the array's address in that context)
+double* na_ptr[MAX_DEVICES] = {};
+void* na_ctx[MAX_DEVICES] = {};
+
+// The current driver context, through the runtime's driver entry point (no
+// link dependency on the driver library); nullptr if unavailable.
+void* na_current_context() {
+  using GetCurrent = int (*)(void**);
+  static GetCurrent fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<GetCurrent>(f);
+  }();
+  void* ctx = nullptr;
+  if (!fn || fn(&ctx) != 0) return nullptr;
+  return ctx;
+}
 
 // errors are reported like those of the other calls: lbe_last_error(NULL)
 lbe_status na_fail(lbe_status st, const char* msg) {
@@ -121,12 +143,16 @@ extern "C" lbe_status lbe_sums_fields_noalloc(const double* const cur[5],
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES)
     return na_fail(LBE_ECUDA, "no usable current CUDA device");
+  // an error left on this thread by earlier, unrelated work is not ours
+  (void)cudaGetLastError();
   double* partial;
   {
-    // set-up, once per device, with that device current: the host-side name
-    // na_partials is only a stand-in, the kernels need the device address
+    // set-up, once per device (and context), with that device current: the
+    // host-side name na_partials is only a stand-in, the kernels need the
+    // device address
     std::lock_guard<std::mutex> lock(na_mutex);
-    if (!na_ptr[dev]) {
+    void* ctx = na_current_context();
+    if (!na_ptr[dev] || na_ctx[dev] != ctx) {
       void* p = nullptr;
       cudaError_t e = cudaGetSymbolAddress(&p, na_partials);
       if (e != cudaSuccess || !p) {
@@ -135,6 +161,7 @@ extern "C" lbe_status lbe_sums_fields_noalloc(const double* const cur[5],
         return na_fail(LBE_ECUDA, m);
       }
       na_ptr[dev] = static_cast<double*>(p);
+      na_ctx[dev] = ctx;
     }
     partial = na_ptr[dev];
   }
@@ -142,14 +169,16 @@ extern "C" lbe_status lbe_sums_fields_noalloc(const double* const cur[5],
   Fields5 f;
   for (int k = 0; k < 5; k++) f.f[k] = cur[k];
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  auto launched = [](const char* which) -> lbe_status {
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) return LBE_OK;
+    char m[256];
+    snprintf(m, sizeof m, "lbe_sums_fields_noalloc %s launch: %s", which, cudaGetErrorString(e));
+    return na_fail(LBE_ECUDA, m);
+  };
   na_pass1<<<nb, NA_THREADS, 0, s>>>(f, prev ? prev[2] : nullptr, prev ? prev[3] : nullptr, n,
                                      partial);
+  if (lbe_status st = launched("pass 1")) return st;
   na_pass2<<<1, NA_THREADS, 0, s>>>(partial, nb, rho_cv, prev ? 1 : 0, out);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) {
-    char m[256];
-    snprintf(m, sizeof m, "lbe_sums_fields_noalloc launch: %s", cudaGetErrorString(e));
-    return na_fail(LBE_ECUDA, m);
-  }
-  return LBE_OK;
+  return launched("pass 2");
 }
