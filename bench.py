@@ -34,10 +34,14 @@ sys.path.insert(0, ROOT)
 METRIC = "coupled-LBE MLUPS & % HBM roofline; mixed/batched vs plain FP32 at stated error"
 UNIT = "MLUPS"
 NX = NY = 4096
-# algorithmic bytes per cell update: every population read once and written
-# once (FP64: 27 x 8; FP32: 27 x 4 plus the FP16 low part of g_0; 16-bit
-# forms: 26 x 2 plus the FP32 g_0 and its FP16 low part), both directions
-BYTES_PER_CELL = {"f64": 432, "f32": 220, "f16dev": 116, "bf16dev": 116, "f16mix": 152}
+# algorithmic bytes per cell update: the 27 populations read once and written
+# once in the storage's element size (FP64: 27 x 8; FP32: 27 x 4; 16-bit
+# deviation forms: 26 x 2 + the FP32 g_0; F16MIX: 9 FP32 f + 8 FP16 g + the
+# FP32 g_0 + 9 FP16 hbar), both directions
+BYTES_PER_CELL = {"f64": 432, "f32": 216, "f16dev": 112, "bf16dev": 112, "f16mix": 148}
+# bytes the storage moves beyond the populations: the FP16 low part of g_0
+# (read and written) in every form but FP64
+OVERHEAD_BYTES_PER_CELL = {"f64": 0, "f32": 4, "f16dev": 4, "bf16dev": 4, "f16mix": 4}
 PROFILE = os.path.join(ROOT, "profiles", "lbe_step_f32_droplet_4096x4096.md")
 
 
@@ -214,6 +218,41 @@ def oracle_sample(target_s: float = 12.0, steps: int | None = None, warmup: int 
                       "(%.1f s)" % (n, dt)}
 
 
+def oracle_configs():
+    """The oracle-timing workloads: the five-problem set's grids that the
+    oracle runs (thermal two-layer Poiseuille 4 x 101, planar Marangoni
+    512 x 256, drop 512 x 1024, the first instance of the 64-drop sweep)."""
+    from paper_1412_6238_gb300 import workloads as wl
+    s0 = wl.batch_sweep(64, seed=0)[0]
+    return [("layered_poiseuille_4x101", wl.layered_poiseuille()),
+            ("planar_marangoni_512x256", wl.planar_marangoni()),
+            ("droplet_512x1024", wl.droplet_512x1024()),
+            ("sweep_instance0_%dx%d" % (s0.nx, s0.ny), s0)]
+
+
+def oracle_timings(target_s: float = 1.5):
+    """Oracle MLUPS at one thread and at all host cores on each workload of
+    oracle_configs(), each a bounded run of about target_s seconds."""
+    import oracle
+    out = []
+    for name, w in oracle_configs():
+        pop0 = oracle.init(w.params, w.c0, w.T0, w.Tbot, w.Ttop)
+        for threads in (1, 0):
+            oracle.set_threads(threads)
+            t = time.perf_counter()
+            pop = oracle.run(w.params, pop0, w.Tbot, w.Ttop, 1)
+            one = time.perf_counter() - t
+            n = max(1, min(200000, int(target_s / max(one, 1e-6))))
+            t = time.perf_counter()
+            oracle.run(w.params, pop, w.Tbot, w.Ttop, n)
+            dt = time.perf_counter() - t
+            out.append({"workload": name, "cells": w.cells, "threads": oracle.num_threads(),
+                        "steps": n, "seconds": round(dt, 3),
+                        "MLUPS": w.cells * n / dt / 1e6})
+    oracle.set_threads(0)
+    return out
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -308,6 +347,8 @@ def run_ours(args, ws, rank, local):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample()
+        cpu["per_workload"] = oracle_timings()
+        cpu["host_cores"] = len(os.sched_getaffinity(0))
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
@@ -327,7 +368,12 @@ def run_ours(args, ws, rank, local):
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
                              "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                              "peak_kind": peak_kind,
-                             "algorithmic_bytes_per_launch": algo_bytes},
+                             "algorithmic_bytes_per_launch": algo_bytes,
+                             "algorithmic_bytes_per_cell": BYTES_PER_CELL[args.storage],
+                             "overhead_bytes_per_cell": OVERHEAD_BYTES_PER_CELL[args.storage],
+                             "frac_with_overhead": cells * (BYTES_PER_CELL[args.storage] +
+                                                            OVERHEAD_BYTES_PER_CELL[args.storage])
+                                                   / (launch_ms / 1e3) / 1e9 / peak},
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "variants": variants,
                 # the stash kernel's step is two launches (step + ghost columns)
                 "gpu_launches": args.steps * (2 if kernel["kernel"] == 7 else 1),

@@ -74,6 +74,8 @@ def lib():
             L.orc_lattice.restype = None
             L.orc_num_threads.argtypes = []
             L.orc_num_threads.restype = ctypes.c_int
+            L.orc_set_threads.argtypes = [ctypes.c_int]
+            L.orc_set_threads.restype = None
             _lib = L
     return _lib
 
@@ -113,6 +115,11 @@ def lattice():
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_threads(n: int) -> None:
+    """OpenMP threads of the following calls (0: one per processor)."""
+    lib().orc_set_threads(int(n))
 
 
 def init(params: dict, c0, T0, Tbot, Ttop) -> np.ndarray:

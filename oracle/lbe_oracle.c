@@ -530,3 +530,14 @@ int orc_num_threads(void) {
   return 1;
 #endif
 }
+
+/* Threads for the following calls (n <= 0: one per processor), for the
+ * one-thread and all-core timings of the CPU baseline.  The arithmetic and
+ * its result do not depend on it. */
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+  omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
+#else
+  (void)n;
+#endif
+}
