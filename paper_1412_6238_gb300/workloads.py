@@ -68,8 +68,71 @@ def eps_from_width(W: float) -> float:
     return W / (4.0 * math.sqrt(2.0))
 
 
+# The transcendental functions of the input fields are evaluated with IEEE
+# basic operations only (+, -, *, /, rounding to an integer and exact scaling
+# by powers of two), each correctly rounded on every platform, so that the
+# inputs -- and the hashes of stored FP64 end states -- are bitwise the same
+# on every machine.  (numpy's own tanh and cos differ in the last bits
+# between its x86 SIMD and Arm builds.)
+_INV_LN2 = 1.0 / math.log(2.0)
+_LN2_HI = 6.93147180369123816490e-01  # ln 2 with its low 32 mantissa bits zero
+_LN2_LO = 1.90821492927058770002e-10  # ln 2 - _LN2_HI
+_EXP_C = [1.0 / math.factorial(n) for n in range(14)]
+_COS_C = [(-1.0) ** n / math.factorial(2 * n) for n in range(10)]
+_SIN_C = [(-1.0) ** n / math.factorial(2 * n + 1) for n in range(9)]
+
+
+def det_exp(x) -> np.ndarray:
+    """exp(x): x = k ln 2 + r with |r| <= ln2/2 (Cody-Waite split of ln 2,
+    k ln2_hi exact for |k| < 2^21), Taylor polynomial of degree 13 in r
+    (truncation below 1e-17 relative), times 2^k (overflow to inf, underflow
+    through the subnormals to 0)."""
+    # beyond +-1100 the result is inf or 0 either way
+    x = np.clip(np.asarray(x, dtype=np.float64), -1100.0, 1100.0)
+    k = np.round(x * _INV_LN2)
+    r = (x - k * _LN2_HI) - k * _LN2_LO
+    p = np.full_like(r, _EXP_C[13])
+    for n in range(12, -1, -1):
+        p = p * r + _EXP_C[n]
+    with np.errstate(over="ignore", under="ignore"):
+        return np.ldexp(p, k.astype(np.int64))
+
+
+def det_cos2pi(q) -> np.ndarray:
+    """cos(2 pi q): q reduced to [-1/2, 1/2] and to the first octant by exact
+    differences, then the Taylor polynomial of cos or sin (degree 18 / 17,
+    |argument| <= pi/4, truncation below 1e-17)."""
+    q = np.asarray(q, dtype=np.float64)
+    a = np.abs(q - np.round(q))
+    two_pi = 2.0 * math.pi
+
+    def cos_p(t):
+        s = t * t
+        p = np.full_like(t, _COS_C[9])
+        for n in range(8, -1, -1):
+            p = p * s + _COS_C[n]
+        return p
+
+    def sin_p(t):
+        s = t * t
+        p = np.full_like(t, _SIN_C[8])
+        for n in range(7, -1, -1):
+            p = p * s + _SIN_C[n]
+        return t * p
+
+    out = np.empty_like(a)
+    m1 = a <= 0.125
+    m3 = a > 0.375
+    m2 = ~(m1 | m3)
+    out[m1] = cos_p(two_pi * a[m1])
+    out[m2] = sin_p(two_pi * (0.25 - a[m2]))
+    out[m3] = -cos_p(two_pi * (0.5 - a[m3]))
+    return out
+
+
 def tanh_profile(d: np.ndarray, W: float) -> np.ndarray:
-    return 0.5 * (1.0 + np.tanh(2.0 * d / W))
+    """(1 + tanh(2 d / W)) / 2, evaluated as 1 / (1 + exp(-4 d / W))."""
+    return 1.0 / (1.0 + det_exp(-4.0 * np.asarray(d, dtype=np.float64) / W))
 
 
 def linear_T(nx: int, ny: int, Tbot, Ttop) -> np.ndarray:
@@ -136,7 +199,7 @@ def planar_marangoni(nx: int = 512, ny: int = 256, eta=0.2, lam_upper=0.2,
     d = (np.arange(ny, dtype=np.float64) - yi)[:, None] * np.ones((1, nx))
     c0 = np.ascontiguousarray(tanh_profile(d, W))
     x = np.arange(nx, dtype=np.float64)
-    Tb = Th + Tr * np.cos(2 * np.pi * x / nx)
+    Tb = Th + Tr * det_cos2pi(x / nx)
     Tt = np.full(nx, float(Tc))
     return Workload("planar_marangoni_%dx%d" % (nx, ny), p, c0,
                     linear_T(nx, ny, Tb, Tt), Tb, Tt, steps,
