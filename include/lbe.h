@@ -38,7 +38,22 @@
  *   - All work is ordered on one CUDA stream per handle (the caller's, or a
  *     private non-blocking stream when NULL is passed).  Waits on the host are
  *     bounded (LBE_TIMEOUT_MS environment variable, default 600000 ms) and
- *     return LBE_ETIMEOUT rather than blocking forever.
+ *     return LBE_ETIMEOUT rather than blocking forever; the work stays
+ *     enqueued and a later wait may still succeed.
+ *   - The strip kernel's waits for its shared-memory copies are bounded too
+ *     (2^22 polls).  A wait that runs out sets a device error word; the CTA
+ *     issues no further copy, drains (bounded) the copies it has in flight
+ *     and returns.  Every later call that waits (lbe_step with check_every,
+ *     lbe_synchronize, lbe_fields, lbe_sums, lbe_get_state, lbe_save, the
+ *     adjoint calls) then returns LBE_ECUDA, and the handle refuses to step
+ *     until lbe_set_state or lbe_load gives it a new state (which clears the
+ *     word).
+ *   - Fault injection on the host, for tests (LBE_FAULT environment variable,
+ *     read by lbe_init / lbe_init_batch): "alloc" makes the call fail as an
+ *     out-of-memory would, before any device work; "withhold:<row>" makes the
+ *     first strip-kernel step of the handle stage nothing for row <row> (its
+ *     slot's barrier still expects the bytes) and give up a copy wait after
+ *     2^12 polls, so that the path above runs without any GPU fault.
  */
 #ifndef LBE_H
 #define LBE_H
@@ -261,12 +276,16 @@ void lbe_destroy(lbe_handle* h);
  *              ||u - u_prev|| / ||u|| (0 without prev), non-finite count
  *   stream     cudaStream_t the two kernels are enqueued on (asynchronous).
  * Its only scratch is a static 384 KiB device array inside the library, held
- * by every GPU that loads it until the process exits; n must be at most
+ * by every GPU that loads it until the process exits (or the device is
+ * reset); n must be at most
  * 33,554,432 (LBE_EINVAL otherwise, message from lbe_last_error(NULL)).  No
  * call allocates or frees memory.  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress) with that device current, so
- * make that first call before any stream capture.  All calls on a device
- * share the array: calls that overlap on the GPU (other streams, other
+ * make that first call before any stream capture; a call made while another
+ * driver context is current on the device looks the address up again for
+ * that context.  A cudaDeviceReset after the first call is not supported (the
+ * module is reloaded and the cached address may be stale).  All calls on a
+ * device share the array: calls that overlap on the GPU (other streams, other
  * threads) race and must be serialized by the caller. */
 lbe_status lbe_sums_fields_noalloc(const double* const cur[5], const double* const prev[5],
                                    int64_t n, double rho_cv, double* out, void* stream);

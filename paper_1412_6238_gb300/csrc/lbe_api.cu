@@ -50,6 +50,9 @@ struct lbe_handle {
   int seg_req = 0;               // strip kernel: rows per work item (0 = auto)
   int seg = 0;
   int* d_err = nullptr;          // device error word (strip kernel wait time-outs)
+  uint32_t* d_seed = nullptr;    // step counter (random bits of the stochastic rounding)
+  int poll_lim = STASH_POLLS;    // polls of one bounded copy wait
+  int withhold = -1;             // test hook: source row whose copies are not issued
   int64_t total_tiles = 0;
   int max_ny = 0;                // largest ny of the instances
   int parity = 0;
@@ -103,7 +106,7 @@ bool fault_alloc() {
 }
 
 // Bounded wait for all work enqueued on the handle's stream so far.
-lbe_status wait(lbe_handle* h) {
+lbe_status wait_stream(lbe_handle* h) {
   CU(h, cudaEventRecord(h->ev, h->stream));
   const auto t0 = std::chrono::steady_clock::now();
   const long lim = timeout_ms();
@@ -122,15 +125,41 @@ lbe_status wait(lbe_handle* h) {
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
-// Bounded wait, then the device error word of the strip kernel.
-lbe_status wait_checked(lbe_handle* h) {
-  lbe_status st = wait(h);
+// Device -> host copy at the end of the handle's stream.  A copy into pageable
+// host memory blocks the calling thread until the stream reaches it, so the
+// stream is first waited for with the bounded wait; the copy then waits only
+// for its own transfer.
+lbe_status to_host(lbe_handle* h, void* dst, const void* src, size_t bytes) {
+  lbe_status st = wait_stream(h);
+  if (st) return st;
+  CU(h, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, h->stream));
+  return LBE_OK;
+}
+
+// Bounded wait, then the device error word of the strip kernel: a copy wait
+// that ran out in any step since the word was last cleared (lbe_init,
+// lbe_set_state, lbe_load) makes every later wait report LBE_ECUDA.
+lbe_status wait(lbe_handle* h) {
+  lbe_status st = wait_stream(h);
   if (st || !h->d_err) return st;
   int e = 0;
   CU(h, cudaMemcpyAsync(&e, h->d_err, sizeof e, cudaMemcpyDeviceToHost, h->stream));
-  if ((st = wait(h))) return st;
-  if (e) return fail(h, LBE_ECUDA, "a strip-kernel copy wait timed out (device error word %d)", e);
+  if ((st = wait_stream(h))) return st;
+  if (e)
+    return fail(h, LBE_ECUDA,
+                "a strip-kernel copy wait ran out of its poll limit (device error word %d); the "
+                "state is lost: set a state or load a checkpoint",
+                e);
   return LBE_OK;
+}
+
+// LBE_FAULT=withhold:<row> (test hook): the strip kernel issues no copies of
+// source row <row>, and a copy wait gives up after STASH_POLLS_TEST polls.
+int fault_withhold() {
+  const char* s = getenv("LBE_FAULT");
+  if (!s || strncmp(s, "withhold:", 9) != 0) return -1;
+  const int r = atoi(s + 9);
+  return r >= 0 ? r : -1;
 }
 
 lbe_status check_params(const lbe_params& p, int index) {
@@ -171,6 +200,7 @@ void fill_desc(lbe_handle* h, int j, InstDev& D) {
   D.f0_off = H.f0_off;
   D.buf[0] = H.arena;
   D.buf[1] = H.arena + H.buf_bytes;
+  D.salt = (uint32_t)j;
   D.Tbot = H.walls;
   D.Ttop = H.walls + H.nx;
   Phys<double>& P = D.pd;
@@ -250,6 +280,7 @@ void free_handle(lbe_handle* h) {
   }
   if (h->d_inst) cudaFree(h->d_inst);
   if (h->d_err) cudaFree(h->d_err);
+  if (h->d_seed) cudaFree(h->d_seed);
   if (h->d_finst) cudaFree(h->d_finst);
   if (h->scratch) cudaFree(h->scratch);
   if (h->d_partial) cudaFree(h->d_partial);
@@ -346,14 +377,25 @@ lbe_status setup_tiles(lbe_handle* h) {
 
 cudaError_t launch_one_step(lbe_handle* h, int parity) {
   if (is_strip(h->tile)) {
+    // the withhold test hook applies to one launch (never inside a graph:
+    // run_steps launches that step directly)
+    const int wh = h->withhold, pl = h->poll_lim;
+    if (wh >= 0) {
+      h->withhold = -1;
+      h->poll_lim = STASH_POLLS;
+    }
     cudaError_t e = launch_stash(h->storage, h->d_inst, h->n, h->total_tiles, h->seg, parity,
-                                 h->grid, h->d_err, h->stream);
-    // the stash kernel leaves the periodic ghost columns to ghost_kernel
-    if (e == cudaSuccess) e = launch_ghosts(h->d_inst, h->n, h->max_ny, parity ^ 1, h->stream);
+                                 h->grid, h->d_err, pl, wh, h->d_seed, h->stream);
+    // the stash kernel leaves the periodic ghost columns to ghost_kernel,
+    // which also advances the step counter
+    if (e == cudaSuccess)
+      e = launch_ghosts(h->d_inst, h->n, h->max_ny, parity ^ 1, h->d_seed, h->stream);
     return e;
   }
-  return launch_step(h->storage, h->tile, h->d_inst, h->n, h->total_tiles, parity, h->grid,
-                     h->stream);
+  cudaError_t e = launch_step(h->storage, h->tile, h->d_inst, h->n, h->total_tiles, parity,
+                              h->grid, h->d_seed, h->stream);
+  if (e == cudaSuccess) e = launch_seed_tick(h->d_seed, h->stream);
+  return e;
 }
 
 lbe_status launch_steps_direct(lbe_handle* h, int64_t k) {
@@ -390,7 +432,12 @@ void ensure_graph(lbe_handle* h) {
 
 lbe_status run_steps(lbe_handle* h, int64_t k) {
   if (k <= 0) return LBE_OK;
-  if (h->parity == 1) {
+  if (h->withhold >= 0 && is_strip(h->tile)) {  // test hook: this step outside the graph
+    lbe_status st = launch_steps_direct(h, 1);
+    if (st) return st;
+    k--;
+  }
+  if (k > 0 && h->parity == 1) {
     lbe_status st = launch_steps_direct(h, 1);
     if (st) return st;
     k--;
@@ -437,7 +484,7 @@ lbe_status sums6(lbe_handle* h, int j, double out6[6]) {
   if (hp && (st = compute_fields(h, j, h->parity ^ 1, prev))) return st;
   cudaError_t e = launch_sums(cur, hp ? prev : nullptr, N, h->d_partial, h->d_sums, h->stream);
   if (e != cudaSuccess) return fail(h, LBE_ECUDA, "sums kernel: %s", cudaGetErrorString(e));
-  CU(h, cudaMemcpyAsync(out6, h->d_sums, 6 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  if ((st = to_host(h, out6, h->d_sums, 6 * sizeof(double)))) return st;
   return wait(h);
 }
 
@@ -587,6 +634,10 @@ lbe_status create(int32_t n, const lbe_params* params, const lbe_init_fields* in
   }
   CUB(cudaMalloc(&h->d_err, sizeof(int)));
   CUB(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
+  CUB(cudaMalloc(&h->d_seed, sizeof(uint32_t)));
+  CUB(cudaMemsetAsync(h->d_seed, 0, sizeof(uint32_t), h->stream));
+  h->withhold = fault_withhold();
+  if (h->withhold >= 0) h->poll_lim = STASH_POLLS_TEST;
   {
     // default kernel: the stash strip kernel where it applies (16/32-bit
     // storage, every instance at least XG columns wide), else the tile kernel
@@ -668,7 +719,7 @@ lbe_status adjoint_run(lbe_handle* h, const lbe_adjoint_spec& sp, double* loss, 
                           cudaMemcpyDeviceToDevice, h->stream));
     const int64_t len = std::min(K, NS - sg * K);
     if ((st = run_steps(h, len))) return st;
-    if ((st = wait_checked(h))) return st;
+    if ((st = wait(h))) return st;
   }
   const int fin_parity = h->parity;
   CU(h, cudaMemcpyAsync(fin.p, cur_buf(), H.buf_bytes, cudaMemcpyDeviceToDevice, h->stream));
@@ -683,6 +734,9 @@ lbe_status adjoint_run(lbe_handle* h, const lbe_adjoint_spec& sp, double* loss, 
     const int64_t n1 = (sg == nseg - 1) ? NS : n0 + K - 1;
     CU(h, cudaMemcpyAsync(cur_buf(), ck.p + (size_t)sg * H.buf_bytes, H.buf_bytes,
                           cudaMemcpyDeviceToDevice, h->stream));
+    // the step counter as in the forward run, so that the stochastic
+    // rounding of a 16-bit storage recomputes the same states
+    CU(h, launch_seed_set(h->d_seed, (uint32_t)(steps0 + n0), h->stream));
     cudaError_t e = launch_pull(h->storage, d1, nx, ny, states.d(), h->parity, h->stream);
     for (int64_t t = 1; e == cudaSuccess && t <= n1 - n0; t++) {
       if ((st = launch_steps_direct(h, 1))) return st;
@@ -700,30 +754,32 @@ lbe_status adjoint_run(lbe_handle* h, const lbe_adjoint_spec& sp, double* loss, 
       have_next = true;
     }
     if (e != cudaSuccess) return fail(h, LBE_ECUDA, "adjoint sweep: %s", cudaGetErrorString(e));
-    if ((st = wait_checked(h))) return st;
+    if ((st = wait(h))) return st;
   }
   // a_nxt = dL/dQ_0
   if (dT0) {
     double* dst = on_device ? dT0 : scr.d();
     cudaError_t e = launch_adjoint_dT0(d1, nx, ny, a_nxt, dst, h->stream);
     if (e != cudaSuccess) return fail(h, LBE_ECUDA, "dT0 kernel: %s", cudaGetErrorString(e));
-    if (!on_device)
-      CU(h, cudaMemcpyAsync(dT0, dst, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream));
+    if (!on_device && (st = to_host(h, dT0, dst, sizeof(double) * N))) return st;
   }
-  if (dQ0)
-    CU(h, cudaMemcpyAsync(dQ0, a_nxt, sizeof(double) * S27,
-                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                          h->stream));
+  if (dQ0) {
+    if (on_device)
+      CU(h, cudaMemcpyAsync(dQ0, a_nxt, sizeof(double) * S27, cudaMemcpyDeviceToDevice,
+                            h->stream));
+    else if ((st = to_host(h, dQ0, a_nxt, sizeof(double) * S27)))
+      return st;
+  }
   std::vector<double> hobs(4 * (size_t)W), hth(4);
-  CU(h, cudaMemcpyAsync(hobs.data(), obs, sizeof(double) * 4 * W, cudaMemcpyDeviceToHost,
-                        h->stream));
-  CU(h, cudaMemcpyAsync(hth.data(), theta, sizeof(double) * 4, cudaMemcpyDeviceToHost, h->stream));
+  if ((st = to_host(h, hobs.data(), obs, sizeof(double) * 4 * W))) return st;
+  if ((st = to_host(h, hth.data(), theta, sizeof(double) * 4))) return st;
   // back to the state after the forward run
   h->parity = fin_parity;
   CU(h, cudaMemcpyAsync(cur_buf(), fin.p, H.buf_bytes, cudaMemcpyDeviceToDevice, h->stream));
   h->steps = steps0 + NS;
+  CU(h, launch_seed_set(h->d_seed, (uint32_t)h->steps, h->stream));
   h->prev_valid = false;
-  if ((st = wait_checked(h))) return st;
+  if ((st = wait(h))) return st;
   if (loss) {
     double L = 0.0;
     for (int64_t j = 0; j < W; j++) L += hobs[4 * j] / hobs[4 * j + 1];
@@ -782,7 +838,7 @@ lbe_status lbe_step(lbe_handle* h, int64_t nsteps) {
 
 lbe_status lbe_synchronize(lbe_handle* h) {
   if (!h) return fail(nullptr, LBE_EINVAL, "handle is NULL");
-  return wait_checked(h);
+  return wait(h);
 }
 
 lbe_status lbe_fields(lbe_handle* h, int32_t instance, uint32_t mask, void* const dst[5],
@@ -803,20 +859,22 @@ lbe_status lbe_fields(lbe_handle* h, int32_t instance, uint32_t mask, void* cons
     if (!(mask >> k & 1u)) continue;
     const double* src = cur + k * N;
     if (dtype == 0) {
-      CU(h, cudaMemcpyAsync(dst[k], src, sizeof(double) * N,
-                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                            h->stream));
+      if (on_device)
+        CU(h, cudaMemcpyAsync(dst[k], src, sizeof(double) * N, cudaMemcpyDeviceToDevice,
+                              h->stream));
+      else if ((st = to_host(h, dst[k], src, sizeof(double) * N)))
+        return st;
     } else if (on_device) {
       cudaError_t e = launch_f64_to_f32(src, reinterpret_cast<float*>(dst[k]), N, h->stream);
       if (e != cudaSuccess) return fail(h, LBE_ECUDA, "cast kernel: %s", cudaGetErrorString(e));
     } else {
       cudaError_t e = launch_f64_to_f32(src, tmp32, N, h->stream);
       if (e != cudaSuccess) return fail(h, LBE_ECUDA, "cast kernel: %s", cudaGetErrorString(e));
-      CU(h, cudaMemcpyAsync(dst[k], tmp32, sizeof(float) * N, cudaMemcpyDeviceToHost, h->stream));
+      if ((st = to_host(h, dst[k], tmp32, sizeof(float) * N))) return st;
       if ((st = wait(h))) return st;  // tmp32 is reused by the next field
     }
   }
-  return wait_checked(h);
+  return wait(h);
 }
 
 lbe_status lbe_sums(lbe_handle* h, int32_t instance, double out[5]) {
@@ -843,9 +901,12 @@ lbe_status lbe_get_state(lbe_handle* h, int32_t instance, double* pops, int32_t 
   double* d = pops;
   if (!on_device) CU(h, cudaMalloc(&d, sizeof(double) * 27 * N));
   cudaError_t e = launch_pull(h->storage, h->d_finst + instance, H.nx, H.ny, d, h->parity, h->stream);
-  if (e == cudaSuccess && !on_device)
-    e = cudaMemcpyAsync(pops, d, sizeof(double) * 27 * N, cudaMemcpyDeviceToHost, h->stream);
-  st = wait(h);
+  if (e == cudaSuccess && !on_device) {
+    st = wait_stream(h);  // (a copy into pageable memory would block unboundedly)
+    if (st == LBE_OK)
+      e = cudaMemcpyAsync(pops, d, sizeof(double) * 27 * N, cudaMemcpyDeviceToHost, h->stream);
+  }
+  if (st == LBE_OK) st = wait(h);
   if (!on_device) cudaFree(d);
   if (e != cudaSuccess) return fail(h, LBE_ECUDA, "get_state: %s", cudaGetErrorString(e));
   return st;
@@ -866,7 +927,10 @@ lbe_status lbe_set_state(lbe_handle* h, int32_t instance, const double* pops, in
       return fail(h, LBE_ECUDA, "set_state copy: %s", cudaGetErrorString(e));
     }
   }
-  cudaError_t e = launch_push(h->storage, h->d_finst + instance, H.nx, H.ny, d, h->parity, h->stream);
+  // a new state: clear the device error word of an earlier copy time-out
+  cudaError_t e = cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream);
+  if (e == cudaSuccess)
+    e = launch_push(h->storage, h->d_finst + instance, H.nx, H.ny, d, h->parity, h->stream);
   st = wait(h);
   if (!on_device) cudaFree(d);
   if (e != cudaSuccess) return fail(h, LBE_ECUDA, "set_state: %s", cudaGetErrorString(e));
@@ -911,7 +975,7 @@ lbe_status lbe_save(lbe_handle* h, const char* path) {
 
 lbe_status lbe_load(lbe_handle* h, const char* path) {
   if (!h || !path) return fail(h, LBE_EINVAL, "handle or path is NULL");
-  lbe_status st = wait(h);
+  lbe_status st = wait_stream(h);  // the error word is cleared below
   if (st) return st;
   FILE* fp = fopen(path, "rb");
   if (!fp) return fail(h, LBE_EINVAL, "cannot open %s", path);
@@ -953,6 +1017,10 @@ lbe_status lbe_load(lbe_handle* h, const char* path) {
     CU(h, cudaMemcpy(H.arena + (size_t)h->parity * H.buf_bytes, raws[j].data(), H.buf_bytes,
                      cudaMemcpyHostToDevice));
   }
+  CU(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
+  // the random bits of the stochastic rounding follow the step count
+  CU(h, launch_seed_set(h->d_seed, (uint32_t)steps, h->stream));
+  if ((st = wait_stream(h))) return st;
   h->steps = steps;
   h->bad = false;
   h->prev_valid = false;
@@ -1027,7 +1095,7 @@ lbe_status lbe_adjoint_step(lbe_handle* h, const double* Q, const double* a_next
                             h->stream);
   if (e != cudaSuccess) return fail(h, LBE_ECUDA, "adjoint step: %s", cudaGetErrorString(e));
   double th[4];
-  CU(h, cudaMemcpyAsync(th, theta, sizeof th, cudaMemcpyDeviceToHost, h->stream));
+  if ((st = to_host(h, th, theta, sizeof th))) return st;
   if ((st = wait(h))) return st;
   if (grad)
     for (int j = 0; j < 3; j++) grad[j] += th[j];
@@ -1046,7 +1114,7 @@ lbe_status lbe_observable(lbe_handle* h, const double* Q, double* out) {
   cudaError_t e = launch_observable(h->d_finst, H.nx, H.ny, Q, scr.d(), small.d(), h->stream);
   if (e != cudaSuccess) return fail(h, LBE_ECUDA, "observable: %s", cudaGetErrorString(e));
   double o[4];
-  CU(h, cudaMemcpyAsync(o, small.d(), sizeof o, cudaMemcpyDeviceToHost, h->stream));
+  if ((st = to_host(h, o, small.d(), sizeof o))) return st;
   if ((st = wait(h))) return st;
   *out = o[0] / o[1];
   return LBE_OK;
@@ -1064,7 +1132,7 @@ int64_t lbe_state_bytes(const lbe_handle* h) {
 
 void lbe_destroy(lbe_handle* h) {
   if (!h) return;
-  if (h->stream) wait(h);  // bounded; the buffers are freed either way
+  if (h->stream) wait_stream(h);  // bounded; the buffers are freed either way
   free_handle(h);
 }
 

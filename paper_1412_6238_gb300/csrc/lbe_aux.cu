@@ -17,12 +17,17 @@ bool tile_available(int storage, int tile) {
 }
 
 cudaError_t launch_stash(int storage, const InstDev* d, int n, int64_t items, int seg, int parity,
-                         int grid, int* err, cudaStream_t s) {
+                         int grid, int* err, int poll_lim, int withhold, const uint32_t* seed,
+                         cudaStream_t s) {
   switch (storage) {
-    case ST_F32: return launch_stash_f32(d, n, items, seg, parity, grid, err, s);
-    case ST_F16DEV: return launch_stash_f16(d, n, items, seg, parity, grid, err, s);
-    case ST_BF16DEV: return launch_stash_bf16(d, n, items, seg, parity, grid, err, s);
-    case ST_F16MIX: return launch_stash_mix(d, n, items, seg, parity, grid, err, s);
+    case ST_F32:
+      return launch_stash_f32(d, n, items, seg, parity, grid, err, poll_lim, withhold, seed, s);
+    case ST_F16DEV:
+      return launch_stash_f16(d, n, items, seg, parity, grid, err, poll_lim, withhold, seed, s);
+    case ST_BF16DEV:
+      return launch_stash_bf16(d, n, items, seg, parity, grid, err, poll_lim, withhold, seed, s);
+    case ST_F16MIX:
+      return launch_stash_mix(d, n, items, seg, parity, grid, err, poll_lim, withhold, seed, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -38,13 +43,13 @@ int stash_occupancy(int storage) {
 }
 
 cudaError_t launch_step(int storage, int tile, const InstDev* d, int n, int64_t total, int parity,
-                        int grid, cudaStream_t s) {
+                        int grid, const uint32_t* seed, cudaStream_t s) {
   switch (storage) {
-    case ST_F64: return launch_step_f64(tile, d, n, total, parity, grid, s);
-    case ST_F32: return launch_step_f32(tile, d, n, total, parity, grid, s);
-    case ST_F16DEV: return launch_step_f16(tile, d, n, total, parity, grid, s);
-    case ST_BF16DEV: return launch_step_bf16(tile, d, n, total, parity, grid, s);
-    case ST_F16MIX: return launch_step_mix(tile, d, n, total, parity, grid, s);
+    case ST_F64: return launch_step_f64(tile, d, n, total, parity, grid, seed, s);
+    case ST_F32: return launch_step_f32(tile, d, n, total, parity, grid, seed, s);
+    case ST_F16DEV: return launch_step_f16(tile, d, n, total, parity, grid, seed, s);
+    case ST_BF16DEV: return launch_step_bf16(tile, d, n, total, parity, grid, seed, s);
+    case ST_F16MIX: return launch_step_mix(tile, d, n, total, parity, grid, seed, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -256,7 +261,9 @@ int sums_blocks() { return SUM_BLOCKS; }
 // pairs + f_0 + 9 hbar + the FP32 g_0 + the low part; F16MIX: 9 planes of
 // 8-byte words + the FP32 g_0.
 // blockIdx.y: instance.
-__global__ void ghost_kernel(const InstDev* __restrict__ insts, int parity) {
+__global__ void ghost_kernel(const InstDev* __restrict__ insts, int parity, uint32_t* seed) {
+  // the step is complete: advance the handle's step counter
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *seed += 1u;
   const InstDev& I = insts[blockIdx.y];
   char* b = I.buf[parity];
   const int nx = I.nx, ny = I.ny;
@@ -313,10 +320,23 @@ __global__ void ghost_kernel(const InstDev* __restrict__ insts, int parity) {
   }
 }
 
-cudaError_t launch_ghosts(const InstDev* d, int n_inst, int max_ny, int parity, cudaStream_t s) {
+cudaError_t launch_ghosts(const InstDev* d, int n_inst, int max_ny, int parity, uint32_t* seed,
+                          cudaStream_t s) {
   const int64_t total = (int64_t)20 * max_ny * (2 * XG);
   const int bx = (int)std::min<int64_t>((total + 255) / 256, 4096);
-  ghost_kernel<<<dim3(bx, n_inst), 256, 0, s>>>(d, parity);
+  ghost_kernel<<<dim3(bx, n_inst), 256, 0, s>>>(d, parity, seed);
+  return cudaGetLastError();
+}
+
+__global__ void seed_kernel(uint32_t* seed, uint32_t value, int set) {
+  *seed = set ? value : *seed + 1u;
+}
+cudaError_t launch_seed_tick(uint32_t* seed, cudaStream_t s) {
+  seed_kernel<<<1, 1, 0, s>>>(seed, 0u, 0);
+  return cudaGetLastError();
+}
+cudaError_t launch_seed_set(uint32_t* seed, uint32_t value, cudaStream_t s) {
+  seed_kernel<<<1, 1, 0, s>>>(seed, value, 1);
   return cudaGetLastError();
 }
 

@@ -176,6 +176,12 @@ template <class S>
 struct Drive {
   using C = typename S::C;
   C mu, Fx, Fy, ux, uy, Trow;
+  // rho c_s^2 u = j + c_s^2 F / 2, the first moment the f equilibrium must
+  // have (FP32 forms, which build its odd part from it), as two floats
+  // J = Jx + Jxl; c_s^2 F / 2 is formed as (w_axis + 2 w_diag) F with the
+  // weights of the forcing term, so that it is half the forcing term's first
+  // moment in the FP32 constants
+  C Jx, Jy, Jxl, Jyl;
 };
 
 template <class S>
@@ -198,21 +204,56 @@ __device__ __forceinline__ Drive<S> drive(const Phys<typename S::C>& P, int gy,
   const C mar = -P.sigmaT * ea;
   d.Fx = cap * s.gcx + mar * (g2 * s.gTx - cdT * s.gcx) + P.Fbx;
   d.Fy = cap * s.gcy + mar * (g2 * s.gTy - cdT * s.gcy) + P.Fby;
-  // S6 (Eq. 13): first moments summed in index order
-  C jx = f[1] - f[3];
-  jx = jx + f[5];
-  jx = jx - f[6];
-  jx = jx - f[7];
-  jx = jx + f[8];
-  C jy = f[2] - f[4];
-  jy = jy + f[5];
-  jy = jy + f[6];
-  jy = jy - f[7];
-  jy = jy - f[8];
+  // S6 (Eq. 13): first moments.  FP64: summed in index order (the order of
+  // the FP64 reference).  FP32: differences of opposite populations first,
+  // each exact (Sterbenz: the two are within a factor 2 of each other), then
+  // their sum, so that j is rounded at its own scale; summed in index order,
+  // every partial sum is of the size of f and rounds at that scale, an error
+  // that is large next to a small j (slow flow, where f is mostly w_i p) and
+  // repeats step after step where the flow is steady.
+  C jx, jy, jxl = C(0), jyl = C(0);
+  if constexpr (sizeof(C) == 4) {
+    // j exactly, as two floats: the three differences are exact, their sums
+    // by error-free two-sums
+    const C d13 = f[1] - f[3], d24 = f[2] - f[4], d57 = f[5] - f[7], d86 = f[8] - f[6];
+    C sx, ex, sy, ey, e2;
+    two_sum(d57, d86, sx, ex);
+    two_sum(d13, sx, jx, e2);
+    jxl = ex + e2;
+    two_sum(d57, -d86, sy, ey);
+    two_sum(d24, sy, jy, e2);
+    jyl = ey + e2;
+  } else {
+    jx = f[1] - f[3];
+    jx = jx + f[5];
+    jx = jx - f[6];
+    jx = jx - f[7];
+    jx = jx + f[8];
+    jy = f[2] - f[4];
+    jy = jy + f[5];
+    jy = jy + f[6];
+    jy = jy - f[7];
+    jy = jy - f[8];
+  }
   const C rho = P.rho, inv_rho = P.inv_rho;
   const C rcs2 = P.rcs2, inv_rcs2 = C(3) * inv_rho;
   d.ux = dv(jx, rcs2, inv_rcs2) + dv(C(0.5) * d.Fx, rho, inv_rho);
   d.uy = dv(jy, rcs2, inv_rcs2) + dv(C(0.5) * d.Fy, rho, inv_rho);
+  const C wa = WGT<C>(1), wd2 = C(2) * WGT<C>(5);
+  if constexpr (sizeof(C) == 4) {
+    // J = j + (w_axis + 2 w_diag) F as two floats (the force term, small
+    // next to j where the momentum matters, is rounded at its own scale)
+    const C cFx = fmaf(wa, d.Fx, wd2 * d.Fx), cFy = fmaf(wa, d.Fy, wd2 * d.Fy);
+    C e;
+    two_sum(jx, cFx, d.Jx, e);
+    d.Jxl = e + jxl;
+    two_sum(jy, cFy, d.Jy, e);
+    d.Jyl = e + jyl;
+  } else {
+    d.Jx = (jx + wa * d.Fx) + wd2 * d.Fx;
+    d.Jy = (jy + wa * d.Fy) + wd2 * d.Fy;
+    d.Jxl = d.Jyl = C(0);
+  }
   return d;
 }
 
@@ -220,14 +261,19 @@ __device__ __forceinline__ Drive<S> drive(const Phys<typename S::C>& P, int gy,
 // post-collision value of population (k, i) (hbar as a deviation in the
 // deviation forms).  16/32-bit forms: g_0 = g[0] + g0lo and c = cc + clo
 // enter as two-float values and the post-collision g_0 leaves as
-// out(1, 0, hi) and *g0lo_out = lo.
+// out(1, 0, hi) and *g0lo_out = lo.  hbar (16/32-bit forms): h[] as pulled,
+// without the change of reference row (from the source row's T_r to this
+// row's) when dhc = rho c_v dT_r/dy, or already in this row's reference when
+// dhc = 0 (the wall rows); the change, w_i xi_iy dhc, enters through the
+// source term instead, (1 - omega_T) times (see below).
 template <class S, class Out>
 __device__ __forceinline__ void collide(const Phys<typename S::C>& P, const typename S::C f[9],
                                         const typename S::C g[9], const typename S::C h[9],
                                         typename S::C cc, typename S::C pp, typename S::C TT,
                                         typename S::C gpx, typename S::C gpy, const Drive<S>& d,
                                         Out&& out, typename S::C g0lo = 0, typename S::C clo = 0,
-                                        typename S::C* g0lo_out = nullptr) {
+                                        typename S::C* g0lo_out = nullptr,
+                                        typename S::C dhc = 0) {
   using C = typename S::C;
   const C inv_rho = P.inv_rho;
   const C rcs2 = P.rcs2, inv_rcs2 = C(3) * inv_rho;
@@ -257,11 +303,25 @@ __device__ __forceinline__ void collide(const Phys<typename S::C>& P, const type
     // q = a + ((a^2 - u^2/c_s^2)/2), Gamma_i = w_i (1 + q); opposite
     // directions share (a^2 - u^2/c_s^2)/2; F.(xi_i - u) = F.xi_i - F.u.
     // The eight moving directions come first and the rest direction takes
-    // the remainder of the c and rho c_v T equilibria (the moment minus the
-    // sum of the other eight; the same value in exact arithmetic).  Computed
-    // directly, w_0 H_0 carries the FP32 representation error of w_0 = 4/9
-    // in the same direction at every bulk cell, a systematic drift of sum c
-    // (and of the energy) over long runs.
+    // the remainder of the p, c and rho c_v T equilibria (the moment minus
+    // the sum of the other eight; the same value in exact arithmetic).
+    // Computed directly, w_0 carries the FP32 representation error of 4/9 in
+    // the same direction at every bulk cell, a systematic drift of the
+    // conserved sums over long runs.
+    // The odd part of the f equilibrium, w_i rho c_s^2 xi_i.u/c_s^2 =
+    // 3 w_i xi_i.J with J = rho c_s^2 u, is formed from J with weights
+    // K_axis = fl(1/3) and K_diag = (1 - 2 K_axis)/4, whose first-moment sum
+    // 2 K_axis + 4 K_diag is exactly 1: the equilibrium then carries the
+    // momentum J itself.  From u with the FP32 values of w_i and rho c_s^2
+    // it carried J (1 + 3.7e-8) at every cell, which relaxation turns into a
+    // growth of the momentum by 3e-8 per step: over the viscous time of a
+    // flow near steady state, a bias of 1e-4 of the velocity.  J enters as
+    // two floats and the relaxation f_i + omega (f_eq,i - f_i) + source is
+    // formed as f_i + (omega (((S - f_i) +- A_hi) +- A_lo) + source): the
+    // difference S - f_i is exact, so every rounding before the last falls
+    // at the scale of the increment, and the equilibrium momentum is J to
+    // its two-float precision (rounded to one float, J alone left a 3e-6
+    // velocity error after the 40 000 steps of the 512 x 1024 drop).
     const C Fdu = Fx * ux + Fy * uy, Gdu = Gx * ux + Gy * uy;
     const C sg = cc * inv_rcs2;  // c / (rho c_s^2)
     const C agsg = ag * sg, aTi = aT * inv_rcs2;
@@ -281,11 +341,16 @@ __device__ __forceinline__ void collide(const Phys<typename S::C>& P, const type
     const float2 omg = make_float2(omega_g, omega_g), omT = make_float2(omega_T, omega_T);
     const float2 agsgv = make_float2(agsg, agsg), aTiv = make_float2(aTi, aTi);
     const float2 m1 = make_float2(-1.f, -1.f);
-    auto dir2 = [&](int i, int j, C W, C a, C hq, C Fxi, C Gxi) {
+    C dfs = C(0), dhs = C(0);  // sums of the moving f and hbar increments
+    const float2 omTc = make_float2(omega_T - C(1), omega_T - C(1));
+    auto dir2 = [&](int i, int j, C W, C K, C a, C hq, C Ja, C Jal, C Fxi, C Gxi, C offi) {
       const float2 Wv = make_float2(W, W);
       const float2 q = make_float2(a + hq, hq - a);
       const float2 G = __ffma2_rn(Wv, q, Wv);                          // Gamma_i
-      const float2 feq = __fmul2_rn(Wv, __ffma2_rn(rcs2v, q, ppv));     // Eq. 5
+      // Eq. 5: even part w_i (p + rho c_s^2 hq), odd part K_i xi_i.J (two
+      // floats: the product's rounding error recovered by an FMA)
+      const float Sf = W * fmaf(rcs2, hq, pp), Af = K * Ja;
+      const float Afl = fmaf(K, Ja, -Af) + K * Jal;
       const float2 geq = __fmul2_rn(Wv, __ffma2_rn(ccv, q, Hiv));       // Eq. 21
       const float2 heqd = __ffma2_rn(rTd, G, __fmul2_rn(rTr, __fmul2_rn(Wv, q)));
       sge += geq.x + geq.y;
@@ -295,12 +360,21 @@ __device__ __forceinline__ void collide(const Phys<typename S::C>& P, const type
       const float2 hv = make_float2(h[i], h[j]);
       const float2 Fd = make_float2(Fxi - Fdu, -Fxi - Fdu);  // F.(xi - u)
       const float2 gd = make_float2(Gxi - Gdu, -Gxi - Gdu);  // (F - grad p).(xi - u)
-      float2 fo = __ffma2_rn(omf, __ffma2_rn(fv, m1, feq), fv);
-      fo = __ffma2_rn(afv, __fmul2_rn(Fd, G), fo);
+      const float2 fdel = make_float2(((Sf - fv.x) + Af) + Afl, ((Sf - fv.y) - Af) - Afl);
+      const float2 finc = __ffma2_rn(omf, fdel, __fmul2_rn(afv, __fmul2_rn(Fd, G)));
+      const float2 fo = __fadd2_rn(fv, finc);
       float2 go = __ffma2_rn(omg, __ffma2_rn(gv, m1, geq), gv);
       go = __ffma2_rn(__fmul2_rn(agsgv, gd), G, go);
       float2 ho = __ffma2_rn(omT, __ffma2_rn(hv, m1, heqd), hv);
-      ho = __ffma2_rn(__fmul2_rn(aTiv, gd), __fmul2_rn(rT, G), ho);
+      // source plus the change of reference row of a raw pulled value,
+      // -(1 - omega_T) xi_iy w_i dhc: relaxing (h_raw - off) gives
+      // h_raw + omega (heq - h_raw) + source - (1 - omega) off
+      const float2 sT = __ffma2_rn(omTc, make_float2(offi, -offi),
+                                   __fmul2_rn(__fmul2_rn(aTiv, gd), __fmul2_rn(rT, G)));
+      ho = __fadd2_rn(ho, sT);
+      // increments, whose sum the rest direction takes with the opposite sign
+      dfs += finc.x + finc.y;
+      dhs += (ho.x - hv.x) + (ho.y - hv.y);
       out(0, i, fo.x);
       out(0, j, fo.y);
       out(1, i, go.x);
@@ -308,25 +382,39 @@ __device__ __forceinline__ void collide(const Phys<typename S::C>& P, const type
       out(2, i, ho.x);
       out(2, j, ho.y);
     };
+    constexpr float Ka = 1.0f / 3.0f;                 // fl(1/3)
+    constexpr float Kd = (1.0f - 2.0f * Ka) / 4.0f;  // exact: 2 Ka + 4 Kd = 1
+    const C Jx = d.Jx, Jy = d.Jy, Jxl = d.Jxl, Jyl = d.Jyl;
+    C Jp, Jpl, Jm, Jml;  // Jx + Jy and Jy - Jx as two floats
+    two_sum(Jx, Jy, Jp, Jpl);
+    Jpl += Jxl + Jyl;
+    two_sum(Jy, -Jx, Jm, Jml);
+    Jml += Jyl - Jxl;
     C a = ux3, hq = C(0.5) * (a * a - uu);
-    dir2(1, 3, wa, a, hq, Fx, Gx);
+    dir2(1, 3, wa, Ka, a, hq, Jx, Jxl, Fx, Gx, C(0));
     a = uy3;
     hq = C(0.5) * (a * a - uu);
-    dir2(2, 4, wa, a, hq, Fy, Gy);
+    dir2(2, 4, wa, Ka, a, hq, Jy, Jyl, Fy, Gy, wa * dhc);
     a = ux3 + uy3;
     hq = C(0.5) * (a * a - uu);
-    dir2(5, 7, wd, a, hq, Fx + Fy, Gx + Gy);
+    dir2(5, 7, wd, Kd, a, hq, Jp, Jpl, Fx + Fy, Gx + Gy, wd * dhc);
     a = uy3 - ux3;
     hq = C(0.5) * (a * a - uu);
-    dir2(6, 8, wd, a, hq, Fy - Fx, Gy - Gx);
+    dir2(6, 8, wd, Kd, a, hq, Jm, Jml, Fy - Fx, Gy - Gx, wd * dhc);
     const C W0 = WGT<C>(0);
     const C G0 = W0 + W0 * hu;
-    // rest direction: f and hbar as above; g_0 in two-float arithmetic
-    // (g_0 + omega_g (g_eq,0 - g_0) + source, g_eq,0 = c - sum of the moving
-    // g_eq), so that c keeps the precision of its two-float moment
-    out(0, 0, f[0] + omega_f * (W0 * (pp + rcs2 * hu) - f[0]) + af * ((C(0) - Fdu) * G0));
-    out(2, 0, h[0] + omega_T * (((dev_h<S>() ? rcvTd : rcvT) - she) - h[0]) +
-                  (aTi * (C(0) - Gdu)) * (rcvT * G0));
+    // rest direction: f and hbar take minus the sum of the moving increments
+    // (the collision conserves sum f and sum hbar and the sources have no
+    // zeroth moment, so this is the relaxation of f_0 and hbar_0 in exact
+    // arithmetic): the cell's mass and energy then change only by the
+    // rounding of its stored values, not by the rounding of p or T' (a
+    // bias that repeats step after step where the fields are steady); g_0
+    // in two-float arithmetic (g_0 + omega_g (g_eq,0 - g_0) + source,
+    // g_eq,0 = c - sum of the moving g_eq), so that c keeps the precision of
+    // its two-float moment
+    (void)she;
+    out(0, 0, f[0] - dfs);
+    out(2, 0, h[0] - dhs);
     {
       const C src0 = (agsg * (C(0) - Gdu)) * G0;
       C s0, e0;

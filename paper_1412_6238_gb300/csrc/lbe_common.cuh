@@ -100,6 +100,7 @@ struct InstDev {
   Phys<float> pf;
   float s[3];           // 16-bit codec scales s_k
   double hr0, hr1;      // T_r(y) = hr0 + hr1 y (double, for state conversion)
+  uint32_t salt;        // the instance's index in its handle (random bits)
 };
 
 template <class C>
@@ -108,6 +109,88 @@ template <>
 __device__ __forceinline__ const Phys<double>& phys<double>(const InstDev& I) { return I.pd; }
 template <>
 __device__ __forceinline__ const Phys<float>& phys<float>(const InstDev& I) { return I.pf; }
+
+// ------------------------------------------------------- stochastic rounding
+// The 16-bit forms round the values they store stochastically: to one of the
+// two neighbouring 16-bit values, with probabilities that make the expected
+// stored value the exact one.  Rounded to nearest instead, a cell of a flow
+// near steady state makes the same rounding error step after step, so the
+// errors add up over the flow's relaxation time instead of averaging out.
+// Random bits: a counter-based hash per cell and step (the finaliser of
+// MurmurHash3 over the step counter, the instance and the cell), then, for
+// population v = 9 k + i, term v of a linear congruential sequence started at
+// that hash, reached in one multiply-add from closed-form constants, so that
+// every kernel draws the same bits for a given value.
+__host__ __device__ constexpr uint32_t mix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+// LCG s -> LCG_A s + LCG_C (Numerical Recipes' constants); term v from s:
+// a_v s + c_v with a_v = LCG_A^v and c_v = LCG_C (1 + LCG_A + ... + LCG_A^(v-1)),
+// tabulated at compile time for v = 0..27 (read with constant indices)
+constexpr uint32_t LCG_A = 1664525u, LCG_C = 1013904223u;
+struct LcgTable {
+  uint32_t a[28], c[28];
+};
+constexpr LcgTable make_lcg_table() {
+  LcgTable t{};
+  t.a[0] = 1u;
+  t.c[0] = 0u;
+  for (int v = 1; v < 28; v++) {
+    t.a[v] = LCG_A * t.a[v - 1];
+    t.c[v] = LCG_A * t.c[v - 1] + LCG_C;
+  }
+  return t;
+}
+static __constant__ LcgTable LCG_TAB = make_lcg_table();
+// hash of a step and an instance (uniform over a work item)
+__device__ __forceinline__ uint32_t sr_step_key(uint32_t step, uint32_t salt) {
+  return mix32(step * 0x9E3779B9u ^ mix32(salt + 0x632BE5ABu));
+}
+// the cell's hash
+__device__ __forceinline__ uint32_t sr_cell(uint32_t step_key, uint32_t cell) {
+  return mix32(step_key ^ (cell * 0x85EBCA77u));
+}
+// 32 random bits for population (k, i) of a cell (k and i fold to constants
+// in the unrolled loops)
+__device__ __forceinline__ uint32_t sr_bits(int k, int i, uint32_t cell_hash) {
+  return LCG_TAB.a[9 * k + i + 1] * cell_hash + LCG_TAB.c[9 * k + i + 1];
+}
+// x with MB-bit target mantissa (10: FP16, 7: BF16) plus a random integer
+// below the target's last mantissa bit, added to x's FP32 bit pattern (that
+// is, to its magnitude): truncating the result toward zero to the target
+// format rounds x up or down with probabilities proportional to the
+// distances, wherever the target value is normal (for FP16 below 2^-14,
+// where fewer mantissa bits remain, the rounding is partly toward zero).
+template <int MB>
+__device__ __forceinline__ float sr_dither(float x, uint32_t r) {
+  return __uint_as_float(__float_as_uint(x) + (r >> (9 + MB)));
+}
+// (a, b) to a packed FP16 / BF16 pair (a in the low half), stochastically;
+// the two dithers take bits 19-31 and 6-18 (FP16) or 16-31 and 0-15 (BF16)
+// of one random word
+__device__ __forceinline__ uint32_t sr_pack_half2(float a, float b, uint32_t r) {
+  uint32_t out;
+  asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(out) : "f"(sr_dither<10>(b, r << 13)),
+      "f"(sr_dither<10>(a, r)));
+  return out;
+}
+__device__ __forceinline__ uint32_t sr_pack_bf162(float a, float b, uint32_t r) {
+  uint32_t out;
+  asm("cvt.rz.bf16x2.f32 %0, %1, %2;" : "=r"(out) : "f"(sr_dither<7>(b, r << 16)),
+      "f"(sr_dither<7>(a, r)));
+  return out;
+}
+__device__ __forceinline__ __half sr_half(float x, uint32_t r) {
+  return __float2half_rz(sr_dither<10>(x, r));
+}
+__device__ __forceinline__ __nv_bfloat16 sr_bf16(float x, uint32_t r) {
+  return __float2bfloat16_rz(sr_dither<7>(x, r));
+}
 
 // ------------------------------------------------------------ storage codecs
 // ld / st take (k, i) as template-folded constants through the unrolled loops.
@@ -119,6 +202,10 @@ __device__ __forceinline__ const Phys<float>& phys<float>(const InstDev& I) { re
 struct StF64 {
   using C = double;
   static constexpr int kind = ST_F64;
+  static constexpr bool SR = false;  // stores round to nearest
+  __device__ static __forceinline__ C sr_value(const InstDev&, int, int, C v, uint32_t) {
+    return v;
+  }
   __device__ static __forceinline__ C ld(const InstDev& I, const Phys<C>&, const char* b, int k,
                                          int i, size_t idx) {
     return __ldg(reinterpret_cast<const double*>(b + (size_t)(k * 9 + i) * I.plane_bytes) + idx);
@@ -132,6 +219,10 @@ struct StF64 {
 struct StF32 {
   using C = float;
   static constexpr int kind = ST_F32;
+  static constexpr bool SR = false;
+  __device__ static __forceinline__ C sr_value(const InstDev&, int, int, C v, uint32_t) {
+    return v;
+  }
   __device__ static __forceinline__ C ld(const InstDev& I, const Phys<C>&, const char* b, int k,
                                          int i, size_t idx) {
     if (k < 2)
@@ -158,6 +249,8 @@ template <class E, int KIND>
 struct StDev {
   using C = float;
   static constexpr int kind = KIND;
+  static constexpr bool SR = true;  // the 16-bit values round stochastically
+  static constexpr bool BF = KIND == ST_BF16DEV;
   __device__ static __forceinline__ float cvt(__half q) { return __half2float(q); }
   __device__ static __forceinline__ float cvt(__nv_bfloat16 q) { return __bfloat162float(q); }
   // two adjacent 16-bit values (4-byte aligned) to FP32
@@ -202,6 +295,40 @@ struct StDev {
     put2(reinterpret_cast<E*>(b + (size_t)(i - 1) * I.pair_bytes) + 2 * idx, fv * I.s[0],
          gv * I.s[1]);
   }
+  // the same, stochastically rounded with the random word r
+  __device__ static __forceinline__ void st_fg_sr(const InstDev& I, char* b, int i, size_t idx,
+                                                  float fv, float gv, uint32_t r) {
+    const uint32_t q = BF ? sr_pack_bf162(fv * I.s[0], gv * I.s[1], r)
+                          : sr_pack_half2(fv * I.s[0], gv * I.s[1], r);
+    *reinterpret_cast<uint32_t*>(reinterpret_cast<E*>(b + (size_t)(i - 1) * I.pair_bytes) +
+                                 2 * idx) = q;
+  }
+  // one 16-bit value (not g_0), stochastically rounded
+  __device__ static __forceinline__ void st_sr(const InstDev& I, char* b, int k, int i, size_t idx,
+                                               C v, uint32_t r) {
+    E* p = const_cast<E*>(at(I, b, k, i, idx));
+    if constexpr (BF)
+      *p = sr_bf16(v * I.s[k], r);
+    else
+      *p = sr_half(v * I.s[k], r);
+  }
+  // the dither word of value (k, i) of a cell with hash hc: one word per
+  // (f_i, g_i) pair (f from its top bits, g from the word shifted left, as
+  // sr_pack_* take them), one per f_0 and per hbar_i
+  __device__ static __forceinline__ uint32_t sr_word(int k, int i, uint32_t hc) {
+    if (k == 1) return sr_bits(0, i, hc) << (BF ? 16 : 13);
+    return sr_bits(k, i, hc);
+  }
+  // v rounded stochastically to a value the store then represents exactly
+  // (g_0, kept in FP32, as it is)
+  __device__ static __forceinline__ C sr_value(const InstDev& I, int k, int i, C v, uint32_t hc) {
+    if (k == 1 && i == 0) return v;
+    const uint32_t r = sr_word(k, i, hc);
+    if constexpr (BF)
+      return __bfloat162float(sr_bf16(v * I.s[k], r)) * I.pf.inv_s[k];
+    else
+      return __half2float(sr_half(v * I.s[k], r)) * I.pf.inv_s[k];
+  }
 };
 
 // F16MIX: direction i of cell idx is the 8-byte word at pair plane i
@@ -211,6 +338,7 @@ struct StDev {
 struct StMix {
   using C = float;
   static constexpr int kind = ST_F16MIX;
+  static constexpr bool SR = true;  // the FP16 g_i and hbar_i round stochastically
   template <class B>  // const char or char
   __device__ static __forceinline__ B* word(const InstDev& I, B* b, int i, size_t idx) {
     return b + (size_t)i * I.pair_bytes + 8 * idx;
@@ -236,6 +364,19 @@ struct StMix {
     } else {
       *reinterpret_cast<__half*>(w + half_at(k, i)) = __float2half_rn(v * I.s[k]);
     }
+  }
+  // the dither word of value (k, i) of a cell with hash hc: one word per
+  // (g_i, hbar_i) pair of a direction word (g from its top bits, hbar from
+  // the word shifted left, as sr_pack_half2 takes them), one for hbar_0
+  __device__ static __forceinline__ uint32_t sr_word(int k, int i, uint32_t hc) {
+    if (i == 0) return sr_bits(2, 0, hc);
+    return k == 1 ? sr_bits(1, i, hc) : sr_bits(1, i, hc) << 13;
+  }
+  // v rounded stochastically to a value the store then represents exactly
+  // (the FP32 f_i and g_0 as they are)
+  __device__ static __forceinline__ C sr_value(const InstDev& I, int k, int i, C v, uint32_t hc) {
+    if (k == 0 || (k == 1 && i == 0)) return v;
+    return __half2float(sr_half(v * I.s[k], sr_word(k, i, hc))) * I.pf.inv_s[k];
   }
 };
 

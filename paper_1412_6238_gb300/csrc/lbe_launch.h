@@ -32,18 +32,29 @@ bool tile_available(int storage, int tile);
 
 // Stash strip kernel (16/32-bit storages): one step of every instance over
 // `items` work items (strips x segments of seg rows); reads buf[parity],
-// writes buf[parity ^ 1]; *err is set if a copy wait times out.
+// writes buf[parity ^ 1]; *err is set if a copy wait runs out of its
+// poll_lim polls.  withhold >= 0 (test hook): the copies of that source row
+// are not issued, so that the waits for it run out.
+constexpr int STASH_POLLS = 1 << 22;       // polls of one bounded copy wait
+constexpr int STASH_POLLS_TEST = 1 << 12;  // with the withhold test hook
+// seed: the handle's step counter (device), read for the random bits of the
+// stochastic rounding of the 16-bit forms.
 cudaError_t launch_stash(int storage, const InstDev* d, int n, int64_t items, int seg, int parity,
-                         int grid, int* err, cudaStream_t s);
+                         int grid, int* err, int poll_lim, int withhold, const uint32_t* seed,
+                         cudaStream_t s);
 int stash_occupancy(int storage);
 cudaError_t launch_stash_f32(const InstDev* d, int n, int64_t items, int seg, int parity, int grid,
-                             int* err, cudaStream_t s);
+                             int* err, int poll_lim, int withhold,
+                             const uint32_t* seed, cudaStream_t s);
 cudaError_t launch_stash_f16(const InstDev* d, int n, int64_t items, int seg, int parity, int grid,
-                             int* err, cudaStream_t s);
+                             int* err, int poll_lim, int withhold,
+                             const uint32_t* seed, cudaStream_t s);
 cudaError_t launch_stash_bf16(const InstDev* d, int n, int64_t items, int seg, int parity,
-                              int grid, int* err, cudaStream_t s);
+                              int grid, int* err, int poll_lim, int withhold,
+                             const uint32_t* seed, cudaStream_t s);
 cudaError_t launch_stash_mix(const InstDev* d, int n, int64_t items, int seg, int parity,
-                             int grid, int* err, cudaStream_t s);
+                             int grid, int* err, int poll_lim, int withhold,
+                             const uint32_t* seed, cudaStream_t s);
 int stash_occupancy_f32();
 int stash_occupancy_f16();
 int stash_occupancy_bf16();
@@ -52,7 +63,8 @@ int stash_occupancy_mix();
 // One step of every instance in d_inst[0..n_inst): persistent grid of `grid`
 // CTAs over total_tiles tiles; reads buf[parity], writes buf[parity ^ 1].
 cudaError_t launch_step(int storage, int tile, const InstDev* d_inst, int n_inst,
-                        int64_t total_tiles, int parity, int grid, cudaStream_t s);
+                        int64_t total_tiles, int parity, int grid, const uint32_t* seed,
+                        cudaStream_t s);
 
 // Resident CTAs per SM of the step kernel (0 if unavailable).
 int step_occupancy(int storage, int tile);
@@ -64,15 +76,15 @@ cudaError_t launch_fields(int storage, const InstDev* d_one, int64_t tiles, int 
 
 // Per-storage entry points (defined in lbe_step_<storage>.cu).
 cudaError_t launch_step_f64(int tile, const InstDev* d, int n, int64_t total, int parity,
-                            int grid, cudaStream_t s);
+                            int grid, const uint32_t* seed, cudaStream_t s);
 cudaError_t launch_step_f32(int tile, const InstDev* d, int n, int64_t total, int parity,
-                            int grid, cudaStream_t s);
+                            int grid, const uint32_t* seed, cudaStream_t s);
 cudaError_t launch_step_f16(int tile, const InstDev* d, int n, int64_t total, int parity,
-                            int grid, cudaStream_t s);
+                            int grid, const uint32_t* seed, cudaStream_t s);
 cudaError_t launch_step_bf16(int tile, const InstDev* d, int n, int64_t total, int parity,
-                             int grid, cudaStream_t s);
+                             int grid, const uint32_t* seed, cudaStream_t s);
 cudaError_t launch_step_mix(int tile, const InstDev* d, int n, int64_t total, int parity,
-                            int grid, cudaStream_t s);
+                            int grid, const uint32_t* seed, cudaStream_t s);
 int occupancy_f64(int tile);
 int occupancy_f32(int tile);
 int occupancy_f16(int tile);
@@ -103,7 +115,13 @@ cudaError_t launch_sums(const double* cur, const double* prev, int64_t n, double
 cudaError_t launch_f64_to_f32(const double* in, float* out, int64_t n, cudaStream_t s);
 // Periodic ghost columns of buffer `parity` of n_inst instances (16/32-bit
 // storages), after a step of the stash kernel.
-cudaError_t launch_ghosts(const InstDev* d, int n_inst, int max_ny, int parity, cudaStream_t s);
+// (also advances the handle's step counter *seed by one)
+cudaError_t launch_ghosts(const InstDev* d, int n_inst, int max_ny, int parity, uint32_t* seed,
+                          cudaStream_t s);
+// The handle's step counter: +1 after every step (the ghost-column kernel
+// does it for the strip kernel; this one after a tile-kernel step), or set.
+cudaError_t launch_seed_tick(uint32_t* seed, cudaStream_t s);
+cudaError_t launch_seed_set(uint32_t* seed, uint32_t value, cudaStream_t s);
 
 // Adjoint kernels (lbe_adjoint.cu), FP64, one instance d_one of nx x ny.
 // Scratch: adjoint_scratch_doubles(nx, ny) doubles.

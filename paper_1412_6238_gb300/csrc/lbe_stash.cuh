@@ -27,8 +27,14 @@
 //      mirror row, rows above the top wall copy the mirror rows in the rings;
 //   barrier; 4. unit normal of row i+1 (S2).
 // Every population is read from HBM once per step.  Every mbarrier wait is
-// bounded: on time-out the kernel sets *err, waits (bounded) for the copies
-// in flight and returns.
+// bounded (poll_lim polls): on the first time-out the CTA sets *err, issues
+// no further copy, waits (bounded again) for the copies it has in flight and
+// returns.  A drain wait that also runs out means a copy that was issued has
+// not landed within the whole limit; the CTA returns all the same (it cannot
+// wait forever), and the host then treats the handle's state as lost.
+// withhold >= 0 is a test hook: the copies of source row `withhold` are not
+// issued (their barrier still expects the bytes), so that the waits for that
+// row run out with nothing in flight.
 #pragma once
 
 #include "lbe_tile.cuh"
@@ -45,9 +51,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                : "memory");
 }
-// Bounded wait for the phase with the given parity; false on time-out.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (int it = 0; it < (1 << 22); ++it) {
+// Bounded wait for the phase with the given parity (at most `limit` polls);
+// false on time-out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int limit) {
+  for (int it = 0; it < limit; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -189,9 +196,11 @@ __device__ __forceinline__ float stash_val(const char* slot, int k, int i, int c
 // the wall substitution copied the reversed population of the cell itself.
 // Rules of pull9 (lbe_tile.cuh): anti-bounce-back for hbar at the walls, and
 // the deviation offsets of hbar between rows.
-// SUM: the values only enter a sum over i (the moment): in an interior row
-// the hbar deviation offsets +-w_i dh then cancel exactly and are left out.
-template <class S, int K, bool SUM = false>
+// RAW: in an interior row, the hbar deviations as stored, relative to their
+// source rows' T_r, without the offsets +-w_i dh to this row's T_r: they
+// cancel exactly in the moment, and collide() applies them through its
+// source term.
+template <class S, int K, bool RAW = false>
 __device__ __forceinline__ void wstash_pull(const InstDev& I, const Phys<float>& P,
                                             const char* slot, int c0, int c0g, int y, int xw,
                                             float out[9]) {
@@ -206,8 +215,8 @@ __device__ __forceinline__ void wstash_pull(const InstDev& I, const Phys<float>&
 #pragma unroll
     for (int i = 0; i < 9; i++) {
       float v = stash_val<S>(slot, K, i, col(i, true), P);
-      if (DEV && !SUM && EY(i) == 1) v -= WGT<float>(i) * P.dh;
-      if (DEV && !SUM && EY(i) == -1) v += WGT<float>(i) * P.dh;
+      if (DEV && !RAW && EY(i) == 1) v -= WGT<float>(i) * P.dh;
+      if (DEV && !RAW && EY(i) == -1) v += WGT<float>(i) * P.dh;
       out[i] = v;
     }
     return;
@@ -285,8 +294,8 @@ __device__ __forceinline__ void wstash_pull_fg16(const InstDev& I, const Phys<fl
 // three follow the same neighbour, and the same wall rule but for the
 // anti-bounce-back of hbar), with the rules of pull9 (lbe_tile.cuh) for
 // hbar; g_0 from the FP32 row and its low part from word 0.  c0: the
-// thread's own column in a row.  SUM: as in wstash_pull.
-template <bool SUM>
+// thread's own column in a row.  RAW: as in wstash_pull.
+template <bool RAW>
 __device__ __forceinline__ void wstash_pull_mix(const InstDev& I, const Phys<float>& P,
                                                 const char* slot, int c0, int y, int xw,
                                                 float f[9], float g[9], float h[9],
@@ -316,8 +325,8 @@ __device__ __forceinline__ void wstash_pull_mix(const InstDev& I, const Phys<flo
       f[i] = __uint_as_float(v.x);
       g[i] = q.x * sg;
       float hv = q.y * sh;
-      if (!SUM && EY(i) == 1) hv -= WGT<float>(i) * P.dh;
-      if (!SUM && EY(i) == -1) hv += WGT<float>(i) * P.dh;
+      if (!RAW && EY(i) == 1) hv -= WGT<float>(i) * P.dh;
+      if (!RAW && EY(i) == -1) hv += WGT<float>(i) * P.dh;
       h[i] = hv;
     }
     return;
@@ -440,7 +449,8 @@ __device__ __forceinline__ void issue_row(const CopyPlan& c, uint32_t dst, uint3
 template <class S, int NC>
 __global__ void __launch_bounds__(NC, (StashCfg<S, NC>::MINB))
 stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items, int seg_rows,
-             int parity, int* __restrict__ err) {
+             int parity, int* __restrict__ err, int poll_lim, int withhold,
+             const uint32_t* __restrict__ seed) {
   using Cfg = StashCfg<S, NC>;
   using Fmt = typename Cfg::Fmt;
   using C = float;
@@ -469,6 +479,8 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
   __syncthreads();
   unsigned phase = 0;    // bit s: parity of the next completion of slot s
   unsigned pending = 0;  // bit s: slot s has copies not yet waited for
+  // the handle's step counter (random bits of the stochastic rounding)
+  const uint32_t step = S::SR ? __ldg(seed) : 0u;
 
   for (int64_t item = blockIdx.x; item < total_items; item += gridDim.x) {
     int lo = 0, hi = n_inst - 1;
@@ -487,6 +499,7 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
     char* __restrict__ dst = I.buf[parity ^ 1];
     const Phys<C> P = phys<C>(I);
     const C en2 = P.eta_n2;
+    const uint32_t skey = S::SR ? sr_step_key(step, I.salt) : 0u;
     const size_t pitch = (size_t)I.pitch;
     const int x = x0 - 2 + t;
     const int xw = wrapx(x, nx);
@@ -524,7 +537,9 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(bar, Cfg::TX);
         const int mr = m >= 0 ? m : -1 - m;
-        if (mr > 0 && mr < ny - 1)
+        if (mr == withhold) {
+          // test hook: nothing issued, the wait for this slot runs out
+        } else if (mr > 0 && mr < ny - 1)
           issue_row<S, false>(cp, dstw, bar, mr, ny);
         else
           issue_row<S, true>(cp, dstw, bar, mr, ny);
@@ -533,7 +548,7 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
     auto wait_row = [&](int m) -> bool {
       if (!loadable(m)) return true;
       const int s = m & (Cfg::SR - 1);
-      const bool ok = mbar_wait(bars_u + 8 * s, (phase >> s) & 1u);
+      const bool ok = mbar_wait(bars_u + 8 * s, (phase >> s) & 1u, poll_lim);
       if (ok) {
         phase ^= 1u << s;
         pending &= ~(1u << s);
@@ -558,15 +573,17 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
       if (r >= ya && r < yb && collides) {
         const char* s = slot(r);
         C f[9], g[9], h[9], g0lo;
+        // hbar as pulled (without the change of reference row in interior
+        // rows, which collide() applies through the source term)
         if constexpr (MIX) {
-          wstash_pull_mix<false>(I, P, s, c0, r, x, f, g, h, g0lo);
+          wstash_pull_mix<true>(I, P, s, c0, r, x, f, g, h, g0lo);
         } else {
           if constexpr (!W16) {
             wstash_pull_fg(I, s, c0, r, f, g);
           } else {
             wstash_pull_fg16<S>(I, P, s, c0, c0g, r, f, g);
           }
-          wstash_pull<S, 2>(I, P, s, c0, c0g, r, x, h);
+          wstash_pull<S, 2, true>(I, P, s, c0, c0g, r, x, h);
           g0lo = __half2float(reinterpret_cast<const __half*>(s + Fmt::LO)[c0lo]) * G0LO_INV;
         }
         const int ps = rr(-2), p0 = rr(-1), pn = rr(0);  // rows r-1, r, r+1
@@ -590,22 +607,25 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
         const Drive<S> d = drive<S>(P, r, f, cc, TT, st);
         C o[27];
         C lo_out = C(0);
+        const C dhc = (r > 0 && r < I.ny - 1) ? P.dh : C(0);
         collide<S>(P, f, g, h, cc, pp, TT, st.gpx, st.gpy, d,
-                   [&](int k, int ii, C v) { o[k * 9 + ii] = v; }, g0lo, clo, &lo_out);
+                   [&](int k, int ii, C v) { o[k * 9 + ii] = v; }, g0lo, clo, &lo_out, dhc);
         const size_t e = (size_t)r * pitch + XG + x;
+        // 16-bit forms: the cell's random bits for the stochastic rounding
+        const uint32_t hc = S::SR ? sr_cell(skey, (uint32_t)r * (uint32_t)nx + (uint32_t)x) : 0u;
         if constexpr (MIX) {
           // word i: (f_i, g_i, hbar_i); word 0: (f_0, hbar_0, g_0 low part)
           const float s1 = I.s[1], s2 = I.s[2];
-          auto word = [&](int ii, float fv, float a, float b) {
-            const __half2 q = __floats2half2_rn(a, b);
-            uint32_t u;
-            memcpy(&u, &q, 4);
+          auto word = [&](int ii, float fv, uint32_t u) {
             reinterpret_cast<uint2*>(dst + (size_t)ii * I.pair_bytes)[e] =
                 make_uint2(__float_as_uint(fv), u);
           };
-          word(0, o[0], o[18] * s2, lo_out * G0LO_SCALE);
+          word(0, o[0],
+               (uint32_t)__half_as_ushort(sr_half(o[18] * s2, S::sr_word(2, 0, hc))) |
+                   ((uint32_t)__half_as_ushort(__float2half_rn(lo_out * G0LO_SCALE)) << 16));
 #pragma unroll
-          for (int ii = 1; ii < 9; ii++) word(ii, o[ii], o[9 + ii] * s1, o[18 + ii] * s2);
+          for (int ii = 1; ii < 9; ii++)
+            word(ii, o[ii], sr_pack_half2(o[9 + ii] * s1, o[18 + ii] * s2, S::sr_word(1, ii, hc)));
           reinterpret_cast<float*>(dst + I.g0_off)[e] = o[9];
         } else if constexpr (!W16) {
           st_g0lo<S>(I, dst, e, lo_out);
@@ -615,12 +635,14 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
           for (int ii = 0; ii < 9; ii++) S::st(I, dst, 2, ii, e, o[18 + ii]);
         } else {
           st_g0lo<S>(I, dst, e, lo_out);
-          S::st(I, dst, 0, 0, e, o[0]);
+          S::st_sr(I, dst, 0, 0, e, o[0], S::sr_word(0, 0, hc));
           S::st(I, dst, 1, 0, e, o[9]);
 #pragma unroll
-          for (int ii = 1; ii < 9; ii++) S::st_fg(I, dst, ii, e, o[ii], o[9 + ii]);
+          for (int ii = 1; ii < 9; ii++)
+            S::st_fg_sr(I, dst, ii, e, o[ii], o[9 + ii], S::sr_word(0, ii, hc));
 #pragma unroll
-          for (int ii = 0; ii < 9; ii++) S::st(I, dst, 2, ii, e, o[18 + ii]);
+          for (int ii = 0; ii < 9; ii++)
+            S::st_sr(I, dst, 2, ii, e, o[18 + ii], S::sr_word(2, ii, hc));
         }
         // (the periodic ghost columns are refreshed by ghost_kernel after the
         // step, not here: the branch costs this kernel about 7 %)
@@ -689,9 +711,11 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
     }
     __syncthreads();
     if (s_abort) {
-      // bounded wait for the copies still in flight, then stop
+      // no copy is issued after the failed wait (the loop left at the barrier
+      // that followed it); bounded wait for the copies still in flight, then
+      // stop.  Every thread tracks the same pending slots.
       for (int sl = 0; sl < Cfg::SR; sl++)
-        if (pending & (1u << sl)) mbar_wait(bars_u + 8 * sl, (phase >> sl) & 1u);
+        if (pending & (1u << sl)) mbar_wait(bars_u + 8 * sl, (phase >> sl) & 1u, poll_lim);
       __syncthreads();
       return;
     }

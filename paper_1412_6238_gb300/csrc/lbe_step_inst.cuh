@@ -15,10 +15,10 @@ namespace lbe {
 namespace {
 template <int TX, int TY>
 cudaError_t launch_one(const InstDev* d, int n, int64_t total, int parity, int grid,
-                       cudaStream_t s) {
+                       const uint32_t* seed, cudaStream_t s) {
   if (grid <= 0) grid = 1;
   if ((int64_t)grid > total) grid = (int)total;
-  tile_kernel<LBE_ST, TX, TY, 0><<<grid, TX * TY, 0, s>>>(d, n, total, parity, nullptr);
+  tile_kernel<LBE_ST, TX, TY, 0><<<grid, TX * TY, 0, s>>>(d, n, total, parity, nullptr, seed);
   return cudaGetLastError();
 }
 template <int TX, int TY>
@@ -32,14 +32,15 @@ int occ_one() {
 }  // namespace
 
 cudaError_t LBE_CAT(launch_step_, LBE_SUFFIX)(int tile, const InstDev* d, int n, int64_t total,
-                                               int parity, int grid, cudaStream_t s) {
+                                               int parity, int grid, const uint32_t* seed,
+                                               cudaStream_t s) {
   switch (tile) {
-    case 0: return launch_one<32, 8>(d, n, total, parity, grid, s);
+    case 0: return launch_one<32, 8>(d, n, total, parity, grid, seed, s);
 #if LBE_ALL_TILES
-    case 1: return launch_one<64, 4>(d, n, total, parity, grid, s);
-    case 2: return launch_one<32, 16>(d, n, total, parity, grid, s);
-    case 3: return launch_one<64, 8>(d, n, total, parity, grid, s);
-    case 4: return launch_one<128, 4>(d, n, total, parity, grid, s);
+    case 1: return launch_one<64, 4>(d, n, total, parity, grid, seed, s);
+    case 2: return launch_one<32, 16>(d, n, total, parity, grid, seed, s);
+    case 3: return launch_one<64, 8>(d, n, total, parity, grid, seed, s);
+    case 4: return launch_one<128, 4>(d, n, total, parity, grid, seed, s);
 #endif
     default: return cudaErrorInvalidValue;
   }
@@ -62,7 +63,7 @@ cudaError_t LBE_CAT(fields_, LBE_SUFFIX)(const InstDev* d, int64_t tiles, int pa
                                           cudaStream_t s) {
   if (tiles <= 0) return cudaSuccess;
   const unsigned grid = (unsigned)(tiles < 2147483647 ? tiles : 2147483647);
-  tile_kernel<LBE_ST, 32, 8, 1><<<grid, 256, 0, s>>>(d, 1, tiles, parity, out);
+  tile_kernel<LBE_ST, 32, 8, 1><<<grid, 256, 0, s>>>(d, 1, tiles, parity, out, nullptr);
   return cudaGetLastError();
 }
 
@@ -83,12 +84,14 @@ bool stash_attr() {
 }
 template <int NC>
 cudaError_t stash_one(const InstDev* d, int n, int64_t items, int seg, int parity, int grid,
-                      int* err, cudaStream_t s) {
+                      int* err, int poll_lim, int withhold, const uint32_t* seed,
+                      cudaStream_t s) {
   if (!stash_attr<NC>()) return cudaErrorInvalidValue;
   if (grid <= 0) grid = 1;
   if ((int64_t)grid > items) grid = (int)items;
   stash_kernel<LBE_ST, NC>
-      <<<grid, NC, StashCfg<LBE_ST, NC>::SMEM, s>>>(d, n, items, seg, parity, err);
+      <<<grid, NC, StashCfg<LBE_ST, NC>::SMEM, s>>>(d, n, items, seg, parity, err, poll_lim,
+                                                    withhold, seed);
   return cudaGetLastError();
 }
 template <int NC>
@@ -103,8 +106,10 @@ int stash_occ() {
 }  // namespace
 
 cudaError_t LBE_CAT(launch_stash_, LBE_SUFFIX)(const InstDev* d, int n, int64_t items, int seg,
-                                                int parity, int grid, int* err, cudaStream_t s) {
-  return stash_one<128>(d, n, items, seg, parity, grid, err, s);
+                                                int parity, int grid, int* err, int poll_lim,
+                                                int withhold, const uint32_t* seed,
+                                                cudaStream_t s) {
+  return stash_one<128>(d, n, items, seg, parity, grid, err, poll_lim, withhold, seed, s);
 }
 int LBE_CAT(stash_occupancy_, LBE_SUFFIX)() { return stash_occ<128>(); }
 #endif

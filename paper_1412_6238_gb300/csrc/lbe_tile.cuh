@@ -46,15 +46,18 @@ __device__ __forceinline__ typename S::C wall_T(const InstDev& I, int x, int whi
   }
 }
 
-template <class S, int K>
+// RAW: in an interior row, the hbar deviations as stored (relative to their
+// source rows' T_r), for the moment T' (whose offsets cancel) and for
+// collide() with dhc = dh.
+template <class S, int K, bool RAW = false>
 __device__ __forceinline__ void pull9(const InstDev& I, const Phys<typename S::C>& P,
                                       const char* __restrict__ src, const Cell<S>& q,
                                       typename S::C out[9]) {
   using C = typename S::C;
-  constexpr bool DEV = (K == 2) && dev_h<S>();
   const size_t pitch = (size_t)I.pitch;
   const size_t r0 = (size_t)q.y * pitch + XG;
   const bool wb = (q.y == 0), wt = (q.y == I.ny - 1);
+  const bool DEV = (K == 2) && dev_h<S>() && (!RAW || wb || wt);
   C Tw = C(0);
   if (K == 2 && (wb || wt)) Tw = wall_T<S>(I, q.x, wb ? 0 : 1);
   const C dh = DEV ? P.dh : C(0);  // rho c_v (T_r(y) - T_r(y-1))
@@ -148,7 +151,7 @@ __device__ __forceinline__ void region_values(const InstDev& I, const Phys<typen
   if (need_pT) {
     pull9<S, 0>(I, P, src, q, v);
     p = sum9(v);
-    pull9<S, 2>(I, P, src, q, v);
+    pull9<S, 2, true>(I, P, src, q, v);
     T = dv(sum9(v), P.rho_cv, P.inv_rho_cv);
     if (ghost != 0) T = ghost_T<S>(I, q.x, ghost < 0, T);
   } else {
@@ -176,7 +179,7 @@ struct Tile {
   };
 
   __device__ static void run(const InstDev& I, int64_t tile, int parity, Smem& sm,
-                             double* __restrict__ out) {
+                             double* __restrict__ out, uint32_t step) {
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
     const int nx = I.nx, ny = I.ny;
@@ -195,7 +198,7 @@ struct Tile {
     if (active) {
       pull9<S, 0>(I, P, src, q, f);
       pull9<S, 1>(I, P, src, q, g);
-      pull9<S, 2>(I, P, src, q, h);
+      pull9<S, 2, true>(I, P, src, q, h);
       if constexpr (S::kind != ST_F64) {
         g0lo = ld_g0lo<S>(I, src, (size_t)gy * I.pitch + XG + gx);
         cc = moment_c(g, g0lo, clo);
@@ -276,9 +279,16 @@ struct Tile {
       char* __restrict__ dst = I.buf[parity ^ 1];
       const size_t rowbase = (size_t)gy * I.pitch;
       C lo_out = C(0);
+      // 16-bit forms: the cell's random bits for the stochastic rounding
+      const uint32_t hc =
+          S::SR ? sr_cell(sr_step_key(step, I.salt), (uint32_t)gy * (uint32_t)nx + (uint32_t)gx)
+                : 0u;
       collide<S>(P, f, g, h, cc, pp, TT, st.gpx, st.gpy, d,
-                 [&](int k, int i, C v) { st_cell<S>(I, dst, k, i, rowbase, gx, v); }, g0lo,
-                 clo, &lo_out);
+                 [&](int k, int i, C v) {
+                   if constexpr (S::SR) v = S::sr_value(I, k, i, v, hc);
+                   st_cell<S>(I, dst, k, i, rowbase, gx, v);
+                 },
+                 g0lo, clo, &lo_out, (gy > 0 && gy < ny - 1) ? P.dh : C(0));
       if constexpr (S::kind != ST_F64) st_cell_g0lo<S>(I, dst, rowbase, gx, (float)lo_out);
     }
   }
@@ -288,9 +298,11 @@ struct Tile {
 template <class S, int TX, int TY, int MODE>
 __global__ void __launch_bounds__(TX * TY, (S::kind == ST_F64 || TX * TY >= 512) ? 1 : 2)
 tile_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_tiles, int parity,
-            double* __restrict__ out) {
+            double* __restrict__ out, const uint32_t* __restrict__ seed) {
   using T = Tile<S, TX, TY, MODE>;
   __shared__ typename T::Smem sm;
+  // the step counter of the handle (random bits of the stochastic rounding)
+  const uint32_t step = (S::SR && MODE == 0) ? __ldg(seed) : 0u;
   for (int64_t t = blockIdx.x; t < total_tiles; t += gridDim.x) {
     int lo = 0, hi = n_inst - 1;
     while (lo < hi) {
@@ -298,7 +310,7 @@ tile_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_tiles, 
       if (insts[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
     }
     const InstDev& I = insts[lo];
-    T::run(I, t - I.tile_begin, parity, sm, out);
+    T::run(I, t - I.tile_begin, parity, sm, out, step);
     __syncthreads();
   }
 }
