@@ -393,11 +393,50 @@ def _timed(sim, steps):
     return t0.elapsed_time(t1)
 
 
+GOLDEN_DROP = os.path.join(ROOT, "tests", "golden", "longrun_drop.json")
+
+
+def error_vs_oracle(storage: str):
+    """Relative L2 error of u (as a vector) and T against the FP64 oracle's
+    stored end state of the 512 x 1024 drop after its stated 40 000 steps
+    (tests/golden/longrun_drop.json, written from the oracle alone), over the
+    golden's sampled points; None if the golden is missing or was made from
+    other inputs."""
+    import hashlib
+
+    import numpy as np
+
+    from paper_1412_6238_gb300 import workloads as wl
+    from paper_1412_6238_gb300.lbe import LBE
+    try:
+        G = json.load(open(GOLDEN_DROP))
+    except (OSError, ValueError):
+        return None
+    w = wl.droplet_512x1024()
+    h = hashlib.sha256()
+    for a in (w.c0, w.T0, w.Tbot, w.Ttop):
+        h.update(np.ascontiguousarray(a, dtype=np.float64).tobytes())
+    if h.hexdigest() != G["input_sha256"]:
+        return None
+    sim = LBE(w, storage=storage)
+    sim.step(G["steps"])
+    F = {k: v.numpy() for k, v in sim.fields(device="cpu").items()}
+    del sim
+    s, o = G["stride"], G["offset"]
+    A = {k: F[k][o::s, o::s] for k in ("ux", "uy", "T")}
+    B = {k: np.asarray(G["samples"][k]) for k in ("ux", "uy", "T")}
+    ua, ub = np.stack([A["ux"], A["uy"]]), np.stack([B["ux"], B["uy"]])
+    rel = lambda a, b: float(np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()))  # noqa: E731
+    return {"u": rel(ua, ub), "T": rel(A["T"], B["T"]), "steps": G["steps"],
+            "problem": "drop 512 x 1024, R = 32, Re = 1, Ma = 10, Ca = 0.05, ratios 0.5"}
+
+
 def measure_variants(args, w, ref_fields):
     """The same workload with 16-bit deviation storage (timed like the main
-    line; fields compared with the FP32 run after the same steps), and the
-    batched parameter sweep of 64 drops of uneven size in one persistent
-    launch per step against 64 sequential FP32 runs."""
+    line), each storage's error against the FP64 oracle on the 512 x 1024
+    drop after its 40 000 steps, and the batched parameter sweep of 64 drops
+    of uneven size in one persistent launch per step (launch shape chosen by
+    the autotuner) against 64 sequential FP32 runs."""
     import numpy as np
     import torch
 
@@ -429,19 +468,31 @@ def measure_variants(args, w, ref_fields):
                    "steps_compared": args.warmup + args.steps}
         del F
         torch.cuda.empty_cache()
+    # every storage's error against the oracle at the stated step count
+    out["error_vs_oracle"] = {st: error_vs_oracle(st)
+                              for st in ("f32", "f16mix", "f16dev", "bf16dev")}
+    torch.cuda.empty_cache()
 
     # batched sweep (64 drops, grids 128x256 .. 768x1536, seed 0)
     sweep = wl.batch_sweep(64, seed=0)
     cells = sum(x.cells for x in sweep)
     K = args.batch_steps
     res = {"instances": len(sweep), "cells": cells, "steps": K}
-    for st in ("f16mix", "f16dev", "f32"):
-        sim = LBE(sweep, storage=st)
-        sim.step(3)
-        ms = _timed(sim, K)
-        res["batched_" + st] = cells * K / (ms / 1e3) / 1e6
-        del sim
-        torch.cuda.empty_cache()
+    from paper_1412_6238_gb300 import autotune
+    tuned = {}
+    with tempfile.TemporaryDirectory() as td:
+        os.environ["LBE_AUTOTUNE_CACHE"] = os.path.join(td, "tune.json")
+        for st in ("f16mix", "f16dev", "f32"):
+            sim = LBE(sweep, storage=st)
+            sim.step(3)
+            best = autotune.tune(sim, steps=5, warmup=2)
+            tuned[st] = {k: best[k] for k in ("kernel", "grid", "seg_rows")}
+            ms = _timed(sim, K)
+            res["batched_" + st] = cells * K / (ms / 1e3) / 1e6
+            del sim
+            torch.cuda.empty_cache()
+        os.environ.pop("LBE_AUTOTUNE_CACHE", None)
+    res["autotuned"] = tuned
     seq_ms = 0.0
     for x in sweep:
         sim = LBE(x, storage="f32")

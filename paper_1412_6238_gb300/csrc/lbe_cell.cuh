@@ -470,6 +470,20 @@ __device__ __forceinline__ void collide(const Phys<typename S::C>& P, const type
   }
 }
 
+// 16-bit forms: g_0 as c minus the stored (16-bit, stochastically rounded)
+// moving g_i, gsum (their exact sum: eight 16-bit values), as two floats:
+// the stored populations then carry the cell's c exactly, whatever the
+// rounding of the g_i, so that sum c is conserved to the two-float precision
+// of g_0 (a rounding of the g_i toward zero, as for the tiniest FP16 values,
+// would otherwise drain it).  In exact arithmetic this is the relaxed g_0,
+// since the collision conserves c and the source has no zeroth moment.
+__device__ __forceinline__ void g0_remainder(float cc, float clo, float gsum, float& hi,
+                                             float& lo) {
+  float s, e;
+  two_sum(cc, -gsum, s, e);
+  fast_two_sum(s, e + clo, hi, lo);
+}
+
 // Store one population of cell x (row base offset rowbase) and its periodic
 // ghost copies: element XG + x holds cell x; elements 0..XG-1 repeat cells
 // nx-XG..nx-1 and elements nx+XG..nx+2XG-1 repeat cells 0..XG-1.

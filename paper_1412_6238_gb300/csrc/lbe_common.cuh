@@ -295,13 +295,18 @@ struct StDev {
     put2(reinterpret_cast<E*>(b + (size_t)(i - 1) * I.pair_bytes) + 2 * idx, fv * I.s[0],
          gv * I.s[1]);
   }
-  // the same, stochastically rounded with the random word r
-  __device__ static __forceinline__ void st_fg_sr(const InstDev& I, char* b, int i, size_t idx,
-                                                  float fv, float gv, uint32_t r) {
+  // the same, stochastically rounded with the random word r; returns the
+  // stored g_i scaled by s_1 (exact)
+  __device__ static __forceinline__ float st_fg_sr(const InstDev& I, char* b, int i, size_t idx,
+                                                   float fv, float gv, uint32_t r) {
     const uint32_t q = BF ? sr_pack_bf162(fv * I.s[0], gv * I.s[1], r)
                           : sr_pack_half2(fv * I.s[0], gv * I.s[1], r);
     *reinterpret_cast<uint32_t*>(reinterpret_cast<E*>(b + (size_t)(i - 1) * I.pair_bytes) +
                                  2 * idx) = q;
+    if constexpr (BF)
+      return __uint_as_float(q & 0xffff0000u);
+    else
+      return __half2float(__ushort_as_half((unsigned short)(q >> 16)));
   }
   // one 16-bit value (not g_0), stochastically rounded
   __device__ static __forceinline__ void st_sr(const InstDev& I, char* b, int k, int i, size_t idx,

@@ -620,13 +620,20 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
             reinterpret_cast<uint2*>(dst + (size_t)ii * I.pair_bytes)[e] =
                 make_uint2(__float_as_uint(fv), u);
           };
+          float gs = 0.f;  // the stored g_i, times s_1
+#pragma unroll
+          for (int ii = 1; ii < 9; ii++) {
+            const uint32_t q =
+                sr_pack_half2(o[9 + ii] * s1, o[18 + ii] * s2, S::sr_word(1, ii, hc));
+            gs += __half2float(__ushort_as_half((unsigned short)(q & 0xffffu)));
+            word(ii, o[ii], q);
+          }
+          float g0h, g0l;
+          g0_remainder(cc, clo, gs * P.inv_s[1], g0h, g0l);
           word(0, o[0],
                (uint32_t)__half_as_ushort(sr_half(o[18] * s2, S::sr_word(2, 0, hc))) |
-                   ((uint32_t)__half_as_ushort(__float2half_rn(lo_out * G0LO_SCALE)) << 16));
-#pragma unroll
-          for (int ii = 1; ii < 9; ii++)
-            word(ii, o[ii], sr_pack_half2(o[9 + ii] * s1, o[18 + ii] * s2, S::sr_word(1, ii, hc)));
-          reinterpret_cast<float*>(dst + I.g0_off)[e] = o[9];
+                   ((uint32_t)__half_as_ushort(__float2half_rn(g0l * G0LO_SCALE)) << 16));
+          reinterpret_cast<float*>(dst + I.g0_off)[e] = g0h;
         } else if constexpr (!W16) {
           st_g0lo<S>(I, dst, e, lo_out);
 #pragma unroll
@@ -634,12 +641,15 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
 #pragma unroll
           for (int ii = 0; ii < 9; ii++) S::st(I, dst, 2, ii, e, o[18 + ii]);
         } else {
-          st_g0lo<S>(I, dst, e, lo_out);
           S::st_sr(I, dst, 0, 0, e, o[0], S::sr_word(0, 0, hc));
-          S::st(I, dst, 1, 0, e, o[9]);
+          float gs = 0.f;  // the stored g_i, times s_1
 #pragma unroll
           for (int ii = 1; ii < 9; ii++)
-            S::st_fg_sr(I, dst, ii, e, o[ii], o[9 + ii], S::sr_word(0, ii, hc));
+            gs += S::st_fg_sr(I, dst, ii, e, o[ii], o[9 + ii], S::sr_word(0, ii, hc));
+          float g0h, g0l;
+          g0_remainder(cc, clo, gs * P.inv_s[1], g0h, g0l);
+          S::st(I, dst, 1, 0, e, g0h);
+          st_g0lo<S>(I, dst, e, g0l);
 #pragma unroll
           for (int ii = 0; ii < 9; ii++)
             S::st_sr(I, dst, 2, ii, e, o[18 + ii], S::sr_word(2, ii, hc));

@@ -283,12 +283,23 @@ struct Tile {
       const uint32_t hc =
           S::SR ? sr_cell(sr_step_key(step, I.salt), (uint32_t)gy * (uint32_t)nx + (uint32_t)gx)
                 : 0u;
+      C gs = C(0);  // 16-bit forms: the stored moving g_i
       collide<S>(P, f, g, h, cc, pp, TT, st.gpx, st.gpy, d,
                  [&](int k, int i, C v) {
-                   if constexpr (S::SR) v = S::sr_value(I, k, i, v, hc);
+                   if constexpr (S::SR) {
+                     v = S::sr_value(I, k, i, v, hc);
+                     if (k == 1 && i > 0) gs += v;
+                   }
                    st_cell<S>(I, dst, k, i, rowbase, gx, v);
                  },
                  g0lo, clo, &lo_out, (gy > 0 && gy < ny - 1) ? P.dh : C(0));
+      if constexpr (S::SR) {
+        // g_0 as c minus the stored g_i (as the strip kernel stores it)
+        float g0h, g0l;
+        g0_remainder(cc, clo, gs, g0h, g0l);
+        st_cell<S>(I, dst, 1, 0, rowbase, gx, g0h);
+        lo_out = g0l;
+      }
       if constexpr (S::kind != ST_F64) st_cell_g0lo<S>(I, dst, rowbase, gx, (float)lo_out);
     }
   }

@@ -78,15 +78,18 @@ def test_copy_wait_runs_out_reports_ecuda_and_recovers(lbe_mod, storage):
         sim.step(1)
     assert e3.value.status == -6
     # a new state clears the condition; the hook applied to one launch only,
-    # so the handle then follows a fresh one (to the rounding of the state's
-    # round trip through FP64: measured 1.4e-7 of the maximum of u in FP32)
+    # so the handle then follows a fresh one: in FP32 to the rounding of the
+    # state's round trip through FP64 (measured 1.4e-7 of the maximum of u);
+    # with 16-bit storage to its stochastic rounding, whose random bits
+    # follow the handle's step count (3 steps ahead of the fresh handle's)
     sim.set_state(start)
     sim.step(7)
     sim.synchronize()
     got = sim.fields(device="cpu")
+    tol = 1e-6 if storage == "f32" else 1e-2
     for k in ("c", "ux", "uy", "T"):
         a, b = got[k].numpy(), want[k].numpy()
-        assert np.abs(a - b).max() <= 1e-6 * np.abs(b).max(), k
+        assert np.abs(a - b).max() <= tol * np.abs(b).max(), (k, np.abs(a - b).max())
 
 
 def test_host_wait_limit_returns_etimeout(lbe_mod):
