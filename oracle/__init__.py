@@ -32,8 +32,8 @@ PARAM_KEYS = ("rho", "cv", "eta1", "eta2", "lam1", "lam2", "sigma0", "sigmaT",
 
 class _Params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
-                ("periodic_y", ctypes.c_int32), ("reserved", ctypes.c_int32)] + \
-               [(k, ctypes.c_double) for k in PARAM_KEYS]
+                ("periodic_y", ctypes.c_int32), ("ablate", ctypes.c_int32)] + \
+               [(k, ctypes.c_double) for k in PARAM_KEYS] + [("rho2", ctypes.c_double)]
 
 
 _lock = threading.Lock()
@@ -86,6 +86,10 @@ def _p(params: dict, nx: int, ny: int) -> _Params:
     s.periodic_y = int(params.get("periodic_y", 0))
     for k in PARAM_KEYS:
         setattr(s, k, float(params[k]))
+    # density of phase c = 1 (default: uniform density); ablate: test hook
+    # planting a mistake in the density terms (see lbe_oracle.c)
+    s.rho2 = float(params.get("rho2", params["rho"]))
+    s.ablate = int(params.get("ablate", 0))
     return s
 
 

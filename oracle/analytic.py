@@ -2,7 +2,8 @@
 
 TEST INFRASTRUCTURE ONLY (part of the oracle package).
 
-* Two-layer thermal Poiseuille flow: steady u_x(y), Eq. 32, and T(y), Eq. 33.
+* Two-layer thermal Poiseuille flow: steady u_x(y), Eq. 32, and T(y), Eq. 33;
+  the same flow with layers of unequal density under a body force rho a.
 * Two superimposed planar fluids with a sinusoidal wall temperature (Pendse and
   Esmaeeli, as restated in Sec. IV.B), with three misprints read as follows:
   "cost(kx)" is cos(kx); the first of the two printed C^h_2 is C^h_1; C^h_3 is
@@ -31,6 +32,22 @@ def poiseuille_u(y, h, H, eta_lower, eta_upper, rho, ax):
         -(y / H) ** 2
         + ((e1 - h * h / (H * H) * e2) / (e1 + h / H * e2)) * (y / H)
         + (1 + h / H) * h * e2 / (e1 * H + e2 * h))
+    return np.where(y <= 0, lo, up)
+
+
+def poiseuille_u_rho(y, h, H, eta_lower, eta_upper, rho_lower, rho_upper, ax):
+    """Steady u_x of two layers of unequal density under the body force
+    rho_k ax of each: eta_k u'' = -rho_k ax in each layer, no slip at y = -h
+    and y = H, u and eta u' continuous at y = 0.  With rho_lower = rho_upper
+    this is Eq. 32.  u_k = -rho_k ax y^2 / (2 eta_k) + A_k y + B with
+    eta_lower A_lower = eta_upper A_upper and B from the wall conditions."""
+    y = np.asarray(y, dtype=np.float64)
+    e1, e2, r1, r2 = eta_lower, eta_upper, rho_lower, rho_upper
+    A1 = (r2 * ax * H * H / (2 * e2) - r1 * ax * h * h / (2 * e1)) / (h + e1 * H / e2)
+    A2 = e1 * A1 / e2
+    B = r1 * ax * h * h / (2 * e1) + A1 * h
+    lo = -r1 * ax * y * y / (2 * e1) + A1 * y + B
+    up = -r2 * ax * y * y / (2 * e2) + A2 * y + B
     return np.where(y <= 0, lo, up)
 
 

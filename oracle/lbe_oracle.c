@@ -51,14 +51,26 @@
 typedef struct {
   int32_t nx, ny;
   int32_t periodic_y; /* 0: walls at y=-1/2 and y=ny-1/2; 1: periodic in y */
-  int32_t reserved;
-  double rho, cv;
+  int32_t ablate;     /* test hook, 0 normally: bit 0 drops the grad(rho cs2)
+                         source of Eq. 12, bit 1 the pressure correction of
+                         Eq. 13, bit 2 grad(rho cs2) in Fbar (planted
+                         mistakes the density pins must detect) */
+  double rho, cv;     /* rho: density of phase c = 0 (see rho2) */
   double eta1, eta2, lam1, lam2; /* phase c=0 and phase c=1 */
   double sigma0, sigmaT, Tref;   /* sigma = sigma0 - sigmaT (T - Tref) */
   double eps, beta, tau_g, mobility;
   double ax, ay;   /* body acceleration */
   double eta_n;    /* regularisation of n = grad c / sqrt(|grad c|^2+eta_n^2) */
+  double rho2;     /* density of phase c = 1 (rho2 = rho: uniform density) */
 } orc_params;
+
+/* Density of a cell, linear in c like eta and lambda (the paper states no
+ * interpolation): rho(c) = rho1 + c (rho2 - rho1).  With rho2 = rho1 every
+ * expression below reduces exactly to the uniform-density one. */
+static double rho_of(const orc_params* P, double c) {
+  return P->rho + c * (P->rho2 - P->rho);
+}
+static int varying_rho(const orc_params* P) { return P->rho2 != P->rho; }
 
 /* ---- D2Q9 lattice (the paper names D2Q9 weights but does not list them) */
 static const int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
@@ -116,11 +128,15 @@ static double h_equilibrium(int i, double rho, double cv, double T, double ux,
 }
 
 /* ---- Eq. 12 source (without the (1 - omega/2) factor):
- *      F.(xi_i - u) Gamma_i(u) + (xi_i - u).grad(rho cs2) (Gamma_i(u) - Gamma_i(0)).
- *      rho is uniform here, so the second term vanishes (grad rho = 0). */
-static double f_source(int i, double Fx, double Fy, double ux, double uy) {
+ *      F.(xi_i - u) Gamma_i(u) + (xi_i - u).grad(rho cs2) (Gamma_i(u) - Gamma_i(0)),
+ *      Gamma_i(0) = w_i; (dRx, dRy) = grad(rho cs2), zero for uniform rho
+ *      (then the second term is left out). */
+static double f_source(int i, double Fx, double Fy, double ux, double uy, double dRx,
+                       double dRy, int with_drho) {
   double G = gamma_i(i, ux, uy);
-  return (Fx * (EX[i] - ux) + Fy * (EY[i] - uy)) * G;
+  double s = (Fx * (EX[i] - ux) + Fy * (EY[i] - uy)) * G;
+  if (with_drho) s += ((EX[i] - ux) * dRx + (EY[i] - uy) * dRy) * (G - W[i]);
+  return s;
 }
 
 /* ---- Eq. 27 source (without the (1 - omega/2) factor):
@@ -134,11 +150,15 @@ static double g_source(int i, double c, double rho, double Fx, double Fy,
 
 /* ---- Eq. aEq12 source (without the (1 - omega/2) factor):
  *      Fbar.(xi_i - u)/(rho cs2) h_eq_i, Fbar = grad(rho cs2) - grad p + F
- *      (after Eq. aEq4); grad(rho cs2) = 0 for uniform rho. */
+ *      (after Eq. aEq4); grad(rho cs2) = (dRx, dRy), zero for uniform rho. */
 static double h_source(int i, double rho, double cv, double T, double Fx,
                        double Fy, double gpx, double gpy, double ux,
-                       double uy) {
+                       double uy, double dRx, double dRy, int with_drho) {
   double Fbx = Fx - gpx, Fby = Fy - gpy;
+  if (with_drho) {
+    Fbx = dRx + Fbx;
+    Fby = dRy + Fby;
+  }
   return (Fbx * (EX[i] - ux) + Fby * (EY[i] - uy)) / (rho * CS2) *
          h_equilibrium(i, rho, cv, T, ux, uy);
 }
@@ -154,9 +174,9 @@ void orc_cell_terms(const orc_params* P, double c, double p, double T,
     feq[i] = f_equilibrium(i, p, P->rho, ux, uy);
     geq[i] = g_equilibrium(i, c, mu, Gm, ux, uy);
     heq[i] = h_equilibrium(i, P->rho, P->cv, T, ux, uy);
-    fsrc[i] = f_source(i, Fx, Fy, ux, uy);
+    fsrc[i] = f_source(i, Fx, Fy, ux, uy, 0.0, 0.0, 0);
     gsrc[i] = g_source(i, c, P->rho, Fx, Fy, gpx, gpy, ux, uy);
-    hsrc[i] = h_source(i, P->rho, P->cv, T, Fx, Fy, gpx, gpy, ux, uy);
+    hsrc[i] = h_source(i, P->rho, P->cv, T, Fx, Fy, gpx, gpy, ux, uy, 0.0, 0.0, 0);
   }
 }
 
@@ -292,8 +312,8 @@ static void scalar_stage(const orc_params* P, const double* Tbot,
       Fx += -P->sigmaT * ea * (g2 * gTx - cdT * gcx);
       Fy += -P->sigmaT * ea * (g2 * gTy - cdT * gcy);
       /* body force, part of the total F of Eq. 1 */
-      Fx += P->rho * P->ax;
-      Fy += P->rho * P->ay;
+      Fx += rho_of(P, cc) * P->ax;
+      Fy += rho_of(P, cc) * P->ay;
 
       o->gcx[k] = gcx;
       o->gcy[k] = gcy;
@@ -362,11 +382,39 @@ static void moments(const orc_params* P, const double* pop, double* c,
       sh += pop[(size_t)(18 + i) * N + k];
     }
     c[k] = sg;           /* Eq. 28 */
-    p[k] = sf;           /* Eq. 13; u.grad(rho cs2) = 0 for uniform rho */
-    T[k] = sh / (P->rho * P->cv); /* Eq. aEq13 */
+    p[k] = sf;           /* Eq. 13 without (dt/2) u.grad(rho cs2): see p_correct */
+    T[k] = sh / (rho_of(P, sg) * P->cv); /* Eq. aEq13 */
     jx[k] = sx;
     jy[k] = sy;
   }
+}
+
+/* Eq. 13 with a varying density: p = sum f_i + (dt/2) u.grad(rho cs2), with
+ * grad(rho cs2) = cs2 (rho2 - rho1) grad c (the isotropic gradient of the
+ * interpolated density: the stencil is linear).  p is corrected in place. */
+static void p_correct(const orc_params* P, const double* c, const double* ux,
+                      const double* uy, const scalar_out* o, double* p) {
+  const size_t N = (size_t)P->nx * P->ny;
+  const double dr = CS2 * (P->rho2 - P->rho);
+  (void)c;
+  for (size_t k = 0; k < N; k++)
+    p[k] = p[k] + 0.5 * (ux[k] * (dr * o->gcx[k]) + uy[k] * (dr * o->gcy[k]));
+}
+
+/* The isotropic gradient of a cell field whose ghost rows mirror (as p's). */
+static void grad_mirrored(const orc_params* P, const double* Tbot, const double* Ttop,
+                          const double* v, double* gx, double* gy) {
+  const int nx = P->nx, ny = P->ny;
+  ext_field e = ext_new(nx, ny, 1);
+  for (int y = 0; y < ny; y++)
+    for (int x = 0; x < nx; x++) *ext_at(&e, x, y) = v[(size_t)y * nx + x];
+  fill_ghosts(P, &e, 0, Tbot, Ttop);
+  for (int y = 0; y < ny; y++)
+    for (int x = 0; x < nx; x++) {
+      size_t k = (size_t)y * nx + x;
+      grad_iso(&e, x, y, &gx[k], &gy[k]);
+    }
+  free(e.v);
 }
 
 /* Macroscopic fields (c, p, u, T) of a population state. */
@@ -380,9 +428,11 @@ void orc_fields(const orc_params* P, const double* Tbot, const double* Ttop,
   scalar_out o = scalar_out_new(N);
   scalar_stage(P, Tbot, Ttop, c, p, T, &o);
   for (size_t k = 0; k < N; k++) {
-    ux[k] = jx[k] / (P->rho * CS2) + 0.5 * o.Fx[k] / P->rho;
-    uy[k] = jy[k] / (P->rho * CS2) + 0.5 * o.Fy[k] / P->rho;
+    const double rho = rho_of(P, c[k]);
+    ux[k] = jx[k] / (rho * CS2) + 0.5 * o.Fx[k] / rho;
+    uy[k] = jy[k] / (rho * CS2) + 0.5 * o.Fy[k] / rho;
   }
+  if (varying_rho(P) && !(P->ablate & 2)) p_correct(P, c, ux, uy, &o, p);
   scalar_out_free(&o);
   free(jx);
   free(jy);
@@ -395,10 +445,27 @@ static void step_once(const orc_params* P, const double* Tbot,
                       double* jx, double* jy, scalar_out* o) {
   const int nx = P->nx, ny = P->ny;
   const size_t N = (size_t)nx * ny;
-  const double rho = P->rho, cv = P->cv;
+  const double cv = P->cv;
+  const int vrho = varying_rho(P);
+  const double dr = CS2 * (P->rho2 - P->rho); /* grad(rho cs2) = dr grad c */
 
   moments(P, in, c, p, T, jx, jy);
   scalar_stage(P, Tbot, Ttop, c, p, T, o);
+  if (vrho && !(P->ablate & 2)) {
+    /* Eq. 13: p needs u, u needs F, F needs no p; grad p is then taken of
+       the corrected p */
+    double* ux = malloc(N * sizeof(double));
+    double* uy = malloc(N * sizeof(double));
+    for (size_t k = 0; k < N; k++) {
+      const double rho = rho_of(P, c[k]);
+      ux[k] = jx[k] / (rho * CS2) + 0.5 * o->Fx[k] / rho;
+      uy[k] = jy[k] / (rho * CS2) + 0.5 * o->Fy[k] / rho;
+    }
+    p_correct(P, c, ux, uy, o, p);
+    grad_mirrored(P, Tbot, Ttop, p, o->gpx, o->gpy);
+    free(ux);
+    free(uy);
+  }
 
   const double omega_g = 1.0 / P->tau_g;             /* Eq. 27 */
   const double Gm = P->mobility / (P->tau_g - 0.5);  /* M = Gamma (tau_g - 1/2), Eq. 16 */
@@ -407,6 +474,7 @@ static void step_once(const orc_params* P, const double* Tbot,
   for (long long kk = 0; kk < (long long)N; kk++) {
     size_t k = (size_t)kk;
     double cc = c[k], TT = T[k];
+    const double rho = rho_of(P, cc);
     /* properties, linear in c */
     double eta = P->eta1 + cc * (P->eta2 - P->eta1);
     double lam = P->lam1 + cc * (P->lam2 - P->lam1);
@@ -418,11 +486,14 @@ static void step_once(const orc_params* P, const double* Tbot,
     double Fx = o->Fx[k], Fy = o->Fy[k];
     double ux = jx[k] / (rho * CS2) + 0.5 * Fx / rho;
     double uy = jy[k] / (rho * CS2) + 0.5 * Fy / rho;
+    const double dRx = dr * o->gcx[k], dRy = dr * o->gcy[k];
     for (int i = 0; i < 9; i++) {
       double f = in[(size_t)i * N + k];
       double feq = f_equilibrium(i, p[k], rho, ux, uy);
       post[(size_t)i * N + k] =
-          f - omega_f * (f - feq) + (1.0 - 0.5 * omega_f) * f_source(i, Fx, Fy, ux, uy);
+          f - omega_f * (f - feq) +
+          (1.0 - 0.5 * omega_f) *
+              f_source(i, Fx, Fy, ux, uy, dRx, dRy, vrho && !(P->ablate & 1));
 
       double g = in[(size_t)(9 + i) * N + k];
       double geq = g_equilibrium(i, cc, o->mu[k], Gm, ux, uy);
@@ -436,7 +507,8 @@ static void step_once(const orc_params* P, const double* Tbot,
       post[(size_t)(18 + i) * N + k] =
           h - omega_T * (h - heq) +
           (1.0 - 0.5 * omega_T) *
-              h_source(i, rho, cv, TT, Fx, Fy, o->gpx[k], o->gpy[k], ux, uy);
+              h_source(i, rho, cv, TT, Fx, Fy, o->gpx[k], o->gpy[k], ux, uy, dRx, dRy,
+                       vrho && !(P->ablate & 4));
     }
   }
 
@@ -467,7 +539,7 @@ static void step_once(const orc_params* P, const double* Tbot,
           out[(size_t)(9 + i) * N + k] = post[(size_t)(9 + o_) * N + k];
           /* anti-bounce-back fixes T = T_w at the wall (u = 0 there) */
           out[(size_t)(18 + i) * N + k] =
-              -post[(size_t)(18 + o_) * N + k] + 2.0 * W[i] * rho * cv * Tw;
+              -post[(size_t)(18 + o_) * N + k] + 2.0 * W[i] * rho_of(P, c[k]) * cv * Tw;
         }
       }
     }
@@ -514,7 +586,8 @@ int orc_init(const orc_params* P, const double* c0, const double* T0,
     for (int i = 0; i < 9; i++) {
       pop[(size_t)i * N + k] = f_equilibrium(i, 0.0, P->rho, 0.0, 0.0);
       pop[(size_t)(9 + i) * N + k] = g_equilibrium(i, c0[k], o.mu[k], Gm, 0.0, 0.0);
-      pop[(size_t)(18 + i) * N + k] = h_equilibrium(i, P->rho, P->cv, T0[k], 0.0, 0.0);
+      pop[(size_t)(18 + i) * N + k] =
+          h_equilibrium(i, rho_of(P, c0[k]), P->cv, T0[k], 0.0, 0.0);
     }
   }
   scalar_out_free(&o);
