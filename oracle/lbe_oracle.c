@@ -512,11 +512,15 @@ static void step_once(const orc_params* P, const double* Tbot,
     }
   }
 
-  /* streaming, pull form: P_i(x, t+1) = P*_i(x - xi_i, t) */
+  /* streaming, pull form: P_i(x, t+1) = P*_i(x - xi_i, t); f and g first,
+     then hbar, whose anti-bounce-back at a wall takes rho of the cell's new
+     c (the c the next step's moments see; with a varying density this is
+     the density the wall term needs at the time the pull applies it) */
 #pragma omp parallel for schedule(static)
   for (int y = 0; y < ny; y++)
     for (int x = 0; x < nx; x++) {
       size_t k = (size_t)y * nx + x;
+      for (int pass = 0; pass < 2; pass++)
       for (int i = 0; i < 9; i++) {
         int xs = ((x - EX[i]) % nx + nx) % nx;
         int ys = y - EY[i];
@@ -527,19 +531,27 @@ static void step_once(const orc_params* P, const double* Tbot,
           wall = 1;
         if (!wall) {
           size_t ks = (size_t)ys * nx + xs;
-          out[(size_t)i * N + k] = post[(size_t)i * N + ks];
-          out[(size_t)(9 + i) * N + k] = post[(size_t)(9 + i) * N + ks];
-          out[(size_t)(18 + i) * N + k] = post[(size_t)(18 + i) * N + ks];
+          if (pass == 0) {
+            out[(size_t)i * N + k] = post[(size_t)i * N + ks];
+            out[(size_t)(9 + i) * N + k] = post[(size_t)(9 + i) * N + ks];
+          } else {
+            out[(size_t)(18 + i) * N + k] = post[(size_t)(18 + i) * N + ks];
+          }
         } else {
           /* halfway bounce-back: the population that left this cell towards
              the wall returns reversed one step later */
           int o_ = OPP[i];
           double Tw = (ys < 0) ? Tbot[x] : Ttop[x];
-          out[(size_t)i * N + k] = post[(size_t)o_ * N + k];
-          out[(size_t)(9 + i) * N + k] = post[(size_t)(9 + o_) * N + k];
-          /* anti-bounce-back fixes T = T_w at the wall (u = 0 there) */
-          out[(size_t)(18 + i) * N + k] =
-              -post[(size_t)(18 + o_) * N + k] + 2.0 * W[i] * rho_of(P, c[k]) * cv * Tw;
+          if (pass == 0) {
+            out[(size_t)i * N + k] = post[(size_t)o_ * N + k];
+            out[(size_t)(9 + i) * N + k] = post[(size_t)(9 + o_) * N + k];
+          } else {
+            /* anti-bounce-back fixes T = T_w at the wall (u = 0 there) */
+            double cn = 0.0;
+            for (int j = 0; j < 9; j++) cn += out[(size_t)(9 + j) * N + k];
+            out[(size_t)(18 + i) * N + k] =
+                -post[(size_t)(18 + o_) * N + k] + 2.0 * W[i] * rho_of(P, cn) * cv * Tw;
+          }
         }
       }
     }
