@@ -64,7 +64,7 @@
 extern "C" {
 #endif
 
-#define LBE_ABI_VERSION 1
+#define LBE_ABI_VERSION 2
 
 typedef struct lbe_handle lbe_handle;
 
@@ -95,15 +95,16 @@ typedef enum {
 } lbe_storage;
 
 /* Parameters of one instance, lattice units.  Validity (LBE_EINVAL
- * otherwise): nx >= 1, ny >= 2, rho > 0, cv > 0, eta1, eta2 > 0,
- * lam1, lam2 >= 0, eps > 0, tau_g > 1/2, mobility >= 0, eta_n > 0, and
- * 0 < omega < 2 for every relaxation rate at c = 0 and c = 1. */
+ * otherwise): nx >= 1, ny >= 2, rho > 0, rho2 >= 0, cv > 0, eta1,
+ * eta2 > 0, lam1, lam2 >= 0, eps > 0, tau_g > 1/2, mobility >= 0,
+ * eta_n > 0, and 0 < omega < 2 for every relaxation rate at c = 0 and
+ * c = 1.  Layout change from ABI version 1: rho2 appended. */
 typedef struct {
   int32_t nx, ny;       /* cells; periodic in x, walls in y           */
   int32_t storage;      /* lbe_storage; must be equal for all instances */
   int32_t check_every;  /* FP64 sums + NaN scan every k steps of lbe_step
                            (then lbe_step waits for the stream); 0 = off */
-  double rho, cv;       /* density (uniform), specific heat            */
+  double rho, cv;       /* density of phase c = 0, specific heat       */
   double eta1, eta2;    /* dynamic viscosity of phase c=0, c=1         */
   double lam1, lam2;    /* conductivity of phase c=0, c=1              */
   double sigma0, sigmaT, Tref; /* sigma = sigma0 - sigmaT (T - Tref)   */
@@ -113,6 +114,14 @@ typedef struct {
   double mobility;      /* M = Gamma (tau_g - 1/2) (Eq. 16)            */
   double ax, ay;        /* body acceleration (force rho a)             */
   double eta_n;         /* n = grad c / sqrt(|grad c|^2 + eta_n^2)      */
+  double rho2;          /* density of phase c = 1; 0 (or rho): uniform.
+                           A density varying with c, rho(c) = rho + c
+                           (rho2 - rho), brings in the grad(rho c_s^2)
+                           source of Eq. 12, the pressure correction
+                           (dt/2) u.grad(rho c_s^2) of Eq. 13 and
+                           grad(rho c_s^2) in the thermal force of Eq. aEq4;
+                           it needs FP64 storage (LBE_EINVAL otherwise) and
+                           is not covered by lbe_adjoint                  */
 } lbe_params;
 
 /* Initial and boundary data of one instance (host pointers, copied). */

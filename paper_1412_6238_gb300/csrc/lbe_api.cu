@@ -27,6 +27,7 @@ struct InstHost {
   uint64_t pair_bytes = 0, h_off = 0, f0_off = 0;  // pair layouts
   char* arena = nullptr;  // two buffers of buf_bytes
   double* walls = nullptr;  // device: Tbot[nx], Ttop[nx], then 4 float tables
+  double* pcorr = nullptr;  // device [ny][nx]: corrected p (varying density only)
   std::vector<double> Tbot, Ttop;
   std::vector<float> wdev;  // host copy of the T_w - T_r tables
 };
@@ -44,6 +45,10 @@ struct lbe_handle {
   std::vector<InstDev> idev;     // step descriptors (tile_begin for the step shape)
   InstDev* d_inst = nullptr;     // [n] for the step kernel
   InstDev* d_finst = nullptr;    // [n] for the field kernel (shape 0, tile_begin 0)
+  bool vrho = false;             // varying density (rho2 != rho; FP64 storage)
+  InstDev* d_pinst = nullptr;    // [n] shape-0 work list of the pcorr pass (vrho)
+  int64_t p_tiles = 0;           // its tiles
+  int p_grid = 0;                // its CTAs
   int tile = 0;
   int grid_req = 0;              // 0 = auto, -1 = one CTA per tile, >0 = CTAs
   int grid = 0;
@@ -162,6 +167,10 @@ int fault_withhold() {
   return r >= 0 ? r : -1;
 }
 
+// Density of phase c = 1 differs from that of phase c = 0 (rho2 = 0 means
+// rho2 = rho).
+bool varying_rho(const lbe_params& p) { return p.rho2 > 0 && p.rho2 != p.rho; }
+
 lbe_status check_params(const lbe_params& p, int index) {
   auto bad = [&](const char* what) {
     return fail(nullptr, LBE_EINVAL, "instance %d: %s", index, what);
@@ -181,6 +190,9 @@ lbe_status check_params(const lbe_params& p, int index) {
   const double vals[] = {p.beta, p.sigma0, p.sigmaT, p.Tref, p.ax, p.ay};
   for (double v : vals)
     if (!std::isfinite(v)) return bad("non-finite parameter");
+  if (!(p.rho2 >= 0) || !std::isfinite(p.rho2)) return bad("rho2 must be >= 0 (0: rho2 = rho)");
+  if (varying_rho(p) && p.storage != LBE_F64)
+    return bad("a density ratio (rho2 != rho) needs FP64 storage");
   return LBE_OK;
 }
 
@@ -225,6 +237,10 @@ void fill_desc(lbe_handle* h, int j, InstDev& D) {
   P.Gm = p.mobility / (p.tau_g - 0.5);
   P.Fbx = p.rho * p.ax;
   P.Fby = p.rho * p.ay;
+  P.ax = p.ax;
+  P.ay = p.ay;
+  P.drho = varying_rho(p) ? p.rho2 - p.rho : 0.0;
+  D.pcorr = H.pcorr;
   P.eta_n2 = p.eta_n * p.eta_n;
   // hbar reference: linear profile between the mean wall temperatures
   double tb = 0, tt = 0;
@@ -277,8 +293,10 @@ void free_handle(lbe_handle* h) {
   for (auto& H : h->inst) {
     if (H.arena) cudaFree(H.arena);
     if (H.walls) cudaFree(H.walls);
+    if (H.pcorr) cudaFree(H.pcorr);
   }
   if (h->d_inst) cudaFree(h->d_inst);
+  if (h->d_pinst) cudaFree(h->d_pinst);
   if (h->d_err) cudaFree(h->d_err);
   if (h->d_seed) cudaFree(h->d_seed);
   if (h->d_finst) cudaFree(h->d_finst);
@@ -392,8 +410,13 @@ cudaError_t launch_one_step(lbe_handle* h, int parity) {
       e = launch_ghosts(h->d_inst, h->n, h->max_ny, parity ^ 1, h->d_seed, h->stream);
     return e;
   }
-  cudaError_t e = launch_step(h->storage, h->tile, h->d_inst, h->n, h->total_tiles, parity,
-                              h->grid, h->d_seed, h->stream);
+  cudaError_t e = cudaSuccess;
+  // varying density: the corrected p of Eq. 13 (and so its gradient) needs
+  // u of every cell first, a pass of its own
+  if (h->vrho) e = pcorr_f64(h->d_pinst, h->n, h->p_tiles, parity, h->p_grid, h->stream);
+  if (e == cudaSuccess)
+    e = launch_step(h->storage, h->tile, h->d_inst, h->n, h->total_tiles, parity, h->grid,
+                    h->d_seed, h->stream);
   if (e == cudaSuccess) e = launch_seed_tick(h->d_seed, h->stream);
   return e;
 }
@@ -581,6 +604,10 @@ lbe_status create(int32_t n, const lbe_params* params, const lbe_init_fields* in
                         h->stream));
     CUB(cudaMemcpyAsync(H.walls + H.nx, H.Ttop.data(), sizeof(double) * H.nx,
                         cudaMemcpyHostToDevice, h->stream));
+    if (varying_rho(H.p)) {
+      h->vrho = true;
+      CUB(cudaMalloc(&H.pcorr, sizeof(double) * (size_t)H.nx * H.ny));
+    }
     fill_desc(h, j, h->idev[j]);
     {
       const InstDev& D = h->idev[j];
@@ -608,6 +635,19 @@ lbe_status create(int32_t n, const lbe_params* params, const lbe_init_fields* in
     }
     CUB(cudaMemcpyAsync(h->d_finst, f.data(), sizeof(InstDev) * n, cudaMemcpyHostToDevice,
                         h->stream));
+    if (h->vrho) {
+      // the pcorr pass: shape-0 tiles of all instances in one work list
+      int64_t begin = 0;
+      for (auto& D : f) {
+        D.tile_begin = begin;
+        begin += (int64_t)D.tiles_x * D.tiles_y;
+      }
+      h->p_tiles = begin;
+      h->p_grid = (int)std::min<int64_t>(begin, (int64_t)2 * h->num_sms);
+      CUB(cudaMalloc(&h->d_pinst, sizeof(InstDev) * n));
+      CUB(cudaMemcpyAsync(h->d_pinst, f.data(), sizeof(InstDev) * n, cudaMemcpyHostToDevice,
+                          h->stream));
+    }
     CUB(cudaStreamSynchronize(h->stream));
   }
   // initial state of each instance: compute the pre-collision state at rest
@@ -684,6 +724,7 @@ lbe_status check_adjoint_handle(lbe_handle* h) {
   lbe_status st = check_handle(h, 0);
   if (st) return st;
   if (h->n != 1) return fail(h, LBE_EINVAL, "the adjoint needs a handle of one instance (has %d)", h->n);
+  if (h->vrho) return fail(h, LBE_EINVAL, "the adjoint is of the uniform-density step (rho2 = rho)");
   if (h->bad) return fail(h, LBE_ESTATE, "handle is in an error state; set a state or load a checkpoint");
   return LBE_OK;
 }

@@ -80,7 +80,7 @@ cudaError_t launch_fields(int storage, const InstDev* d, int64_t tiles, int pari
 // ------------------------------------------------------------- initial state
 // At rest (u = 0, p = 0): f_i = f_eq(0, 0) = 0; g_i = g_eq(c0, mu0, 0) with
 // mu0 = 2 beta c0 (c0-1)(2c0-1) - eps^2 lap c0 (Eq. 21-22), lap c0 by the
-// isotropic stencil with mirrored ghost rows; hbar_i = w_i rho c_v T0
+// isotropic stencil with mirrored ghost rows; hbar_i = w_i rho(c0) c_v T0
 // (Eq. aEq9 at u = 0).
 __global__ void init_state_kernel(const InstDev* __restrict__ d, int nx, int ny,
                                   const double* __restrict__ c0, const double* __restrict__ T0,
@@ -114,7 +114,7 @@ __global__ void init_state_kernel(const InstDev* __restrict__ d, int nx, int ny,
     const double W0 = WGT<double>(0);
     const double H0 = (v0 - (1.0 - W0) * P.Gm * mu / cs2) / W0;
     const double Hi = P.Gm * mu / cs2;
-    const double rcvT = P.rho * P.cv * T0[k];
+    const double rcvT = rho_at(P, v0) * P.cv * T0[k];
     for (int i = 0; i < 9; i++) {
       const double w = WGT<double>(i);
       pre[(int64_t)i * N + k] = 0.0;
@@ -138,7 +138,8 @@ cudaError_t launch_init_state(const InstDev* d, int nx, int ny, const double* c0
 // returns reversed to x), so it has an exact inverse, the push:
 //   P*_j(x) = P_j(x + xi_j)                 if x + xi_j is a cell,
 //   P*_j(x) = P_jbar(x)                      at a wall for f and g,
-//   P*_j(x) = 2 w_j rho c_v T_w - P_jbar(x)  at a wall for hbar.
+//   P*_j(x) = 2 w_j rho c_v T_w - P_jbar(x)  at a wall for hbar,
+// rho that of the cell's c = sum_i g_i (with a varying density).
 template <class S>
 __global__ void push_kernel(const InstDev* __restrict__ d, int nx, int ny,
                             const double* __restrict__ pre, int parity) {
@@ -152,6 +153,9 @@ __global__ void push_kernel(const InstDev* __restrict__ d, int nx, int ny,
     const size_t rowbase = (size_t)y * I.pitch;
     // hbar deviation reference of this row (storage forms other than FP64)
     const double rref = dev_h<S>() ? I.pd.rho * I.pd.cv * (I.hr0 + I.hr1 * y) : 0.0;
+    double cn = 0.0;
+    for (int j = 0; j < 9; j++) cn += pre[(int64_t)(9 + j) * N + k];
+    const double rc = rho_at(I.pd, cn);
 #pragma unroll
     for (int j = 0; j < 9; j++) {
       const int xt = ((x + EX(j)) % nx + nx) % nx;
@@ -167,7 +171,7 @@ __global__ void push_kernel(const InstDev* __restrict__ d, int nx, int ny,
             v = pb;
           } else {
             const double Tw = (yt < 0) ? I.Tbot[x] : I.Ttop[x];
-            v = 2.0 * WGT<double>(j) * I.pd.rho * I.pd.cv * Tw - pb;
+            v = 2.0 * WGT<double>(j) * rc * I.pd.cv * Tw - pb;
           }
         }
         if (kk == 2) v -= WGT<double>(j) * rref;
@@ -200,7 +204,9 @@ __global__ void pull_kernel(const InstDev* __restrict__ d, int nx, int ny, doubl
     for (int i = 0; i < 9; i++) pre[(int64_t)(9 + i) * N + k] = (double)v[i];
     if constexpr (S::kind != ST_F64)
       pre[(int64_t)9 * N + k] += (double)ld_g0lo<S>(I, buf, (size_t)y * I.pitch + XG + x);
-    pull9<S, 2>(I, P, buf, q, v);
+    C cn = C(0);
+    for (int i = 0; i < 9; i++) cn += v[i];
+    pull9<S, 2>(I, P, buf, q, v, rho_at(P, cn));
     const double rref = dev_h<S>() ? I.pd.rho * I.pd.cv * (I.hr0 + I.hr1 * y) : 0.0;
     for (int i = 0; i < 9; i++)
       pre[(int64_t)(18 + i) * N + k] = (double)v[i] + WGT<double>(i) * rref;

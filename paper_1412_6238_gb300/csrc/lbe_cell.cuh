@@ -176,6 +176,9 @@ template <class S>
 struct Drive {
   using C = typename S::C;
   C mu, Fx, Fy, ux, uy, Trow;
+  // varying density (FP64): rho(c) and grad(rho c_s^2) = c_s^2 (rho2 - rho1)
+  // grad c (the isotropic gradient of the interpolated density)
+  C rho, dRx, dRy;
   // rho c_s^2 u = j + c_s^2 F / 2, the first moment the f equilibrium must
   // have (FP32 forms, which build its odd part from it), as two floats
   // J = Jx + Jxl; c_s^2 F / 2 is formed as (w_axis + 2 w_diag) F with the
@@ -202,8 +205,14 @@ __device__ __forceinline__ Drive<S> drive(const Phys<typename S::C>& P, int gy,
   const C ea = P.ea;
   const C cap = -sigma * s.kappa * ea * gabs;
   const C mar = -P.sigmaT * ea;
-  d.Fx = cap * s.gcx + mar * (g2 * s.gTx - cdT * s.gcx) + P.Fbx;
-  d.Fy = cap * s.gcy + mar * (g2 * s.gTy - cdT * s.gcy) + P.Fby;
+  // varying density (FP64 storage only): rho(c) in the body force, u, the
+  // relaxation times, the equilibria and the sources
+  const bool vr = sizeof(C) == 8 && P.drho != C(0);
+  d.rho = vr ? rho_at(P, cc) : P.rho;
+  d.dRx = vr ? (cs2<C>() * P.drho) * s.gcx : C(0);
+  d.dRy = vr ? (cs2<C>() * P.drho) * s.gcy : C(0);
+  d.Fx = cap * s.gcx + mar * (g2 * s.gTx - cdT * s.gcx) + (vr ? d.rho * P.ax : P.Fbx);
+  d.Fy = cap * s.gcy + mar * (g2 * s.gTy - cdT * s.gcy) + (vr ? d.rho * P.ay : P.Fby);
   // S6 (Eq. 13): first moments.  FP64: summed in index order (the order of
   // the FP64 reference).  FP32: differences of opposite populations first,
   // each exact (Sterbenz: the two are within a factor 2 of each other), then
@@ -235,8 +244,8 @@ __device__ __forceinline__ Drive<S> drive(const Phys<typename S::C>& P, int gy,
     jy = jy - f[7];
     jy = jy - f[8];
   }
-  const C rho = P.rho, inv_rho = P.inv_rho;
-  const C rcs2 = P.rcs2, inv_rcs2 = C(3) * inv_rho;
+  const C rho = d.rho, inv_rho = P.inv_rho;
+  const C rcs2 = vr ? d.rho * C(1.0 / 3.0) : P.rcs2, inv_rcs2 = C(3) * inv_rho;
   d.ux = dv(jx, rcs2, inv_rcs2) + dv(C(0.5) * d.Fx, rho, inv_rho);
   d.uy = dv(jy, rcs2, inv_rcs2) + dv(C(0.5) * d.Fy, rho, inv_rho);
   const C wa = WGT<C>(1), wd2 = C(2) * WGT<C>(5);
@@ -275,14 +284,15 @@ __device__ __forceinline__ void collide(const Phys<typename S::C>& P, const type
                                         typename S::C* g0lo_out = nullptr,
                                         typename S::C dhc = 0) {
   using C = typename S::C;
+  const bool vr = sizeof(C) == 8 && P.drho != C(0);  // varying density (FP64)
   const C inv_rho = P.inv_rho;
-  const C rcs2 = P.rcs2, inv_rcs2 = C(3) * inv_rho;
+  const C rcs2 = vr ? d.rho * C(1.0 / 3.0) : P.rcs2, inv_rcs2 = C(3) * inv_rho;
   // S3: properties, linear in c
   const C eta = P.eta1 + cc * P.deta;
   const C lam = P.lam1 + cc * P.dlam;
   const C tau_f = dv(eta, rcs2, inv_rcs2) + C(0.5);
   const C omega_f = C(1) / tau_f;
-  const C tau_h = dv(lam, P.rcvcs2, C(3) * P.inv_rho_cv);
+  const C tau_h = dv(lam, vr ? (d.rho * P.cv) * C(1.0 / 3.0) : P.rcvcs2, C(3) * P.inv_rho_cv);
   const C omega_T = C(2) / (C(2) * tau_h + C(1));
   const C omega_g = P.omega_g;
   const C af = C(1) - C(0.5) * omega_f;
@@ -295,7 +305,7 @@ __device__ __forceinline__ void collide(const Phys<typename S::C>& P, const type
   // H_i of Eq. 22 (H_0 below, in the FP64 branch)
   const C Hi = dv(Gm * d.mu, cs2<C>(), C(3));
   const C Gx = Fx - gpx, Gy = Fy - gpy;  // F - grad p (= Fbar, uniform rho)
-  const C rcvT = P.rho * P.cv * (TT + d.Trow);  // rho c_v T (full T)
+  const C rcvT = (vr ? d.rho : P.rho) * P.cv * (TT + d.Trow);  // rho c_v T (full T)
   const C rcvTr = P.rho_cv * d.Trow;            // rho c_v T_r(y)
   const C rcvTd = P.rho_cv * TT;                // rho c_v T'
   if constexpr (sizeof(C) == 4) {
@@ -451,9 +461,11 @@ __device__ __forceinline__ void collide(const Phys<typename S::C>& P, const type
       const C G = W * (C(1) + xu + hq);
       const C q = xu + hq;  // velocity part, without the cancelling w_i
       const C dx = C(EX(i)) - ux, dy = C(EY(i)) - uy;
-      // f (Eq. 12 with Eq. 5)
+      // f (Eq. 12 with Eq. 5; with a varying density the source's
+      // (xi_i - u).grad(rho c_s^2) (Gamma_i(u) - w_i) term)
       const C feq = W * (pp + rcs2 * q);
-      const C fs = (Fx * dx + Fy * dy) * G;
+      C fs = (Fx * dx + Fy * dy) * G;
+      if (vr) fs = fs + (dx * d.dRx + dy * d.dRy) * (G - W);
       out(0, i, f[i] - omega_f * (f[i] - feq) + af * fs);
       // g (Eq. 27 with Eq. 21-22)
       const C geq = W * ((i == 0 ? H0 : Hi) + cc * q);
@@ -462,7 +474,9 @@ __device__ __forceinline__ void collide(const Phys<typename S::C>& P, const type
       // hbar (Eq. aEq12 with Eq. aEq9); deviation form:
       // h_eq - w_i rho c_v T_r = rho c_v (T' Gamma_i + T_r w_i q_i)
       const C heq = rcvT * G;
-      const C hs = dv(Gx * dx + Gy * dy, rcs2, inv_rcs2) * heq;
+      // Fbar = grad(rho c_s^2) - grad p + F
+      const C Hx = vr ? d.dRx + Gx : Gx, Hy = vr ? d.dRy + Gy : Gy;
+      const C hs = dv(Hx * dx + Hy * dy, rcs2, inv_rcs2) * heq;
       const C heqd = dev_h<S>() ? rcvTd * G + rcvTr * (W * q) : heq;
       out(2, i, h[i] - omega_T * (h[i] - heqd) + aT * hs);
     }

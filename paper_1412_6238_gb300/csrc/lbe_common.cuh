@@ -77,7 +77,15 @@ struct Phys {
   C eta_n2;
   C hr0, hr1, dh;          // T_r(y) = hr0 + hr1 y; dh = rho c_v hr1
   C inv_s[3];              // 16-bit codec: 1/s_k (1 for the other storages)
+  C drho;                  // rho2 - rho1 (0: uniform density; FP64 storage only)
+  C ax, ay;                // body acceleration (the force rho(c) a)
 };
+
+// The density of a cell, linear in c: rho(c) = rho1 + c (rho2 - rho1).
+template <class C>
+__device__ __forceinline__ C rho_at(const Phys<C>& P, C c) {
+  return P.drho != C(0) ? P.rho + c * P.drho : P.rho;
+}
 
 // Per-instance descriptor, built on the host, read by the kernels.
 struct InstDev {
@@ -101,6 +109,7 @@ struct InstDev {
   float s[3];           // 16-bit codec scales s_k
   double hr0, hr1;      // T_r(y) = hr0 + hr1 y (double, for state conversion)
   uint32_t salt;        // the instance's index in its handle (random bits)
+  double* pcorr;        // varying density: p of Eq. 13 with its correction, [ny][nx]
 };
 
 template <class C>

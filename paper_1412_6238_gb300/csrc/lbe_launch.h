@@ -91,6 +91,10 @@ int occupancy_f16(int tile);
 int occupancy_bf16(int tile);
 int occupancy_mix(int tile);
 cudaError_t fields_f64(const InstDev* d, int64_t tiles, int parity, double* out, cudaStream_t s);
+// Varying density (FP64 storage only): the corrected p of Eq. 13 of every
+// cell into each instance's pcorr; d is a work list of tile shape 0.
+cudaError_t pcorr_f64(const InstDev* d, int n, int64_t total, int parity, int grid,
+                      cudaStream_t s);
 cudaError_t fields_f32(const InstDev* d, int64_t tiles, int parity, double* out, cudaStream_t s);
 cudaError_t fields_f16(const InstDev* d, int64_t tiles, int parity, double* out, cudaStream_t s);
 cudaError_t fields_bf16(const InstDev* d, int64_t tiles, int parity, double* out, cudaStream_t s);

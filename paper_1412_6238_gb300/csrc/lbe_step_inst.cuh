@@ -59,6 +59,18 @@ int LBE_CAT(occupancy_, LBE_SUFFIX)(int tile) {
   }
 }
 
+#if LBE_PCORR
+// Varying density: the corrected p of every cell of every instance into its
+// pcorr (tiles of shape 0 over a work list of that shape), before the step.
+cudaError_t LBE_CAT(pcorr_, LBE_SUFFIX)(const InstDev* d, int n, int64_t total, int parity,
+                                         int grid, cudaStream_t s) {
+  if (grid <= 0) grid = 1;
+  if ((int64_t)grid > total) grid = (int)total;
+  tile_kernel<LBE_ST, 32, 8, 2><<<grid, 256, 0, s>>>(d, n, total, parity, nullptr, nullptr);
+  return cudaGetLastError();
+}
+#endif
+
 cudaError_t LBE_CAT(fields_, LBE_SUFFIX)(const InstDev* d, int64_t tiles, int parity, double* out,
                                           cudaStream_t s) {
   if (tiles <= 0) return cudaSuccess;

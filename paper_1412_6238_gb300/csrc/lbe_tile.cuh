@@ -17,8 +17,10 @@
 //       (lbe_cell.cuh).
 //   S10 store the 27 post-collision values at the cell (the pull of the next
 //       step streams them).
-// Density is uniform, so the grad(rho c_s^2) terms of Eq. 12, Eq. 13 and Fbar
-// vanish.
+// At uniform density the grad(rho c_s^2) terms of Eq. 12, Eq. 13 and Fbar
+// vanish; with a density varying with c (FP64 storage) p is corrected by
+// (dt/2) u.grad(rho c_s^2) in a pass of its own (MODE 2), since the
+// gradient of p needs the correction at the neighbours too.
 #pragma once
 
 #include "lbe_cell.cuh"
@@ -49,10 +51,12 @@ __device__ __forceinline__ typename S::C wall_T(const InstDev& I, int x, int whi
 // RAW: in an interior row, the hbar deviations as stored (relative to their
 // source rows' T_r), for the moment T' (whose offsets cancel) and for
 // collide() with dhc = dh.
+// rho_cell: the cell's density (of its pulled c) for hbar's anti-bounce-back
+// with a varying density; ignored at uniform density.
 template <class S, int K, bool RAW = false>
 __device__ __forceinline__ void pull9(const InstDev& I, const Phys<typename S::C>& P,
                                       const char* __restrict__ src, const Cell<S>& q,
-                                      typename S::C out[9]) {
+                                      typename S::C out[9], typename S::C rho_cell = 0) {
   using C = typename S::C;
   const size_t pitch = (size_t)I.pitch;
   const size_t r0 = (size_t)q.y * pitch + XG;
@@ -63,7 +67,8 @@ __device__ __forceinline__ void pull9(const InstDev& I, const Phys<typename S::C
   const C dh = DEV ? P.dh : C(0);  // rho c_v (T_r(y) - T_r(y-1))
   auto bb = [&](int i) -> C {
     C v = S::ld(I, P, src, K, OPP(i), r0 + q.x);
-    if (K == 2) return -v + C(2) * WGT<C>(i) * P.rho * P.cv * Tw;
+    if (K == 2)
+      return -v + C(2) * WGT<C>(i) * (P.drho != C(0) ? rho_cell : P.rho) * P.cv * Tw;
     return v;
   };
   out[0] = S::ld(I, P, src, K, 0, r0 + q.x);
@@ -131,7 +136,7 @@ __device__ __forceinline__ typename S::C ghost_T(const InstDev& I, int x, bool b
 template <class S>
 __device__ __forceinline__ void region_values(const InstDev& I, const Phys<typename S::C>& P,
                                               const char* __restrict__ src, int gx, int gy,
-                                              bool need_pT,
+                                              bool need_pT, bool use_pcorr,
                                               typename S::C& c, typename S::C& p,
                                               typename S::C& T) {
   using C = typename S::C;
@@ -149,10 +154,12 @@ __device__ __forceinline__ void region_values(const InstDev& I, const Phys<typen
   pull9<S, 1>(I, P, src, q, v);
   c = sum9(v);
   if (need_pT) {
+    const C rc = rho_at(P, c);
     pull9<S, 0>(I, P, src, q, v);
-    p = sum9(v);
-    pull9<S, 2, true>(I, P, src, q, v);
-    T = dv(sum9(v), P.rho_cv, P.inv_rho_cv);
+    // p of Eq. 13: with a varying density, the corrected p of pcorr
+    p = (use_pcorr && P.drho != C(0)) ? (C)I.pcorr[(size_t)y * nx + q.x] : sum9(v);
+    pull9<S, 2, true>(I, P, src, q, v, rc);
+    T = P.drho != C(0) ? dv(sum9(v), rc * P.cv, C(1)) : dv(sum9(v), P.rho_cv, P.inv_rho_cv);
     if (ghost != 0) T = ghost_T<S>(I, q.x, ghost < 0, T);
   } else {
     p = C(0);
@@ -162,6 +169,8 @@ __device__ __forceinline__ void region_values(const InstDev& I, const Phys<typen
 
 // Tile work.  MODE 0: full step (collide and store into the other buffer).
 // MODE 1: export c, p, ux, uy, T of the current state into out[5][ny][nx].
+// MODE 2 (varying density): the corrected p of Eq. 13 of every cell into
+// I.pcorr, which MODE 0 then reads for p and its gradient.
 template <class S, int TX, int TY, int MODE>
 struct Tile {
   using C = typename S::C;
@@ -187,6 +196,9 @@ struct Tile {
     const int y0 = (int)(tile / I.tiles_x) * TY;
     const char* __restrict__ src = I.buf[parity];
     const Phys<C> P = phys<C>(I);  // constants in registers for the whole tile
+    // the pcorr pass has nothing to do for a uniform-density instance (it
+    // holds no pcorr); the whole CTA leaves together
+    if (MODE == 2 && (P.drho == C(0) || I.pcorr == nullptr)) return;
 
     // ---- S1: own cell
     const int gx = x0 + tx, gy = y0 + ty;
@@ -198,17 +210,19 @@ struct Tile {
     if (active) {
       pull9<S, 0>(I, P, src, q, f);
       pull9<S, 1>(I, P, src, q, g);
-      pull9<S, 2, true>(I, P, src, q, h);
       if constexpr (S::kind != ST_F64) {
         g0lo = ld_g0lo<S>(I, src, (size_t)gy * I.pitch + XG + gx);
         cc = moment_c(g, g0lo, clo);
       } else {
         cc = sum9(g);
       }
-      pp = sum9(f);
-      TT = dv(sum9(h), P.rho_cv, P.inv_rho_cv);
+      const C rc = rho_at(P, cc);
+      pull9<S, 2, true>(I, P, src, q, h, rc);
+      // p of Eq. 13 (with a varying density the corrected p, MODE 2 / pcorr)
+      pp = (P.drho != C(0) && MODE == 0) ? (C)I.pcorr[(size_t)gy * nx + gx] : sum9(f);
+      TT = P.drho != C(0) ? dv(sum9(h), rc * P.cv, C(1)) : dv(sum9(h), P.rho_cv, P.inv_rho_cv);
     } else if (gy <= ny + 1) {
-      region_values<S>(I, P, src, gx, gy, true, cc, pp, TT);
+      region_values<S>(I, P, src, gx, gy, true, MODE == 0, cc, pp, TT);
     }
     sm.c[(ty + 2) * RW + tx + 2] = cc;
     sm.p[(ty + 1) * QW + tx + 1] = pp;
@@ -232,7 +246,8 @@ struct Tile {
       const int hx = x0 - 2 + rx, hy = y0 - 2 + ry;
       const bool inner = rx >= 1 && rx <= TX + 2 && ry >= 1 && ry <= TY + 2;
       C vc = C(0), vp = C(0), vT = C(0);
-      if (hy >= -2 && hy <= ny + 1) region_values<S>(I, P, src, hx, hy, inner, vc, vp, vT);
+      if (hy >= -2 && hy <= ny + 1)
+        region_values<S>(I, P, src, hx, hy, inner, MODE == 0, vc, vp, vT);
       sm.c[ry * RW + rx] = vc;
       if (inner) {
         sm.p[(ry - 1) * QW + rx - 1] = vp;
@@ -266,10 +281,16 @@ struct Tile {
       st.kappa = d1 + d2;
       const Drive<S> d = drive<S>(P, gy, f, cc, TT, st);
 
+      // Eq. 13 with a varying density: p = sum f_i + (dt/2) u.grad(rho c_s^2)
+      const C pcor = P.drho != C(0) ? pp + C(0.5) * (d.ux * d.dRx + d.uy * d.dRy) : pp;
+      if (MODE == 2) {  // the corrected p for the step that follows
+        I.pcorr[(size_t)gy * nx + gx] = (double)pcor;
+        return;
+      }
       if (MODE == 1) {
         const size_t N = (size_t)nx * ny, k = (size_t)gy * nx + gx;
         out[k] = (double)cc + (double)clo;
-        out[N + k] = (double)pp;
+        out[N + k] = (double)pcor;
         out[2 * N + k] = (double)d.ux;
         out[3 * N + k] = (double)d.uy;
         out[4 * N + k] = dev_h<S>() ? (double)TT + (I.hr0 + I.hr1 * gy) : (double)TT;

@@ -38,7 +38,8 @@ class LBEError(RuntimeError):
 
 class Params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("storage", ctypes.c_int32),
-                ("check_every", ctypes.c_int32)] + [(k, ctypes.c_double) for k in PARAM_KEYS]
+                ("check_every", ctypes.c_int32)] + [(k, ctypes.c_double) for k in PARAM_KEYS] + \
+               [("rho2", ctypes.c_double)]
 
 
 class InitFields(ctypes.Structure):
@@ -131,6 +132,7 @@ def make_params(params: dict, storage: str | int, check_every: int = 0) -> Param
     p.check_every = int(check_every)
     for k in PARAM_KEYS:
         setattr(p, k, float(params[k]))
+    p.rho2 = float(params.get("rho2", 0.0))  # 0: uniform density
     return p
 
 

@@ -29,7 +29,7 @@ def test_library_exports_every_declared_symbol():
     for name in sorted(decl):
         assert hasattr(L, name), name
     assert set(lbe.EXPORTS) <= decl
-    assert L.lbe_abi_version() == 1
+    assert L.lbe_abi_version() == 2
 
 
 def test_tile_table():
@@ -61,6 +61,8 @@ def _init(params, storage="f32"):
     (dict(eta1=0.0), "eta1"), (dict(eps=-1.0), "eps"), (dict(eta_n=0.0), "eta_n"),
     (dict(lam2=-1e-3), "lam"), (dict(rho=0.0), "rho"), (dict(sigmaT=float("nan")), "non-finite"),
     (dict(nx=65536, ny=65537), "2^31"),
+    (dict(rho2=-1.0), "rho2"), (dict(rho2=float("inf")), "rho2"),
+    (dict(rho2=3.0), "FP64"),  # a density ratio with FP32 storage
 ])
 def test_invalid_parameters_rejected(bad, msg):
     st, err, h = _init(bad)
