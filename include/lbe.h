@@ -197,7 +197,7 @@ lbe_status lbe_load(lbe_handle* h, const char* path);
 /* Step-kernel choice (autotuner hook).  Kernel ids 0 .. lbe_num_tiles()-1:
  * ids whose shape has ty > 0 are the tile kernel with TX x TY cells per CTA
  * (any storage; FP64 provides id 0 only); id 7 (ty == 0) is the strip kernel
- * with 124 output columns per CTA marching over rows, staging each row's
+ * with 128 output columns per CTA marching over rows, staging each row's
  * pulled populations in shared memory with bulk copies (16/32-bit and
  * F16MIX storages, every instance at least 4 columns wide; the default
  * there); ids 5 and 6 are retired and rejected.

@@ -14,17 +14,19 @@ struct TileShape {
 // Kernel ids: 0..4 tile kernel with these tile shapes; 5, 6 retired (strip
 // kernels with a TMA ring of whole source rows, superseded by the stash
 // kernel; not built); 7 strip kernel with a per-warp stash of pulled
-// populations, 124 output columns (16/32-bit storages; ty = 0: a strip
+// populations, 128 output columns (16/32-bit storages; ty = 0: a strip
 // marches over its rows).
 constexpr int NUM_TILE_SHAPES = 5;
 constexpr int NUM_TILES = 8;
 constexpr int STRIP_FIRST = 5;
 constexpr int STASH_ID = 7;
 // bytes allocated after an instance's two population buffers, covering the
-// widest read past the end of a row of the stash kernel (36 + 96 elements)
-constexpr size_t ARENA_TAIL = 1024;
+// widest read past the end of a row of the stash kernel: a stash row of 136
+// elements of up to 8 bytes from a strip start x0 <= nx - 1, against a
+// pitch of at least nx + 8 elements (at most 127 x 8 bytes)
+constexpr size_t ARENA_TAIL = 2048;
 constexpr TileShape TILE_SHAPES[NUM_TILES] = {{32, 8},  {64, 4},  {32, 16}, {64, 8},
-                                              {128, 4}, {124, 0}, {60, 0},  {124, 0}};
+                                              {128, 4}, {124, 0}, {60, 0},  {128, 0}};
 inline bool is_strip(int tile) { return tile >= STRIP_FIRST && tile < NUM_TILES; }
 
 // Does the step kernel of this storage exist for this kernel id?

@@ -1,10 +1,13 @@
 // The fused step as a column-strip marching kernel with a stash of pulled
 // populations (FP32 and 16-bit storages).
 //
-// A work item is a strip of NC - 4 output columns and a segment of rows
-// [ya, yb) of one instance: a CTA of NC threads marches up the rows, thread t
-// owning column x0 - 2 + t so that the two halo columns on each side are
-// ordinary threads.  Instead of staging whole source rows (as a TMA tiled
+// A work item is a strip of NC output columns and a segment of rows [ya, yb)
+// of one instance: a CTA of NC threads marches up the rows, thread t owning
+// column x0 + t.  The stencils also need the moments of the two halo columns
+// on each side (c at x0 - 2 .. x0 + NC + 1, p and T at x0 - 1 .. x0 + NC):
+// four lanes of the last warp form those as extra work, so that no thread
+// of the CTA is spent on a column it does not collide (NC a power of two:
+// the strips tile power-of-two grids exactly).  Instead of staging whole source rows (as a TMA tiled
 // row ring would, 7 rows for the pull and the stencils), the CTA stages, for
 // each moment row m, what its cells pull: for each population row of the
 // layout (FP32: the 9 (f_i, g_i) pair rows, the 9 hbar_i rows and the g_0 low
@@ -23,7 +26,7 @@
 //      that row i-1 has just freed (as early as possible: the copies then
 //      have the rest of this iteration and the next collision to land);
 //   2. wait for the copies of row i+2 and form its moments c, p, T (S1) into
-//      the rings; rows below the bottom wall use the pulled values of their
+//      the rings (own columns, then the four halo columns); rows below the bottom wall use the pulled values of their
 //      mirror row, rows above the top wall copy the mirror rows in the rings;
 //   barrier; 4. unit normal of row i+1 (S2).
 // Every population is read from HBM once per step.  Every mbarrier wait is
@@ -78,22 +81,23 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
       : "memory");
 }
 
-// Threads (= columns, two halo columns on each side) of a strip CTA.
+// Threads (= output columns) of a strip CTA.
 constexpr int STASH_NC = 128;
 
 // Stash layout of one row for a storage form: population (k, i) has a row of
-// EW elements at byte offset off(k, i) of the slot, covering the CTA's
-// columns and the pulls' reach.  Every form adds the FP16 row of the g_0 low
-// part (NC + 8 elements from x0 rounded down to a multiple of 8) at byte LO.
+// EW = NC + 8 elements at byte offset off(k, i) of the slot, from storage
+// element x0 (x0 a multiple of NC: 16-byte aligned in every form), covering
+// the CTA's columns, the halo columns and the pulls' reach (columns x0 - 3
+// .. x0 + NC + 2 are elements x0 + 1 .. x0 + NC + 6).  Every form adds the
+// FP16 row of the g_0 low part at byte LO.
 template <class S>
 struct StashFmt;
-// FP32: 9 rows of (f_i, g_i) pairs (NC + 4 cells x 8 bytes from element x0),
-// 9 rows of hbar_i (NC + 4 x 4 bytes); off(k, i) is the byte offset of the
-// row holding (k, i).
+// FP32: 9 rows of (f_i, g_i) pairs (EW cells x 8 bytes), 9 rows of hbar_i
+// (EW x 4 bytes); off(k, i) is the byte offset of the row holding (k, i).
 template <>
 struct StashFmt<StF32> {
   using E = float;
-  static constexpr int EW = STASH_NC + 4;             // cells per row
+  static constexpr int EW = STASH_NC + 8;             // cells per row
   static constexpr int PROW = EW * 8;                 // pair row bytes
   static constexpr int ROW = EW * 4;                  // hbar row bytes
   static constexpr int HOFF = 9 * PROW;
@@ -108,8 +112,7 @@ struct StashFmt<StF32> {
                 "bulk copies: 16-byte sizes and offsets");
 };
 // 16-bit: 8 rows of (f_i, g_i) pairs, i = 1..8, the f_0 row and 9 hbar rows
-// (NC + 8 cells from x0 rounded down to a multiple of 8: 4 and 2 bytes per
-// cell), the FP32 g_0 row (NC + 4 x 4 bytes from x0).
+// (4 and 2 bytes per cell), the FP32 g_0 row.
 template <class E16>
 struct StashFmt16 {
   using E = E16;
@@ -119,7 +122,7 @@ struct StashFmt16 {
   static constexpr int F0 = 8 * PROW;
   static constexpr int HOFF = F0 + ROW;
   static constexpr int G0 = HOFF + 9 * ROW;
-  static constexpr int G0B = (STASH_NC + 4) * 4;
+  static constexpr int G0B = EW * 4;
   static constexpr int LO = G0 + G0B;
   static constexpr int LOB = ROW;
   static constexpr int SLOT_RAW = LO + LOB;
@@ -131,13 +134,12 @@ struct StashFmt16 {
                     LO % 16 == 0,
                 "bulk copies: 16-byte sizes and offsets");
 };
-// F16MIX: 9 rows of the 8-byte direction words (f_i FP32, two FP16 values;
-// NC + 4 cells from x0) and the FP32 g_0 row (NC + 4 cells from x0); the g_0
-// low part travels in the words of row 0.
+// F16MIX: 9 rows of the 8-byte direction words (f_i FP32, two FP16 values)
+// and the FP32 g_0 row; the g_0 low part travels in the words of row 0.
 template <>
 struct StashFmt<StMix> {
   using E = float;
-  static constexpr int EW = STASH_NC + 4;
+  static constexpr int EW = STASH_NC + 8;
   static constexpr int WROW = EW * 8;  // word row bytes
   static constexpr int G0 = 9 * WROW;
   static constexpr int G0B = EW * 4;
@@ -155,16 +157,20 @@ struct StashCfg {
   using Fmt = StashFmt<S>;
   static_assert(NC == STASH_NC, "the stash formats are laid out for STASH_NC columns");
   static_assert(Fmt::SLOT_RAW % 16 == 0, "16-byte slots");
-  static constexpr int NCO = NC - 4;          // output columns
+  static constexpr int NCO = NC;              // output columns
   static constexpr int NW = NC / 32;          // warps
   static constexpr int SR = 4;                // stash rows
   static constexpr int SLOT = Fmt::SLOT_RAW;  // bytes of one row
   static constexpr int TX = Fmt::SLOT_RAW;    // bytes copied per row
   static constexpr int CR = 5, PR = 5, NR = 4;  // moment / normal ring rows
   static_assert(CR == PR, "c, p and T rings share their row index");
+  // ring row widths: c (and its low part) at x0 - 2 .. x0 + NC + 1, p, T
+  // and the unit normal at x0 - 1 .. x0 + NC
+  static constexpr int CW = NC + 4, QW = NC + 2;
   static constexpr int STASH = SR * SLOT;
   // FP32 rings of c, p, T, n_x, n_y and the FP16 ring of the c low part
-  static constexpr int RINGS = (CR + 2 * PR + 2 * NR) * NC * 4 + CR * NC * 2;
+  static constexpr int RINGS = (CR * CW + 2 * PR * QW + 2 * NR * QW) * 4 + CR * CW * 2;
+  static_assert(RINGS % 8 == 0, "the slot barriers follow the rings");
   static constexpr int SMEM = STASH + RINGS + SR * 8;
   // resident CTAs per SM the kernel is compiled for (registers)
   static constexpr int MINB = Fmt::MINB;
@@ -457,16 +463,23 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
   constexpr bool W16 = sizeof(typename Fmt::E) == 2;
   constexpr bool MIX = S::kind == ST_F16MIX;
   extern __shared__ __align__(128) char smem[];
-  C* cring = reinterpret_cast<C*>(smem + Cfg::STASH);  // [CR][NC]
-  C* pring = cring + Cfg::CR * NC;                       // [PR][NC]
-  C* Tring = pring + Cfg::PR * NC;                       // [PR][NC]
-  C* nxr = Tring + Cfg::PR * NC;                         // [NR][NC]
-  C* nyr = nxr + Cfg::NR * NC;
-  __half* clr = reinterpret_cast<__half*>(nyr + Cfg::NR * NC);  // [CR][NC], lo * 2^24
+  constexpr int CW = Cfg::CW, QW = Cfg::QW;
+  // ring entry of column x0 + j: c (and its low part) at j + 2, p, T, n at j + 1
+  C* cring = reinterpret_cast<C*>(smem + Cfg::STASH);  // [CR][CW]
+  C* pring = cring + Cfg::CR * CW;                       // [PR][QW]
+  C* Tring = pring + Cfg::PR * QW;                       // [PR][QW]
+  C* nxr = Tring + Cfg::PR * QW;                         // [NR][QW]
+  C* nyr = nxr + Cfg::NR * QW;
+  __half* clr = reinterpret_cast<__half*>(nyr + Cfg::NR * QW);  // [CR][CW], lo * 2^24
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Cfg::STASH + Cfg::RINGS);  // [SR]
   __shared__ int s_abort;
   const int t = threadIdx.x;
   const int wu = __shfl_sync(0xffffffffu, t >> 5, 0);  // the warp index, warp-uniform
+  // halo lanes: lanes 0..3 of the last warp form the moments of columns
+  // x0 - 2, x0 - 1, x0 + NC, x0 + NC + 1 (offset hj from x0)
+  const int lane = t & 31;
+  const bool halo = wu == Cfg::NW - 1 && lane < 4;
+  const int hj = lane < 2 ? lane - 2 : NC - 2 + lane;
   const uint32_t stash_u = smem_u32(smem);
   const uint32_t bars_u = smem_u32(bars);
   // the slots' barriers are initialised once; every copy issued in an item is
@@ -501,26 +514,26 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
     const C en2 = P.eta_n2;
     const uint32_t skey = S::SR ? sr_step_key(step, I.salt) : 0u;
     const size_t pitch = (size_t)I.pitch;
-    const int x = x0 - 2 + t;
+    const int x = x0 + t;
     const int xw = wrapx(x, nx);
-    const bool collides = t >= 2 && t < NC - 2 && x < nx;
+    const bool collides = x < nx;
     // staged elements of the strip's population rows (storage element e
-    // holds column e - XG): its cells are columns x0 - 2 + t, their pulls
-    // reach elements x0 + 1 .. x0 + NC + 2.  FP32 rows (and the FP32 g_0 row
-    // of the 16-bit forms) start at x0 (a multiple of 4: 16-byte aligned),
-    // 16-bit rows at x0 rounded down to a multiple of 8.
+    // holds column e - XG): column x0 + j is element j + XG of a stash row,
+    // which starts at element x0 (a multiple of NC: 16-byte aligned).
     const int e16 = x0 & ~7;
-    const int c0 = (W16 ? x0 - e16 : 0) + t + 2;  // own column in a population row
-    const int c0g = t + 2;                         // own column in the FP32 g_0 row
-    const int c0lo = x0 - e16 + t + 2;             // own column in the g_0 low-part row
+    static_assert(XG == 4, "stash columns: column x0 + j at element j + 4 of a row");
+    const int c0 = (W16 ? x0 - e16 : 0) + t + XG;  // own column in a population row
+    const int c0g = t + XG;                         // own column in the FP32 g_0 row
+    const int c0lo = x0 - e16 + t + XG;             // own column in the g_0 low-part row
+    const int hd = hj - t;                          // halo lanes: column offset from own
+    const int hxw = wrapx(x0 + hj, nx);
     const CopyPlan cp = copy_plan(I, parity, x0);
     __syncthreads();  // the previous item is done with the rings and stashes
     if (t == 0) s_abort = 0;
 
     auto slot = [&](int m) { return smem + (m & (Cfg::SR - 1)) * Cfg::SLOT; };
-    auto cr = [](int m) { return (((m % Cfg::CR) + Cfg::CR) % Cfg::CR) * NC; };
-    auto pr = [](int m) { return (((m % Cfg::PR) + Cfg::PR) % Cfg::PR) * NC; };
-    auto nr = [](int m) { return (m & (Cfg::NR - 1)) * NC; };
+    auto rrow = [](int m) { return ((m % Cfg::CR) + Cfg::CR) % Cfg::CR; };
+    auto nr = [](int m) { return (m & (Cfg::NR - 1)) * QW; };
     auto loadable = [&](int m) { return m <= yb + 1 && m < ny; };
     // the copies of the populations pulled by moment row m (the mirror row's
     // below the bottom wall), issued by one elected lane of warp 0 after a
@@ -559,11 +572,10 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
     issue(ya - 2);
     int i5 = (((ya - 4) % Cfg::CR) + Cfg::CR) % Cfg::CR;  // i mod CR
     for (int i = ya - 4; i <= yb; i++, i5 = (i5 == Cfg::CR - 1) ? 0 : i5 + 1) {
-      // ring row of i + d (|d| < CR), times NC
+      // ring row of i + d (|d| < CR)
       auto rr = [&](int d) {
         int v = i5 + d;
-        v = v < 0 ? v + Cfg::CR : (v >= Cfg::CR ? v - Cfg::CR : v);
-        return v * NC;
+        return v < 0 ? v + Cfg::CR : (v >= Cfg::CR ? v - Cfg::CR : v);
       };
       __syncthreads();
       if (s_abort) break;
@@ -587,19 +599,26 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
           g0lo = __half2float(reinterpret_cast<const __half*>(s + Fmt::LO)[c0lo]) * G0LO_INV;
         }
         const int ps = rr(-2), p0 = rr(-1), pn = rr(0);  // rows r-1, r, r+1
-        const C* cs = cring + ps;
-        const C* c0 = cring + p0;
-        const C* cn = cring + pn;
+        // rows of the rings from column x0 (index t: the own column)
+        const C* cs = cring + ps * CW + 2;
+        const C* c0 = cring + p0 * CW + 2;
+        const C* cn = cring + pn * CW + 2;
         const C cc = c0[t];
-        const C clo = lo_at(clr + p0, t);
-        const C pp = pring[p0 + t], TT = Tring[p0 + t];
+        const C clo = lo_at(clr + p0 * CW + 2, t);
+        const C* Ts = Tring + ps * QW + 1;
+        const C* T0 = Tring + p0 * QW + 1;
+        const C* Tn = Tring + pn * QW + 1;
+        const C* qs = pring + ps * QW + 1;
+        const C* q0 = pring + p0 * QW + 1;
+        const C* qn = pring + pn * QW + 1;
+        const C pp = q0[t], TT = T0[t];
         Stencils<C> st;
         grad3(cs, c0, cn, t, st.gcx, st.gcy);
         st.lapc = lap3(cs, c0, cn, t);
-        grad3(Tring + ps, Tring + p0, Tring + pn, t, st.gTx, st.gTy);
+        grad3(Ts, T0, Tn, t, st.gTx, st.gTy);
         if (dev_h<S>()) st.gTy += P.hr1;
-        grad3(pring + ps, pring + p0, pring + pn, t, st.gpx, st.gpy);
-        const int ns = nr(r - 1), n0 = nr(r), nn = nr(r + 1);
+        grad3(qs, q0, qn, t, st.gpx, st.gpy);
+        const int ns = nr(r - 1) + 1, n0 = nr(r) + 1, nn = nr(r + 1) + 1;
         C d1, d2, dum;
         grad3(nxr + ns, nxr + n0, nxr + nn, t, d1, dum);
         grad3(nyr + ns, nyr + n0, nyr + nn, t, dum, d2);
@@ -670,53 +689,75 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
         atomicOr(err, 1);
       }
       if (m <= yb + 1) {
-        const int ci = rr(2) + t, pi = ci;
-        if (m < ny) {
-          const int mr = m >= 0 ? m : -1 - m;
-          const char* s = slot(m);
-          C v[9], vf[9];
-          if constexpr (MIX) {
-            C vh[9], g0lo, clo;
-            wstash_pull_mix<true>(I, P, s, c0, mr, xw, vf, v, vh, g0lo);
-            cring[ci] = moment_c(v, g0lo, clo);
-            clr[ci] = __float2half_rn(clo * G0LO_SCALE);
-            pring[pi] = sum9(vf);
-            C T = dv(sum9(vh), P.rho_cv, P.inv_rho_cv);
-            if (m < 0) T = ghost_T<S>(I, xw, true, T);
-            Tring[pi] = T;
-          } else {
-            if constexpr (!W16) {
-              wstash_pull_fg(I, s, c0, mr, vf, v);
+        const int rm = rr(2);
+        // moments of the column at offset dj from the own one into ring
+        // entries ci (c) and, if pt, pi (p, T)
+        auto moments = [&](int dj, int cxw, int ci, int pi, bool pt) {
+          if (m < ny) {
+            const int mr = m >= 0 ? m : -1 - m;
+            const char* s = slot(m);
+            C v[9], vf[9];
+            if constexpr (MIX) {
+              C vh[9], g0lo, clo;
+              wstash_pull_mix<true>(I, P, s, c0 + dj, mr, cxw, vf, v, vh, g0lo);
+              cring[ci] = moment_c(v, g0lo, clo);
+              clr[ci] = __float2half_rn(clo * G0LO_SCALE);
+              if (pt) {
+                pring[pi] = sum9(vf);
+                C T = dv(sum9(vh), P.rho_cv, P.inv_rho_cv);
+                if (m < 0) T = ghost_T<S>(I, cxw, true, T);
+                Tring[pi] = T;
+              }
             } else {
-              wstash_pull_fg16<S>(I, P, s, c0, c0g, mr, vf, v);
+              if constexpr (!W16) {
+                wstash_pull_fg(I, s, c0 + dj, mr, vf, v);
+              } else {
+                wstash_pull_fg16<S>(I, P, s, c0 + dj, c0g + dj, mr, vf, v);
+              }
+              const C g0lo =
+                  __half2float(reinterpret_cast<const __half*>(s + Fmt::LO)[c0lo + dj]) *
+                  G0LO_INV;
+              C clo;
+              cring[ci] = moment_c(v, g0lo, clo);
+              clr[ci] = __float2half_rn(clo * G0LO_SCALE);
+              if (pt) {
+                pring[pi] = sum9(vf);
+                wstash_pull<S, 2, true>(I, P, s, c0 + dj, c0g + dj, mr, cxw, v);
+                C T = dv(sum9(v), P.rho_cv, P.inv_rho_cv);
+                if (m < 0) T = ghost_T<S>(I, cxw, true, T);
+                Tring[pi] = T;
+              }
             }
-            const C g0lo =
-                __half2float(reinterpret_cast<const __half*>(s + Fmt::LO)[c0lo]) * G0LO_INV;
-            C clo;
-            cring[ci] = moment_c(v, g0lo, clo);
-            clr[ci] = __float2half_rn(clo * G0LO_SCALE);
-            pring[pi] = sum9(vf);
-            wstash_pull<S, 2, true>(I, P, s, c0, c0g, mr, xw, v);
-            C T = dv(sum9(v), P.rho_cv, P.inv_rho_cv);
-            if (m < 0) T = ghost_T<S>(I, xw, true, T);
-            Tring[pi] = T;
+          } else {
+            // above the top wall: the mirror row's moments
+            const int mm = rrow(2 * ny - 1 - m);
+            const int cm = ci - rm * CW + mm * CW, pm = pi - rm * QW + mm * QW;
+            cring[ci] = cring[cm];
+            clr[ci] = clr[cm];
+            if (pt) {
+              pring[pi] = pring[pm];
+              Tring[pi] = ghost_T<S>(I, cxw, false, Tring[pm]);
+            }
           }
-        } else {
-          const int mm = 2 * ny - 1 - m;
-          cring[ci] = cring[cr(mm) + t];
-          clr[ci] = clr[cr(mm) + t];
-          pring[pi] = pring[pr(mm) + t];
-          Tring[pi] = ghost_T<S>(I, xw, false, Tring[pr(mm) + t]);
-        }
+        };
+        moments(0, xw, rm * CW + t + 2, rm * QW + t + 1, true);
+        // the halo columns: c of all four, p and T of x0 - 1 and x0 + NC
+        if (halo)
+          moments(hd, hxw, rm * CW + hj + 2, rm * QW + hj + 1, lane == 1 || lane == 2);
       }
       __syncthreads();
       if (s_abort) break;
 
       // ---- 4. unit normal of row i + 1
       const int mn = i + 1;
-      if (mn >= ya - 1 && mn <= yb && t >= 1 && t < NC - 1) {
-        const int ni = nr(mn) + t;
-        normal3(cring + rr(0), cring + rr(1), cring + rr(2), t, en2, nxr[ni], nyr[ni]);
+      if (mn >= ya - 1 && mn <= yb) {
+        const C* ca = cring + rr(0) * CW;
+        const C* cb = cring + rr(1) * CW;
+        const C* cc2 = cring + rr(2) * CW;
+        normal3(ca, cb, cc2, t + 2, en2, nxr[nr(mn) + t + 1], nyr[nr(mn) + t + 1]);
+        // the halo columns x0 - 1 and x0 + NC
+        if (halo && (lane == 1 || lane == 2))
+          normal3(ca, cb, cc2, hj + 2, en2, nxr[nr(mn) + hj + 1], nyr[nr(mn) + hj + 1]);
       }
     }
     __syncthreads();

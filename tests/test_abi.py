@@ -36,10 +36,10 @@ def test_tile_table():
     shapes = lbe.tile_shapes()
     assert len(shapes) >= 1 and shapes[0] == (32, 8)
     for tx, ty in shapes:
-        # tile kernel: TX multiple of a warp; strip kernel: TX output columns
-        # plus 4 halo columns per CTA
-        assert (tx % 32 == 0 and ty > 0) or (ty == 0 and (tx + 4) % 32 == 0)
-    assert any(ty == 0 for _, ty in shapes)  # a strip kernel
+        # tile kernel: TX multiple of a warp; strip kernels: TX output
+        # columns per CTA (the retired ones had 4 halo threads besides)
+        assert (tx % 32 == 0 and ty > 0) or (ty == 0 and tx % 32 in (0, 28))
+    assert shapes[7] == (128, 0)  # the stash strip kernel: one thread per output column
 
 
 def _init(params, storage="f32"):

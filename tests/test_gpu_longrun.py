@@ -115,7 +115,10 @@ def test_sweep_instances_inside_the_batch(storage, bu, bT):
     """The 64-instance sweep advanced 10 000 steps in one launch per step;
     the instances with stored oracle end states compared.  (The sweep's
     16-bit storage is F16MIX, FP16 deviations of g and hbar with f in FP32;
-    FP16DEV, which also stores f in 16 bits, cannot resolve its slow flows.)"""
+    FP16DEV, which also stores f in 16 bits, cannot resolve its slow flows.)
+    FP64 arithmetic is slow on this part, so the FP64 batch holds the
+    instances with stored end states and the smallest (128 x 256) ones in
+    between, not all 64."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -133,14 +136,18 @@ def test_sweep_instances_inside_the_batch(storage, bu, bT):
             goldens[j] = G
     if not goldens:
         pytest.skip("sweep goldens missing")
-    sim = LBE(ws, storage=storage)
+    keep = list(range(len(ws)))
+    if storage == "f64":
+        keep = sorted(set(goldens) | {j for j, w in enumerate(ws) if w.nx * w.ny <= 128 * 256})
+    slot = {j: k for k, j in enumerate(keep)}
+    sim = LBE([ws[j] for j in keep], storage=storage)
     sim.step(10000)
     for j, G in goldens.items():
         if storage == "f64":
-            st = np.ascontiguousarray(sim.get_state(j).numpy())
+            st = np.ascontiguousarray(sim.get_state(slot[j]).numpy())
             assert hashlib.sha256(st.tobytes()).hexdigest() == G["state_sha256"], j
             print("sweep instance", j, "f64: end-state hash equal to the oracle's")
-        F = {k: v.numpy() for k, v in sim.fields(j, device="cpu").items()}
+        F = {k: v.numpy() for k, v in sim.fields(slot[j], device="cpu").items()}
         e = _errors(F, G)
         print("sweep instance", j, storage, e)
         assert e["u"] < bu and e["T"] < bT, (j, e)
