@@ -61,7 +61,7 @@ def parse_args():
     ap.add_argument("--batch-steps", type=int, default=50)
     ap.add_argument("--kernel", type=int, default=-1,
                     help="step kernel id (lbe_set_tile); default: the library's choice")
-    ap.add_argument("--seg", type=int, default=0, help="rows per strip work item (0 = auto)")
+    ap.add_argument("--seg", type=int, default=0, help="rows per strip work item (0 = auto; < 0: balanced ranges in pieces of at most -seg rows)")
     return ap.parse_args()
 
 
@@ -282,7 +282,7 @@ def run_ours(args, ws, rank, local):
     w = wl.droplet_scaled(args.nx, args.ny)
     cells = w.cells
     sim = LBE(w, storage=args.storage)
-    if args.kernel >= 0 or args.seg > 0:
+    if args.kernel >= 0 or args.seg != 0:
         sim.set_tile(args.kernel if args.kernel >= 0 else sim.get_tile()["kernel"], 0, args.seg)
     kernel = sim.get_tile()
     stream = sim.stream

@@ -202,7 +202,11 @@ lbe_status lbe_load(lbe_handle* h, const char* path);
  * F16MIX storages, every instance at least 4 columns wide; the default
  * there); ids 5 and 6 are retired and rejected.
  * grid_ctas: persistent grid size (0 = resident CTAs x SMs, -1 = one CTA per
- * work item).  seg_rows: rows per strip work item (0 = chosen from the wave
+ * work item).  seg_rows > 0: rows per strip work item, items taken
+ * round-robin; < 0: balanced: the strips of all instances laid end to end
+ * and cut into one contiguous range of rows per CTA, marched in pieces of
+ * at most -seg_rows rows; 0: automatic (balanced ranges when the instances
+ * differ in size, else items with the row count chosen from the wave
  * count, at most 96).  LBE_EINVAL for a kernel the handle cannot use.
  * lbe_get_tile() reports {kernel id, grid CTAs, seg rows, work items}. */
 int32_t lbe_num_tiles(void);

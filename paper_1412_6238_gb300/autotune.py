@@ -61,7 +61,9 @@ def candidates(storage: str, shapes, num_tiles: int, tile_shape):
         if ty == 0:  # strip kernel
             if storage == "f64" or min_nx < 4:
                 continue
-            for seg in (0, max(8, max_ny // 16), max(8, max_ny // 8), max(8, max_ny // 4)):
+            # 0 automatic, -max_ny balanced row ranges (uncut), > 0 items of
+            # that many rows
+            for seg in (0, -max_ny, 72, 96, max(8, max_ny // 8), max(8, max_ny // 4)):
                 out.append((k, 0, seg))
         else:
             out.append((k, 0, 0))

@@ -151,9 +151,10 @@ lbe_status wait(lbe_handle* h) {
   CU(h, cudaMemcpyAsync(&e, h->d_err, sizeof e, cudaMemcpyDeviceToHost, h->stream));
   if ((st = wait_stream(h))) return st;
   if (e)
-    return fail(h, LBE_ECUDA,
-                "a strip-kernel copy wait ran out of its poll limit (device error word %d); the "
-                "state is lost: set a state or load a checkpoint",
+    return fail(h, LBE_ECUDA, "%s (device error word %d); the state is lost: set a state or "
+                "load a checkpoint",
+                (e & 1) ? "a strip-kernel copy wait ran out of its poll limit"
+                        : "a strip-kernel work range did not advance",
                 e);
   return LBE_OK;
 }
@@ -318,14 +319,24 @@ lbe_status setup_tiles(lbe_handle* h) {
     int max_ny = 1;
     for (auto& H : h->inst) max_ny = std::max(max_ny, H.ny);
     h->max_ny = max_ny;
-    if (h->seg_req > 0) {
+    // default: balanced row ranges for instances of different sizes, items
+    // of a fixed row count for one grid size.  Measured on the 64-drop
+    // sweep (four grid sizes, 36 M cells; FP32, 3 CTAs per SM): balanced
+    // 22.8 GLUPS, fixed items of 72 / 96 / 128 rows 21.6 / 22.2 / 22.2 (the
+    // last wave partly idle); on one 4096^2 grid fixed items of 72 rows (4
+    // whole waves) 24.0, balanced ranges 23.4 (also when cut into pieces of
+    // 48 to 160 rows).
+    bool one_size = true;
+    for (auto& H : h->inst)
+      one_size = one_size && H.nx == h->inst[0].nx && H.ny == h->inst[0].ny;
+    if (h->seg_req > 0 || (h->seg_req < 0 && h->grid_req != -1)) {
       h->seg = h->seg_req;
+    } else if (h->grid_req != -1 && !one_size) {
+      h->seg = 0;  // balanced contiguous row ranges, one per CTA
     } else {
-      // rows per work item: minimise (waves of the persistent grid) x (rows
-      // per item + the warm-up rows every item recomputes).  The stash
-      // kernel measured slower with items longer than about 96 rows (4096^2:
-      // 80 rows 18.3 GLUPS, 128 rows 16.5, 316 rows in one wave 17.7) and an
-      // item start costs it about 6 rows.
+      // rows per item that minimise (waves of the persistent grid, or of the
+      // resident CTAs with one CTA per item) x (rows per item + the warm-up
+      // rows every item recomputes, about 6 for the stash kernel)
       const int64_t slots = h->grid_req == -1 ? (int64_t)occ * h->num_sms : h->grid;
       const bool stash = h->tile == STASH_ID;
       const int seg_lo = std::min(8, max_ny);
@@ -346,13 +357,20 @@ lbe_status setup_tiles(lbe_handle* h) {
       }
       h->seg = best_seg;
     }
-    int64_t begin = 0;
+    // tile_begin: the instance's first item (seg > 0) or first strip row
+    // (seg == 0: the rows of all strips end to end, tiles_y the band height
+    // of the band-by-band order, about one CTA's share of the rows)
+    int64_t begin = 0, rows = 0;
+    for (auto& H : h->inst) rows += (int64_t)((H.nx + nc - 1) / nc) * H.ny;
+    const int64_t ctas = h->grid_req == -1 ? 1 : std::max(1, h->grid);
+    const int64_t band = std::max<int64_t>(1, (rows + ctas - 1) / ctas);
     for (int j = 0; j < h->n; j++) {
       InstDev& D = h->idev[j];
       D.tiles_x = (D.nx + nc - 1) / nc;
-      D.tiles_y = (D.ny + h->seg - 1) / h->seg;
+      D.tiles_y = h->seg > 0 ? (D.ny + h->seg - 1) / h->seg
+                             : (int)std::min<int64_t>(band, D.ny);
       D.tile_begin = begin;
-      begin += (int64_t)D.tiles_x * D.tiles_y;
+      begin += (int64_t)D.tiles_x * (h->seg > 0 ? D.tiles_y : D.ny);
     }
     h->total_tiles = begin;
     if (h->grid_req == -1) h->grid = (int)std::min<int64_t>(begin, 2147483647);
@@ -1086,7 +1104,8 @@ lbe_status lbe_set_tile(lbe_handle* h, int32_t tile_id, int32_t grid_ctas, int32
     for (auto& H : h->inst)
       if (H.nx < XG) return fail(h, LBE_EINVAL, "the strip kernel needs nx >= %d", XG);
   if (grid_ctas < -1) return fail(h, LBE_EINVAL, "grid_ctas must be >= -1");
-  if (seg_rows < 0) return fail(h, LBE_EINVAL, "seg_rows must be >= 0");
+  if (seg_rows < 0 && !is_strip(tile_id))
+    return fail(h, LBE_EINVAL, "seg_rows < 0 (balanced pieces) is for the strip kernel");
   lbe_status st = wait(h);
   if (st) return st;
   h->tile = tile_id;
@@ -1100,7 +1119,11 @@ lbe_status lbe_get_tile(const lbe_handle* h, int32_t out[4]) {
   out[0] = h->tile;
   out[1] = h->grid;
   out[2] = is_strip(h->tile) ? h->seg : 0;
-  out[3] = (int32_t)std::min<int64_t>(h->total_tiles, 2147483647);
+  // work items: with balanced ranges (strip kernel, seg <= 0), one per CTA
+  const int64_t items = (is_strip(h->tile) && h->seg <= 0)
+                            ? std::min<int64_t>(h->total_tiles, h->grid)
+                            : h->total_tiles;
+  out[3] = (int32_t)std::min<int64_t>(items, 2147483647);
   return LBE_OK;
 }
 

@@ -141,7 +141,7 @@ STRIP_SHAPES = [(4, 8), (5, 3), (7, 40), (64, 17), (130, 19), (200, 33), (257, 7
 
 @pytest.mark.parametrize("nx,ny", STRIP_SHAPES)
 @pytest.mark.parametrize("storage", ["f32", "f16dev", "bf16dev", "f16mix"])
-@pytest.mark.parametrize("seg", [1, 3, 0])
+@pytest.mark.parametrize("seg", [1, 3, 0, -5])
 def test_strip_kernel_equals_tile_kernel(LBE, storage, nx, ny, seg):
     """The stash strip kernel (id 7) on
     narrow, ragged and partial strips, with segments of 1, 3 and automatic
@@ -157,8 +157,9 @@ def test_strip_kernel_equals_tile_kernel(LBE, storage, nx, ny, seg):
     a.set_tile(0)
     a.step(5)
     for tile in (7,):
-        # grid 0: as many CTAs as fit; grid 1: one CTA walks every work item
-        for grid in (0, 1):
+        # grid 0: as many CTAs as fit; grid 1: one CTA walks every work
+        # item; grid 7: (seg 0) ranges that start and end inside strips
+        for grid in (0, 1, 7):
             b = LBE(w, storage=storage)
             b.set_tile(tile, grid, seg)
             assert b.get_tile()["kernel"] == tile
@@ -346,6 +347,22 @@ def test_batch_of_uneven_instances_matches_each_alone(LBE, orc):
                                                               w.Ttop), w.Tbot, w.Ttop, n))
         e = field_errors(F, G)
         assert max(e["u"], e["T"], e["c"]) < 1e-12, (j, e)
+
+
+@pytest.mark.parametrize("grid", [0, 3, 1])
+def test_strip_batch_ranges_cross_instances(LBE, grid):
+    """FP32 batch on the strip kernel with balanced row ranges (3 CTAs: every
+    range spans several strips and instances): each instance bitwise equal
+    to the same instance advanced alone."""
+    ws = wl.batch_sweep(n=5, seed=3, grids=((40, 80), (136, 48), (64, 128)))
+    n = 12
+    sim = LBE(ws, storage="f32")
+    sim.set_tile(7, grid, 0)
+    sim.step(n)
+    for j, w in enumerate(ws):
+        one = LBE(w, storage="f32")
+        one.step(n)
+        assert np.array_equal(sim.get_state(j).numpy(), one.get_state().numpy()), j
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16dev", "f16mix"])
