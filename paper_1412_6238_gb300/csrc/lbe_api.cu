@@ -153,7 +153,8 @@ lbe_status wait(lbe_handle* h) {
   if (e)
     return fail(h, LBE_ECUDA, "%s (device error word %d); the state is lost: set a state or "
                 "load a checkpoint",
-                (e & 1) ? "a strip-kernel copy wait ran out of its poll limit"
+                (e & 1) ? "a strip-kernel wait (for copies or a stash slot) ran out of its poll "
+                          "limit"
                         : "a strip-kernel work range did not advance",
                 e);
   return LBE_OK;

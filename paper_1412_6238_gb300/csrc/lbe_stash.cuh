@@ -21,13 +21,16 @@
 //
 // Iteration i (from ya - 4 to yb):
 //   barrier; 1. collide row i-1 (S2-S9 of lbe_cell.cuh) from its stash slot
-//      and the moment rings, and store its 27 values;
-//   barrier; one elected lane issues the copies of row i+3 into the slot
-//      that row i-1 has just freed (as early as possible: the copies then
-//      have the rest of this iteration and the next collision to land);
-//   2. wait for the copies of row i+2 and form its moments c, p, T (S1) into
-//      the rings (own columns, then the four halo columns); rows below the bottom wall use the pulled values of their
-//      mirror row, rows above the top wall copy the mirror rows in the rings;
+//      and the moment rings, and store its 27 values; every thread arrives
+//      on the slot's empty mbarrier right after its pulls;
+//   2. one elected lane of warp 0 waits for that empty barrier and issues
+//      the copies of row i+3 into the slot (as early as possible: the
+//      copies then have the rest of this iteration and the next collision
+//      to land), while the other warps go on;
+//   3. wait for the copies of row i+2 and form its moments c, p, T (S1) into
+//      the rings (own columns, then the four halo columns); rows below the
+//      bottom wall use the pulled values of their mirror row, rows above the
+//      top wall copy the mirror rows in the rings;
 //   barrier; 4. unit normal of row i+1 (S2).
 // Every population is read from HBM once per step.  Every mbarrier wait is
 // bounded (poll_lim polls): on the first time-out the CTA sets *err, issues
@@ -53,6 +56,9 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 // Bounded wait for the phase with the given parity (at most `limit` polls);
 // false on time-out.
@@ -171,7 +177,9 @@ struct StashCfg {
   // FP32 rings of c, p, T, n_x, n_y and the FP16 ring of the c low part
   static constexpr int RINGS = (CR * CW + 2 * PR * QW + 2 * NR * QW) * 4 + CR * CW * 2;
   static_assert(RINGS % 8 == 0, "the slot barriers follow the rings");
-  static constexpr int SMEM = STASH + RINGS + SR * 8;
+  // a "full" (copies landed) and an "empty" (every thread done with the
+  // slot) mbarrier per stash slot
+  static constexpr int SMEM = STASH + RINGS + 2 * SR * 8;
   // resident CTAs per SM the kernel is compiled for (registers)
   static constexpr int MINB = Fmt::MINB;
   static_assert(NC % 32 == 0, "whole warps");
@@ -403,17 +411,16 @@ __device__ __forceinline__ CopyPlan copy_plan(const InstDev& I, int parity, int 
 }
 
 // The copies of one row: the populations pulled by the cells of moment row
-// mr (or, at a wall, the reversed populations of row mr itself) into the
-// stash slot at shared address dst, completing on bar.
+// mr (or, at a wall, the reversed populations of row mr itself), as calls
+// copy(byte offset in the stash slot, source address, bytes).
 //   FP32 (19 copies): the 9 (f_i, g_i) pair rows, the 9 hbar_i rows, the
 //     g_0 low part.
 //   16-bit (20 copies): the 8 pair rows (i = 1..8), f_0, the 9 hbar_i rows,
 //     the FP32 g_0 row, the g_0 low part.
 //   F16MIX (10 copies): the 9 rows of direction words, the FP32 g_0 row.
 // WALL: mr is the first or the last row (else the pulls need no wall rule).
-template <class S, bool WALL>
-__device__ __forceinline__ void issue_row(const CopyPlan& c, uint32_t dst, uint32_t bar, int mr,
-                                          int ny) {
+template <class S, bool WALL, class Copy>
+__device__ __forceinline__ void row_copies(const CopyPlan& c, int mr, int ny, Copy&& copy) {
   using Fmt = StashFmt<S>;
   const bool wb = WALL && mr == 0, wt = WALL && mr == ny - 1;
   // source row and plane of population i (the reversed one at a wall)
@@ -428,28 +435,36 @@ __device__ __forceinline__ void issue_row(const CopyPlan& c, uint32_t dst, uint3
   if constexpr (S::kind == ST_F16MIX) {
 #pragma unroll
     for (int i = 0; i < 9; i++)
-      bulk_load(dst + i * Fmt::WROW, c.pair + pl(i) * c.pp + at(i, c.row8), Fmt::WROW, bar);
-    bulk_load(dst + Fmt::G0, c.g0 + (int64_t)mr * c.row4, Fmt::G0B, bar);
+      copy(i * Fmt::WROW, c.pair + pl(i) * c.pp + at(i, c.row8), Fmt::WROW);
+    copy(Fmt::G0, c.g0 + (int64_t)mr * c.row4, Fmt::G0B);
   } else if constexpr (S::kind == ST_F32) {
 #pragma unroll
     for (int i = 0; i < 9; i++)
-      bulk_load(dst + Fmt::off(0, i), c.pair + pl(i) * c.pp + at(i, c.row8), Fmt::PROW, bar);
+      copy(Fmt::off(0, i), c.pair + pl(i) * c.pp + at(i, c.row8), Fmt::PROW);
 #pragma unroll
     for (int i = 0; i < 9; i++)
-      bulk_load(dst + Fmt::off(2, i), c.h + pl(i) * c.pb + at(i, c.row4), Fmt::ROW, bar);
+      copy(Fmt::off(2, i), c.h + pl(i) * c.pb + at(i, c.row4), Fmt::ROW);
   } else {
 #pragma unroll
     for (int i = 1; i < 9; i++)
-      bulk_load(dst + Fmt::off(0, i), c.pair + (pl(i) - 1) * c.pp + at(i, c.row4), Fmt::PROW,
-                bar);
-    bulk_load(dst + Fmt::F0, c.f0 + (int64_t)mr * c.row2, Fmt::ROW, bar);
+      copy(Fmt::off(0, i), c.pair + (pl(i) - 1) * c.pp + at(i, c.row4), Fmt::PROW);
+    copy(Fmt::F0, c.f0 + (int64_t)mr * c.row2, Fmt::ROW);
 #pragma unroll
     for (int i = 0; i < 9; i++)
-      bulk_load(dst + Fmt::off(2, i), c.h + pl(i) * c.pb + at(i, c.row2), Fmt::ROW, bar);
-    bulk_load(dst + Fmt::G0, c.g0 + (int64_t)mr * c.row4, Fmt::G0B, bar);
+      copy(Fmt::off(2, i), c.h + pl(i) * c.pb + at(i, c.row2), Fmt::ROW);
+    copy(Fmt::G0, c.g0 + (int64_t)mr * c.row4, Fmt::G0B);
   }
-  if constexpr (S::kind != ST_F16MIX)
-    bulk_load(dst + Fmt::LO, c.lo + (int64_t)mr * c.row2, Fmt::LOB, bar);
+  if constexpr (S::kind != ST_F16MIX) copy(Fmt::LO, c.lo + (int64_t)mr * c.row2, Fmt::LOB);
+}
+
+// The row's copies into the stash slot at shared address dst, completing on
+// the slot's barrier bar.
+template <class S, bool WALL>
+__device__ __forceinline__ void issue_row(const CopyPlan& c, uint32_t dst, uint32_t bar, int mr,
+                                          int ny) {
+  row_copies<S, WALL>(c, mr, ny, [&](int off, const char* src, int bytes) {
+    bulk_load(dst + (uint32_t)off, src, (uint32_t)bytes, bar);
+  });
 }
 
 template <class S, int NC>
@@ -471,7 +486,8 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
   C* nxr = Tring + Cfg::PR * QW;                         // [NR][QW]
   C* nyr = nxr + Cfg::NR * QW;
   __half* clr = reinterpret_cast<__half*>(nyr + Cfg::NR * QW);  // [CR][CW], lo * 2^24
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Cfg::STASH + Cfg::RINGS);  // [SR]
+  // [SR] full barriers, then [SR] empty barriers
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Cfg::STASH + Cfg::RINGS);
   __shared__ int s_abort;
   const int t = threadIdx.x;
   const int wu = __shfl_sync(0xffffffffu, t >> 5, 0);  // the warp index, warp-uniform
@@ -482,15 +498,20 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
   const int hj = lane < 2 ? lane - 2 : NC - 2 + lane;
   const uint32_t stash_u = smem_u32(smem);
   const uint32_t bars_u = smem_u32(bars);
+  const uint32_t empty_u = bars_u + 8 * Cfg::SR;
   // the slots' barriers are initialised once; every copy issued in an item is
   // waited for in that item, so the phase bits carry over between items
   if (t == 0) {
-    for (int s = 0; s < Cfg::SR; s++) mbar_init(bars_u + 8 * s, 1);
+    for (int s = 0; s < Cfg::SR; s++) {
+      mbar_init(bars_u + 8 * s, 1);
+      mbar_init(empty_u + 8 * s, NC);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   __syncthreads();
   unsigned phase = 0;    // bit s: parity of the next completion of slot s
+  unsigned ephase = 0;   // bit s: parity of the next release of slot s
   unsigned pending = 0;  // bit s: slot s has copies not yet waited for
   // the handle's step counter (random bits of the stochastic rounding)
   const uint32_t step = S::SR ? __ldg(seed) : 0u;
@@ -578,15 +599,26 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
     auto nr = [](int m) { return (m & (Cfg::NR - 1)) * QW; };
     auto loadable = [&](int m) { return m <= yb + 1 && m < ny; };
     // the copies of the populations pulled by moment row m (the mirror row's
-    // below the bottom wall), issued by one elected lane of warp 0 after a
-    // barrier that every thread passed after its last read of the slot
-    auto issue = [&](int m) {
-      if (!loadable(m)) return;
+    // below the bottom wall), issued by one elected lane of warp 0.  In the
+    // row loop the slot is that of the row collided in the same iteration:
+    // the lane first waits (bounded) for the slot's empty barrier, on which
+    // every thread arrives once per iteration after its last read of the
+    // slot (release = false: the slot is free already, at an item start).
+    auto issue = [&](int m, bool release) {
       const int sl = m & (Cfg::SR - 1);
+      const unsigned epar = (ephase >> sl) & 1u;
+      if (release) ephase ^= 1u << sl;  // one release of this slot per iteration
+      if (!loadable(m)) return;
       pending |= 1u << sl;
       if (wu != 0) return;
       __syncwarp();
       if (elect_one()) {
+        if (release && !mbar_wait(empty_u + 8 * sl, epar, poll_lim)) {
+          // no copy issued after a failed wait (the slot may still be read)
+          s_abort = 1;
+          atomicOr(err, 1);
+          return;
+        }
         const uint32_t bar = bars_u + (uint32_t)(sl * 8);
         const uint32_t dstw = stash_u + (uint32_t)(sl * Cfg::SLOT);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -611,7 +643,7 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
       return ok;
     };
 
-    issue(ya - 2);
+    issue(ya - 2, false);
     int i5 = (((ya - 4) % Cfg::CR) + Cfg::CR) % Cfg::CR;  // i mod CR
     for (int i = ya - 4; i <= yb; i++, i5 = (i5 == Cfg::CR - 1) ? 0 : i5 + 1) {
       // ring row of i + d (|d| < CR)
@@ -622,8 +654,9 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
       __syncthreads();
       if (s_abort) break;
 
-      // ---- 1. collide row r = i - 1
+      // ---- 1. collide row r = i - 1 (every thread then releases its slot)
       const int r = i - 1;
+      const uint32_t ebar = empty_u + 8u * (uint32_t)(r & (Cfg::SR - 1));
       if (r >= ya && r < yb && collides) {
         const char* s = slot(r);
         C f[9], g[9], h[9], g0lo;
@@ -640,6 +673,7 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
           wstash_pull<S, 2, true>(I, P, s, c0, c0g, r, x, h);
           g0lo = __half2float(reinterpret_cast<const __half*>(s + Fmt::LO)[c0lo]) * G0LO_INV;
         }
+        mbar_arrive(ebar);  // done with the slot (the arrive orders the reads before it)
         const int ps = rr(-2), p0 = rr(-1), pn = rr(0);  // rows r-1, r, r+1
         // rows of the rings from column x0 (index t: the own column)
         const C* cs = cring + ps * CW + 2;
@@ -717,12 +751,15 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
         }
         // (the periodic ghost columns are refreshed by ghost_kernel after the
         // step, not here: the branch costs this kernel about 7 %)
+      } else {
+        mbar_arrive(ebar);
       }
 
-      // ---- 2. the copies of row i + 3 into the slot of row i - 1, which
-      // every thread is done with
-      __syncthreads();
-      issue(i + 3);
+      // ---- 2. the copies of row i + 3 into the slot of row i - 1, once
+      // every thread has released it (no CTA barrier: the other warps go on
+      // to the moments of row i + 2, which touch neither that slot nor the
+      // ring rows the collision reads)
+      issue(i + 3, true);
 
       // ---- 3. moments of row m = i + 2
       const int m = i + 2;

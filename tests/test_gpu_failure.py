@@ -68,7 +68,7 @@ def test_copy_wait_runs_out_reports_ecuda_and_recovers(lbe_mod, storage):
         sim.synchronize()
     dt = time.time() - t0
     assert ei.value.status == -3, ei.value
-    assert "copy wait ran out" in str(ei.value)
+    assert "ran out of its poll limit" in str(ei.value)
     print("withheld row: LBE_ECUDA after %.3f s: %s" % (dt, ei.value))
     # every later wait reports it, and the handle refuses to step
     with pytest.raises(lbe_mod.LBEError) as e2:
