@@ -520,8 +520,8 @@ def measure_variants(args, w, ref_fields):
         "seconds": ta, "loss": r["loss"], "grad_sigmaT": r["grad"][0],
         "grad_eta_ratio": r["grad"][1], "grad_lam_ratio": r["grad"][2],
         "forward_plus_reverse_MLUPS": mw.cells * 2000 / ta / 1e6,
-        "note": "FP32 forward (stash kernel), FP64 reverse sweep over recomputed segments; "
-                "wall clock of one lbe_adjoint call"}
+        "note": "FP32 forward (stash kernel), reverse sweep over recomputed segments with FP32 "
+                "per-cell products and FP64 adjoint vectors; wall clock of one lbe_adjoint call"}
     return out
 
 

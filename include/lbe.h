@@ -241,7 +241,11 @@ typedef struct {
 
 /* Forward N steps from the handle's current state (the handle's storage and
  * kernel; checkpoints of the raw storage every k steps), then the backward
- * sweep in FP64 over the recomputed states.  Outputs (each may be NULL):
+ * sweep over the recomputed states (kept as FP64).  The backward arithmetic
+ * follows the forward's: FP64 for an LBE_F64 handle; FP32 per-cell products
+ * for the other storages, whose trajectory is an FP32 one (the adjoint
+ * vectors and the parameter sums stay FP64; the loss is always FP64).
+ * Outputs (each may be NULL):
  *   loss     host double: L
  *   grad     host double[3]: dL/dsigmaT, dL/d(eta2/eta1), dL/d(lam2/lam1)
  *   dT0      [ny][nx] doubles: dL/dT0
@@ -255,7 +259,8 @@ typedef struct {
 lbe_status lbe_adjoint(lbe_handle* h, const lbe_adjoint_spec* spec, double* loss,
                        double grad[3], double* dT0, double* dQ0, int32_t on_device);
 
-/* One adjoint step at an explicit state, for tests and custom losses.  With
+/* One adjoint step at an explicit state, for tests and custom losses (FP64
+ * arithmetic whatever the storage).  With
  * Q = Q_n ([27][ny][nx] device doubles, instance 0's parameters) and
  * a_next = dL/dQ_{n+1} (device, same layout):
  *   a_out = (dQ_{n+1}/dQ_n)^T a_next + wl * dl/dQ_n          (device)

@@ -70,24 +70,25 @@ __device__ __forceinline__ double eget(const double* e, const Geo& G, int x, int
   return e[(int64_t)(y + 1) * G.nx + wrap(x, G.nx)];
 }
 
-// isotropic gradient, index order i = 1..8, of a field given by an accessor
-template <class Fn>
-__device__ __forceinline__ void grad_at(Fn v, int x, int y, double& gx, double& gy) {
-  double sx = 0.0, sy = 0.0;
+// isotropic gradient, index order i = 1..8, of a field given by an accessor,
+// in the arithmetic type R
+template <class R, class Fn>
+__device__ __forceinline__ void grad_at(Fn v, int x, int y, R& gx, R& gy) {
+  R sx = R(0), sy = R(0);
   for (int i = 1; i < 9; i++) {
-    const double a = v(x + EX(i), y + EY(i));
-    sx += WGT<double>(i) * EX(i) * a;
-    sy += WGT<double>(i) * EY(i) * a;
+    const R a = (R)v(x + EX(i), y + EY(i));
+    sx += WGT<R>(i) * R(EX(i)) * a;
+    sy += WGT<R>(i) * R(EY(i)) * a;
   }
-  gx = sx * ICS2;
-  gy = sy * ICS2;
+  gx = sx * R(ICS2);
+  gy = sy * R(ICS2);
 }
-template <class Fn>
-__device__ __forceinline__ double lap_at(Fn v, int x, int y) {
-  const double v0 = v(x, y);
-  double s = 0.0;
-  for (int i = 1; i < 9; i++) s += WGT<double>(i) * (v(x + EX(i), y + EY(i)) - v0);
-  return 2.0 * s * ICS2;
+template <class R, class Fn>
+__device__ __forceinline__ R lap_at(Fn v, int x, int y) {
+  const R v0 = (R)v(x, y);
+  R s = R(0);
+  for (int i = 1; i < 9; i++) s += WGT<R>(i) * ((R)v(x + EX(i), y + EY(i)) - v0);
+  return R(2) * s * R(ICS2);
 }
 
 // ---------------------------------------------------------------- M, N, P
@@ -116,7 +117,7 @@ __global__ void pass_N(Geo G, const InstDev* __restrict__ d, const double* __res
        k += (int64_t)gridDim.x * blockDim.x) {
     const int x = (int)(k % G.nx), y = (int)(k / G.nx) - 1;
     double gx, gy;
-    grad_at([&](int a, int b) { return cget(C, G, a, b); }, x, y, gx, gy);
+    grad_at<double>([&](int a, int b) { return cget(C, G, a, b); }, x, y, gx, gy);
     const double inv = 1.0 / sqrt(gx * gx + gy * gy + I.pd.eta_n2);
     NX[k] = gx * inv;
     NY[k] = gy * inv;
@@ -158,8 +159,13 @@ __device__ __forceinline__ void block_sum(double v[4], double* sh) {
 
 // MODE 0: observable partials (sum c u_y, sum c) into part[blk][4].
 // MODE 1: adjoint of the step at this state.
-template <int MODE>
-__global__ void __launch_bounds__(TPB)
+// R: the arithmetic type (the planes stay FP64): double for an FP64 handle,
+// float for a handle whose forward step is FP32 or 16-bit arithmetic (the
+// adjoint is then linearised about an FP32 trajectory anyway; GB300's FP64
+// rate is a small fraction of its FP32 rate, and this pass is most of the
+// reverse sweep).  The theta partials are summed in FP64.
+template <int MODE, class R>
+__global__ void __launch_bounds__(TPB, sizeof(R) == 4 ? 2 : 1)
 pass_A(Geo G, const InstDev* __restrict__ d, const double* __restrict__ Q,
        const double* __restrict__ C, const double* __restrict__ Pp, const double* __restrict__ T,
        const double* __restrict__ NX, const double* __restrict__ NY, const double* __restrict__ b,
@@ -167,110 +173,112 @@ pass_A(Geo G, const InstDev* __restrict__ d, const double* __restrict__ Q,
        double* __restrict__ S, double* __restrict__ part) {
   __shared__ double sh[4 * TPB];
   const InstDev& I = *d;
-  const Phys<double>& P = I.pd;
+  const Phys<R>& P = phys<R>(I);
+  const R I3 = R(ICS2), H = R(0.5), ONE = R(1), TWO = R(2);
   double acc[4] = {0, 0, 0, 0};
   for (int64_t k = blockIdx.x * (int64_t)TPB + threadIdx.x; k < G.N;
        k += (int64_t)RBLK * TPB) {
     const int x = (int)(k % G.nx), y = (int)(k / G.nx);
-    double f[9], g[9], h[9];
+    R f[9], g[9], h[9];
     for (int i = 0; i < 9; i++) {
-      f[i] = Q[(int64_t)i * G.N + k];
-      g[i] = Q[(int64_t)(9 + i) * G.N + k];
-      h[i] = Q[(int64_t)(18 + i) * G.N + k];
+      f[i] = (R)Q[(int64_t)i * G.N + k];
+      g[i] = (R)Q[(int64_t)(9 + i) * G.N + k];
+      h[i] = (R)Q[(int64_t)(18 + i) * G.N + k];
     }
-    const double cc = C[k], pp = Pp[k], TT = T[k];
+    const R cc = (R)C[k], pp = (R)Pp[k], TT = (R)T[k];
     auto cf = [&](int a, int bb) { return cget(C, G, a, bb); };
     auto pf = [&](int a, int bb) { return cget(Pp, G, a, bb); };
     auto Tf = [&](int a, int bb) { return Tget(T, G, I, a, bb); };
-    double gcx, gcy, gTx, gTy, gpx, gpy, d1, d2, dum;
-    grad_at(cf, x, y, gcx, gcy);
-    const double lapc = lap_at(cf, x, y);
-    grad_at(Tf, x, y, gTx, gTy);
-    grad_at(pf, x, y, gpx, gpy);
-    grad_at([&](int a, int bb) { return eget(NX, G, a, bb); }, x, y, d1, dum);
-    grad_at([&](int a, int bb) { return eget(NY, G, a, bb); }, x, y, dum, d2);
-    const double kappa = d1 + d2;
+    R gcx, gcy, gTx, gTy, gpx, gpy, d1, d2, dum;
+    grad_at<R>(cf, x, y, gcx, gcy);
+    const R lapc = lap_at<R>(cf, x, y);
+    grad_at<R>(Tf, x, y, gTx, gTy);
+    grad_at<R>(pf, x, y, gpx, gpy);
+    grad_at<R>([&](int a, int bb) { return eget(NX, G, a, bb); }, x, y, d1, dum);
+    grad_at<R>([&](int a, int bb) { return eget(NY, G, a, bb); }, x, y, dum, d2);
+    const R kappa = d1 + d2;
     // forward (same expressions as the FP64 step)
-    const double mu = P.beta2 * cc * (cc - 1.0) * (2.0 * cc - 1.0) - P.eps2 * lapc;
-    const double sigma = P.sigma0 - P.sigmaT * (TT - P.Tref);
-    const double g2 = gcx * gcx + gcy * gcy;
-    const double gabs = sqrt(g2);
-    const double cdT = gcx * gTx + gcy * gTy;
-    const double ea = P.ea;
-    const double cap = -sigma * kappa * ea * gabs;
-    const double mar = -P.sigmaT * ea;
-    const double Fx = cap * gcx + mar * (g2 * gTx - cdT * gcx) + P.Fbx;
-    const double Fy = cap * gcy + mar * (g2 * gTy - cdT * gcy) + P.Fby;
-    double jx = f[1] - f[3];
+    const R mu = P.beta2 * cc * (cc - ONE) * (TWO * cc - ONE) - P.eps2 * lapc;
+    const R sigma = P.sigma0 - P.sigmaT * (TT - P.Tref);
+    const R g2 = gcx * gcx + gcy * gcy;
+    const R gabs = sqrt(g2);
+    const R cdT = gcx * gTx + gcy * gTy;
+    const R ea = P.ea;
+    const R cap = -sigma * kappa * ea * gabs;
+    const R mar = -P.sigmaT * ea;
+    const R Fx = cap * gcx + mar * (g2 * gTx - cdT * gcx) + P.Fbx;
+    const R Fy = cap * gcy + mar * (g2 * gTy - cdT * gcy) + P.Fby;
+    R jx = f[1] - f[3];
     jx = jx + f[5];
     jx = jx - f[6];
     jx = jx - f[7];
     jx = jx + f[8];
-    double jy = f[2] - f[4];
+    R jy = f[2] - f[4];
     jy = jy + f[5];
     jy = jy + f[6];
     jy = jy - f[7];
     jy = jy - f[8];
-    const double rho = P.rho, rcs2 = P.rcs2;
+    const R rho = P.rho, rcs2 = P.rcs2;
     // reciprocals once per cell: the FP64 divisions dominated this pass
-    const double irc = 1.0 / rcs2, irho = 1.0 / rho;
-    const double ux = jx * irc + 0.5 * Fx * irho;
-    const double uy = jy * irc + 0.5 * Fy * irho;
+    const R irc = ONE / rcs2, irho = ONE / rho;
+    const R ux = jx * irc + H * Fx * irho;
+    const R uy = jy * irc + H * Fy * irho;
     if (MODE == 0) {
-      acc[0] += cc * uy;
-      acc[1] += cc;
+      acc[0] += (double)(cc * uy);
+      acc[1] += (double)cc;
       continue;
     }
-    const double eta = P.eta1 + cc * P.deta;
-    const double lam = P.lam1 + cc * P.dlam;
-    const double tau_f = eta * irc + 0.5;
-    const double omega_f = 1.0 / tau_f;
-    const double ircv = 1.0 / P.rcvcs2;
-    const double tau_h = lam * ircv;
-    const double omega_T = 2.0 / (2.0 * tau_h + 1.0);
-    const double omega_g = P.omega_g;
-    const double af = 1.0 - 0.5 * omega_f, ag = 1.0 - 0.5 * omega_g, aT = 1.0 - 0.5 * omega_T;
-    const double uu = (ux * ux + uy * uy) * ICS2;
-    const double Gm = P.Gm;
-    const double W0 = WGT<double>(0);
-    const double Hi = Gm * mu * ICS2;
-    const double H0 = (cc - (1.0 - W0) * Gm * mu * ICS2) * (1.0 / W0);
-    const double Gx = Fx - gpx, Gy = Fy - gpy;
-    const double rcvT = P.rho * P.cv * TT;
+    const R eta = P.eta1 + cc * P.deta;
+    const R lam = P.lam1 + cc * P.dlam;
+    const R tau_f = eta * irc + H;
+    const R omega_f = ONE / tau_f;
+    const R ircv = ONE / P.rcvcs2;
+    const R tau_h = lam * ircv;
+    const R omega_T = TWO / (TWO * tau_h + ONE);
+    const R omega_g = P.omega_g;
+    const R af = ONE - H * omega_f, ag = ONE - H * omega_g, aT = ONE - H * omega_T;
+    const R uu = (ux * ux + uy * uy) * I3;
+    const R Gm = P.Gm;
+    const R W0 = WGT<R>(0);
+    const R Hi = Gm * mu * I3;
+    const R H0 = (cc - (ONE - W0) * Gm * mu * I3) * (ONE / W0);
+    const R Gx = Fx - gpx, Gy = Fy - gpy;
+    const R rcvT = P.rho * P.cv * TT;
 
     // ---- reverse through the collisions
-    double fb[9], gbr[9], hb[9];
-    double cb = 0, pb = 0, Tb = 0, uxb = 0, uyb = 0, Fxb = 0, Fyb = 0, Gxb = 0, Gyb = 0;
-    double uub = 0, Hib = 0, H0b = 0, rcvTb = 0, wfb = 0, wTb = 0, afb = 0, aTb = 0;
+    R fb[9], gbr[9], hb[9];
+    R cb = 0, pb = 0, Tb = 0, uxb = 0, uyb = 0, Fxb = 0, Fyb = 0, Gxb = 0, Gyb = 0;
+    R uub = 0, Hib = 0, H0b = 0, rcvTb = 0, wfb = 0, wTb = 0, afb = 0, aTb = 0;
     for (int i = 0; i < 9; i++) {
-      const double W = WGT<double>(i);
-      const double xu = (EX(i) * ux + EY(i) * uy) * ICS2;
-      const double hq = 0.5 * (xu * xu - uu);
-      const double Gam = W * (1.0 + xu + hq);
-      const double q = xu + hq;
-      const double dx = EX(i) - ux, dy = EY(i) - uy;
-      const double feq = W * (pp + rcs2 * q);
-      const double fsd = Fx * dx + Fy * dy;
-      const double fs = fsd * Gam;
-      const double Hx = (i == 0 ? H0 : Hi);
-      const double geq = W * (Hx + cc * q);
-      const double gdot = dx * Gx + dy * Gy;
-      const double sgv = cc * gdot * irc;
-      const double heq = rcvT * Gam;
-      const double shv = (Gx * dx + Gy * dy) * irc;
-      const double hs = shv * heq;
-      const double bf = b[(int64_t)i * G.N + k], bg = b[(int64_t)(9 + i) * G.N + k],
-                   bh = b[(int64_t)(18 + i) * G.N + k];
-      double Gamb = 0, qb = 0, dxb = 0, dyb = 0, xub = 0, hqb = 0;
+      const R W = WGT<R>(i);
+      const R ex = R(EX(i)), ey = R(EY(i));
+      const R xu = (ex * ux + ey * uy) * I3;
+      const R hq = H * (xu * xu - uu);
+      const R Gam = W * (ONE + xu + hq);
+      const R q = xu + hq;
+      const R dx = ex - ux, dy = ey - uy;
+      const R feq = W * (pp + rcs2 * q);
+      const R fsd = Fx * dx + Fy * dy;
+      const R fs = fsd * Gam;
+      const R Hx = (i == 0 ? H0 : Hi);
+      const R geq = W * (Hx + cc * q);
+      const R gdot = dx * Gx + dy * Gy;
+      const R sgv = cc * gdot * irc;
+      const R heq = rcvT * Gam;
+      const R shv = (Gx * dx + Gy * dy) * irc;
+      const R hs = shv * heq;
+      const R bf = (R)b[(int64_t)i * G.N + k], bg = (R)b[(int64_t)(9 + i) * G.N + k],
+              bh = (R)b[(int64_t)(18 + i) * G.N + k];
+      R Gamb = 0, qb = 0, dxb = 0, dyb = 0, xub = 0, hqb = 0;
       // h: ho = h - wT (h - heq) + aT hs
-      hb[i] = bh * (1.0 - omega_T);
+      hb[i] = bh * (ONE - omega_T);
       wTb += bh * (heq - h[i]);
-      double heqb = bh * omega_T;
-      const double hsb = bh * aT;
+      R heqb = bh * omega_T;
+      const R hsb = bh * aT;
       aTb += bh * hs;
-      const double shb = hsb * heq;
+      const R shb = hsb * heq;
       heqb += hsb * shv;
-      const double shr = shb * irc;
+      const R shr = shb * irc;
       Gxb += shr * dx;
       Gyb += shr * dy;
       dxb += shr * Gx;
@@ -278,12 +286,12 @@ pass_A(Geo G, const InstDev* __restrict__ d, const double* __restrict__ Q,
       rcvTb += heqb * Gam;
       Gamb += heqb * rcvT;
       // g: go = g - wg (g - geq) + ag gs, gs = (c gdot / rcs2) Gam
-      gbr[i] = bg * (1.0 - omega_g);
-      const double geqb = bg * omega_g;
-      const double gsb = bg * ag;
-      const double sgb = gsb * Gam;
+      gbr[i] = bg * (ONE - omega_g);
+      const R geqb = bg * omega_g;
+      const R gsb = bg * ag;
+      const R sgb = gsb * Gam;
       Gamb += gsb * sgv;
-      const double sgr = sgb * irc, sgc = sgr * cc;
+      const R sgr = sgb * irc, sgc = sgr * cc;
       cb += sgr * gdot;
       Gxb += sgc * dx;
       Gyb += sgc * dy;
@@ -293,10 +301,10 @@ pass_A(Geo G, const InstDev* __restrict__ d, const double* __restrict__ Q,
       cb += geqb * W * q;
       qb += geqb * W * cc;
       // f: fo = f - wf (f - feq) + af fs, fs = (F.(xi - u)) Gam
-      fb[i] = bf * (1.0 - omega_f);
+      fb[i] = bf * (ONE - omega_f);
       wfb += bf * (feq - f[i]);
-      const double feqb = bf * omega_f;
-      const double fsb = bf * af;
+      const R feqb = bf * omega_f;
+      const R fsb = bf * af;
       afb += bf * fs;
       Fxb += fsb * Gam * dx;
       Fyb += fsb * Gam * dy;
@@ -312,85 +320,85 @@ pass_A(Geo G, const InstDev* __restrict__ d, const double* __restrict__ Q,
       xub += Gamb * W + qb;
       hqb += Gamb * W + qb;
       xub += hqb * xu;
-      uub -= 0.5 * hqb;
-      uxb += xub * EX(i) * ICS2;
-      uyb += xub * EY(i) * ICS2;
+      uub -= H * hqb;
+      uxb += xub * ex * I3;
+      uyb += xub * ey * I3;
     }
     Tb += rcvTb * P.rho * P.cv;
     Fxb += Gxb;
     Fyb += Gyb;
-    double gpxb = -Gxb, gpyb = -Gyb;
-    double mub = Hib * Gm * ICS2;
-    cb += H0b * (1.0 / W0);
-    mub -= H0b * (1.0 - W0) * Gm * (ICS2 / W0);
-    uxb += uub * 2.0 * ux * ICS2;
-    uyb += uub * 2.0 * uy * ICS2;
-    wTb -= 0.5 * aTb;
-    wfb -= 0.5 * afb;
-    const double tauhb = -wTb * omega_T * omega_T;
-    const double lamb = tauhb * ircv;
-    const double taufb = -wfb * omega_f * omega_f;
-    const double etab = taufb * irc;
+    R gpxb = -Gxb, gpyb = -Gyb;
+    R mub = Hib * Gm * I3;
+    cb += H0b * (ONE / W0);
+    mub -= H0b * (ONE - W0) * Gm * (I3 / W0);
+    uxb += uub * TWO * ux * I3;
+    uyb += uub * TWO * uy * I3;
+    wTb -= H * aTb;
+    wfb -= H * afb;
+    const R tauhb = -wTb * omega_T * omega_T;
+    const R lamb = tauhb * ircv;
+    const R taufb = -wfb * omega_f * omega_f;
+    const R etab = taufb * irc;
     cb += etab * P.deta + lamb * P.dlam;
-    double th_eta = etab * cc * P.eta1;  // d eta / d (eta2/eta1) = c eta1
-    double th_lam = lamb * cc * P.lam1;
+    R th_eta = etab * cc * P.eta1;  // d eta / d (eta2/eta1) = c eta1
+    R th_lam = lamb * cc * P.lam1;
     // the observable at this step: l = A/B, dl/dc = u_y/B - A/B^2, dl/du_y = c/B
     if (wl != 0.0) {
-      const double A = obs[0], B = obs[1];
-      cb += wl * (uy / B - A / (B * B));
-      uyb += wl * cc / B;
+      const R A = (R)obs[0], B = (R)obs[1], wr = (R)wl;
+      cb += wr * (uy / B - A / (B * B));
+      uyb += wr * cc / B;
     }
     // u = j/(rho cs2) + F/(2 rho)
-    const double jxb = uxb * irc, jyb = uyb * irc;
-    Fxb += 0.5 * uxb * irho;
-    Fyb += 0.5 * uyb * irho;
-    for (int i = 0; i < 9; i++) fb[i] += EX(i) * jxb + EY(i) * jyb;
+    const R jxb = uxb * irc, jyb = uyb * irc;
+    Fxb += H * uxb * irho;
+    Fyb += H * uyb * irho;
+    for (int i = 0; i < 9; i++) fb[i] += R(EX(i)) * jxb + R(EY(i)) * jyb;
     // F = cap gc + mar (g2 gT - cdT gc) + rho a
-    const double capb = Fxb * gcx + Fyb * gcy;
-    const double marb = Fxb * (g2 * gTx - cdT * gcx) + Fyb * (g2 * gTy - cdT * gcy);
-    double gcxb = Fxb * cap - Fxb * mar * cdT;
-    double gcyb = Fyb * cap - Fyb * mar * cdT;
-    double g2b = mar * (Fxb * gTx + Fyb * gTy);
-    double gTxb = mar * g2 * Fxb, gTyb = mar * g2 * Fyb;
-    const double cdTb = -mar * (Fxb * gcx + Fyb * gcy);
-    double th_sig = -marb * ea;
+    const R capb = Fxb * gcx + Fyb * gcy;
+    const R marb = Fxb * (g2 * gTx - cdT * gcx) + Fyb * (g2 * gTy - cdT * gcy);
+    R gcxb = Fxb * cap - Fxb * mar * cdT;
+    R gcyb = Fyb * cap - Fyb * mar * cdT;
+    R g2b = mar * (Fxb * gTx + Fyb * gTy);
+    R gTxb = mar * g2 * Fxb, gTyb = mar * g2 * Fyb;
+    const R cdTb = -mar * (Fxb * gcx + Fyb * gcy);
+    R th_sig = -marb * ea;
     // cap = -sigma kappa ea gabs
-    const double sigb = -capb * kappa * ea * gabs;
-    const double kapb = -capb * sigma * ea * gabs;
-    const double gabsb = -capb * sigma * kappa * ea;
+    const R sigb = -capb * kappa * ea * gabs;
+    const R kapb = -capb * sigma * ea * gabs;
+    const R gabsb = -capb * sigma * kappa * ea;
     gcxb += cdTb * gTx;
     gcyb += cdTb * gTy;
     gTxb += cdTb * gcx;
     gTyb += cdTb * gcy;
-    if (gabs > 0.0) g2b += gabsb / (2.0 * gabs);
-    gcxb += 2.0 * g2b * gcx;
-    gcyb += 2.0 * g2b * gcy;
+    if (gabs > R(0)) g2b += gabsb / (TWO * gabs);
+    gcxb += TWO * g2b * gcx;
+    gcyb += TWO * g2b * gcy;
     // sigma = sigma0 - sigmaT (T - Tref)
     Tb += -sigb * P.sigmaT;
     th_sig += -sigb * (TT - P.Tref);
     // mu = 2 beta c (c-1)(2c-1) - eps^2 lap c
-    cb += mub * P.beta2 * (6.0 * cc * cc - 6.0 * cc + 1.0);
-    const double lapb = -mub * P.eps2;
+    cb += mub * P.beta2 * (R(6) * cc * cc - R(6) * cc + ONE);
+    const R lapb = -mub * P.eps2;
 
     for (int i = 0; i < 9; i++) {
-      aout[(int64_t)i * G.N + k] = fb[i];
-      aout[(int64_t)(9 + i) * G.N + k] = gbr[i];
-      aout[(int64_t)(18 + i) * G.N + k] = hb[i];
+      aout[(int64_t)i * G.N + k] = (double)fb[i];
+      aout[(int64_t)(9 + i) * G.N + k] = (double)gbr[i];
+      aout[(int64_t)(18 + i) * G.N + k] = (double)hb[i];
     }
-    S[(int64_t)S_GCX * G.N + k] = gcxb;
-    S[(int64_t)S_GCY * G.N + k] = gcyb;
-    S[(int64_t)S_LAP * G.N + k] = lapb;
-    S[(int64_t)S_GTX * G.N + k] = gTxb;
-    S[(int64_t)S_GTY * G.N + k] = gTyb;
-    S[(int64_t)S_GPX * G.N + k] = gpxb;
-    S[(int64_t)S_GPY * G.N + k] = gpyb;
-    S[(int64_t)S_KAP * G.N + k] = kapb;
-    S[(int64_t)S_C * G.N + k] = cb;
-    S[(int64_t)S_P * G.N + k] = pb;
-    S[(int64_t)S_T * G.N + k] = Tb;
-    acc[0] += th_sig;
-    acc[1] += th_eta;
-    acc[2] += th_lam;
+    S[(int64_t)S_GCX * G.N + k] = (double)gcxb;
+    S[(int64_t)S_GCY * G.N + k] = (double)gcyb;
+    S[(int64_t)S_LAP * G.N + k] = (double)lapb;
+    S[(int64_t)S_GTX * G.N + k] = (double)gTxb;
+    S[(int64_t)S_GTY * G.N + k] = (double)gTyb;
+    S[(int64_t)S_GPX * G.N + k] = (double)gpxb;
+    S[(int64_t)S_GPY * G.N + k] = (double)gpyb;
+    S[(int64_t)S_KAP * G.N + k] = (double)kapb;
+    S[(int64_t)S_C * G.N + k] = (double)cb;
+    S[(int64_t)S_P * G.N + k] = (double)pb;
+    S[(int64_t)S_T * G.N + k] = (double)Tb;
+    acc[0] += (double)th_sig;
+    acc[1] += (double)th_eta;
+    acc[2] += (double)th_lam;
   }
   block_sum(acc, sh);
   if (threadIdx.x == 0)
@@ -401,6 +409,8 @@ pass_A(Geo G, const InstDev* __restrict__ d, const double* __restrict__ Q,
 // kappa(X) = sum_i (w_i/cs2) xi_i . n(X + xi_i)  =>  n-bar(Y) = sum_i
 // (w_i/cs2) xi_i kappa-bar(Y - xi_i) over cells Y - xi_i; then through
 // n = v / s, s = sqrt(|v|^2 + eta_n^2): v-bar = n-bar/s - v (v.n-bar)/s^3.
+// R: the arithmetic type, as for pass A.
+template <class R>
 __global__ void pass_B(Geo G, const InstDev* __restrict__ d, const double* __restrict__ C,
                        const double* __restrict__ S, double* __restrict__ VX,
                        double* __restrict__ VY) {
@@ -410,25 +420,27 @@ __global__ void pass_B(Geo G, const InstDev* __restrict__ d, const double* __res
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < NE;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int x = (int)(k % G.nx), y = (int)(k / G.nx) - 1;
-    double nbx = 0, nby = 0;
+    R nbx = 0, nby = 0;
     for (int i = 1; i < 9; i++) {
       const int yy = y - EY(i);
       if (yy < 0 || yy >= G.ny) continue;
-      const double kv = kb[(int64_t)yy * G.nx + wrap(x - EX(i), G.nx)];
-      nbx += WGT<double>(i) * EX(i) / CS2 * kv;
-      nby += WGT<double>(i) * EY(i) / CS2 * kv;
+      const R kv = (R)kb[(int64_t)yy * G.nx + wrap(x - EX(i), G.nx)];
+      nbx += WGT<R>(i) * R(EX(i)) / R(CS2) * kv;
+      nby += WGT<R>(i) * R(EY(i)) / R(CS2) * kv;
     }
-    double vx, vy;
-    grad_at([&](int a, int bb) { return cget(C, G, a, bb); }, x, y, vx, vy);
-    const double s2 = vx * vx + vy * vy + I.pd.eta_n2;
-    const double s = sqrt(s2);
-    const double vn = vx * nbx + vy * nby;
-    VX[k] = nbx / s - vx * vn / (s2 * s);
-    VY[k] = nby / s - vy * vn / (s2 * s);
+    R vx, vy;
+    grad_at<R>([&](int a, int bb) { return cget(C, G, a, bb); }, x, y, vx, vy);
+    const R s2 = vx * vx + vy * vy + phys<R>(I).eta_n2;
+    const R s = sqrt(s2);
+    const R vn = vx * nbx + vy * nby;
+    VX[k] = (double)(nbx / s - vx * vn / (s2 * s));
+    VY[k] = (double)(nby / s - vy * vn / (s2 * s));
   }
 }
 
 // ---------------------------------------------------------------- CD
+// R: the arithmetic type, as for pass A.
+template <class R>
 __global__ void pass_CD(Geo G, const InstDev* __restrict__ d, const double* __restrict__ S,
                         const double* __restrict__ VX, const double* __restrict__ VY,
                         double* __restrict__ aout) {
@@ -437,13 +449,13 @@ __global__ void pass_CD(Geo G, const InstDev* __restrict__ d, const double* __re
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < G.N;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int x = (int)(k % G.nx), y = (int)(k / G.nx);
-    double cb = S[(int64_t)S_C * G.N + k];
-    double pb = S[(int64_t)S_P * G.N + k];
-    double Tb = S[(int64_t)S_T * G.N + k];
+    R cb = (R)S[(int64_t)S_C * G.N + k];
+    R pb = (R)S[(int64_t)S_P * G.N + k];
+    R Tb = (R)S[(int64_t)S_T * G.N + k];
     // Laplacian centre term
-    double sw = 0.0;
-    for (int i = 1; i < 9; i++) sw += WGT<double>(i);
-    cb += -2.0 * sw / CS2 * S[(int64_t)S_LAP * G.N + k];
+    R sw = R(0);
+    for (int i = 1; i < 9; i++) sw += WGT<R>(i);
+    cb += R(-2) * sw / R(CS2) * (R)S[(int64_t)S_LAP * G.N + k];
     // positions q holding c(x, y): the cell and its ghost images
     int qs[5], nq = 0;
     qs[nq++] = y;
@@ -455,32 +467,33 @@ __global__ void pass_CD(Geo G, const InstDev* __restrict__ d, const double* __re
     for (int jq = 0; jq < nq; jq++) {
       const int qy = qs[jq];
       const bool depth1 = qy >= -1 && qy <= ny;  // p, T ghosts reach one row
-      const double tsign = (qy == y) ? 1.0 : -1.0;
+      const R tsign = (qy == y) ? R(1) : R(-1);
       for (int i = 1; i < 9; i++) {
         const int X = wrap(x - EX(i), G.nx), Y = qy - EY(i);
-        const double wa = WGT<double>(i) / CS2;
+        const R wa = WGT<R>(i) / R(CS2);
+        const R ex = R(EX(i)), ey = R(EY(i));
         if (Y >= 0 && Y < ny) {
           const int64_t kk = (int64_t)Y * G.nx + X;
-          cb += wa * (EX(i) * S[(int64_t)S_GCX * G.N + kk] + EY(i) * S[(int64_t)S_GCY * G.N + kk]);
-          cb += 2.0 * wa * S[(int64_t)S_LAP * G.N + kk];
+          cb += wa * (ex * (R)S[(int64_t)S_GCX * G.N + kk] + ey * (R)S[(int64_t)S_GCY * G.N + kk]);
+          cb += R(2) * wa * (R)S[(int64_t)S_LAP * G.N + kk];
           if (depth1) {
-            pb += wa * (EX(i) * S[(int64_t)S_GPX * G.N + kk] +
-                        EY(i) * S[(int64_t)S_GPY * G.N + kk]);
+            pb += wa * (ex * (R)S[(int64_t)S_GPX * G.N + kk] +
+                        ey * (R)S[(int64_t)S_GPY * G.N + kk]);
             Tb += tsign * wa *
-                  (EX(i) * S[(int64_t)S_GTX * G.N + kk] + EY(i) * S[(int64_t)S_GTY * G.N + kk]);
+                  (ex * (R)S[(int64_t)S_GTX * G.N + kk] + ey * (R)S[(int64_t)S_GTY * G.N + kk]);
           }
         }
         if (Y >= -1 && Y <= ny) {
           const int64_t ke = (int64_t)(Y + 1) * G.nx + X;
-          cb += wa * (EX(i) * VX[ke] + EY(i) * VY[ke]);
+          cb += wa * (ex * (R)VX[ke] + ey * (R)VY[ke]);
         }
       }
     }
-    const double Tsc = Tb / (I.pd.rho * I.pd.cv);
+    const R Tsc = Tb / (phys<R>(I).rho * phys<R>(I).cv);
     for (int i = 0; i < 9; i++) {
-      aout[(int64_t)i * G.N + k] += pb;
-      aout[(int64_t)(9 + i) * G.N + k] += cb;
-      aout[(int64_t)(18 + i) * G.N + k] += Tsc;
+      aout[(int64_t)i * G.N + k] += (double)pb;
+      aout[(int64_t)(9 + i) * G.N + k] += (double)cb;
+      aout[(int64_t)(18 + i) * G.N + k] += (double)Tsc;
     }
   }
 }
@@ -533,15 +546,15 @@ cudaError_t launch_observable(const InstDev* d, int nx, int ny, const double* Q,
   const int gE = (int)((NE + TPB - 1) / TPB < 65535 ? (NE + TPB - 1) / TPB : 65535);
   pass_M<<<gN, TPB, 0, s>>>(G, d, Q, C, Pp, T);
   pass_N<<<gE, TPB, 0, s>>>(G, d, C, NX, NY);
-  pass_A<0><<<RBLK, TPB, 0, s>>>(G, d, Q, C, Pp, T, NX, NY, nullptr, nullptr, 0.0, nullptr,
-                                 nullptr, part);
+  pass_A<0, double><<<RBLK, TPB, 0, s>>>(G, d, Q, C, Pp, T, NX, NY, nullptr, nullptr, 0.0,
+                                         nullptr, nullptr, part);
   reduce_parts<<<1, TPB, 0, s>>>(part, out4, 0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_step(const InstDev* d, int nx, int ny, const double* Q,
                                 const double* a_next, double wl, const double* obs,
-                                double* a_out, double* theta_acc, double* scratch,
+                                double* a_out, double* theta_acc, double* scratch, bool fp32,
                                 cudaStream_t s) {
   using namespace adj;
   const Geo G{nx, ny, (int64_t)nx * ny};
@@ -566,10 +579,18 @@ cudaError_t launch_adjoint_step(const InstDev* d, int nx, int ny, const double* 
     cudaError_t e = cudaMemsetAsync(b, 0, sizeof(double) * 27 * G.N, s);
     if (e != cudaSuccess) return e;
   }
-  pass_A<1><<<RBLK, TPB, 0, s>>>(G, d, Q, C, Pp, T, NX, NY, b, obs, wl, a_out, S, part);
-  reduce_parts<<<1, TPB, 0, s>>>(part, theta_acc, 1);
-  pass_B<<<gE, TPB, 0, s>>>(G, d, C, S, VX, VY);
-  pass_CD<<<gN, TPB, 0, s>>>(G, d, S, VX, VY, a_out);
+  if (fp32) {
+    pass_A<1, float><<<RBLK, TPB, 0, s>>>(G, d, Q, C, Pp, T, NX, NY, b, obs, wl, a_out, S, part);
+    reduce_parts<<<1, TPB, 0, s>>>(part, theta_acc, 1);
+    pass_B<float><<<gE, TPB, 0, s>>>(G, d, C, S, VX, VY);
+    pass_CD<float><<<gN, TPB, 0, s>>>(G, d, S, VX, VY, a_out);
+  } else {
+    pass_A<1, double><<<RBLK, TPB, 0, s>>>(G, d, Q, C, Pp, T, NX, NY, b, obs, wl, a_out, S,
+                                           part);
+    reduce_parts<<<1, TPB, 0, s>>>(part, theta_acc, 1);
+    pass_B<double><<<gE, TPB, 0, s>>>(G, d, C, S, VX, VY);
+    pass_CD<double><<<gN, TPB, 0, s>>>(G, d, S, VX, VY, a_out);
+  }
   return cudaGetLastError();
 }
 

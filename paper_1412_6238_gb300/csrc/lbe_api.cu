@@ -758,6 +758,9 @@ lbe_status adjoint_run(lbe_handle* h, const lbe_adjoint_spec& sp, double* loss, 
   const int64_t nseg = (NS + K - 1) / K;
   const int64_t kk = K < NS ? K : NS;
   const InstDev* d1 = h->d_finst;
+  // the reverse sweep's arithmetic follows the forward's: FP64 for an FP64
+  // handle, FP32 otherwise (the trajectory is then an FP32 one anyway)
+  const bool fp32 = h->storage != LBE_F64;
   lbe_status st;
   DevBuf ck, states, abuf, scr, small, fin;
   if ((st = dalloc(h, ck, (size_t)nseg * H.buf_bytes, "checkpoints"))) return st;
@@ -809,7 +812,7 @@ lbe_status adjoint_run(lbe_handle* h, const lbe_adjoint_spec& sp, double* loss, 
       if (o) e = launch_observable(d1, nx, ny, Q, scr.d(), o, h->stream);
       if (e == cudaSuccess)
         e = launch_adjoint_step(d1, nx, ny, Q, have_next ? a_nxt : nullptr, wl, o, a_cur, theta,
-                                scr.d(), h->stream);
+                                scr.d(), fp32, h->stream);
       std::swap(a_cur, a_nxt);
       have_next = true;
     }
@@ -1157,7 +1160,7 @@ lbe_status lbe_adjoint_step(lbe_handle* h, const double* Q, const double* a_next
   if (wl != 0.0) e = launch_observable(h->d_finst, H.nx, H.ny, Q, scr.d(), obs, h->stream);
   if (e == cudaSuccess)
     e = launch_adjoint_step(h->d_finst, H.nx, H.ny, Q, a_next, wl, obs, a_out, theta, scr.d(),
-                            h->stream);
+                            false, h->stream);
   if (e != cudaSuccess) return fail(h, LBE_ECUDA, "adjoint step: %s", cudaGetErrorString(e));
   double th[4];
   if ((st = to_host(h, th, theta, sizeof th))) return st;

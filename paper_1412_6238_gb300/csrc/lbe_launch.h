@@ -137,10 +137,11 @@ cudaError_t launch_observable(const InstDev* d_one, int nx, int ny, const double
                               double* scratch, double* out4, cudaStream_t s);
 // a_out = Post'(Q)^T Pull^T a_next + wl dl/dQ with obs = {sum c u_y, sum c} of
 // Q (device, read only if wl != 0); theta_acc[0..2] (device) += the parameter
-// partials.  a_next may be nullptr (zero).
+// partials.  a_next may be nullptr (zero).  fp32: the per-cell products in
+// FP32 arithmetic (the planes and the parameter sums stay FP64).
 cudaError_t launch_adjoint_step(const InstDev* d_one, int nx, int ny, const double* Q,
                                 const double* a_next, double wl, const double* obs,
-                                double* a_out, double* theta_acc, double* scratch,
+                                double* a_out, double* theta_acc, double* scratch, bool fp32,
                                 cudaStream_t s);
 // dT0[k] = rho c_v sum_i w_i a[18 + i][k]
 cudaError_t launch_adjoint_dT0(const InstDev* d_one, int nx, int ny, const double* a,
