@@ -33,7 +33,9 @@ PARAM_KEYS = ("rho", "cv", "eta1", "eta2", "lam1", "lam2", "sigma0", "sigmaT",
 class _Params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
                 ("periodic_y", ctypes.c_int32), ("ablate", ctypes.c_int32)] + \
-               [(k, ctypes.c_double) for k in PARAM_KEYS] + [("rho2", ctypes.c_double)]
+               [(k, ctypes.c_double) for k in PARAM_KEYS] + [("rho2", ctypes.c_double)] + \
+               [("interp", ctypes.c_int32), ("wall_mid", ctypes.c_int32),
+                ("cos_wet", ctypes.c_double)]
 
 
 _lock = threading.Lock()
@@ -90,6 +92,11 @@ def _p(params: dict, nx: int, ny: int) -> _Params:
     # planting a mistake in the density terms (see lbe_oracle.c)
     s.rho2 = float(params.get("rho2", params["rho"]))
     s.ablate = int(params.get("ablate", 0))
+    # variants: property law (0 linear, 1 harmonic), wall temperature at the
+    # link's crossing point, contact angle of phase 1 (cos; 0: neutral)
+    s.interp = int(params.get("interp", 0))
+    s.wall_mid = int(params.get("wall_mid", 0))
+    s.cos_wet = float(params.get("cos_wet", 0.0))
     return s
 
 

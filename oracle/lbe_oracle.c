@@ -33,6 +33,12 @@
  *      anti-bounce-back for hbar at walls half a cell outside the first and
  *      last rows.
  *
+ * Variants the paper leaves open (orc_params; each off by default): a
+ * density varying with c (the grad(rho c_s^2) terms of Eq. 12, Eq. 13 and
+ * Fbar); the harmonic property law; the anti-bounce-back's wall temperature
+ * taken where the link crosses the wall; wetting walls with a contact angle
+ * (Young's law through a cubic wall energy).
+ *
  * Population storage: one array of 27 planes [k*9+i][y][x], k = 0 (f), 1 (g),
  * 2 (hbar), x fastest.  Velocity order i: 0 (0,0), 1 (1,0), 2 (0,1), 3 (-1,0),
  * 4 (0,-1), 5 (1,1), 6 (-1,1), 7 (-1,-1), 8 (1,-1).
@@ -62,6 +68,12 @@ typedef struct {
   double ax, ay;   /* body acceleration */
   double eta_n;    /* regularisation of n = grad c / sqrt(|grad c|^2+eta_n^2) */
   double rho2;     /* density of phase c = 1 (rho2 = rho: uniform density) */
+  /* boundary and property variants (0: the scheme as the paper states it) */
+  int32_t interp;   /* eta(c), lambda(c): 0 linear, 1 harmonic */
+  int32_t wall_mid; /* 1: the anti-bounce-back of a link takes T_w where the
+                       link crosses the wall (x - xi_x/2, interpolated) */
+  double cos_wet;   /* cos of the contact angle of phase 1 at both walls
+                       (0: neutral wetting, the mirror ghost rows) */
 } orc_params;
 
 /* Density of a cell, linear in c like eta and lambda (the paper states no
@@ -71,6 +83,28 @@ static double rho_of(const orc_params* P, double c) {
   return P->rho + c * (P->rho2 - P->rho);
 }
 static int varying_rho(const orc_params* P) { return P->rho2 != P->rho; }
+
+/* A property of a cell between its phase-0 value a and phase-1 value b.
+ * Linear in c (the default; the paper gives no law), or harmonic,
+ * 1/((1 - c)/a + c/b), whose series form keeps the flux continuous across
+ * a layered interface (conduction, shear). */
+static double prop_of(const orc_params* P, double a, double b, double c) {
+  if (P->interp == 1) return 1.0 / ((1.0 - c) / a + c / b);
+  return a + c * (b - a);
+}
+
+/* Wetting walls: the free energy beta c^2 (c-1)^2 + (eps^2/2)|grad c|^2 with
+ * the cubic wall energy -sigma cos(theta) (3c^2 - 2c^3), sigma =
+ * eps sqrt(2 beta)/6, gives at a wall the condition
+ *   dc/dn_out = (sqrt(2 beta)/eps) cos(theta) c (1 - c)
+ * (n_out pointing out of the fluid): Young's law with contact angle theta of
+ * phase 1.  Ghost row -1-j (or ny+j) of c: its mirror cell j plus
+ * (2j+1) times that flux, evaluated at the mirror cell's c (the normal
+ * distance between the two is 2j+1). */
+static double wet_ghost(const orc_params* P, double cm, int j) {
+  const double kw = P->cos_wet * sqrt(2.0 * P->beta) / P->eps;
+  return cm + (double)(2 * j + 1) * kw * cm * (1.0 - cm);
+}
 
 /* ---- D2Q9 lattice (the paper names D2Q9 weights but does not list them) */
 static const int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
@@ -223,9 +257,11 @@ static double lap_iso(const ext_field* e, int x, int y) {
   return 2.0 * s / CS2;
 }
 
-/* Fill ghost rows.  Walls: c and p mirror about the wall
- * (phi(-1-j) = phi(j)); T is antisymmetric about the wall temperature at the
- * same column (T(-1-j) = 2 T_w - T(j)).  Periodic y: wrap. */
+/* Fill ghost rows.  Walls: p (is_T = 0) and c (is_T = 2) mirror about the
+ * wall (phi(-1-j) = phi(j)), c with the wetting flux added when the contact
+ * angle is not 90 degrees; T (is_T = 1) is antisymmetric about the wall
+ * temperature at the same column (T(-1-j) = 2 T_w - T(j)).  Periodic y:
+ * wrap. */
 static void fill_ghosts(const orc_params* P, ext_field* e, int is_T,
                         const double* Tbot, const double* Ttop) {
   int nx = e->nx, ny = e->ny;
@@ -234,9 +270,12 @@ static void fill_ghosts(const orc_params* P, ext_field* e, int is_T,
       if (P->periodic_y) {
         *ext_at(e, x, -1 - j) = ext_get(e, x, ny - 1 - j);
         *ext_at(e, x, ny + j) = ext_get(e, x, j);
-      } else if (is_T) {
+      } else if (is_T == 1) {
         *ext_at(e, x, -1 - j) = 2.0 * Tbot[x] - ext_get(e, x, j);
         *ext_at(e, x, ny + j) = 2.0 * Ttop[x] - ext_get(e, x, ny - 1 - j);
+      } else if (is_T == 2 && P->cos_wet != 0.0) {
+        *ext_at(e, x, -1 - j) = wet_ghost(P, ext_get(e, x, j), j);
+        *ext_at(e, x, ny + j) = wet_ghost(P, ext_get(e, x, ny - 1 - j), j);
       } else {
         *ext_at(e, x, -1 - j) = ext_get(e, x, j);
         *ext_at(e, x, ny + j) = ext_get(e, x, ny - 1 - j);
@@ -264,7 +303,7 @@ static void scalar_stage(const orc_params* P, const double* Tbot,
       *ext_at(&pE, x, y) = p[(size_t)y * nx + x];
       *ext_at(&TE, x, y) = T[(size_t)y * nx + x];
     }
-  fill_ghosts(P, &cE, 0, Tbot, Ttop);
+  fill_ghosts(P, &cE, 2, Tbot, Ttop);
   fill_ghosts(P, &pE, 0, Tbot, Ttop);
   fill_ghosts(P, &TE, 1, Tbot, Ttop);
 
@@ -476,8 +515,8 @@ static void step_once(const orc_params* P, const double* Tbot,
     double cc = c[k], TT = T[k];
     const double rho = rho_of(P, cc);
     /* properties, linear in c */
-    double eta = P->eta1 + cc * (P->eta2 - P->eta1);
-    double lam = P->lam1 + cc * (P->lam2 - P->lam1);
+    double eta = prop_of(P, P->eta1, P->eta2, cc);
+    double lam = prop_of(P, P->lam1, P->lam2, cc);
     double tau_f = eta / (rho * CS2) + 0.5;
     double omega_f = 1.0 / tau_f;
     double tau_h = lam / (rho * cv * CS2);
@@ -541,7 +580,10 @@ static void step_once(const orc_params* P, const double* Tbot,
           /* halfway bounce-back: the population that left this cell towards
              the wall returns reversed one step later */
           int o_ = OPP[i];
-          double Tw = (ys < 0) ? Tbot[x] : Ttop[x];
+          const double* Twall = (ys < 0) ? Tbot : Ttop;
+          double Tw = Twall[x];
+          if (P->wall_mid && EX[i] != 0) /* the link crosses the wall at x - xi_x/2 */
+            Tw = 0.5 * (Twall[x] + Twall[((x - EX[i]) % nx + nx) % nx]);
           if (pass == 0) {
             out[(size_t)i * N + k] = post[(size_t)o_ * N + k];
             out[(size_t)(9 + i) * N + k] = post[(size_t)(9 + o_) * N + k];
