@@ -96,9 +96,11 @@ typedef enum {
 
 /* Parameters of one instance, lattice units.  Validity (LBE_EINVAL
  * otherwise): nx >= 1, ny >= 2, rho > 0, rho2 >= 0, cv > 0, eta1,
- * eta2 > 0, lam1, lam2 >= 0, eps > 0, tau_g > 1/2, mobility >= 0,
- * eta_n > 0, and 0 < omega < 2 for every relaxation rate at c = 0 and
- * c = 1.  Layout change from ABI version 1: rho2 appended. */
+ * eta2 > 0, lam1, lam2 >= 0 (> 0 with interp = 1), eps > 0,
+ * tau_g > 1/2, mobility >= 0, eta_n > 0, interp and wall_mid 0 or 1,
+ * -1 <= cos_wet <= 1, and 0 < omega < 2 for every relaxation rate at
+ * c = 0 and c = 1.  Layout change from ABI version 1: rho2, interp,
+ * wall_mid and cos_wet appended. */
 typedef struct {
   int32_t nx, ny;       /* cells; periodic in x, walls in y           */
   int32_t storage;      /* lbe_storage; must be equal for all instances */
@@ -122,6 +124,18 @@ typedef struct {
                            grad(rho c_s^2) in the thermal force of Eq. aEq4;
                            it needs FP64 storage (LBE_EINVAL otherwise) and
                            is not covered by lbe_adjoint                  */
+  /* Boundary and property variants the paper leaves open (0: off; none is
+     covered by lbe_adjoint, which then returns LBE_EINVAL):              */
+  int32_t interp;       /* eta(c), lambda(c): 0 linear, 1 harmonic
+                           1/((1-c)/a + c/b)                              */
+  int32_t wall_mid;     /* 1: the anti-bounce-back of hbar on a diagonal
+                           link takes the wall temperature where the link
+                           crosses the wall, (T_w(x) + T_w(x -+ 1))/2     */
+  double cos_wet;       /* cos of the contact angle of phase 1 at both
+                           walls (0: neutral, mirror ghost rows of c).  The
+                           ghost rows of c gain the flux (sqrt(2 beta)/eps)
+                           cos(theta) c (1 - c) of a cubic wall energy
+                           (Young's law)                                  */
 } lbe_params;
 
 /* Initial and boundary data of one instance (host pointers, copied). */

@@ -46,6 +46,7 @@ struct lbe_handle {
   InstDev* d_inst = nullptr;     // [n] for the step kernel
   InstDev* d_finst = nullptr;    // [n] for the field kernel (shape 0, tile_begin 0)
   bool vrho = false;             // varying density (rho2 != rho; FP64 storage)
+  bool variants = false;         // some instance uses interp / wall_mid / cos_wet
   InstDev* d_pinst = nullptr;    // [n] shape-0 work list of the pcorr pass (vrho)
   int64_t p_tiles = 0;           // its tiles
   int p_grid = 0;                // its CTAs
@@ -193,6 +194,11 @@ lbe_status check_params(const lbe_params& p, int index) {
   for (double v : vals)
     if (!std::isfinite(v)) return bad("non-finite parameter");
   if (!(p.rho2 >= 0) || !std::isfinite(p.rho2)) return bad("rho2 must be >= 0 (0: rho2 = rho)");
+  if (p.interp != 0 && p.interp != 1) return bad("interp must be 0 (linear) or 1 (harmonic)");
+  if (p.interp == 1 && !(p.lam1 > 0 && p.lam2 > 0))
+    return bad("the harmonic law (interp = 1) needs lam1, lam2 > 0");
+  if (p.wall_mid != 0 && p.wall_mid != 1) return bad("wall_mid must be 0 or 1");
+  if (!(p.cos_wet >= -1.0 && p.cos_wet <= 1.0)) return bad("cos_wet must be in [-1, 1]");
   if (varying_rho(p) && p.storage != LBE_F64)
     return bad("a density ratio (rho2 != rho) needs FP64 storage");
   return LBE_OK;
@@ -242,6 +248,15 @@ void fill_desc(lbe_handle* h, int j, InstDev& D) {
   P.ax = p.ax;
   P.ay = p.ay;
   P.drho = varying_rho(p) ? p.rho2 - p.rho : 0.0;
+  P.harm = p.interp == 1 ? 1.0 : 0.0;
+  P.eta2 = p.eta2;
+  P.lam2 = p.lam2;
+  P.ie1 = 1.0 / p.eta1;
+  P.ie2 = 1.0 / p.eta2;
+  P.il1 = p.lam1 > 0 ? 1.0 / p.lam1 : 0.0;
+  P.il2 = p.lam2 > 0 ? 1.0 / p.lam2 : 0.0;
+  P.wmid = p.wall_mid == 1 ? 1.0 : 0.0;
+  P.kw = p.cos_wet * std::sqrt(2.0 * p.beta) / p.eps;
   D.pcorr = H.pcorr;
   P.eta_n2 = p.eta_n * p.eta_n;
   // hbar reference: linear profile between the mean wall temperatures
@@ -422,7 +437,7 @@ cudaError_t launch_one_step(lbe_handle* h, int parity) {
       h->poll_lim = STASH_POLLS;
     }
     cudaError_t e = launch_stash(h->storage, h->d_inst, h->n, h->total_tiles, h->seg, parity,
-                                 h->grid, h->d_err, pl, wh, h->d_seed, h->stream);
+                                 h->grid, h->d_err, pl, wh, h->d_seed, h->variants, h->stream);
     // the stash kernel leaves the periodic ghost columns to ghost_kernel,
     // which also advances the step counter
     if (e == cudaSuccess)
@@ -623,6 +638,7 @@ lbe_status create(int32_t n, const lbe_params* params, const lbe_init_fields* in
                         h->stream));
     CUB(cudaMemcpyAsync(H.walls + H.nx, H.Ttop.data(), sizeof(double) * H.nx,
                         cudaMemcpyHostToDevice, h->stream));
+    if (H.p.interp != 0 || H.p.wall_mid != 0 || H.p.cos_wet != 0.0) h->variants = true;
     if (varying_rho(H.p)) {
       h->vrho = true;
       CUB(cudaMalloc(&H.pcorr, sizeof(double) * (size_t)H.nx * H.ny));
@@ -744,6 +760,12 @@ lbe_status check_adjoint_handle(lbe_handle* h) {
   if (st) return st;
   if (h->n != 1) return fail(h, LBE_EINVAL, "the adjoint needs a handle of one instance (has %d)", h->n);
   if (h->vrho) return fail(h, LBE_EINVAL, "the adjoint is of the uniform-density step (rho2 = rho)");
+  {
+    const lbe_params& p = h->inst[0].p;
+    if (p.interp != 0 || p.wall_mid != 0 || p.cos_wet != 0.0)
+      return fail(h, LBE_EINVAL,
+                  "the adjoint is of the default variants (interp, wall_mid, cos_wet all 0)");
+  }
   if (h->bad) return fail(h, LBE_ESTATE, "handle is in an error state; set a state or load a checkpoint");
   return LBE_OK;
 }

@@ -18,16 +18,20 @@ bool tile_available(int storage, int tile) {
 
 cudaError_t launch_stash(int storage, const InstDev* d, int n, int64_t items, int seg, int parity,
                          int grid, int* err, int poll_lim, int withhold, const uint32_t* seed,
-                         cudaStream_t s) {
+                         bool var, cudaStream_t s) {
   switch (storage) {
     case ST_F32:
-      return launch_stash_f32(d, n, items, seg, parity, grid, err, poll_lim, withhold, seed, s);
+      return launch_stash_f32(d, n, items, seg, parity, grid, err, poll_lim, withhold, seed, var,
+                              s);
     case ST_F16DEV:
-      return launch_stash_f16(d, n, items, seg, parity, grid, err, poll_lim, withhold, seed, s);
+      return launch_stash_f16(d, n, items, seg, parity, grid, err, poll_lim, withhold, seed, var,
+                              s);
     case ST_BF16DEV:
-      return launch_stash_bf16(d, n, items, seg, parity, grid, err, poll_lim, withhold, seed, s);
+      return launch_stash_bf16(d, n, items, seg, parity, grid, err, poll_lim, withhold, seed, var,
+                              s);
     case ST_F16MIX:
-      return launch_stash_mix(d, n, items, seg, parity, grid, err, poll_lim, withhold, seed, s);
+      return launch_stash_mix(d, n, items, seg, parity, grid, err, poll_lim, withhold, seed, var,
+                              s);
   }
   return cudaErrorInvalidValue;
 }
@@ -90,10 +94,12 @@ __global__ void init_state_kernel(const InstDev* __restrict__ d, int nx, int ny,
        k += (int64_t)gridDim.x * blockDim.x) {
     const int x = (int)(k % nx), y = (int)(k / nx);
     const InstDev& I = *d;
+    // c0 with its ghost rows (the mirror, plus the wetting flux at a wetting
+    // wall)
     auto cat = [&](int xx, int yy) -> double {
       xx = (xx % nx + nx) % nx;
-      if (yy < 0) yy = -1 - yy;
-      if (yy >= ny) yy = 2 * ny - 1 - yy;
+      if (yy < 0) return wet_ghost(I.pd, c0[(int64_t)(-1 - yy) * nx + xx], -1 - yy);
+      if (yy >= ny) return wet_ghost(I.pd, c0[(int64_t)(2 * ny - 1 - yy) * nx + xx], yy - ny);
       return c0[(int64_t)yy * nx + xx];
     };
     const double v0 = c0[k];
@@ -170,7 +176,11 @@ __global__ void push_kernel(const InstDev* __restrict__ d, int nx, int ny,
           if (kk < 2) {
             v = pb;
           } else {
-            const double Tw = (yt < 0) ? I.Tbot[x] : I.Ttop[x];
+            // the inverse of the pull's anti-bounce-back of population
+            // OPP(j), whose link crosses the wall at x + xi_jx/2
+            const double* Twall = (yt < 0) ? I.Tbot : I.Ttop;
+            double Tw = Twall[x];
+            if (I.pd.wmid != 0.0 && EX(j) != 0) Tw = 0.5 * (Tw + Twall[xt]);
             v = 2.0 * WGT<double>(j) * rc * I.pd.cv * Tw - pb;
           }
         }

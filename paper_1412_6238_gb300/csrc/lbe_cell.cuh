@@ -288,8 +288,8 @@ __device__ __forceinline__ void collide(const Phys<typename S::C>& P, const type
   const C inv_rho = P.inv_rho;
   const C rcs2 = vr ? d.rho * C(1.0 / 3.0) : P.rcs2, inv_rcs2 = C(3) * inv_rho;
   // S3: properties, linear in c
-  const C eta = P.eta1 + cc * P.deta;
-  const C lam = P.lam1 + cc * P.dlam;
+  const C eta = prop_at(P, P.eta1, P.deta, P.eta2, P.ie1, P.ie2, cc);
+  const C lam = prop_at(P, P.lam1, P.dlam, P.lam2, P.il1, P.il2, cc);
   const C tau_f = dv(eta, rcs2, inv_rcs2) + C(0.5);
   const C omega_f = C(1) / tau_f;
   const C tau_h = dv(lam, vr ? (d.rho * P.cv) * C(1.0 / 3.0) : P.rcvcs2, C(3) * P.inv_rho_cv);

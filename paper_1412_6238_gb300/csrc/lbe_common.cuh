@@ -79,7 +79,35 @@ struct Phys {
   C inv_s[3];              // 16-bit codec: 1/s_k (1 for the other storages)
   C drho;                  // rho2 - rho1 (0: uniform density; FP64 storage only)
   C ax, ay;                // body acceleration (the force rho(c) a)
+  // variants (0: off): harmonic property law (with the phase-1 values and
+  // the four reciprocals), wall temperature at the link's wall crossing,
+  // wetting flux coefficient cos(theta) sqrt(2 beta) / eps
+  C harm, eta2, lam2, ie1, ie2, il1, il2;
+  C wmid;
+  C kw;
 };
+
+// eta(c) or lambda(c) between the phase values a (c = 0) and b (c = 1):
+// linear (a + c (b - a), d = b - a) or, with P.harm, harmonic
+// 1/((1 - c)/a + c/b) (ia, ib: the reciprocals, used by the FP32 forms).
+template <class C>
+__device__ __forceinline__ C prop_at(const Phys<C>& P, C a, C d, C b, C ia, C ib, C c) {
+  if (P.harm != C(0)) {
+    if constexpr (sizeof(C) == 8)
+      return C(1) / ((C(1) - c) / a + c / b);
+    else
+      return C(1) / ((C(1) - c) * ia + c * ib);
+  }
+  return a + c * d;
+}
+
+// Wetting walls: ghost row -1-j (or ny+j) of c from its mirror cell's c, the
+// mirror value plus (2j+1) times the wall flux (sqrt(2 beta)/eps) cos(theta)
+// c (1 - c) (Young's law through a cubic wall energy).
+template <class C>
+__device__ __forceinline__ C wet_ghost(const Phys<C>& P, C cm, int j) {
+  return P.kw != C(0) ? cm + C(2 * j + 1) * P.kw * cm * (C(1) - cm) : cm;
+}
 
 // The density of a cell, linear in c: rho(c) = rho1 + c (rho2 - rho1).
 template <class C>

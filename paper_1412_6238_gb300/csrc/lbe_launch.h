@@ -40,23 +40,28 @@ bool tile_available(int storage, int tile);
 constexpr int STASH_POLLS = 1 << 22;       // polls of one bounded copy wait
 constexpr int STASH_POLLS_TEST = 1 << 12;  // with the withhold test hook
 // seed: the handle's step counter (device), read for the random bits of the
-// stochastic rounding of the 16-bit forms.
+// stochastic rounding of the 16-bit forms.  var: some instance uses a
+// boundary or property variant (the kernel built with them).
 cudaError_t launch_stash(int storage, const InstDev* d, int n, int64_t items, int seg, int parity,
                          int grid, int* err, int poll_lim, int withhold, const uint32_t* seed,
-                         cudaStream_t s);
+                         bool var, cudaStream_t s);
 int stash_occupancy(int storage);
 cudaError_t launch_stash_f32(const InstDev* d, int n, int64_t items, int seg, int parity, int grid,
                              int* err, int poll_lim, int withhold,
-                             const uint32_t* seed, cudaStream_t s);
+                             const uint32_t* seed, bool var,
+                             cudaStream_t s);
 cudaError_t launch_stash_f16(const InstDev* d, int n, int64_t items, int seg, int parity, int grid,
                              int* err, int poll_lim, int withhold,
-                             const uint32_t* seed, cudaStream_t s);
+                             const uint32_t* seed, bool var,
+                             cudaStream_t s);
 cudaError_t launch_stash_bf16(const InstDev* d, int n, int64_t items, int seg, int parity,
                               int grid, int* err, int poll_lim, int withhold,
-                             const uint32_t* seed, cudaStream_t s);
+                             const uint32_t* seed, bool var,
+                             cudaStream_t s);
 cudaError_t launch_stash_mix(const InstDev* d, int n, int64_t items, int seg, int parity,
                              int grid, int* err, int poll_lim, int withhold,
-                             const uint32_t* seed, cudaStream_t s);
+                             const uint32_t* seed, bool var,
+                             cudaStream_t s);
 int stash_occupancy_f32();
 int stash_occupancy_f16();
 int stash_occupancy_bf16();

@@ -214,6 +214,18 @@ __device__ __forceinline__ float stash_val(const char* slot, int k, int i, int c
 // source rows' T_r, without the offsets +-w_i dh to this row's T_r: they
 // cancel exactly in the moment, and collide() applies them through its
 // source term.
+// The wall temperature of the anti-bounce-back link of population i at
+// column xw (Tw: the wall temperature at xw): with P.wmid, where the link
+// crosses the wall, x - xi_ix/2, between the two columns.
+template <class S>
+__device__ __forceinline__ float link_T(const InstDev& I, const Phys<float>& P, int xw, int i,
+                                        int which, float Tw) {
+  if (P.wmid == 0.f || EX(i) == 0) return Tw;
+  int xs = xw - EX(i);
+  xs = xs < 0 ? xs + I.nx : (xs >= I.nx ? xs - I.nx : xs);
+  return 0.5f * (Tw + wall_T<S>(I, xs, which));
+}
+
 template <class S, int K, bool RAW = false>
 __device__ __forceinline__ void wstash_pull(const InstDev& I, const Phys<float>& P,
                                             const char* slot, int c0, int c0g, int y, int xw,
@@ -245,7 +257,7 @@ __device__ __forceinline__ void wstash_pull(const InstDev& I, const Phys<float>&
                    : stash_val<S>(slot, K, i, col(i, true), P);
     if (K == 2) {
       if (wall) {
-        v = -v + 2.f * WGT<float>(i) * P.rho * P.cv * Tw;
+        v = -v + 2.f * WGT<float>(i) * P.rho * P.cv * link_T<S>(I, P, xw, i, wb ? 0 : 1, Tw);
       } else if (DEV && EY(i) == 1) {
         v -= WGT<float>(i) * dh;
       } else if (DEV && EY(i) == -1) {
@@ -355,7 +367,7 @@ __device__ __forceinline__ void wstash_pull_mix(const InstDev& I, const Phys<flo
     g[i] = q.x * sg;
     float hv = q.y * sh;
     if (wall) {
-      hv = -hv + 2.f * WGT<float>(i) * P.rho * P.cv * Tw;
+      hv = -hv + 2.f * WGT<float>(i) * P.rho * P.cv * link_T<StMix>(I, P, xw, i, wb ? 0 : 1, Tw);
     } else if (EY(i) == 1) {
       hv -= WGT<float>(i) * P.dh;
     } else if (EY(i) == -1) {
@@ -467,7 +479,10 @@ __device__ __forceinline__ void issue_row(const CopyPlan& c, uint32_t dst, uint3
   });
 }
 
-template <class S, int NC>
+// VAR: the boundary and property variants (harmonic law, wall temperature
+// at the link's wall crossing, wetting walls) compiled in; without them the
+// kernel carries none of their registers.
+template <class S, int NC, bool VAR>
 __global__ void __launch_bounds__(NC, (StashCfg<S, NC>::MINB))
 stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items, int seg_rows,
              int parity, int* __restrict__ err, int poll_lim, int withhold,
@@ -573,7 +588,12 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
     ya = __shfl_sync(0xffffffffu, ya, 0);
     yb = __shfl_sync(0xffffffffu, yb, 0);
     char* __restrict__ dst = I.buf[parity ^ 1];
-    const Phys<C> P = phys<C>(I);
+    Phys<C> P = phys<C>(I);
+    if constexpr (!VAR) {  // the variants are off: known to the compiler
+      P.harm = C(0);
+      P.wmid = C(0);
+      P.kw = C(0);
+    }
     const C en2 = P.eta_n2;
     const uint32_t skey = S::SR ? sr_step_key(step, I.salt) : 0u;
     const size_t pitch = (size_t)I.pitch;
@@ -780,6 +800,7 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
               C vh[9], g0lo, clo;
               wstash_pull_mix<true>(I, P, s, c0 + dj, mr, cxw, vf, v, vh, g0lo);
               cring[ci] = moment_c(v, g0lo, clo);
+              if (m < 0) cring[ci] = wet_ghost(P, cring[ci], -1 - m);
               clr[ci] = __float2half_rn(clo * G0LO_SCALE);
               if (pt) {
                 pring[pi] = sum9(vf);
@@ -798,6 +819,7 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
                   G0LO_INV;
               C clo;
               cring[ci] = moment_c(v, g0lo, clo);
+              if (m < 0) cring[ci] = wet_ghost(P, cring[ci], -1 - m);
               clr[ci] = __float2half_rn(clo * G0LO_SCALE);
               if (pt) {
                 pring[pi] = sum9(vf);
@@ -811,7 +833,7 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
             // above the top wall: the mirror row's moments
             const int mm = rrow(2 * ny - 1 - m);
             const int cm = ci - rm * CW + mm * CW, pm = pi - rm * QW + mm * QW;
-            cring[ci] = cring[cm];
+            cring[ci] = wet_ghost(P, cring[cm], m - ny);
             clr[ci] = clr[cm];
             if (pt) {
               pring[pi] = pring[pm];

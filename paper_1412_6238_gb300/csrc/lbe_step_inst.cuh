@@ -81,36 +81,37 @@ cudaError_t LBE_CAT(fields_, LBE_SUFFIX)(const InstDev* d, int64_t tiles, int pa
 
 #if LBE_STASH
 namespace {
-template <int NC>
+template <int NC, bool VAR>
 bool stash_attr() {
   static bool done[64] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
   if (!done[dev]) {
-    if (cudaFuncSetAttribute(stash_kernel<LBE_ST, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(stash_kernel<LBE_ST, NC, VAR>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
                              StashCfg<LBE_ST, NC>::SMEM) != cudaSuccess)
       return false;
     done[dev] = true;
   }
   return true;
 }
-template <int NC>
+template <int NC, bool VAR>
 cudaError_t stash_one(const InstDev* d, int n, int64_t items, int seg, int parity, int grid,
                       int* err, int poll_lim, int withhold, const uint32_t* seed,
                       cudaStream_t s) {
-  if (!stash_attr<NC>()) return cudaErrorInvalidValue;
+  if (!stash_attr<NC, VAR>()) return cudaErrorInvalidValue;
   if (grid <= 0) grid = 1;
   if ((int64_t)grid > items) grid = (int)items;
-  stash_kernel<LBE_ST, NC>
+  stash_kernel<LBE_ST, NC, VAR>
       <<<grid, NC, StashCfg<LBE_ST, NC>::SMEM, s>>>(d, n, items, seg, parity, err, poll_lim,
                                                     withhold, seed);
   return cudaGetLastError();
 }
-template <int NC>
+template <int NC, bool VAR>
 int stash_occ() {
-  if (!stash_attr<NC>()) return 0;
+  if (!stash_attr<NC, VAR>()) return 0;
   int b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, stash_kernel<LBE_ST, NC>, NC,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, stash_kernel<LBE_ST, NC, VAR>, NC,
                                                     StashCfg<LBE_ST, NC>::SMEM) != cudaSuccess)
     return 0;
   return b;
@@ -119,11 +120,18 @@ int stash_occ() {
 
 cudaError_t LBE_CAT(launch_stash_, LBE_SUFFIX)(const InstDev* d, int n, int64_t items, int seg,
                                                 int parity, int grid, int* err, int poll_lim,
-                                                int withhold, const uint32_t* seed,
+                                                int withhold, const uint32_t* seed, bool var,
                                                 cudaStream_t s) {
-  return stash_one<128>(d, n, items, seg, parity, grid, err, poll_lim, withhold, seed, s);
+  return var ? stash_one<128, true>(d, n, items, seg, parity, grid, err, poll_lim, withhold,
+                                    seed, s)
+             : stash_one<128, false>(d, n, items, seg, parity, grid, err, poll_lim, withhold,
+                                     seed, s);
 }
-int LBE_CAT(stash_occupancy_, LBE_SUFFIX)() { return stash_occ<128>(); }
+// resident CTAs per SM (the smaller of the two builds)
+int LBE_CAT(stash_occupancy_, LBE_SUFFIX)() {
+  const int a = stash_occ<128, false>(), b = stash_occ<128, true>();
+  return a < b ? a : b;
+}
 #endif
 
 }  // namespace lbe

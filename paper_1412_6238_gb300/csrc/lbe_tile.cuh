@@ -67,8 +67,17 @@ __device__ __forceinline__ void pull9(const InstDev& I, const Phys<typename S::C
   const C dh = DEV ? P.dh : C(0);  // rho c_v (T_r(y) - T_r(y-1))
   auto bb = [&](int i) -> C {
     C v = S::ld(I, P, src, K, OPP(i), r0 + q.x);
-    if (K == 2)
-      return -v + C(2) * WGT<C>(i) * (P.drho != C(0) ? rho_cell : P.rho) * P.cv * Tw;
+    if (K == 2) {
+      // the wall temperature where the link crosses the wall (x - xi_x/2,
+      // between the columns) when P.wmid, else at the cell's column
+      C Twi = Tw;
+      if (P.wmid != C(0) && EX(i) != 0) {
+        int xs = q.x - EX(i);
+        xs = xs < 0 ? xs + I.nx : (xs >= I.nx ? xs - I.nx : xs);
+        Twi = C(0.5) * (Tw + wall_T<S>(I, xs, wb ? 0 : 1));
+      }
+      return -v + C(2) * WGT<C>(i) * (P.drho != C(0) ? rho_cell : P.rho) * P.cv * Twi;
+    }
     return v;
   };
   out[0] = S::ld(I, P, src, K, 0, r0 + q.x);
@@ -152,9 +161,11 @@ __device__ __forceinline__ void region_values(const InstDev& I, const Phys<typen
   const Cell<S> q = make_cell<S>(wrapx(gx, nx), y, nx);
   C v[9];
   pull9<S, 1>(I, P, src, q, v);
-  c = sum9(v);
+  const C cm = sum9(v);  // c of the cell (of the mirror cell for a ghost row)
+  // ghost rows of c: the mirror, plus the wetting flux at a wetting wall
+  c = ghost != 0 ? wet_ghost(P, cm, ghost < 0 ? y : ny - 1 - y) : cm;
   if (need_pT) {
-    const C rc = rho_at(P, c);
+    const C rc = rho_at(P, cm);
     pull9<S, 0>(I, P, src, q, v);
     // p of Eq. 13: with a varying density, the corrected p of pcorr
     p = (use_pcorr && P.drho != C(0)) ? (C)I.pcorr[(size_t)y * nx + q.x] : sum9(v);

@@ -39,7 +39,8 @@ class LBEError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("storage", ctypes.c_int32),
                 ("check_every", ctypes.c_int32)] + [(k, ctypes.c_double) for k in PARAM_KEYS] + \
-               [("rho2", ctypes.c_double)]
+               [("rho2", ctypes.c_double), ("interp", ctypes.c_int32),
+                ("wall_mid", ctypes.c_int32), ("cos_wet", ctypes.c_double)]
 
 
 class InitFields(ctypes.Structure):
@@ -133,6 +134,11 @@ def make_params(params: dict, storage: str | int, check_every: int = 0) -> Param
     for k in PARAM_KEYS:
         setattr(p, k, float(params[k]))
     p.rho2 = float(params.get("rho2", 0.0))  # 0: uniform density
+    # variants (0: off): harmonic property law, wall temperature at the
+    # link's wall crossing, contact angle of phase 1 (cos)
+    p.interp = int(params.get("interp", 0))
+    p.wall_mid = int(params.get("wall_mid", 0))
+    p.cos_wet = float(params.get("cos_wet", 0.0))
     return p
 
 

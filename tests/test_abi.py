@@ -63,6 +63,9 @@ def _init(params, storage="f32"):
     (dict(nx=65536, ny=65537), "2^31"),
     (dict(rho2=-1.0), "rho2"), (dict(rho2=float("inf")), "rho2"),
     (dict(rho2=3.0), "FP64"),  # a density ratio with FP32 storage
+    (dict(interp=2), "interp"), (dict(interp=1, lam1=0.0), "harmonic"),
+    (dict(wall_mid=3), "wall_mid"), (dict(cos_wet=1.5), "cos_wet"),
+    (dict(cos_wet=float("nan")), "cos_wet"),
 ])
 def test_invalid_parameters_rejected(bad, msg):
     st, err, h = _init(bad)
