@@ -35,7 +35,8 @@ class _Params(ctypes.Structure):
                 ("periodic_y", ctypes.c_int32), ("ablate", ctypes.c_int32)] + \
                [(k, ctypes.c_double) for k in PARAM_KEYS] + [("rho2", ctypes.c_double)] + \
                [("interp", ctypes.c_int32), ("wall_mid", ctypes.c_int32),
-                ("cos_wet", ctypes.c_double)]
+                ("cos_wet", ctypes.c_double), ("dissip", ctypes.c_int32),
+                ("pad_", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -97,6 +98,8 @@ def _p(params: dict, nx: int, ny: int) -> _Params:
     s.interp = int(params.get("interp", 0))
     s.wall_mid = int(params.get("wall_mid", 0))
     s.cos_wet = float(params.get("cos_wet", 0.0))
+    # the pressure-work / viscous-dissipation term of Eq. aEq7 (0: dropped)
+    s.dissip = int(params.get("dissip", 0))
     return s
 
 

@@ -37,7 +37,8 @@
  * density varying with c (the grad(rho c_s^2) terms of Eq. 12, Eq. 13 and
  * Fbar); the harmonic property law; the anti-bounce-back's wall temperature
  * taken where the link crosses the wall; wetting walls with a contact angle
- * (Young's law through a cubic wall energy).
+ * (Young's law through a cubic wall energy); the pressure-work and
+ * viscous-dissipation term of Eq. aEq7 that Eq. aEq8 drops.
  *
  * Population storage: one array of 27 planes [k*9+i][y][x], k = 0 (f), 1 (g),
  * 2 (hbar), x fastest.  Velocity order i: 0 (0,0), 1 (1,0), 2 (0,1), 3 (-1,0),
@@ -74,6 +75,9 @@ typedef struct {
                        link crosses the wall (x - xi_x/2, interpolated) */
   double cos_wet;   /* cos of the contact angle of phase 1 at both walls
                        (0: neutral wetting, the mirror ghost rows) */
+  int32_t dissip;   /* 1: keep the -fbar_i q_i term of Eq. aEq7 (pressure
+                       work and viscous dissipation) that Eq. aEq8 drops */
+  int32_t pad_;
 } orc_params;
 
 /* Density of a cell, linear in c like eta and lambda (the paper states no
@@ -197,6 +201,36 @@ static double h_source(int i, double rho, double cv, double T, double Fx,
          h_equilibrium(i, rho, cv, T, ux, uy);
 }
 
+/* The pressure-work / viscous-dissipation term of Eq. aEq7 (kept when the
+ * variant `dissip` is on; Eq. aEq8 drops it), per direction:
+ *   S_i = -fbar_i q_i,  q_i = (xi_i - u).(d_t u + (xi_i.grad) u).
+ * - Sign: h = |xi - u|^2/2 fbar (Eq. aEq6) gives -fbar q on differentiating
+ *   (the printed + would make viscous dissipation cool the fluid).
+ * - fbar_i, the density distribution, from the f lattice by the change of
+ *   variables behind Eq. 5, f_i = c_s^2 fbar_i + w_i (p - rho c_s^2), its
+ *   non-equilibrium part scaled by (1 - omega_f/2) to the physical
+ *   distribution of the trapezoidal scheme (whose stress is the viscous
+ *   stress of eta = rho c_s^2 (tau_f - 1/2)).
+ * - The d_t u part is left out: its zeroth moment, (sum_i fbar_i (xi_i - u)).
+ *   d_t u, vanishes (sum fbar xi = rho u), so the energy equation does not
+ *   see it.
+ * Then sum_i S_i = -p_th div u + the viscous dissipation (eta/2)|grad u +
+ * grad u^T|^2 with p_th = rho c_s^2.  In the collision the isotropic part
+ * w_i sum_j S_j enters whole and the rest with the trapezoidal factor
+ * (1 - omega_T/2) of Eq. aEq12: T = sum hbar / (rho c_v) has no half-step
+ * correction for a source with a zeroth moment, and through (1 - omega_T/2)
+ * alone the fluid would gain only that fraction of the heat.  du =
+ * {d_x u_x, d_y u_x, d_x u_y, d_y u_y}. */
+static double work_source(int i, double rho, double p, double f, double omega_f, double ux,
+                          double uy, const double du[4]) {
+  const double fbe = rho * gamma_i(i, ux, uy);
+  const double fb = (f - W[i] * (p - rho * CS2)) / CS2;
+  const double fph = fbe + (1.0 - 0.5 * omega_f) * (fb - fbe);
+  const double dx = EX[i] - ux, dy = EY[i] - uy;
+  const double q = dx * (EX[i] * du[0] + EY[i] * du[1]) + dy * (EX[i] * du[2] + EY[i] * du[3]);
+  return -fph * q;
+}
+
 /* Per-cell terms for the moment pins in the tests: equilibria and sources. */
 void orc_cell_terms(const orc_params* P, double c, double p, double T,
                     double mu, double ux, double uy, double Fx, double Fy,
@@ -273,6 +307,9 @@ static void fill_ghosts(const orc_params* P, ext_field* e, int is_T,
       } else if (is_T == 1) {
         *ext_at(e, x, -1 - j) = 2.0 * Tbot[x] - ext_get(e, x, j);
         *ext_at(e, x, ny + j) = 2.0 * Ttop[x] - ext_get(e, x, ny - 1 - j);
+      } else if (is_T == 3) { /* velocity: zero at the wall (no slip) */
+        *ext_at(e, x, -1 - j) = -ext_get(e, x, j);
+        *ext_at(e, x, ny + j) = -ext_get(e, x, ny - 1 - j);
       } else if (is_T == 2 && P->cos_wet != 0.0) {
         *ext_at(e, x, -1 - j) = wet_ghost(P, ext_get(e, x, j), j);
         *ext_at(e, x, ny + j) = wet_ghost(P, ext_get(e, x, ny - 1 - j), j);
@@ -506,6 +543,31 @@ static void step_once(const orc_params* P, const double* Tbot,
     free(uy);
   }
 
+  /* velocity gradients of every cell for the dissipation term (the same u
+     as the collision's; ghost rows antisymmetric: no slip at the walls) */
+  double* du = NULL;
+  if (P->dissip) {
+    du = malloc(4 * N * sizeof(double));
+    ext_field uxE = ext_new(nx, ny, 1), uyE = ext_new(nx, ny, 1);
+    for (int y = 0; y < ny; y++)
+      for (int x = 0; x < nx; x++) {
+        const size_t k = (size_t)y * nx + x;
+        const double rho = rho_of(P, c[k]);
+        *ext_at(&uxE, x, y) = jx[k] / (rho * CS2) + 0.5 * o->Fx[k] / rho;
+        *ext_at(&uyE, x, y) = jy[k] / (rho * CS2) + 0.5 * o->Fy[k] / rho;
+      }
+    fill_ghosts(P, &uxE, 3, Tbot, Ttop);
+    fill_ghosts(P, &uyE, 3, Tbot, Ttop);
+    for (int y = 0; y < ny; y++)
+      for (int x = 0; x < nx; x++) {
+        const size_t k = (size_t)y * nx + x;
+        grad_iso(&uxE, x, y, &du[k], &du[N + k]);
+        grad_iso(&uyE, x, y, &du[2 * N + k], &du[3 * N + k]);
+      }
+    free(uxE.v);
+    free(uyE.v);
+  }
+
   const double omega_g = 1.0 / P->tau_g;             /* Eq. 27 */
   const double Gm = P->mobility / (P->tau_g - 0.5);  /* M = Gamma (tau_g - 1/2), Eq. 16 */
 
@@ -526,6 +588,15 @@ static void step_once(const orc_params* P, const double* Tbot,
     double ux = jx[k] / (rho * CS2) + 0.5 * Fx / rho;
     double uy = jy[k] / (rho * CS2) + 0.5 * Fy / rho;
     const double dRx = dr * o->gcx[k], dRy = dr * o->gcy[k];
+    /* the work / dissipation term of Eq. aEq7 per direction, and its sum */
+    double ws[9], ws0 = 0.0;
+    if (du) {
+      const double dk[4] = {du[k], du[N + k], du[2 * N + k], du[3 * N + k]};
+      for (int i = 0; i < 9; i++) {
+        ws[i] = work_source(i, rho, p[k], in[(size_t)i * N + k], omega_f, ux, uy, dk);
+        ws0 += ws[i];
+      }
+    }
     for (int i = 0; i < 9; i++) {
       double f = in[(size_t)i * N + k];
       double feq = f_equilibrium(i, p[k], rho, ux, uy);
@@ -543,13 +614,19 @@ static void step_once(const orc_params* P, const double* Tbot,
 
       double h = in[(size_t)(18 + i) * N + k];
       double heq = h_equilibrium(i, rho, cv, TT, ux, uy);
-      post[(size_t)(18 + i) * N + k] =
-          h - omega_T * (h - heq) +
-          (1.0 - 0.5 * omega_T) *
-              h_source(i, rho, cv, TT, Fx, Fy, o->gpx[k], o->gpy[k], ux, uy, dRx, dRy,
-                       vrho && !(P->ablate & 4));
+      double hs = h_source(i, rho, cv, TT, Fx, Fy, o->gpx[k], o->gpy[k], ux, uy, dRx, dRy,
+                           vrho && !(P->ablate & 4));
+      if (du) {
+        post[(size_t)(18 + i) * N + k] = h - omega_T * (h - heq) +
+                                         (1.0 - 0.5 * omega_T) * (hs + (ws[i] - W[i] * ws0)) +
+                                         W[i] * ws0;
+      } else {
+        post[(size_t)(18 + i) * N + k] = h - omega_T * (h - heq) + (1.0 - 0.5 * omega_T) * hs;
+      }
     }
   }
+
+  free(du);
 
   /* streaming, pull form: P_i(x, t+1) = P*_i(x - xi_i, t); f and g first,
      then hbar, whose anti-bounce-back at a wall takes rho of the cell's new
