@@ -98,9 +98,10 @@ typedef enum {
  * otherwise): nx >= 1, ny >= 2, rho > 0, rho2 >= 0, cv > 0, eta1,
  * eta2 > 0, lam1, lam2 >= 0 (> 0 with interp = 1), eps > 0,
  * tau_g > 1/2, mobility >= 0, eta_n > 0, interp and wall_mid 0 or 1,
- * -1 <= cos_wet <= 1, and 0 < omega < 2 for every relaxation rate at
- * c = 0 and c = 1.  Layout change from ABI version 1: rho2, interp,
- * wall_mid and cos_wet appended. */
+ * -1 <= cos_wet <= 1, dissip 0 or 1 (1 with FP64 storage), reserved 0,
+ * and 0 < omega < 2 for every relaxation rate at c = 0 and c = 1.  Layout
+ * change from ABI version 1: rho2, interp, wall_mid, cos_wet, dissip and
+ * reserved appended. */
 typedef struct {
   int32_t nx, ny;       /* cells; periodic in x, walls in y           */
   int32_t storage;      /* lbe_storage; must be equal for all instances */
@@ -136,6 +137,13 @@ typedef struct {
                            ghost rows of c gain the flux (sqrt(2 beta)/eps)
                            cos(theta) c (1 - c) of a cubic wall energy
                            (Young's law)                                  */
+  int32_t dissip;       /* 1: keep the pressure-work / viscous-dissipation
+                           term -fbar_i q_i of Eq. aEq7 that Eq. aEq8 drops
+                           (fbar from the f lattice, q_i = (xi_i - u).
+                           (xi_i.grad) u; the velocity gradients from a
+                           pass of their own before each step); needs FP64
+                           storage                                        */
+  int32_t reserved;     /* 0 */
 } lbe_params;
 
 /* Initial and boundary data of one instance (host pointers, copied). */

@@ -28,6 +28,7 @@ struct InstHost {
   char* arena = nullptr;  // two buffers of buf_bytes
   double* walls = nullptr;  // device: Tbot[nx], Ttop[nx], then 4 float tables
   double* pcorr = nullptr;  // device [ny][nx]: corrected p (varying density only)
+  double* uvel = nullptr;   // device [2][ny][nx]: u of every cell (dissipation term only)
   std::vector<double> Tbot, Ttop;
   std::vector<float> wdev;  // host copy of the T_w - T_r tables
 };
@@ -47,6 +48,7 @@ struct lbe_handle {
   InstDev* d_finst = nullptr;    // [n] for the field kernel (shape 0, tile_begin 0)
   bool vrho = false;             // varying density (rho2 != rho; FP64 storage)
   bool variants = false;         // some instance uses interp / wall_mid / cos_wet
+  bool dissip = false;           // some instance keeps the dissipation term (FP64)
   InstDev* d_pinst = nullptr;    // [n] shape-0 work list of the pcorr pass (vrho)
   int64_t p_tiles = 0;           // its tiles
   int p_grid = 0;                // its CTAs
@@ -199,6 +201,10 @@ lbe_status check_params(const lbe_params& p, int index) {
     return bad("the harmonic law (interp = 1) needs lam1, lam2 > 0");
   if (p.wall_mid != 0 && p.wall_mid != 1) return bad("wall_mid must be 0 or 1");
   if (!(p.cos_wet >= -1.0 && p.cos_wet <= 1.0)) return bad("cos_wet must be in [-1, 1]");
+  if (p.dissip != 0 && p.dissip != 1) return bad("dissip must be 0 or 1");
+  if (p.dissip == 1 && p.storage != LBE_F64)
+    return bad("the dissipation term (dissip = 1) needs FP64 storage");
+  if (p.reserved != 0) return bad("reserved must be 0");
   if (varying_rho(p) && p.storage != LBE_F64)
     return bad("a density ratio (rho2 != rho) needs FP64 storage");
   return LBE_OK;
@@ -258,6 +264,7 @@ void fill_desc(lbe_handle* h, int j, InstDev& D) {
   P.wmid = p.wall_mid == 1 ? 1.0 : 0.0;
   P.kw = p.cos_wet * std::sqrt(2.0 * p.beta) / p.eps;
   D.pcorr = H.pcorr;
+  D.uvel = H.uvel;
   P.eta_n2 = p.eta_n * p.eta_n;
   // hbar reference: linear profile between the mean wall temperatures
   double tb = 0, tt = 0;
@@ -311,6 +318,7 @@ void free_handle(lbe_handle* h) {
     if (H.arena) cudaFree(H.arena);
     if (H.walls) cudaFree(H.walls);
     if (H.pcorr) cudaFree(H.pcorr);
+    if (H.uvel) cudaFree(H.uvel);
   }
   if (h->d_inst) cudaFree(h->d_inst);
   if (h->d_pinst) cudaFree(h->d_pinst);
@@ -446,8 +454,10 @@ cudaError_t launch_one_step(lbe_handle* h, int parity) {
   }
   cudaError_t e = cudaSuccess;
   // varying density: the corrected p of Eq. 13 (and so its gradient) needs
-  // u of every cell first, a pass of its own
-  if (h->vrho) e = pcorr_f64(h->d_pinst, h->n, h->p_tiles, parity, h->p_grid, h->stream);
+  // u of every cell first, and the dissipation term the gradients of u: a
+  // pass of its own
+  if (h->vrho || h->dissip)
+    e = pcorr_f64(h->d_pinst, h->n, h->p_tiles, parity, h->p_grid, h->stream);
   if (e == cudaSuccess)
     e = launch_step(h->storage, h->tile, h->d_inst, h->n, h->total_tiles, parity, h->grid,
                     h->d_seed, h->stream);
@@ -643,6 +653,10 @@ lbe_status create(int32_t n, const lbe_params* params, const lbe_init_fields* in
       h->vrho = true;
       CUB(cudaMalloc(&H.pcorr, sizeof(double) * (size_t)H.nx * H.ny));
     }
+    if (H.p.dissip == 1) {
+      h->dissip = true;
+      CUB(cudaMalloc(&H.uvel, sizeof(double) * 2 * (size_t)H.nx * H.ny));
+    }
     fill_desc(h, j, h->idev[j]);
     {
       const InstDev& D = h->idev[j];
@@ -670,8 +684,9 @@ lbe_status create(int32_t n, const lbe_params* params, const lbe_init_fields* in
     }
     CUB(cudaMemcpyAsync(h->d_finst, f.data(), sizeof(InstDev) * n, cudaMemcpyHostToDevice,
                         h->stream));
-    if (h->vrho) {
-      // the pcorr pass: shape-0 tiles of all instances in one work list
+    if (h->vrho || h->dissip) {
+      // the pre-pass (corrected p, u): shape-0 tiles of all instances in
+      // one work list
       int64_t begin = 0;
       for (auto& D : f) {
         D.tile_begin = begin;
@@ -762,9 +777,10 @@ lbe_status check_adjoint_handle(lbe_handle* h) {
   if (h->vrho) return fail(h, LBE_EINVAL, "the adjoint is of the uniform-density step (rho2 = rho)");
   {
     const lbe_params& p = h->inst[0].p;
-    if (p.interp != 0 || p.wall_mid != 0 || p.cos_wet != 0.0)
+    if (p.interp != 0 || p.wall_mid != 0 || p.cos_wet != 0.0 || p.dissip != 0)
       return fail(h, LBE_EINVAL,
-                  "the adjoint is of the default variants (interp, wall_mid, cos_wet all 0)");
+                  "the adjoint is of the default variants (interp, wall_mid, cos_wet, dissip "
+                  "all 0)");
   }
   if (h->bad) return fail(h, LBE_ESTATE, "handle is in an error state; set a state or load a checkpoint");
   return LBE_OK;

@@ -282,7 +282,8 @@ __device__ __forceinline__ void collide(const Phys<typename S::C>& P, const type
                                         typename S::C gpx, typename S::C gpy, const Drive<S>& d,
                                         Out&& out, typename S::C g0lo = 0, typename S::C clo = 0,
                                         typename S::C* g0lo_out = nullptr,
-                                        typename S::C dhc = 0) {
+                                        typename S::C dhc = 0,
+                                        const typename S::C* wdu = nullptr) {
   using C = typename S::C;
   const bool vr = sizeof(C) == 8 && P.drho != C(0);  // varying density (FP64)
   const C inv_rho = P.inv_rho;
@@ -453,6 +454,30 @@ __device__ __forceinline__ void collide(const Phys<typename S::C>& P, const type
   } else {
     const C H0 = dv(cc - dv((C(1) - WGT<C>(0)) * Gm * d.mu, cs2<C>(), C(3)), WGT<C>(0),
                     C(9) / C(4));
+    // the pressure-work / viscous-dissipation term of Eq. aEq7 (wdu: the
+    // cell's velocity gradients d_x u_x, d_y u_x, d_x u_y, d_y u_y), per
+    // direction -fbar_i (xi_i - u).(xi_i.grad) u with fbar_i the density
+    // distribution of the f lattice (f_i = c_s^2 fbar_i + w_i (p - rho
+    // c_s^2)), its non-equilibrium part scaled by (1 - omega_f/2); its
+    // isotropic part w_i sum_j enters whole (T = sum hbar/(rho c_v) carries
+    // no half-step correction), the rest with (1 - omega_T/2)
+    C ws[9], ws0 = C(0);
+    if (wdu) {
+#pragma unroll
+      for (int i = 0; i < 9; i++) {
+        const C W = WGT<C>(i);
+        const C xu = dv(C(EX(i)) * ux + C(EY(i)) * uy, cs2<C>(), C(3));
+        const C G = W * (C(1) + xu + C(0.5) * (xu * xu - uu));
+        const C fbe = d.rho * G;
+        const C fb = (f[i] - W * (pp - rcs2)) / cs2<C>();
+        const C fph = fbe + (C(1) - C(0.5) * omega_f) * (fb - fbe);
+        const C dx = C(EX(i)) - ux, dy = C(EY(i)) - uy;
+        const C q = dx * (C(EX(i)) * wdu[0] + C(EY(i)) * wdu[1]) +
+                    dy * (C(EX(i)) * wdu[2] + C(EY(i)) * wdu[3]);
+        ws[i] = -fph * q;
+        ws0 += ws[i];
+      }
+    }
 #pragma unroll
     for (int i = 0; i < 9; i++) {
       const C W = WGT<C>(i);
@@ -478,7 +503,10 @@ __device__ __forceinline__ void collide(const Phys<typename S::C>& P, const type
       const C Hx = vr ? d.dRx + Gx : Gx, Hy = vr ? d.dRy + Gy : Gy;
       const C hs = dv(Hx * dx + Hy * dy, rcs2, inv_rcs2) * heq;
       const C heqd = dev_h<S>() ? rcvTd * G + rcvTr * (W * q) : heq;
-      out(2, i, h[i] - omega_T * (h[i] - heqd) + aT * hs);
+      if (wdu)
+        out(2, i, h[i] - omega_T * (h[i] - heqd) + aT * (hs + (ws[i] - W * ws0)) + W * ws0);
+      else
+        out(2, i, h[i] - omega_T * (h[i] - heqd) + aT * hs);
     }
     if (g0lo_out) *g0lo_out = C(0);
   }

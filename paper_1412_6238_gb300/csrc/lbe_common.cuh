@@ -138,6 +138,7 @@ struct InstDev {
   double hr0, hr1;      // T_r(y) = hr0 + hr1 y (double, for state conversion)
   uint32_t salt;        // the instance's index in its handle (random bits)
   double* pcorr;        // varying density: p of Eq. 13 with its correction, [ny][nx]
+  double* uvel;         // dissipation term: u of every cell, [2][ny][nx] (FP64)
 };
 
 template <class C>

@@ -207,9 +207,11 @@ struct Tile {
     const int y0 = (int)(tile / I.tiles_x) * TY;
     const char* __restrict__ src = I.buf[parity];
     const Phys<C> P = phys<C>(I);  // constants in registers for the whole tile
-    // the pcorr pass has nothing to do for a uniform-density instance (it
-    // holds no pcorr); the whole CTA leaves together
-    if (MODE == 2 && (P.drho == C(0) || I.pcorr == nullptr)) return;
+    // the pre-pass has nothing to do for an instance without a varying
+    // density (pcorr) or the dissipation term (uvel); the whole CTA leaves
+    // together
+    const bool wants_p = P.drho != C(0) && I.pcorr != nullptr;
+    if (MODE == 2 && !wants_p && I.uvel == nullptr) return;
 
     // ---- S1: own cell
     const int gx = x0 + tx, gy = y0 + ty;
@@ -294,8 +296,13 @@ struct Tile {
 
       // Eq. 13 with a varying density: p = sum f_i + (dt/2) u.grad(rho c_s^2)
       const C pcor = P.drho != C(0) ? pp + C(0.5) * (d.ux * d.dRx + d.uy * d.dRy) : pp;
-      if (MODE == 2) {  // the corrected p for the step that follows
-        I.pcorr[(size_t)gy * nx + gx] = (double)pcor;
+      if (MODE == 2) {  // the corrected p and u for the step that follows
+        const size_t k = (size_t)gy * nx + gx;
+        if (wants_p) I.pcorr[k] = (double)pcor;
+        if (I.uvel) {
+          I.uvel[k] = (double)d.ux;
+          I.uvel[(size_t)nx * ny + k] = (double)d.uy;
+        }
         return;
       }
       if (MODE == 1) {
@@ -316,6 +323,36 @@ struct Tile {
           S::SR ? sr_cell(sr_step_key(step, I.salt), (uint32_t)gy * (uint32_t)nx + (uint32_t)gx)
                 : 0u;
       C gs = C(0);  // 16-bit forms: the stored moving g_i
+      // the dissipation term: velocity gradients from the pre-pass's u
+      // (isotropic stencil in index order; no slip: the ghost rows hold
+      // minus the mirror cell's u)
+      C du[4] = {C(0), C(0), C(0), C(0)};
+      if (I.uvel != nullptr) {
+        const size_t N = (size_t)nx * ny;
+        C s0 = C(0), s1 = C(0), s2 = C(0), s3 = C(0);
+        for (int i = 1; i < 9; i++) {
+          int xx = gx + EX(i), yy = gy + EY(i);
+          xx = xx < 0 ? xx + nx : (xx >= nx ? xx - nx : xx);
+          C sg = C(1);
+          if (yy < 0) {
+            yy = -1 - yy;
+            sg = C(-1);
+          } else if (yy >= ny) {
+            yy = 2 * ny - 1 - yy;
+            sg = C(-1);
+          }
+          const size_t kk = (size_t)yy * nx + xx;
+          const C vx = sg * (C)I.uvel[kk], vy = sg * (C)I.uvel[N + kk];
+          s0 += WGT<C>(i) * C(EX(i)) * vx;
+          s1 += WGT<C>(i) * C(EY(i)) * vx;
+          s2 += WGT<C>(i) * C(EX(i)) * vy;
+          s3 += WGT<C>(i) * C(EY(i)) * vy;
+        }
+        du[0] = dv(s0, cs2<C>(), C(3));
+        du[1] = dv(s1, cs2<C>(), C(3));
+        du[2] = dv(s2, cs2<C>(), C(3));
+        du[3] = dv(s3, cs2<C>(), C(3));
+      }
       collide<S>(P, f, g, h, cc, pp, TT, st.gpx, st.gpy, d,
                  [&](int k, int i, C v) {
                    if constexpr (S::SR) {
@@ -324,7 +361,8 @@ struct Tile {
                    }
                    st_cell<S>(I, dst, k, i, rowbase, gx, v);
                  },
-                 g0lo, clo, &lo_out, (gy > 0 && gy < ny - 1) ? P.dh : C(0));
+                 g0lo, clo, &lo_out, (gy > 0 && gy < ny - 1) ? P.dh : C(0),
+                 I.uvel != nullptr ? du : nullptr);
       if constexpr (S::SR) {
         // g_0 as c minus the stored g_i (as the strip kernel stores it)
         float g0h, g0l;

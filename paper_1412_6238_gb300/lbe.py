@@ -40,7 +40,8 @@ class Params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("storage", ctypes.c_int32),
                 ("check_every", ctypes.c_int32)] + [(k, ctypes.c_double) for k in PARAM_KEYS] + \
                [("rho2", ctypes.c_double), ("interp", ctypes.c_int32),
-                ("wall_mid", ctypes.c_int32), ("cos_wet", ctypes.c_double)]
+                ("wall_mid", ctypes.c_int32), ("cos_wet", ctypes.c_double),
+                ("dissip", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class InitFields(ctypes.Structure):
@@ -139,6 +140,7 @@ def make_params(params: dict, storage: str | int, check_every: int = 0) -> Param
     p.interp = int(params.get("interp", 0))
     p.wall_mid = int(params.get("wall_mid", 0))
     p.cos_wet = float(params.get("cos_wet", 0.0))
+    p.dissip = int(params.get("dissip", 0))  # the dissipation term of Eq. aEq7 (FP64)
     return p
 
 

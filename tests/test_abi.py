@@ -66,6 +66,7 @@ def _init(params, storage="f32"):
     (dict(interp=2), "interp"), (dict(interp=1, lam1=0.0), "harmonic"),
     (dict(wall_mid=3), "wall_mid"), (dict(cos_wet=1.5), "cos_wet"),
     (dict(cos_wet=float("nan")), "cos_wet"),
+    (dict(dissip=2), "dissip"), (dict(dissip=1), "FP64"),  # FP32 storage
 ])
 def test_invalid_parameters_rejected(bad, msg):
     st, err, h = _init(bad)

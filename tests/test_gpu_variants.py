@@ -1,6 +1,7 @@
 """Parity of the CUDA path with the oracle for the boundary and property
 variants (harmonic property law, the anti-bounce-back wall temperature at
-the link's wall crossing, wetting walls), alone and together: FP64 storage
+the link's wall crossing, wetting walls; the dissipation term of Eq. aEq7
+in FP64), alone and together: FP64 storage
 to 1e-13 of each lattice's magnitude per state (1e-12 on fields), FP32 to
 1e-5 and F16MIX to 1e-3 on u, T and c; the strip kernel equal to the tile
 kernel; a sessile drop reaching its contact angle on the GPU.
@@ -119,6 +120,45 @@ def test_sessile_drop_contact_angle_f32(LBE, orc):
     th = _contact_angle(F["c"])
     print("GPU contact angle", th)
     assert abs(th - 60.0) < 4.0
+
+
+@pytest.mark.parametrize("extra", [dict(), dict(rho2=3.0), dict(interp=1, cos_wet=0.4)])
+@pytest.mark.parametrize("nx,ny", [(5, 7), (33, 9), (130, 19)])
+def test_dissipation_one_step_f64(LBE, orc, extra, nx, ny):
+    """The pressure-work / viscous-dissipation term of Eq. aEq7 (FP64; the
+    velocity gradients from the pre-pass), alone, with a density ratio and
+    with other variants: one step from the oracle's state equals one oracle
+    step."""
+    w = drop(nx, ny, max(1.5, min(nx, ny) / 2.5), "wall_mid")
+    w.params.update(dict(extra, dissip=1))
+    w.params["ax"] = 1e-5
+    pop0 = orc.run(w.params, orc.init(w.params, w.c0, w.T0, w.Tbot, w.Ttop), w.Tbot, w.Ttop, 3)
+    sim = LBE(w, storage="f64")
+    sim.set_state(pop0)
+    sim.step(1)
+    ref = orc.run(w.params, pop0, w.Tbot, w.Ttop, 1)
+    assert state_err(sim.get_state().numpy(), ref) < 1e-13
+
+
+def test_dissipation_brinkman_f64(LBE, orc):
+    """The oracle's Brinkman pin on the GPU: plane Poiseuille flow (4 x 64,
+    U = 0.02, eta = 0.1) heated by its own viscous dissipation, 60 000 FP64
+    steps: the fields equal the oracle's (1e-12) and T reaches 1.3346e-4
+    at the centre (the closed form from the run's own u: 1.3333e-4)."""
+    nx, ny, U, eta = 4, 64, 0.02, 0.1
+    p = wl.base_params(nx, ny, eta1=eta, eta2=eta, lam1=0.1, lam2=0.1, sigma0=0.0, sigmaT=0.0,
+                       Tref=0.0)
+    p["ax"] = 2 * U * eta / (p["rho"] * (ny / 2.0) ** 2)
+    p["dissip"] = 1
+    Z, Tb = np.zeros((ny, nx)), np.zeros(nx)
+    w = wl.Workload("brinkman", p, Z, Z, Tb, Tb, 60000)
+    sim = LBE(w, storage="f64")
+    sim.step(w.steps)
+    F = gpu_fields(sim)
+    G = orc.fields(p, orc.run(p, orc.init(p, Z, Z, Tb, Tb), Tb, Tb, w.steps), Tb, Tb)
+    e = field_errors(F, G)
+    assert max(e["u"], e["T"]) < 1e-12, e
+    assert abs(F["T"].max() - 1.3346e-4) < 2e-7
 
 
 def test_adjoint_rejects_variants(LBE):
