@@ -328,21 +328,26 @@ def run_ours(args, ws, rank, local):
         outs = {k: torch.empty((w.ny, w.nx), dtype=torch.float64).pin_memory()
                 for k in ("c", "p", "ux", "uy", "T")}
         w2 = wl.Workload(w.name, w.params, c0.numpy(), T0.numpy(), w.Tbot, w.Ttop, w.steps)
-        barrier(ws)
-        torch.cuda.synchronize()
-        ts = time.perf_counter()
-        s2 = LBE(w2, storage=args.storage)
-        s2.step(args.steps)
-        s2.fields(out=outs)  # device -> pinned host buffers
-        te = time.perf_counter() - ts
+        # one untimed pass of the same calls first (module and allocator
+        # warm-up, like the warm-up steps of the device-timed line)
+        for timed in (False, True):
+            barrier(ws)
+            torch.cuda.synchronize()
+            ts = time.perf_counter()
+            s2 = LBE(w2, storage=args.storage)
+            s2.step(args.steps)
+            s2.fields(out=outs)  # device -> pinned host buffers
+            te = time.perf_counter() - ts
+            del s2
+            if not timed:
+                torch.cuda.empty_cache()
         te = allmax(ws, te)
-        del s2
         h2d = (2 * cells + 2 * w.nx) * 8
         d2h = 5 * cells * 8
         e2e = {"value": cells * args.steps * ws / te / 1e6, "unit": UNIT,
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                "note": "lbe_init from host c0/T0/walls + %d steps + lbe_fields to host, "
-                       "wall clock" % args.steps}
+                       "wall clock of the second of two identical passes" % args.steps}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
