@@ -377,6 +377,77 @@ __device__ __forceinline__ void wstash_pull_mix(const InstDev& I, const Phys<flo
   }
 }
 
+// Moments c (two floats), p and T' of a cell of an interior row (no wall
+// rule) of the 16-bit forms, from the stash: the 16-bit values are summed as
+// stored and each sum is scaled once by its power-of-two 1/s_k, which gives
+// the sums of the scaled values bit for bit (a power of two commutes with
+// every rounding in the normal range) with 1/s_k applied to 3 sums instead
+// of 26 values.  Same order of additions as sum9 and moment_c.
+template <class S>
+__device__ __forceinline__ void moments16_interior(const Phys<float>& P, const char* slot,
+                                                   int c0, int c0g, float& c, float& clo,
+                                                   float& p, float& Tp, float g0lo) {
+  using Fmt = StashFmt<S>;
+  using E = typename Fmt::E;
+  float qf[9], qg[9], qh[9];
+  qf[0] = S::cvt(reinterpret_cast<const E*>(slot + Fmt::F0)[c0]);
+#pragma unroll
+  for (int i = 1; i < 9; i++) {
+    const E* r = reinterpret_cast<const E*>(slot + (i - 1) * Fmt::PROW);
+    const float2 v = S::cvt2(r + 2 * (c0 - EX(i)));
+    qf[i] = v.x;
+    qg[i] = v.y;
+  }
+#pragma unroll
+  for (int i = 0; i < 9; i++)
+    qh[i] = S::cvt(reinterpret_cast<const E*>(slot + Fmt::off(2, i))[c0 - EX(i)]);
+  p = sum9(qf) * P.inv_s[0];
+  const float s8 = (((qg[1] + qg[2]) + (qg[3] + qg[4])) + ((qg[5] + qg[6]) + (qg[7] + qg[8]))) *
+                   P.inv_s[1];
+  const float g0 = reinterpret_cast<const float*>(slot + Fmt::G0)[c0g];
+  float e;
+  two_sum(g0, s8, c, e);
+  clo = e + g0lo;
+  Tp = dv(sum9(qh) * P.inv_s[2], P.rho_cv, P.inv_rho_cv);
+}
+// The same for F16MIX (f in FP32 as it is; g_i and the hbar deviations as
+// stored, their sums scaled once).
+__device__ __forceinline__ void moments_mix_interior(const Phys<float>& P, const char* slot, int c0,
+                                                     float& c, float& clo, float& p, float& Tp) {
+  using Fmt = StashFmt<StMix>;
+  const uint2* b = reinterpret_cast<const uint2*>(slot) + c0;
+  auto two = [](uint32_t u) {
+    __half2 q;
+    memcpy(&q, &u, 4);
+    return __half22float2(q);
+  };
+  float f[9], qg[9], qh[9];
+  float g0lo;
+  {
+    const uint2 v = b[0];
+    const float2 q = two(v.y);
+    f[0] = __uint_as_float(v.x);
+    qh[0] = q.x;
+    g0lo = q.y * G0LO_INV;
+  }
+#pragma unroll
+  for (int i = 1; i < 9; i++) {
+    const uint2 v = b[i * Fmt::EW - EX(i)];
+    const float2 q = two(v.y);
+    f[i] = __uint_as_float(v.x);
+    qg[i] = q.x;
+    qh[i] = q.y;
+  }
+  p = sum9(f);
+  const float s8 = (((qg[1] + qg[2]) + (qg[3] + qg[4])) + ((qg[5] + qg[6]) + (qg[7] + qg[8]))) *
+                   P.inv_s[1];
+  const float g0 = reinterpret_cast<const float*>(slot + Fmt::G0)[c0];
+  float e;
+  two_sum(g0, s8, c, e);
+  clo = e + g0lo;
+  Tp = dv(sum9(qh) * P.inv_s[2], P.rho_cv, P.inv_rho_cv);
+}
+
 // True in exactly one lane of the (converged) warp.
 __device__ __forceinline__ bool elect_one() {
   uint32_t e;
@@ -796,7 +867,30 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
             const int mr = m >= 0 ? m : -1 - m;
             const char* s = slot(m);
             C v[9], vf[9];
-            if constexpr (MIX) {
+            bool done = false;
+            if constexpr (MIX || W16) {
+              if (mr > 0 && mr < ny - 1) {
+                // interior row of a 16-bit form: sums of the stored values
+                C cv, clo, pv, Tv;
+                if constexpr (MIX) {
+                  moments_mix_interior(P, s, c0 + dj, cv, clo, pv, Tv);
+                } else {
+                  const C g0lo =
+                      __half2float(reinterpret_cast<const __half*>(s + Fmt::LO)[c0lo + dj]) *
+                      G0LO_INV;
+                  moments16_interior<S>(P, s, c0 + dj, c0g + dj, cv, clo, pv, Tv, g0lo);
+                }
+                cring[ci] = m < 0 ? wet_ghost(P, cv, -1 - m) : cv;
+                clr[ci] = __float2half_rn(clo * G0LO_SCALE);
+                if (pt) {
+                  pring[pi] = pv;
+                  Tring[pi] = m < 0 ? ghost_T<S>(I, cxw, true, Tv) : Tv;
+                }
+                done = true;
+              }
+            }
+            if (done) {
+            } else if constexpr (MIX) {
               C vh[9], g0lo, clo;
               wstash_pull_mix<true>(I, P, s, c0 + dj, mr, cxw, vf, v, vh, g0lo);
               cring[ci] = moment_c(v, g0lo, clo);
