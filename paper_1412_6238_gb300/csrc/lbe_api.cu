@@ -700,25 +700,29 @@ lbe_status create(int32_t n, const lbe_params* params, const lbe_init_fields* in
     }
     CUB(cudaStreamSynchronize(h->stream));
   }
-  // initial state of each instance: compute the pre-collision state at rest
-  // and push it into buffer 0
-  for (int j = 0; j < n; j++) {
-    InstHost& H = h->inst[j];
-    const size_t N = (size_t)H.nx * H.ny;
-    double *c0 = nullptr, *pre = nullptr;
-    CUB(cudaMalloc(&c0, sizeof(double) * 2 * N));
-    cudaError_t e = cudaMalloc(&pre, sizeof(double) * 27 * N);
-    if (e != cudaSuccess) {
-      cudaFree(c0);
-      CUB(e);
+  // initial state of each instance: the rest state of every cell (three
+  // numbers) from c0 and T0, pushed into buffer 0; one scratch of 5 values
+  // per cell of the largest instance serves them all, in stream order
+  {
+    double* work = nullptr;
+    CUB(cudaMalloc(&work, sizeof(double) * 5 * (size_t)h->max_cells));
+    cudaError_t e = cudaSuccess;
+    for (int j = 0; j < n && e == cudaSuccess; j++) {
+      InstHost& H = h->inst[j];
+      const size_t N = (size_t)H.nx * H.ny;
+      e = cudaMemcpyAsync(work, init[j].c0, sizeof(double) * N, cudaMemcpyHostToDevice,
+                          h->stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(work + N, init[j].T0, sizeof(double) * N, cudaMemcpyHostToDevice,
+                            h->stream);
+      if (e == cudaSuccess)
+        e = launch_rest_state(h->d_finst + j, H.nx, H.ny, work, work + N, work + 2 * N,
+                              h->stream);
+      if (e == cudaSuccess)
+        e = launch_push(h->storage, h->d_finst + j, H.nx, H.ny, work + 2 * N, 0, 1, h->stream);
     }
-    cudaMemcpyAsync(c0, init[j].c0, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream);
-    cudaMemcpyAsync(c0 + N, init[j].T0, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream);
-    e = launch_init_state(h->d_finst + j, H.nx, H.ny, c0, c0 + N, pre, h->stream);
-    if (e == cudaSuccess) e = launch_push(h->storage, h->d_finst + j, H.nx, H.ny, pre, 0, h->stream);
     cudaError_t es = cudaStreamSynchronize(h->stream);
-    cudaFree(c0);
-    cudaFree(pre);
+    cudaFree(work);
     CUB(e);
     CUB(es);
   }
@@ -1031,7 +1035,7 @@ lbe_status lbe_set_state(lbe_handle* h, int32_t instance, const double* pops, in
   // a new state: clear the device error word of an earlier copy time-out
   cudaError_t e = cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream);
   if (e == cudaSuccess)
-    e = launch_push(h->storage, h->d_finst + instance, H.nx, H.ny, d, h->parity, h->stream);
+    e = launch_push(h->storage, h->d_finst + instance, H.nx, H.ny, d, h->parity, 0, h->stream);
   st = wait(h);
   if (!on_device) cudaFree(d);
   if (e != cudaSuccess) return fail(h, LBE_ECUDA, "set_state: %s", cudaGetErrorString(e));

@@ -85,23 +85,29 @@ cudaError_t launch_fields(int storage, const InstDev* d, int64_t tiles, int pari
 // At rest (u = 0, p = 0): f_i = f_eq(0, 0) = 0; g_i = g_eq(c0, mu0, 0) with
 // mu0 = 2 beta c0 (c0-1)(2c0-1) - eps^2 lap c0 (Eq. 21-22), lap c0 by the
 // isotropic stencil with mirrored ghost rows; hbar_i = w_i rho(c0) c_v T0
-// (Eq. aEq9 at u = 0).
-__global__ void init_state_kernel(const InstDev* __restrict__ d, int nx, int ny,
+// (Eq. aEq9 at u = 0).  The rest state of a cell is three numbers, g_i =
+// w_i H_i (H_0 and the common H_i) and hbar_i = w_i rho c_v T0: rest[0..2]
+// [ny][nx] hold them, and the push below builds the 27 populations of every
+// cell from its neighbours' three.  (Grids: x over blocks, rows over
+// blockIdx.y, strided.)
+__global__ void rest_state_kernel(const InstDev* __restrict__ d, int nx, int ny,
                                   const double* __restrict__ c0, const double* __restrict__ T0,
-                                  double* __restrict__ pre) {
+                                  double* __restrict__ rest) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= nx) return;
   const int64_t N = (int64_t)nx * ny;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(k % nx), y = (int)(k / nx);
-    const InstDev& I = *d;
-    // c0 with its ghost rows (the mirror, plus the wetting flux at a wetting
-    // wall)
-    auto cat = [&](int xx, int yy) -> double {
-      xx = (xx % nx + nx) % nx;
-      if (yy < 0) return wet_ghost(I.pd, c0[(int64_t)(-1 - yy) * nx + xx], -1 - yy);
-      if (yy >= ny) return wet_ghost(I.pd, c0[(int64_t)(2 * ny - 1 - yy) * nx + xx], yy - ny);
-      return c0[(int64_t)yy * nx + xx];
-    };
+  const InstDev& I = *d;
+  const Phys<double>& P = I.pd;
+  // c0 with its ghost rows (the mirror, plus the wetting flux at a wetting
+  // wall), periodic in x
+  auto cat = [&](int xx, int yy) -> double {
+    xx = xx < 0 ? xx + nx : (xx >= nx ? xx - nx : xx);
+    if (yy < 0) return wet_ghost(I.pd, c0[(int64_t)(-1 - yy) * nx + xx], -1 - yy);
+    if (yy >= ny) return wet_ghost(I.pd, c0[(int64_t)(2 * ny - 1 - yy) * nx + xx], yy - ny);
+    return c0[(int64_t)yy * nx + xx];
+  };
+  for (int y = blockIdx.y; y < ny; y += gridDim.y) {
+    const int64_t k = (int64_t)y * nx + x;
     const double v0 = c0[k];
     // Laplacian (2/c_s^2) sum_i w_i (c(x + xi_i) - c(x)), terms in index order
     const double wa = WGT<double>(1), wd = WGT<double>(5);
@@ -115,26 +121,18 @@ __global__ void init_state_kernel(const InstDev* __restrict__ d, int nx, int ny,
     t = t + wd * (cat(x + 1, y - 1) - v0);
     const double cs2 = 1.0 / 3.0;
     const double lap = 2.0 * t / cs2;
-    const Phys<double>& P = I.pd;
     const double mu = P.beta2 * v0 * (v0 - 1.0) * (2.0 * v0 - 1.0) - P.eps2 * lap;
     const double W0 = WGT<double>(0);
-    const double H0 = (v0 - (1.0 - W0) * P.Gm * mu / cs2) / W0;
-    const double Hi = P.Gm * mu / cs2;
-    const double rcvT = rho_at(P, v0) * P.cv * T0[k];
-    for (int i = 0; i < 9; i++) {
-      const double w = WGT<double>(i);
-      pre[(int64_t)i * N + k] = 0.0;
-      pre[(int64_t)(9 + i) * N + k] = w * (i == 0 ? H0 : Hi);
-      pre[(int64_t)(18 + i) * N + k] = rcvT * w;
-    }
+    rest[k] = (v0 - (1.0 - W0) * P.Gm * mu / cs2) / W0;  // H_0
+    rest[N + k] = P.Gm * mu / cs2;                        // H_i, i > 0
+    rest[2 * N + k] = rho_at(P, v0) * P.cv * T0[k];      // rho c_v T0
   }
 }
 
-cudaError_t launch_init_state(const InstDev* d, int nx, int ny, const double* c0,
-                              const double* T0, double* pre, cudaStream_t s) {
-  const int64_t N = (int64_t)nx * ny;
-  const int grid = (int)((N + 255) / 256 < 65535 ? (N + 255) / 256 : 65535);
-  init_state_kernel<<<grid, 256, 0, s>>>(d, nx, ny, c0, T0, pre);
+cudaError_t launch_rest_state(const InstDev* d, int nx, int ny, const double* c0,
+                              const double* T0, double* rest, cudaStream_t s) {
+  const dim3 grid((nx + 127) / 128, ny < 65535 ? ny : 65535);
+  rest_state_kernel<<<grid, 128, 0, s>>>(d, nx, ny, c0, T0, rest);
   return cudaGetLastError();
 }
 
@@ -145,52 +143,73 @@ cudaError_t launch_init_state(const InstDev* d, int nx, int ny, const double* c0
 //   P*_j(x) = P_j(x + xi_j)                 if x + xi_j is a cell,
 //   P*_j(x) = P_jbar(x)                      at a wall for f and g,
 //   P*_j(x) = 2 w_j rho c_v T_w - P_jbar(x)  at a wall for hbar,
-// rho that of the cell's c = sum_i g_i (with a varying density).
-template <class S>
-__global__ void push_kernel(const InstDev* __restrict__ d, int nx, int ny,
-                            const double* __restrict__ pre, int parity) {
+// rho that of the cell's c = sum_i g_i (with a varying density).  pre(kk, j,
+// k): pre-collision population (kk, j) of cell k.
+template <class S, class Pre>
+__device__ __forceinline__ void push_cell(const InstDev& I, int nx, int ny, int x, int y,
+                                          int parity, Pre&& pre) {
   using C = typename S::C;
-  const InstDev& I = *d;
-  const int64_t N = (int64_t)nx * ny;
   char* buf = I.buf[parity];
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(k % nx), y = (int)(k / nx);
-    const size_t rowbase = (size_t)y * I.pitch;
-    // hbar deviation reference of this row (storage forms other than FP64)
-    const double rref = dev_h<S>() ? I.pd.rho * I.pd.cv * (I.hr0 + I.hr1 * y) : 0.0;
-    double cn = 0.0;
-    for (int j = 0; j < 9; j++) cn += pre[(int64_t)(9 + j) * N + k];
-    const double rc = rho_at(I.pd, cn);
+  const int64_t k = (int64_t)y * nx + x;
+  const size_t rowbase = (size_t)y * I.pitch;
+  // hbar deviation reference of this row (storage forms other than FP64)
+  const double rref = dev_h<S>() ? I.pd.rho * I.pd.cv * (I.hr0 + I.hr1 * y) : 0.0;
+  double cn = 0.0;
+  for (int j = 0; j < 9; j++) cn += pre(1, j, k);
+  const double rc = rho_at(I.pd, cn);
 #pragma unroll
-    for (int j = 0; j < 9; j++) {
-      const int xt = ((x + EX(j)) % nx + nx) % nx;
-      const int yt = y + EY(j);
-      const bool wall = (yt < 0) || (yt >= ny);
-      for (int kk = 0; kk < 3; kk++) {
-        double v;
-        if (!wall) {
-          v = pre[(int64_t)(kk * 9 + j) * N + (int64_t)yt * nx + xt];
+  for (int j = 0; j < 9; j++) {
+    int xt = x + EX(j);
+    xt = xt < 0 ? xt + nx : (xt >= nx ? xt - nx : xt);
+    const int yt = y + EY(j);
+    const bool wall = (yt < 0) || (yt >= ny);
+    for (int kk = 0; kk < 3; kk++) {
+      double v;
+      if (!wall) {
+        v = pre(kk, j, (int64_t)yt * nx + xt);
+      } else {
+        const double pb = pre(kk, OPP(j), k);
+        if (kk < 2) {
+          v = pb;
         } else {
-          const double pb = pre[(int64_t)(kk * 9 + OPP(j)) * N + k];
-          if (kk < 2) {
-            v = pb;
-          } else {
-            // the inverse of the pull's anti-bounce-back of population
-            // OPP(j), whose link crosses the wall at x + xi_jx/2
-            const double* Twall = (yt < 0) ? I.Tbot : I.Ttop;
-            double Tw = Twall[x];
-            if (I.pd.wmid != 0.0 && EX(j) != 0) Tw = 0.5 * (Tw + Twall[xt]);
-            v = 2.0 * WGT<double>(j) * rc * I.pd.cv * Tw - pb;
-          }
-        }
-        if (kk == 2) v -= WGT<double>(j) * rref;
-        st_cell<S>(I, buf, kk, j, rowbase, x, (C)v);
-        if constexpr (S::kind != ST_F64) {
-          // g_0 = hi + lo: the low part of the rest population
-          if (kk == 1 && j == 0) st_cell_g0lo<S>(I, buf, rowbase, x, (float)(v - (double)(C)v));
+          // the inverse of the pull's anti-bounce-back of population
+          // OPP(j), whose link crosses the wall at x + xi_jx/2
+          const double* Twall = (yt < 0) ? I.Tbot : I.Ttop;
+          double Tw = Twall[x];
+          if (I.pd.wmid != 0.0 && EX(j) != 0) Tw = 0.5 * (Tw + Twall[xt]);
+          v = 2.0 * WGT<double>(j) * rc * I.pd.cv * Tw - pb;
         }
       }
+      if (kk == 2) v -= WGT<double>(j) * rref;
+      st_cell<S>(I, buf, kk, j, rowbase, x, (C)v);
+      if constexpr (S::kind != ST_F64) {
+        // g_0 = hi + lo: the low part of the rest population
+        if (kk == 1 && j == 0) st_cell_g0lo<S>(I, buf, rowbase, x, (float)(v - (double)(C)v));
+      }
+    }
+  }
+}
+
+// push of a [27][ny][nx] pre-collision state (rest == 0), or of the rest
+// state of rest_state_kernel (rest != 0: the same values as the state f_i =
+// 0, g_i = w_i H_i, hbar_i = rho c_v T0 w_i)
+template <class S>
+__global__ void push_kernel(const InstDev* __restrict__ d, int nx, int ny,
+                            const double* __restrict__ pre, int parity, int rest) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= nx) return;
+  const int64_t N = (int64_t)nx * ny;
+  for (int y = blockIdx.y; y < ny; y += gridDim.y) {
+    if (rest) {
+      push_cell<S>(*d, nx, ny, x, y, parity, [&](int kk, int j, int64_t k) -> double {
+        const double w = WGT<double>(j);
+        if (kk == 0) return 0.0;
+        if (kk == 1) return w * (j == 0 ? pre[k] : pre[N + k]);
+        return pre[2 * N + k] * w;
+      });
+    } else {
+      push_cell<S>(*d, nx, ny, x, y, parity,
+                   [&](int kk, int j, int64_t k) { return pre[(int64_t)(kk * 9 + j) * N + k]; });
     }
   }
 }
@@ -225,10 +244,9 @@ __global__ void pull_kernel(const InstDev* __restrict__ d, int nx, int ny, doubl
 
 template <class S>
 static cudaError_t push_t(const InstDev* d, int nx, int ny, const double* pre, int parity,
-                          cudaStream_t s) {
-  const int64_t N = (int64_t)nx * ny;
-  const int grid = (int)((N + 255) / 256 < 65535 ? (N + 255) / 256 : 65535);
-  push_kernel<S><<<grid, 256, 0, s>>>(d, nx, ny, pre, parity);
+                          int rest, cudaStream_t s) {
+  const dim3 grid((nx + 127) / 128, ny < 65535 ? ny : 65535);
+  push_kernel<S><<<grid, 128, 0, s>>>(d, nx, ny, pre, parity, rest);
   return cudaGetLastError();
 }
 template <class S>
@@ -241,13 +259,13 @@ static cudaError_t pull_t(const InstDev* d, int nx, int ny, double* pre, int par
 }
 
 cudaError_t launch_push(int storage, const InstDev* d, int nx, int ny, const double* pre,
-                        int parity, cudaStream_t s) {
+                        int parity, int rest, cudaStream_t s) {
   switch (storage) {
-    case ST_F64: return push_t<StF64>(d, nx, ny, pre, parity, s);
-    case ST_F32: return push_t<StF32>(d, nx, ny, pre, parity, s);
-    case ST_F16DEV: return push_t<StF16>(d, nx, ny, pre, parity, s);
-    case ST_BF16DEV: return push_t<StBF16>(d, nx, ny, pre, parity, s);
-    case ST_F16MIX: return push_t<StMix>(d, nx, ny, pre, parity, s);
+    case ST_F64: return push_t<StF64>(d, nx, ny, pre, parity, rest, s);
+    case ST_F32: return push_t<StF32>(d, nx, ny, pre, parity, rest, s);
+    case ST_F16DEV: return push_t<StF16>(d, nx, ny, pre, parity, rest, s);
+    case ST_BF16DEV: return push_t<StBF16>(d, nx, ny, pre, parity, rest, s);
+    case ST_F16MIX: return push_t<StMix>(d, nx, ny, pre, parity, rest, s);
   }
   return cudaErrorInvalidValue;
 }

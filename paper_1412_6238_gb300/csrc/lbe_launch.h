@@ -108,12 +108,15 @@ cudaError_t fields_bf16(const InstDev* d, int64_t tiles, int parity, double* out
 cudaError_t fields_mix(const InstDev* d, int64_t tiles, int parity, double* out, cudaStream_t s);
 
 // Auxiliary kernels (lbe_aux.cu).
-// Pre-collision state at rest from c0, T0 (device, [ny][nx]) into pre[27][ny][nx].
-cudaError_t launch_init_state(const InstDev* d_one, int nx, int ny, const double* c0,
-                              const double* T0, double* pre, cudaStream_t s);
-// pre[27][ny][nx] (double, pre-collision) -> buf[parity] (inverse of the pull).
+// The rest state of every cell from c0, T0 (device, [ny][nx]) into
+// rest[3][ny][nx]: H_0, H_i (g_i = w_i H_i) and rho c_v T0 (hbar_i = w_i rho
+// c_v T0); f = 0.
+cudaError_t launch_rest_state(const InstDev* d_one, int nx, int ny, const double* c0,
+                              const double* T0, double* rest, cudaStream_t s);
+// pre[27][ny][nx] (double, pre-collision) -> buf[parity] (inverse of the
+// pull); rest != 0: pre is rest[3][ny][nx] of launch_rest_state.
 cudaError_t launch_push(int storage, const InstDev* d_one, int nx, int ny, const double* pre,
-                        int parity, cudaStream_t s);
+                        int parity, int rest, cudaStream_t s);
 // buf[parity] -> pre[27][ny][nx] (the pull).
 cudaError_t launch_pull(int storage, const InstDev* d_one, int nx, int ny, double* pre,
                         int parity, cudaStream_t s);
