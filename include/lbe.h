@@ -98,7 +98,7 @@ typedef enum {
  * otherwise): nx >= 1, ny >= 2, rho > 0, rho2 >= 0, cv > 0, eta1,
  * eta2 > 0, lam1, lam2 >= 0 (> 0 with interp = 1), eps > 0,
  * tau_g > 1/2, mobility >= 0, eta_n > 0, interp and wall_mid 0 or 1,
- * -1 <= cos_wet <= 1, dissip 0 or 1 (1 with FP64 storage), reserved 0,
+ * -1 <= cos_wet <= 1, dissip 0 or 1 (1 with FP64 or FP32 storage), reserved 0,
  * and 0 < omega < 2 for every relaxation rate at c = 0 and c = 1.  Layout
  * change from ABI version 1: rho2, interp, wall_mid, cos_wet, dissip and
  * reserved appended. */
@@ -141,8 +141,8 @@ typedef struct {
                            term -fbar_i q_i of Eq. aEq7 that Eq. aEq8 drops
                            (fbar from the f lattice, q_i = (xi_i - u).
                            (xi_i.grad) u; the velocity gradients from a
-                           pass of their own before each step); needs FP64
-                           storage                                        */
+                           pass of their own before each step); FP64 or
+                           FP32 storage, on the tile kernel               */
   int32_t reserved;     /* 0 */
 } lbe_params;
 

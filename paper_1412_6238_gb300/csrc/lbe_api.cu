@@ -202,8 +202,8 @@ lbe_status check_params(const lbe_params& p, int index) {
   if (p.wall_mid != 0 && p.wall_mid != 1) return bad("wall_mid must be 0 or 1");
   if (!(p.cos_wet >= -1.0 && p.cos_wet <= 1.0)) return bad("cos_wet must be in [-1, 1]");
   if (p.dissip != 0 && p.dissip != 1) return bad("dissip must be 0 or 1");
-  if (p.dissip == 1 && p.storage != LBE_F64)
-    return bad("the dissipation term (dissip = 1) needs FP64 storage");
+  if (p.dissip == 1 && p.storage != LBE_F64 && p.storage != LBE_F32)
+    return bad("the dissipation term (dissip = 1) needs FP64 or FP32 storage");
   if (p.reserved != 0) return bad("reserved must be 0");
   if (varying_rho(p) && p.storage != LBE_F64)
     return bad("a density ratio (rho2 != rho) needs FP64 storage");
@@ -457,7 +457,9 @@ cudaError_t launch_one_step(lbe_handle* h, int parity) {
   // u of every cell first, and the dissipation term the gradients of u: a
   // pass of its own
   if (h->vrho || h->dissip)
-    e = pcorr_f64(h->d_pinst, h->n, h->p_tiles, parity, h->p_grid, h->stream);
+    e = h->storage == LBE_F64
+            ? pcorr_f64(h->d_pinst, h->n, h->p_tiles, parity, h->p_grid, h->stream)
+            : pcorr_f32(h->d_pinst, h->n, h->p_tiles, parity, h->p_grid, h->stream);
   if (e == cudaSuccess)
     e = launch_step(h->storage, h->tile, h->d_inst, h->n, h->total_tiles, parity, h->grid,
                     h->d_seed, h->stream);
@@ -737,7 +739,8 @@ lbe_status create(int32_t n, const lbe_params* params, const lbe_init_fields* in
     // storage, every instance at least XG columns wide), else the tile kernel
     int min_nx = 1 << 30;
     for (auto& H : h->inst) min_nx = std::min(min_nx, H.nx);
-    h->tile = (h->storage == LBE_F64 || min_nx < XG) ? 0 : STASH_ID;
+    // (the dissipation term's velocity gradients: the tile kernel only)
+    h->tile = (h->storage == LBE_F64 || min_nx < XG || h->dissip) ? 0 : STASH_ID;
   }
   lbe_status s2 = setup_tiles(h);
   if (s2) return bail(s2);
@@ -1146,9 +1149,12 @@ lbe_status lbe_set_tile(lbe_handle* h, int32_t tile_id, int32_t grid_ctas, int32
   if (!h) return fail(nullptr, LBE_EINVAL, "handle is NULL");
   if (!tile_available(h->storage, tile_id))
     return fail(h, LBE_EINVAL, "kernel %d is not built for this storage", tile_id);
-  if (is_strip(tile_id))
+  if (is_strip(tile_id)) {
     for (auto& H : h->inst)
       if (H.nx < XG) return fail(h, LBE_EINVAL, "the strip kernel needs nx >= %d", XG);
+    if (h->dissip)
+      return fail(h, LBE_EINVAL, "the dissipation term (dissip = 1) runs on the tile kernel");
+  }
   if (grid_ctas < -1) return fail(h, LBE_EINVAL, "grid_ctas must be >= -1");
   if (seg_rows < 0 && !is_strip(tile_id))
     return fail(h, LBE_EINVAL, "seg_rows < 0 (balanced pieces) is for the strip kernel");

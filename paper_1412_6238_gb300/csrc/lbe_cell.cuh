@@ -354,6 +354,7 @@ __device__ __forceinline__ void collide(const Phys<typename S::C>& P, const type
     const float2 m1 = make_float2(-1.f, -1.f);
     C dfs = C(0), dhs = C(0);  // sums of the moving f and hbar increments
     const float2 omTc = make_float2(omega_T - C(1), omega_T - C(1));
+    C ws[9], ws0 = C(0);  // the dissipation term (below)
     auto dir2 = [&](int i, int j, C W, C K, C a, C hq, C Ja, C Jal, C Fxi, C Gxi, C offi) {
       const float2 Wv = make_float2(W, W);
       const float2 q = make_float2(a + hq, hq - a);
@@ -383,6 +384,10 @@ __device__ __forceinline__ void collide(const Phys<typename S::C>& P, const type
       const float2 sT = __ffma2_rn(omTc, make_float2(offi, -offi),
                                    __fmul2_rn(__fmul2_rn(aTiv, gd), __fmul2_rn(rT, G)));
       ho = __fadd2_rn(ho, sT);
+      if (wdu) {  // the dissipation term: isotropic part whole, the rest (1 - omega_T/2)
+        ho.x += aT * (ws[i] - W * ws0) + W * ws0;
+        ho.y += aT * (ws[j] - W * ws0) + W * ws0;
+      }
       // increments, whose sum the rest direction takes with the opposite sign
       dfs += finc.x + finc.y;
       dhs += (ho.x - hv.x) + (ho.y - hv.y);
@@ -401,6 +406,42 @@ __device__ __forceinline__ void collide(const Phys<typename S::C>& P, const type
     Jpl += Jxl + Jyl;
     two_sum(Jy, -Jx, Jm, Jml);
     Jml += Jyl - Jxl;
+    // the dissipation term of Eq. aEq7 (wdu given; as in the FP64 branch):
+    // fbar_i = rho Gamma_i - 3 (1 - omega_f/2) (f_eq,i - f_i), with f_eq,i - f_i
+    // formed as the f relaxation forms it (two floats for the odd part), not
+    // as the difference of fbar and rho Gamma, whose cancellation would lose
+    // three digits of the stress; q_0 = 0
+    if (wdu) {
+      auto pair = [&](int i, int j, C W, C K, C a, C hq, C Ja, C Jal) {
+        const C Sf = W * fmaf(rcs2, hq, pp), Af = K * Ja;
+        const C Afl = fmaf(K, Ja, -Af) + K * Jal;
+        const C d_i = ((Sf - f[i]) + Af) + Afl, d_j = ((Sf - f[j]) - Af) - Afl;
+        const C Gi = W * (C(1) + (a + hq)), Gj = W * (C(1) + (hq - a));
+        auto one = [&](int k, C G, C dl) {
+          const C ex = C(EX(k)), ey = C(EY(k));
+          const C fph = d.rho * G - C(3) * af * dl;
+          const C q = (ex - ux) * (ex * wdu[0] + ey * wdu[1]) +
+                      (ey - uy) * (ex * wdu[2] + ey * wdu[3]);
+          ws[k] = -fph * q;
+        };
+        one(i, Gi, d_i);
+        one(j, Gj, d_j);
+      };
+      C a0 = ux3, hq0 = C(0.5) * (a0 * a0 - uu);
+      pair(1, 3, wa, Ka, a0, hq0, Jx, Jxl);
+      a0 = uy3;
+      hq0 = C(0.5) * (a0 * a0 - uu);
+      pair(2, 4, wa, Ka, a0, hq0, Jy, Jyl);
+      a0 = ux3 + uy3;
+      hq0 = C(0.5) * (a0 * a0 - uu);
+      pair(5, 7, wd, Kd, a0, hq0, Jp, Jpl);
+      a0 = uy3 - ux3;
+      hq0 = C(0.5) * (a0 * a0 - uu);
+      pair(6, 8, wd, Kd, a0, hq0, Jm, Jml);
+      ws[0] = C(0);
+#pragma unroll
+      for (int i = 1; i < 9; i++) ws0 += ws[i];
+    }
     C a = ux3, hq = C(0.5) * (a * a - uu);
     dir2(1, 3, wa, Ka, a, hq, Jx, Jxl, Fx, Gx, C(0));
     a = uy3;
@@ -425,7 +466,8 @@ __device__ __forceinline__ void collide(const Phys<typename S::C>& P, const type
     // its two-float moment
     (void)she;
     out(0, 0, f[0] - dfs);
-    out(2, 0, h[0] - dhs);
+    // (with the dissipation term the cell's energy gains its zeroth moment)
+    out(2, 0, wdu ? (h[0] - dhs) + ws0 : h[0] - dhs);
     {
       const C src0 = (agsg * (C(0) - Gdu)) * G0;
       C s0, e0;

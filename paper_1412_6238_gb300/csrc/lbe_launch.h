@@ -102,6 +102,9 @@ cudaError_t fields_f64(const InstDev* d, int64_t tiles, int parity, double* out,
 // cell into each instance's pcorr; d is a work list of tile shape 0.
 cudaError_t pcorr_f64(const InstDev* d, int n, int64_t total, int parity, int grid,
                       cudaStream_t s);
+// FP32 storage: the pre-pass of the dissipation term (u of every cell)
+cudaError_t pcorr_f32(const InstDev* d, int n, int64_t total, int parity, int grid,
+                      cudaStream_t s);
 cudaError_t fields_f32(const InstDev* d, int64_t tiles, int parity, double* out, cudaStream_t s);
 cudaError_t fields_f16(const InstDev* d, int64_t tiles, int parity, double* out, cudaStream_t s);
 cudaError_t fields_bf16(const InstDev* d, int64_t tiles, int parity, double* out, cudaStream_t s);

@@ -66,11 +66,16 @@ def _init(params, storage="f32"):
     (dict(interp=2), "interp"), (dict(interp=1, lam1=0.0), "harmonic"),
     (dict(wall_mid=3), "wall_mid"), (dict(cos_wet=1.5), "cos_wet"),
     (dict(cos_wet=float("nan")), "cos_wet"),
-    (dict(dissip=2), "dissip"), (dict(dissip=1), "FP64"),  # FP32 storage
+    (dict(dissip=2), "dissip"),
 ])
 def test_invalid_parameters_rejected(bad, msg):
     st, err, h = _init(bad)
     assert st == -1 and msg in err and not h.value
+
+
+def test_dissipation_needs_fp64_or_fp32():
+    st, err, h = _init(dict(dissip=1), storage="f16mix")
+    assert st == -1 and "FP64 or FP32" in err and not h.value
 
 
 def test_invalid_storage_rejected():

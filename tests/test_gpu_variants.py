@@ -140,11 +140,34 @@ def test_dissipation_one_step_f64(LBE, orc, extra, nx, ny):
     assert state_err(sim.get_state().numpy(), ref) < 1e-13
 
 
-def test_dissipation_brinkman_f64(LBE, orc):
+@pytest.mark.parametrize("extra", [dict(), dict(interp=1, cos_wet=0.4)])
+def test_dissipation_drop_run_f32(LBE, orc, extra):
+    """The dissipation term with FP32 storage (tile kernel; the strip kernel
+    refuses it): 300 steps of the 70 x 45 drop within 1e-5 of the oracle."""
+    w = drop(70, 45, 20.0, "wall_mid")
+    w.params.update(dict(extra, dissip=1))
+    n = 300
+    sim = LBE(w, storage="f32")
+    assert sim.get_tile()["kernel"] == 0
+    with pytest.raises(Exception, match="tile kernel"):
+        sim.set_tile(7)
+    sim.step(n)
+    pop = orc.run(w.params, orc.init(w.params, w.c0, w.T0, w.Tbot, w.Ttop), w.Tbot, w.Ttop, n)
+    e = field_errors(gpu_fields(sim), oracle_fields(orc, w, pop))
+    print("dissipation f32", extra, e)
+    assert e["u"] < 1e-5 and e["T"] < 1e-5 and e["c"] < 1e-5, e
+
+
+@pytest.mark.parametrize("storage,tol_u,tol_T", [("f64", 1e-12, 1e-12), ("f32", 1e-4, 1e-3)])
+def test_dissipation_brinkman(LBE, orc, storage, tol_u, tol_T):
     """The oracle's Brinkman pin on the GPU: plane Poiseuille flow (4 x 64,
-    U = 0.02, eta = 0.1) heated by its own viscous dissipation, 60 000 FP64
-    steps: the fields equal the oracle's (1e-12) and T reaches 1.3346e-4
-    at the centre (the closed form from the run's own u: 1.3333e-4)."""
+    U = 0.02, eta = 0.1) heated by its own viscous dissipation, 60 000
+    steps: the fields equal the oracle's in FP64 (1e-12) and T reaches
+    1.3346e-4 at the centre (the closed form from the run's own u:
+    1.3333e-4).  FP32 (a variant beyond the stated configurations, whose
+    channel flow is FP64): the steady body-force-driven channel flow itself
+    carries an FP32 bias of 6.9e-5 on u after these 60 000 steps (the drop
+    and planar runs stay within 2e-6), and T, quadratic in du/dy, 6.0e-4."""
     nx, ny, U, eta = 4, 64, 0.02, 0.1
     p = wl.base_params(nx, ny, eta1=eta, eta2=eta, lam1=0.1, lam2=0.1, sigma0=0.0, sigmaT=0.0,
                        Tref=0.0)
@@ -152,12 +175,13 @@ def test_dissipation_brinkman_f64(LBE, orc):
     p["dissip"] = 1
     Z, Tb = np.zeros((ny, nx)), np.zeros(nx)
     w = wl.Workload("brinkman", p, Z, Z, Tb, Tb, 60000)
-    sim = LBE(w, storage="f64")
+    sim = LBE(w, storage=storage)
     sim.step(w.steps)
     F = gpu_fields(sim)
     G = orc.fields(p, orc.run(p, orc.init(p, Z, Z, Tb, Tb), Tb, Tb, w.steps), Tb, Tb)
     e = field_errors(F, G)
-    assert max(e["u"], e["T"]) < 1e-12, e
+    print("Brinkman", storage, e)
+    assert e["u"] < tol_u and e["T"] < tol_T, e
     assert abs(F["T"].max() - 1.3346e-4) < 2e-7
 
 
