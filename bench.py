@@ -436,6 +436,52 @@ def error_vs_oracle(storage: str):
             "problem": "drop 512 x 1024, R = 32, Re = 1, Ma = 10, Ca = 0.05, ratios 0.5"}
 
 
+def measure_extensions(args, w):
+    """Throughput of the scheme's extensions on the benchmark drop (4096^2)
+    beside the default scheme on the same kernel: the boundary and property
+    variants (harmonic law, link-crossing wall temperature, wetting walls)
+    on the FP32 strip kernel built with them; the density ratio rho2/rho1 =
+    4 (FP64 tile kernel plus its corrected-p pre-pass); the dissipation term
+    (FP64 and FP32 tile kernel plus the u pre-pass).  Fraction of the
+    measured HBM peak on the 27 populations read and written per cell
+    (pre-passes not counted as traffic: they are part of the step's time)."""
+    import numpy as np
+
+    from paper_1412_6238_gb300.lbe import LBE
+    peak, _ = hbm_peak()
+    x = np.arange(w.nx, dtype=float)
+    Tb = w.Tbot + 1e-3 * np.cos(2 * np.pi * x / w.nx)
+
+    def run(storage, extra, steps, kernel=None, tb=None):
+        p = dict(w.params, **extra)
+        w2 = type(w)(w.name, p, w.c0, w.T0, w.Tbot if tb is None else tb, w.Ttop, w.steps)
+        sim = LBE(w2, storage=storage)
+        if kernel is not None:
+            sim.set_tile(kernel)
+        sim.step(3)
+        ms = _timed(sim, steps)
+        tile = sim.get_tile()["kernel"]
+        del sim
+        ms_step = ms / steps
+        mlups = w.cells * steps / (ms / 1e3) / 1e6
+        return {"value": mlups, "unit": UNIT, "ms_per_step": ms_step, "kernel": tile,
+                "hbm_frac": w.cells * BYTES_PER_CELL[storage] / (ms_step / 1e3) / 1e9 / peak}
+
+    n32, n64 = max(20, args.steps // 4), 10
+    var = dict(interp=1, wall_mid=1, cos_wet=0.3)
+    return {
+        "f32_strip_default": run("f32", {}, n32),
+        "f32_strip_N2_variants": run("f32", var, n32, tb=Tb),
+        "f32_tile_default": run("f32", {}, n32, kernel=0),
+        "f32_tile_N3_dissipation": run("f32", dict(dissip=1), n32),
+        "f64_tile_default": run("f64", {}, n64),
+        "f64_tile_N1_density_ratio_4": run("f64", dict(rho2=4.0), n64),
+        "f64_tile_N3_dissipation": run("f64", dict(dissip=1), n64),
+        "f64_tile_N1_N2_N3": run("f64", dict(var, rho2=4.0, dissip=1), n64, tb=Tb),
+        "problem": "drop 4096 x 4096 (the benchmark workload); rho2 = 4 rho, cos_wet = 0.3",
+    }
+
+
 def measure_variants(args, w, ref_fields):
     """The same workload with 16-bit deviation storage (timed like the main
     line), each storage's error against the FP64 oracle on the 512 x 1024
@@ -476,6 +522,8 @@ def measure_variants(args, w, ref_fields):
     # every storage's error against the oracle at the stated step count
     out["error_vs_oracle"] = {st: error_vs_oracle(st)
                               for st in ("f32", "f16mix", "f16dev", "bf16dev")}
+    torch.cuda.empty_cache()
+    out["extensions"] = measure_extensions(args, w)
     torch.cuda.empty_cache()
 
     # batched sweep (64 drops, grids 128x256 .. 768x1536, seed 0)
