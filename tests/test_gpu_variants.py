@@ -190,3 +190,33 @@ def test_adjoint_rejects_variants(LBE):
     Q = sim.get_state(device="cuda")
     with pytest.raises(Exception, match="default variants"):
         sim.observable(Q)
+
+
+@pytest.mark.parametrize("storage,extra", [
+    ("f64", dict(rho2=4.0, interp=1, wall_mid=1, cos_wet=0.3, dissip=1)),
+    ("f32", dict(interp=1, wall_mid=1, cos_wet=0.3)),
+    ("f32", dict(dissip=1)),
+])
+def test_checkpoint_with_extensions(LBE, tmp_path, storage, extra):
+    """lbe_save / lbe_load with the extensions on: the loaded handle holds
+    the saved state bitwise and continues bitwise like the saved one (the
+    pre-pass buffers are rebuilt from the state each step); a handle with
+    other extension parameters refuses the checkpoint."""
+    w = drop(70, 45, 20.0, "wall_mid")
+    w.params.update(extra)
+    a = LBE(w, storage=storage)
+    a.step(9)
+    path = str(tmp_path / "ck.bin")
+    a.save(path)
+    ref = a.get_state().numpy()
+    a.step(6)
+    after = a.get_state().numpy()
+    b = LBE(w, storage=storage)
+    b.load(path)
+    assert np.array_equal(b.get_state().numpy(), ref)
+    b.step(6)
+    assert np.array_equal(b.get_state().numpy(), after)
+    w2 = drop(70, 45, 20.0, "wall_mid")
+    c = LBE(w2, storage=storage)
+    with pytest.raises(Exception, match="other parameters"):
+        c.load(path)
