@@ -380,8 +380,9 @@ def run_ours(args, ws, rank, local):
                                                             OVERHEAD_BYTES_PER_CELL[args.storage])
                                                    / (launch_ms / 1e3) / 1e9 / peak},
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "variants": variants,
-                # the stash kernel's step is two launches (step + ghost columns)
-                "gpu_launches": args.steps * (2 if kernel["kernel"] == 7 else 1),
+                # the stash kernel's step is two launches (the step, then the
+                # ghost columns and step counter (7) or the step counter (8))
+                "gpu_launches": args.steps * (2 if kernel["kernel"] in (7, 8) else 1),
                 "check": {"sum_c": fin["sum_c"], "nonfinite": fin["nonfinite"]}}
         print(json.dumps(line), flush=True)
 

@@ -218,11 +218,16 @@ lbe_status lbe_load(lbe_handle* h, const char* path);
 
 /* Step-kernel choice (autotuner hook).  Kernel ids 0 .. lbe_num_tiles()-1:
  * ids whose shape has ty > 0 are the tile kernel with TX x TY cells per CTA
- * (any storage; FP64 provides id 0 only); id 7 (ty == 0) is the strip kernel
- * with 128 output columns per CTA marching over rows, staging each row's
- * pulled populations in shared memory with bulk copies (16/32-bit and
- * F16MIX storages, every instance at least 4 columns wide; the default
- * there); ids 5 and 6 are retired and rejected.
+ * (any storage; FP64 provides id 0 only); ids 7 and 8 (ty == 0) are the
+ * strip kernel with 128 output columns per CTA marching over rows, staging
+ * each row's pulled populations in shared memory with bulk copies (16/32-bit
+ * and F16MIX storages, every instance at least 4 columns wide; the default
+ * there).  They differ in who refreshes the periodic ghost columns (4 copies
+ * of the edge cells at each end of a stored row): with 7 a second kernel
+ * after the step, with 8 the step itself (the owner of an edge cell stores
+ * it twice); both give bitwise the same state.  The default is 8 when the
+ * instances are narrow (cells-weighted mean of at most 8 strips of 128
+ * columns), else 7.  Ids 5 and 6 are retired and rejected.
  * grid_ctas: persistent grid size (0 = resident CTAs x SMs, -1 = one CTA per
  * work item).  seg_rows > 0: rows per strip work item, items taken
  * round-robin; < 0: balanced: the strips of all instances laid end to end

@@ -362,7 +362,7 @@ lbe_status setup_tiles(lbe_handle* h) {
       // resident CTAs with one CTA per item) x (rows per item + the warm-up
       // rows every item recomputes, about 6 for the stash kernel)
       const int64_t slots = h->grid_req == -1 ? (int64_t)occ * h->num_sms : h->grid;
-      const bool stash = h->tile == STASH_ID;
+      const bool stash = is_stash(h->tile);
       const int seg_lo = std::min(8, max_ny);
       const int seg_hi = stash ? std::min(96, max_ny) : max_ny;
       const int warm = stash ? 6 : 4;
@@ -444,12 +444,15 @@ cudaError_t launch_one_step(lbe_handle* h, int parity) {
       h->withhold = -1;
       h->poll_lim = STASH_POLLS;
     }
+    const bool own = h->tile == STASH_OWN_ID;
     cudaError_t e = launch_stash(h->storage, h->d_inst, h->n, h->total_tiles, h->seg, parity,
-                                 h->grid, h->d_err, pl, wh, h->d_seed, h->variants, h->stream);
-    // the stash kernel leaves the periodic ghost columns to ghost_kernel,
-    // which also advances the step counter
+                                 h->grid, h->d_err, pl, wh, h->d_seed, h->variants, own,
+                                 h->stream);
+    // kernel 7 leaves the periodic ghost columns to ghost_kernel, which also
+    // advances the step counter; kernel 8 writes them itself
     if (e == cudaSuccess)
-      e = launch_ghosts(h->d_inst, h->n, h->max_ny, parity ^ 1, h->d_seed, h->stream);
+      e = own ? launch_seed_tick(h->d_seed, h->stream)
+              : launch_ghosts(h->d_inst, h->n, h->max_ny, parity ^ 1, h->d_seed, h->stream);
     return e;
   }
   cudaError_t e = cudaSuccess;
@@ -738,9 +741,21 @@ lbe_status create(int32_t n, const lbe_params* params, const lbe_init_fields* in
     // default kernel: the stash strip kernel where it applies (16/32-bit
     // storage, every instance at least XG columns wide), else the tile kernel
     int min_nx = 1 << 30;
-    for (auto& H : h->inst) min_nx = std::min(min_nx, H.nx);
+    double cells = 0.0, strips = 0.0;  // cells-weighted mean strips per instance
+    for (auto& H : h->inst) {
+      min_nx = std::min(min_nx, H.nx);
+      const double c = (double)H.nx * H.ny;
+      cells += c;
+      strips += c * ((H.nx + TILE_SHAPES[STASH_ID].tx - 1) / TILE_SHAPES[STASH_ID].tx);
+    }
+    // which kernel refreshes the periodic ghost columns: the step itself for
+    // narrow instances (a batch of 64 drops 128 to 768 wide, FP32: 23.3
+    // GLUPS against 23.0 with ghost_kernel, F16MIX 27.3 against 26.3),
+    // ghost_kernel for wide ones (4096^2, FP32: 24.2 against 24.0 in the
+    // step, F16MIX 27.3 against 26.9)
+    const int stash = strips <= 8.0 * cells ? STASH_OWN_ID : STASH_ID;
     // (the dissipation term's velocity gradients: the tile kernel only)
-    h->tile = (h->storage == LBE_F64 || min_nx < XG || h->dissip) ? 0 : STASH_ID;
+    h->tile = (h->storage == LBE_F64 || min_nx < XG || h->dissip) ? 0 : stash;
   }
   lbe_status s2 = setup_tiles(h);
   if (s2) return bail(s2);

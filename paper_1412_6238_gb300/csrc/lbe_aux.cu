@@ -12,26 +12,26 @@ bool tile_available(int storage, int tile) {
   if (tile < 0 || tile >= NUM_TILES) return false;
   if (storage == ST_F64) return tile == 0;
   // ids 5 and 6 are retired (TMA-ring strips); the stash kernel is 16/32-bit
-  if (is_strip(tile) && tile != STASH_ID) return false;
+  if (is_strip(tile) && !is_stash(tile)) return false;
   return true;
 }
 
 cudaError_t launch_stash(int storage, const InstDev* d, int n, int64_t items, int seg, int parity,
                          int grid, int* err, int poll_lim, int withhold, const uint32_t* seed,
-                         bool var, cudaStream_t s) {
+                         bool var, bool own_ghosts, cudaStream_t s) {
   switch (storage) {
     case ST_F32:
       return launch_stash_f32(d, n, items, seg, parity, grid, err, poll_lim, withhold, seed, var,
-                              s);
+                              own_ghosts, s);
     case ST_F16DEV:
       return launch_stash_f16(d, n, items, seg, parity, grid, err, poll_lim, withhold, seed, var,
-                              s);
+                              own_ghosts, s);
     case ST_BF16DEV:
       return launch_stash_bf16(d, n, items, seg, parity, grid, err, poll_lim, withhold, seed, var,
-                              s);
+                              own_ghosts, s);
     case ST_F16MIX:
       return launch_stash_mix(d, n, items, seg, parity, grid, err, poll_lim, withhold, seed, var,
-                              s);
+                              own_ghosts, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -293,72 +293,63 @@ int sums_blocks() { return SUM_BLOCKS; }
 // nx+XG..nx+2XG-1 repeat cells 0..XG-1 (element XG + x holds cell x).  Planes:
 // FP32: 9 (f, g) pairs + 9 hbar + the FP16 g_0 low part; 16-bit: 8 (f, g)
 // pairs + f_0 + 9 hbar + the FP32 g_0 + the low part; F16MIX: 9 planes of
-// 8-byte words + the FP32 g_0.
-// blockIdx.y: instance.
-__global__ void ghost_kernel(const InstDev* __restrict__ insts, int parity, uint32_t* seed) {
+// 8-byte words + the FP32 g_0.  One thread per ghost element: 8 neighbouring
+// threads copy one row's 2 XG elements (the sources and the ghosts are
+// disjoint for nx >= XG, which the strip kernel requires).
+template <class T>
+__device__ __forceinline__ void wrap_one(char* plane, size_t row, int dstE, int srcE) {
+  T* q = reinterpret_cast<T*>(plane) + row;
+  q[dstE] = q[srcE];
+}
+
+constexpr int GHOST_THREADS = 256;
+constexpr int GHOST_PLANES = 20;
+
+// blockIdx.y: plane; blockIdx.x walks (instance, chunk of GHOST_THREADS / 2 XG
+// rows) pairs, chunks = row chunks of the tallest instance.
+__global__ void __launch_bounds__(GHOST_THREADS)
+ghost_kernel(const InstDev* __restrict__ insts, int n_inst, int chunks, int parity, uint32_t* seed) {
   // the step is complete: advance the handle's step counter
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *seed += 1u;
-  const InstDev& I = insts[blockIdx.y];
-  char* b = I.buf[parity];
-  const int nx = I.nx, ny = I.ny;
-  const size_t pitch = (size_t)I.pitch;
-  const bool w16 = I.storage == ST_F16DEV || I.storage == ST_BF16DEV;
-  const bool mix = I.storage == ST_F16MIX;
-  const int64_t total = (int64_t)20 * ny * (2 * XG);
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int j = (int)(t % (2 * XG));
-    const int64_t r = t / (2 * XG);
-    const int y = (int)(r % ny), p = (int)(r / ny);
-    const int dstE = j < XG ? j : nx + j;            // left ghosts, then right
-    const int srcE = j < XG ? nx + j : j;            // cells nx-XG+j, then j-XG
-    const size_t row = (size_t)y * pitch;
-    if (mix) {
-      // F16MIX: 9 planes of 8-byte words, the FP32 g_0
-      if (p < 9) {
-        double* q = reinterpret_cast<double*>(b + (size_t)p * I.pair_bytes) + row;
-        q[dstE] = q[srcE];
-      } else if (p == 9) {
-        float* q = reinterpret_cast<float*>(b + I.g0_off) + row;
-        q[dstE] = q[srcE];
-      }
-    } else if (!w16) {
-      // FP32: 9 (f, g) pair planes, 9 hbar planes, the low part
-      if (p < 9) {
-        double* q = reinterpret_cast<double*>(b + (size_t)p * I.pair_bytes) + row;  // 8-byte pairs
-        q[dstE] = q[srcE];
-      } else if (p < 18) {
-        float* q = reinterpret_cast<float*>(b + I.h_off + (size_t)(p - 9) * I.plane_bytes) + row;
-        q[dstE] = q[srcE];
-      } else if (p == 18) {
-        uint16_t* q = reinterpret_cast<uint16_t*>(b + I.g0lo_off) + row;
-        q[dstE] = q[srcE];
-      }
-    } else if (p < 8) {
-      // 16-bit: 8 (f, g) pair planes (4-byte pairs), f_0, 9 hbar, g_0, low part
-      uint32_t* q = reinterpret_cast<uint32_t*>(b + (size_t)p * I.pair_bytes) + row;
-      q[dstE] = q[srcE];
-    } else if (p == 8) {
-      uint16_t* q = reinterpret_cast<uint16_t*>(b + I.f0_off) + row;
-      q[dstE] = q[srcE];
-    } else if (p < 18) {
-      uint16_t* q = reinterpret_cast<uint16_t*>(b + I.h_off + (size_t)(p - 9) * I.plane_bytes) + row;
-      q[dstE] = q[srcE];
-    } else if (p == 18) {
-      float* q = reinterpret_cast<float*>(b + I.g0_off) + row;
-      q[dstE] = q[srcE];
-    } else if (p == 19) {
-      uint16_t* q = reinterpret_cast<uint16_t*>(b + I.g0lo_off) + row;
-      q[dstE] = q[srcE];
+  const int p = blockIdx.y;
+  const int j = threadIdx.x % (2 * XG);
+  const int64_t pairs = (int64_t)n_inst * chunks;
+  for (int64_t g = blockIdx.x; g < pairs; g += gridDim.x) {
+    const InstDev& I = insts[g / chunks];
+    const int y = (int)(g % chunks) * (GHOST_THREADS / (2 * XG)) + (int)threadIdx.x / (2 * XG);
+    if (y >= I.ny) continue;
+    char* b = I.buf[parity];
+    const int nx = I.nx;
+    const int dstE = j < XG ? j : nx + j;  // left ghosts, then right
+    const int srcE = j < XG ? nx + j : j;  // cells nx-XG+j, then j-XG
+    const size_t row = (size_t)y * (size_t)I.pitch;
+    const int st = I.storage;
+    if (st == ST_F16MIX) {
+      if (p < 9) wrap_one<uint64_t>(b + (size_t)p * I.pair_bytes, row, dstE, srcE);
+      else if (p == 9) wrap_one<uint32_t>(b + I.g0_off, row, dstE, srcE);
+    } else if (st == ST_F16DEV || st == ST_BF16DEV) {
+      if (p < 8) wrap_one<uint32_t>(b + (size_t)p * I.pair_bytes, row, dstE, srcE);
+      else if (p == 8) wrap_one<uint16_t>(b + I.f0_off, row, dstE, srcE);
+      else if (p < 18)
+        wrap_one<uint16_t>(b + I.h_off + (size_t)(p - 9) * I.plane_bytes, row, dstE, srcE);
+      else if (p == 18) wrap_one<uint32_t>(b + I.g0_off, row, dstE, srcE);
+      else wrap_one<uint16_t>(b + I.g0lo_off, row, dstE, srcE);
+    } else {  // FP32
+      if (p < 9) wrap_one<uint64_t>(b + (size_t)p * I.pair_bytes, row, dstE, srcE);
+      else if (p < 18)
+        wrap_one<uint32_t>(b + I.h_off + (size_t)(p - 9) * I.plane_bytes, row, dstE, srcE);
+      else if (p == 18) wrap_one<uint16_t>(b + I.g0lo_off, row, dstE, srcE);
     }
   }
 }
 
 cudaError_t launch_ghosts(const InstDev* d, int n_inst, int max_ny, int parity, uint32_t* seed,
                           cudaStream_t s) {
-  const int64_t total = (int64_t)20 * max_ny * (2 * XG);
-  const int bx = (int)std::min<int64_t>((total + 255) / 256, 4096);
-  ghost_kernel<<<dim3(bx, n_inst), 256, 0, s>>>(d, parity, seed);
+  constexpr int rows = GHOST_THREADS / (2 * XG);
+  const int chunks = (max_ny + rows - 1) / rows;
+  const int64_t pairs = (int64_t)n_inst * chunks;
+  const int bx = (int)std::min<int64_t>(pairs, 1 << 16);
+  ghost_kernel<<<dim3(bx, GHOST_PLANES), GHOST_THREADS, 0, s>>>(d, n_inst, chunks, parity, seed);
   return cudaGetLastError();
 }
 

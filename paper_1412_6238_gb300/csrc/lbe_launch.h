@@ -15,19 +15,24 @@ struct TileShape {
 // kernels with a TMA ring of whole source rows, superseded by the stash
 // kernel; not built); 7 strip kernel with a per-warp stash of pulled
 // populations, 128 output columns (16/32-bit storages; ty = 0: a strip
-// marches over its rows).
+// marches over its rows), the periodic ghost columns refreshed by
+// ghost_kernel after the step; 8 the same kernel writing the ghost columns
+// itself (the owner of an edge cell stores it twice).
 constexpr int NUM_TILE_SHAPES = 5;
-constexpr int NUM_TILES = 8;
+constexpr int NUM_TILES = 9;
 constexpr int STRIP_FIRST = 5;
 constexpr int STASH_ID = 7;
+constexpr int STASH_OWN_ID = 8;
 // bytes allocated after an instance's two population buffers, covering the
 // widest read past the end of a row of the stash kernel: a stash row of 136
 // elements of up to 8 bytes from a strip start x0 <= nx - 1, against a
 // pitch of at least nx + 8 elements (at most 127 x 8 bytes)
 constexpr size_t ARENA_TAIL = 2048;
 constexpr TileShape TILE_SHAPES[NUM_TILES] = {{32, 8},  {64, 4},  {32, 16}, {64, 8},
-                                              {128, 4}, {124, 0}, {60, 0},  {128, 0}};
+                                              {128, 4}, {124, 0}, {60, 0},  {128, 0},
+                                              {128, 0}};
 inline bool is_strip(int tile) { return tile >= STRIP_FIRST && tile < NUM_TILES; }
+inline bool is_stash(int tile) { return tile == STASH_ID || tile == STASH_OWN_ID; }
 
 // Does the step kernel of this storage exist for this kernel id?
 bool tile_available(int storage, int tile);
@@ -44,24 +49,24 @@ constexpr int STASH_POLLS_TEST = 1 << 12;  // with the withhold test hook
 // boundary or property variant (the kernel built with them).
 cudaError_t launch_stash(int storage, const InstDev* d, int n, int64_t items, int seg, int parity,
                          int grid, int* err, int poll_lim, int withhold, const uint32_t* seed,
-                         bool var, cudaStream_t s);
+                         bool var, bool own_ghosts, cudaStream_t s);
 int stash_occupancy(int storage);
 cudaError_t launch_stash_f32(const InstDev* d, int n, int64_t items, int seg, int parity, int grid,
                              int* err, int poll_lim, int withhold,
                              const uint32_t* seed, bool var,
-                             cudaStream_t s);
+                             bool own_ghosts, cudaStream_t s);
 cudaError_t launch_stash_f16(const InstDev* d, int n, int64_t items, int seg, int parity, int grid,
                              int* err, int poll_lim, int withhold,
                              const uint32_t* seed, bool var,
-                             cudaStream_t s);
+                             bool own_ghosts, cudaStream_t s);
 cudaError_t launch_stash_bf16(const InstDev* d, int n, int64_t items, int seg, int parity,
                               int grid, int* err, int poll_lim, int withhold,
                              const uint32_t* seed, bool var,
-                             cudaStream_t s);
+                             bool own_ghosts, cudaStream_t s);
 cudaError_t launch_stash_mix(const InstDev* d, int n, int64_t items, int seg, int parity,
                              int grid, int* err, int poll_lim, int withhold,
                              const uint32_t* seed, bool var,
-                             cudaStream_t s);
+                             bool own_ghosts, cudaStream_t s);
 int stash_occupancy_f32();
 int stash_occupancy_f16();
 int stash_occupancy_bf16();

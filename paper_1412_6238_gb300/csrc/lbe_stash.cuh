@@ -553,7 +553,10 @@ __device__ __forceinline__ void issue_row(const CopyPlan& c, uint32_t dst, uint3
 // VAR: the boundary and property variants (harmonic law, wall temperature
 // at the link's wall crossing, wetting walls) compiled in; without them the
 // kernel carries none of their registers.
-template <class S, int NC, bool VAR>
+// OWN: the kernel writes the periodic ghost columns of its output itself
+// (a compile-time choice: compiled in, the ghost stores cost the main
+// stores about 1 % even where no lane takes them).
+template <class S, int NC, bool VAR, bool OWN>
 __global__ void __launch_bounds__(NC, (StashCfg<S, NC>::MINB))
 stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items, int seg_rows,
              int parity, int* __restrict__ err, int poll_lim, int withhold,
@@ -671,6 +674,13 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
     const int x = x0 + t;
     const int xw = wrapx(x, nx);
     const bool collides = x < nx;
+    // OWN: the periodic ghost copies are written by the owner of the cell,
+    // element XG + x + nx for x < XG (right ghosts), XG + x - nx for
+    // x >= nx - XG (left ghosts), both for 4 <= nx < 2 XG; otherwise
+    // ghost_kernel refreshes them after the step
+    const bool gR = OWN && collides && x < XG;
+    const bool gL = OWN && collides && x >= nx - XG;
+    const int ndst = 1 + (int)gR + (int)gL;
     // staged elements of the strip's population rows (storage element e
     // holds column e - XG): column x0 + j is element j + XG of a stash row,
     // which starts at element x0 (a multiple of NC: 16-byte aligned).
@@ -796,52 +806,62 @@ stash_kernel(const InstDev* __restrict__ insts, int n_inst, int64_t total_items,
         const C dhc = (r > 0 && r < I.ny - 1) ? P.dh : C(0);
         collide<S>(P, f, g, h, cc, pp, TT, st.gpx, st.gpy, d,
                    [&](int k, int ii, C v) { o[k * 9 + ii] = v; }, g0lo, clo, &lo_out, dhc);
-        const size_t e = (size_t)r * pitch + XG + x;
         // 16-bit forms: the cell's random bits for the stochastic rounding
         const uint32_t hc = S::SR ? sr_cell(skey, (uint32_t)r * (uint32_t)nx + (uint32_t)x) : 0u;
-        if constexpr (MIX) {
-          // word i: (f_i, g_i, hbar_i); word 0: (f_0, hbar_0, g_0 low part)
-          const float s1 = I.s[1], s2 = I.s[2];
-          auto word = [&](int ii, float fv, uint32_t u) {
-            reinterpret_cast<uint2*>(dst + (size_t)ii * I.pair_bytes)[e] =
-                make_uint2(__float_as_uint(fv), u);
-          };
-          float gs = 0.f;  // the stored g_i, times s_1
+        // the cell's values stored at its element and, with OWN, by the lanes
+        // of the periodic edge columns at its ghost copies (the 16-bit forms
+        // round them again, with the same random bits: the same values)
+        auto store_at = [&](const size_t e) {
+          if constexpr (MIX) {
+            // word i: (f_i, g_i, hbar_i); word 0: (f_0, hbar_0, g_0 low part)
+            const float s1 = I.s[1], s2 = I.s[2];
+            auto word = [&](int ii, float fv, uint32_t u) {
+              reinterpret_cast<uint2*>(dst + (size_t)ii * I.pair_bytes)[e] =
+                  make_uint2(__float_as_uint(fv), u);
+            };
+            float gs = 0.f;  // the stored g_i, times s_1
 #pragma unroll
-          for (int ii = 1; ii < 9; ii++) {
-            const uint32_t q =
-                sr_pack_half2(o[9 + ii] * s1, o[18 + ii] * s2, S::sr_word(1, ii, hc));
-            gs += __half2float(__ushort_as_half((unsigned short)(q & 0xffffu)));
-            word(ii, o[ii], q);
+            for (int ii = 1; ii < 9; ii++) {
+              const uint32_t q =
+                  sr_pack_half2(o[9 + ii] * s1, o[18 + ii] * s2, S::sr_word(1, ii, hc));
+              gs += __half2float(__ushort_as_half((unsigned short)(q & 0xffffu)));
+              word(ii, o[ii], q);
+            }
+            float g0h, g0l;
+            g0_remainder(cc, clo, gs * P.inv_s[1], g0h, g0l);
+            word(0, o[0],
+                 (uint32_t)__half_as_ushort(sr_half(o[18] * s2, S::sr_word(2, 0, hc))) |
+                     ((uint32_t)__half_as_ushort(__float2half_rn(g0l * G0LO_SCALE)) << 16));
+            reinterpret_cast<float*>(dst + I.g0_off)[e] = g0h;
+          } else if constexpr (!W16) {
+            st_g0lo<S>(I, dst, e, lo_out);
+#pragma unroll
+            for (int ii = 0; ii < 9; ii++) S::st_fg(I, dst, ii, e, o[ii], o[9 + ii]);
+#pragma unroll
+            for (int ii = 0; ii < 9; ii++) S::st(I, dst, 2, ii, e, o[18 + ii]);
+          } else {
+            S::st_sr(I, dst, 0, 0, e, o[0], S::sr_word(0, 0, hc));
+            float gs = 0.f;  // the stored g_i, times s_1
+#pragma unroll
+            for (int ii = 1; ii < 9; ii++)
+              gs += S::st_fg_sr(I, dst, ii, e, o[ii], o[9 + ii], S::sr_word(0, ii, hc));
+            float g0h, g0l;
+            g0_remainder(cc, clo, gs * P.inv_s[1], g0h, g0l);
+            S::st(I, dst, 1, 0, e, g0h);
+            st_g0lo<S>(I, dst, e, g0l);
+#pragma unroll
+            for (int ii = 0; ii < 9; ii++)
+              S::st_sr(I, dst, 2, ii, e, o[18 + ii], S::sr_word(2, ii, hc));
           }
-          float g0h, g0l;
-          g0_remainder(cc, clo, gs * P.inv_s[1], g0h, g0l);
-          word(0, o[0],
-               (uint32_t)__half_as_ushort(sr_half(o[18] * s2, S::sr_word(2, 0, hc))) |
-                   ((uint32_t)__half_as_ushort(__float2half_rn(g0l * G0LO_SCALE)) << 16));
-          reinterpret_cast<float*>(dst + I.g0_off)[e] = g0h;
-        } else if constexpr (!W16) {
-          st_g0lo<S>(I, dst, e, lo_out);
-#pragma unroll
-          for (int ii = 0; ii < 9; ii++) S::st_fg(I, dst, ii, e, o[ii], o[9 + ii]);
-#pragma unroll
-          for (int ii = 0; ii < 9; ii++) S::st(I, dst, 2, ii, e, o[18 + ii]);
-        } else {
-          S::st_sr(I, dst, 0, 0, e, o[0], S::sr_word(0, 0, hc));
-          float gs = 0.f;  // the stored g_i, times s_1
-#pragma unroll
-          for (int ii = 1; ii < 9; ii++)
-            gs += S::st_fg_sr(I, dst, ii, e, o[ii], o[9 + ii], S::sr_word(0, ii, hc));
-          float g0h, g0l;
-          g0_remainder(cc, clo, gs * P.inv_s[1], g0h, g0l);
-          S::st(I, dst, 1, 0, e, g0h);
-          st_g0lo<S>(I, dst, e, g0l);
-#pragma unroll
-          for (int ii = 0; ii < 9; ii++)
-            S::st_sr(I, dst, 2, ii, e, o[18 + ii], S::sr_word(2, ii, hc));
+        };
+        store_at((size_t)r * pitch + XG + x);
+        if constexpr (OWN) {
+          if (ndst > 1) {
+#pragma unroll 1
+            for (int dq = 1; dq < ndst; dq++)
+              store_at((size_t)r * pitch + (XG + x + ((dq == 1 && gR) ? nx : -nx)));
+          }
         }
-        // (the periodic ghost columns are refreshed by ghost_kernel after the
-        // step, not here: the branch costs this kernel about 7 %)
       } else {
         mbar_arrive(ebar);
       }

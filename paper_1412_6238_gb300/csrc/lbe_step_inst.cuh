@@ -81,13 +81,13 @@ cudaError_t LBE_CAT(fields_, LBE_SUFFIX)(const InstDev* d, int64_t tiles, int pa
 
 #if LBE_STASH
 namespace {
-template <int NC, bool VAR>
+template <int NC, bool VAR, bool OWN>
 bool stash_attr() {
   static bool done[64] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
   if (!done[dev]) {
-    if (cudaFuncSetAttribute(stash_kernel<LBE_ST, NC, VAR>,
+    if (cudaFuncSetAttribute(stash_kernel<LBE_ST, NC, VAR, OWN>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              StashCfg<LBE_ST, NC>::SMEM) != cudaSuccess)
       return false;
@@ -95,23 +95,23 @@ bool stash_attr() {
   }
   return true;
 }
-template <int NC, bool VAR>
+template <int NC, bool VAR, bool OWN>
 cudaError_t stash_one(const InstDev* d, int n, int64_t items, int seg, int parity, int grid,
                       int* err, int poll_lim, int withhold, const uint32_t* seed,
                       cudaStream_t s) {
-  if (!stash_attr<NC, VAR>()) return cudaErrorInvalidValue;
+  if (!stash_attr<NC, VAR, OWN>()) return cudaErrorInvalidValue;
   if (grid <= 0) grid = 1;
   if ((int64_t)grid > items) grid = (int)items;
-  stash_kernel<LBE_ST, NC, VAR>
+  stash_kernel<LBE_ST, NC, VAR, OWN>
       <<<grid, NC, StashCfg<LBE_ST, NC>::SMEM, s>>>(d, n, items, seg, parity, err, poll_lim,
                                                     withhold, seed);
   return cudaGetLastError();
 }
-template <int NC, bool VAR>
+template <int NC, bool VAR, bool OWN>
 int stash_occ() {
-  if (!stash_attr<NC, VAR>()) return 0;
+  if (!stash_attr<NC, VAR, OWN>()) return 0;
   int b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, stash_kernel<LBE_ST, NC, VAR>, NC,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, stash_kernel<LBE_ST, NC, VAR, OWN>, NC,
                                                     StashCfg<LBE_ST, NC>::SMEM) != cudaSuccess)
     return 0;
   return b;
@@ -121,16 +121,20 @@ int stash_occ() {
 cudaError_t LBE_CAT(launch_stash_, LBE_SUFFIX)(const InstDev* d, int n, int64_t items, int seg,
                                                 int parity, int grid, int* err, int poll_lim,
                                                 int withhold, const uint32_t* seed, bool var,
-                                                cudaStream_t s) {
-  return var ? stash_one<128, true>(d, n, items, seg, parity, grid, err, poll_lim, withhold,
-                                    seed, s)
-             : stash_one<128, false>(d, n, items, seg, parity, grid, err, poll_lim, withhold,
-                                     seed, s);
+                                                bool own_ghosts, cudaStream_t s) {
+#define LBE_STASH_ONE(V, O) \
+  stash_one<128, V, O>(d, n, items, seg, parity, grid, err, poll_lim, withhold, seed, s)
+  if (var) return own_ghosts ? LBE_STASH_ONE(true, true) : LBE_STASH_ONE(true, false);
+  return own_ghosts ? LBE_STASH_ONE(false, true) : LBE_STASH_ONE(false, false);
+#undef LBE_STASH_ONE
 }
 // resident CTAs per SM (the smaller of the two builds)
 int LBE_CAT(stash_occupancy_, LBE_SUFFIX)() {
-  const int a = stash_occ<128, false>(), b = stash_occ<128, true>();
-  return a < b ? a : b;
+  const int o[4] = {stash_occ<128, false, false>(), stash_occ<128, true, false>(),
+                    stash_occ<128, false, true>(), stash_occ<128, true, true>()};
+  int m = o[0];
+  for (int j = 1; j < 4; j++) m = o[j] < m ? o[j] : m;
+  return m;
 }
 #endif
 

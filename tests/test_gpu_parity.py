@@ -118,7 +118,7 @@ def test_one_step_from_same_state(LBE, orc, storage, nx, ny):
     assert state_err(got, ref) < tol
 
 
-@pytest.mark.parametrize("tile", [1, 2, 3, 4, 7])
+@pytest.mark.parametrize("tile", [1, 2, 3, 4, 7, 8])
 def test_kernels_bitwise_identical(LBE, tile):
     """Every tile shape and the stash strip kernel compute the same per-cell
     arithmetic as tile kernel 0; the compiler may contract a different
@@ -143,8 +143,8 @@ STRIP_SHAPES = [(4, 8), (5, 3), (7, 40), (64, 17), (130, 19), (200, 33), (257, 7
 @pytest.mark.parametrize("storage", ["f32", "f16dev", "bf16dev", "f16mix"])
 @pytest.mark.parametrize("seg", [1, 3, 0, -5])
 def test_strip_kernel_equals_tile_kernel(LBE, storage, nx, ny, seg):
-    """The stash strip kernel (id 7) on
-    narrow, ragged and partial strips, with segments of 1, 3 and automatic
+    """The stash strip kernel (ids 7 and 8: ghost columns by a second kernel
+    or by the step) on narrow, ragged and partial strips, with segments of 1, 3 and automatic
     rows (segment seams, bottom and top ghost rows), equal the tile kernel
     for every 16/32-bit storage up to last-bit FMA
     contraction differences (which a 16-bit store may round to one unit of
@@ -156,7 +156,7 @@ def test_strip_kernel_equals_tile_kernel(LBE, storage, nx, ny, seg):
     a = LBE(w, storage=storage)
     a.set_tile(0)
     a.step(5)
-    for tile in (7,):
+    for tile in (7, 8):
         # grid 0: as many CTAs as fit; grid 1: one CTA walks every work
         # item; grid 7: (seg 0) ranges that start and end inside strips
         for grid in (0, 1, 7):
@@ -171,15 +171,19 @@ def test_strip_kernel_equals_tile_kernel(LBE, storage, nx, ny, seg):
 def test_strip_is_default_and_rejects_narrow(LBE):
     from paper_1412_6238_gb300.lbe import LBEError
     w = small_drop()
-    assert LBE(w, storage="f32").get_tile()["kernel"] == 7
-    assert LBE(w, storage="f16dev").get_tile()["kernel"] == 7
-    assert LBE(w, storage="f16mix").get_tile()["kernel"] == 7
+    # narrow instances: the step writes its ghost columns (8); wide ones
+    # (mean above 8 strips of 128 columns): ghost_kernel does (7)
+    assert LBE(w, storage="f32").get_tile()["kernel"] == 8
+    assert LBE(w, storage="f16dev").get_tile()["kernel"] == 8
+    assert LBE(w, storage="f16mix").get_tile()["kernel"] == 8
     assert LBE(w, storage="f64").get_tile()["kernel"] == 0
+    wide = small_drop(nx=1153, ny=6, R=2.0)
+    assert LBE(wide, storage="f32").get_tile()["kernel"] == 7
     narrow = wl.droplet(3, 20, 1.5, 1.5, 10.0, Re=1.0, Ma=10.0, Ca=0.05, eta_m=0.2, eta_r=1.0,
                         lam_r=1.0)
     s = LBE(narrow, storage="f32")
     assert s.get_tile()["kernel"] == 0
-    for tile in (5, 6, 7):  # 5, 6 retired; 7 needs nx >= 4
+    for tile in (5, 6, 7, 8):  # 5, 6 retired; 7, 8 need nx >= 4
         with pytest.raises(LBEError):
             s.set_tile(tile)
 
@@ -349,20 +353,43 @@ def test_batch_of_uneven_instances_matches_each_alone(LBE, orc):
         assert max(e["u"], e["T"], e["c"]) < 1e-12, (j, e)
 
 
+@pytest.mark.parametrize("tile", [7, 8])
 @pytest.mark.parametrize("grid", [0, 3, 1])
-def test_strip_batch_ranges_cross_instances(LBE, grid):
+def test_strip_batch_ranges_cross_instances(LBE, grid, tile):
     """FP32 batch on the strip kernel with balanced row ranges (3 CTAs: every
     range spans several strips and instances): each instance bitwise equal
     to the same instance advanced alone."""
     ws = wl.batch_sweep(n=5, seed=3, grids=((40, 80), (136, 48), (64, 128)))
     n = 12
     sim = LBE(ws, storage="f32")
-    sim.set_tile(7, grid, 0)
+    sim.set_tile(tile, grid, 0)
     sim.step(n)
     for j, w in enumerate(ws):
         one = LBE(w, storage="f32")
         one.step(n)
         assert np.array_equal(sim.get_state(j).numpy(), one.get_state().numpy()), j
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16dev", "bf16dev", "f16mix"])
+def test_own_ghost_columns_equal_ghost_kernel(LBE, storage):
+    """Kernel 8 (the step writes the periodic ghost columns: the owner of an
+    edge cell stores it twice) and kernel 7 (ghost_kernel after the step)
+    give bitwise the same state, on widths where one lane writes both a left
+    and a right ghost (nx < 8), a strip's edge lanes both ghosts (nx <= 128)
+    and the first and last strips one each."""
+    # (Ma 1, Ca 0.2: drops this small are unstable at Ma 10, Ca 0.05)
+    ws = [wl.droplet(nx, ny, max(1.5, min(nx, ny) / 3.0), nx / 2.0 + 0.3, ny / 2.0 - 0.2,
+                     Re=1.0, Ma=1.0, Ca=0.2, eta_m=0.2, eta_r=0.5, lam_r=2.0)
+          for nx, ny in ((4, 9), (5, 12), (7, 10), (9, 11), (128, 30), (130, 21), (300, 17))]
+    out = {}
+    for tile in (7, 8):
+        sim = LBE(ws, storage=storage)
+        sim.set_tile(tile, 0, 0)
+        sim.step(9)
+        out[tile] = [sim.get_state(j).numpy() for j in range(len(ws))]
+    for j in range(len(ws)):
+        assert np.isfinite(out[8][j]).all() and np.abs(out[8][j]).max() < 10.0
+        assert np.array_equal(out[7][j], out[8][j]), (storage, j)
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16dev", "f16mix"])

@@ -90,7 +90,7 @@ def test_strip_kernel_equals_tile_kernel(LBE, storage):
     a.set_tile(0)
     a.step(5)
     b = LBE(w, storage=storage)
-    assert b.get_tile()["kernel"] == 7
+    assert b.get_tile()["kernel"] in (7, 8)
     b.step(5)
     # last-bit differences (the two kernels contract different products
     # into FMAs; the harmonic law divides with -prec-div=false), grown over
