@@ -161,13 +161,18 @@ def hbm_peak():
 
 def kernel_source_sha() -> str:
     """Hash of the sources and flags that make the FP32 step kernel (the
-    traffic figure of the committed ncu summary is valid while it matches)."""
+    traffic figure of the committed ncu summary is valid while it matches);
+    comments and blank space are left out, so that only code changes count."""
+    import re
     from paper_1412_6238_gb300 import build as _b
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1412_6238_gb300", "csrc")
     for f in ("lbe_common.cuh", "lbe_cell.cuh", "lbe_tile.cuh", "lbe_stash.cuh",
               "lbe_step_inst.cuh", "lbe_step_f32.cu"):
-        h.update(open(os.path.join(d, f), "rb").read())
+        src = open(os.path.join(d, f), encoding="utf-8").read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     h.update(repr(_b.UNITS["lbe_step_f32.cu"]).encode())
     return h.hexdigest()[:16]
 

@@ -7,8 +7,9 @@
 // on each side (c at x0 - 2 .. x0 + NC + 1, p and T at x0 - 1 .. x0 + NC):
 // four lanes of the last warp form those as extra work, so that no thread
 // of the CTA is spent on a column it does not collide (NC a power of two:
-// the strips tile power-of-two grids exactly).  Instead of staging whole source rows (as a TMA tiled
-// row ring would, 7 rows for the pull and the stencils), the CTA stages, for
+// the strips tile power-of-two grids exactly).  Instead of staging whole
+// source rows (as a TMA tiled row ring would, 7 rows for the pull and the
+// stencils), the CTA stages, for
 // each moment row m, what its cells pull: for each population row of the
 // layout (FP32: the 9 (f_i, g_i) pair rows, the 9 hbar_i rows and the g_0 low
 // part), the elements of source row m - xi_iy over the strip's columns and
@@ -17,7 +18,10 @@
 // the slot's mbarrier.  A row's values stay in the stash from the time its
 // moments are formed until it collides three iterations later: a 4-row
 // stash (58 KB in FP32) instead of a 7-row ring, so that three CTAs fit on
-// an SM.
+// an SM.  A window that crosses the periodic edge is contiguous because
+// every stored row repeats its first and last XG cells beyond its ends (the
+// ghost columns): with OWN the kernel stores them with the cells' values,
+// otherwise ghost_kernel refreshes them after the step.
 //
 // Iteration i (from ya - 4 to yb):
 //   barrier; 1. collide row i-1 (S2-S9 of lbe_cell.cuh) from its stash slot
