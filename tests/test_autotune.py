@@ -20,6 +20,21 @@ def test_candidates_and_cache_roundtrip(tmp_path, monkeypatch):
     assert autotune.cache_key("GB300", "f32", shapes) == "GB300|f32|128x256,256x512"
 
 
+def test_candidates_from_the_library_table():
+    """With the library's own kernel table the autotuner tries both strip
+    kernels (7: ghost columns by a second kernel, 8: by the step) with the
+    same row counts, and only tile kernel 0 for FP64."""
+    from paper_1412_6238_gb300 import lbe
+    shapes_tbl = lbe.tile_shapes()
+    shapes = [(256, 128), (1536, 768)]
+    c = autotune.candidates("f32", shapes, len(shapes_tbl), lambda k: shapes_tbl[k])
+    segs = lambda k: sorted(s for kk, _, s in c if kk == k)  # noqa: E731
+    assert segs(7) and segs(7) == segs(8)
+    assert 0 in segs(8) and -1536 in segs(8)
+    assert [k for k, _, _ in autotune.candidates("f64", shapes, len(shapes_tbl),
+                                                lambda k: shapes_tbl[k])] == [0, 0]
+
+
 @pytest.mark.gpu
 def test_tune_restores_state_and_caches(tmp_path, monkeypatch):
     torch = pytest.importorskip("torch")
